@@ -1,0 +1,158 @@
+/*
+ * sgn.h - C ABI of the GB300 (sm_103a) 2D Serre-Green-Naghdi hot path.
+ *
+ * Method: Gavrilyuk & Klein, "Numerical study of the Serre-Green-Naghdi
+ * equations in 2D" (arXiv 2306.09731). The library integrates the potential
+ * form of SGN in the variables (h, v = grad phi):
+ *     h_t = -div(h u),  u = v - grad(sigma)/h                  Section 2.2, Eq. (1)
+ *     v_t = -grad( |v|^2/2 - |grad sigma|^2/(2h^2) + g h - 9 sigma^2/(2h^4) )
+ *                                                             Section 3 (v-form of Eq. (2))
+ *     L[sigma] = 3 sigma/h^3 - div(grad sigma / h) = -div v    Section 3, Eq. (sigmav)
+ * by Fourier collocation on a periodic box, left-preconditioned restarted GMRES
+ * with M = 3 + kx^2 + ky^2 for sigma, and classic RK4 in time (Section 3).
+ *
+ * Conventions shared by every call:
+ *  - Grid: Nx x Ny points, both powers of two with 8 <= N <= 4096. Lx, Ly are
+ *    FULL periods (the paper's 2*pi*L_x); the box is [-Lx/2, Lx/2) x [-Ly/2, Ly/2)
+ *    and x_j = -Lx/2 + j*Lx/Nx. h_inf = 1.
+ *  - Field pointers are DEVICE pointers (except the *_host variants) to real
+ *    float64 arrays laid out row-major [Ny][Nx], x fastest, 8-byte aligned,
+ *    not aliasing each other unless stated. The caller owns them.
+ *  - Wavenumbers k = 2*pi*m/L; the Nyquist wavenumber is set to 0 in every i*k
+ *    multiplier and in M, so M equals L exactly at h = 1.
+ *  - Calls are enqueued on the handle's stream (sgn_set_stream; default: the
+ *    legacy default stream). Calls that run GMRES synchronise that stream once
+ *    per GMRES iteration to read the convergence test.
+ *  - Every call returns a status; on failure sgn_last_error() gives a message.
+ *    A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgn_ctx* sgn_t;
+
+typedef enum {
+  SGN_OK = 0,
+  SGN_EINVAL = 1,       /* bad argument: null pointer, size, option */
+  SGN_ENOTCONV = 2,     /* GMRES hit maxit; the best iterate is still returned */
+  SGN_ECAVITATION = 3,  /* h <= 0 somewhere (the paper assumes h > 0, Section 1) */
+  SGN_ENONFINITE = 4,   /* NaN or Inf in h */
+  SGN_ECUDA = 5,        /* a CUDA runtime error; see sgn_last_error */
+  SGN_ENOMEM = 6        /* device allocation failed in sgn_create */
+} sgn_status;
+
+typedef struct {
+  int precision;      /* 0 = FP64 throughout (the only mode built so far) */
+  int restart;        /* GMRES restart length m, 1..64 (default 20) */
+  int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
+  double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */
+  int krasny;         /* 1: Krasny filter after every RK4 step (Section 3); default 0 */
+  double krasny_thr;  /* zero DFT coefficients with |c|/(Nx*Ny) < thr (default 1e-12) */
+  int dealias;        /* 1: 2/3-rule mask on the RHS spectra (not in the paper); default 0 */
+  int guess;          /* GMRES start: 0 = the last computed sigma (Section 3), 1 = zero */
+} sgn_options;
+
+/* Fills *opt with the defaults listed above. */
+void sgn_default_options(sgn_options* opt);
+
+/* Creates a handle for an Nx x Ny grid of full periods Lx x Ly and gravity g.
+ * Allocates every device buffer the calls need (twiddle tables, spectra,
+ * the Krylov basis of restart+1 vectors) on the current device. opt may be
+ * NULL for the defaults. Returns SGN_EINVAL for unsupported sizes, SGN_ENOMEM
+ * if allocation fails. */
+sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g,
+                      const sgn_options* opt, sgn_t* out);
+
+/* Frees the handle and its device memory (after synchronising its stream). */
+sgn_status sgn_destroy(sgn_t ctx);
+
+/* Sets the CUDA stream (a cudaStream_t passed as void*) for later calls. */
+sgn_status sgn_set_stream(sgn_t ctx, void* cuda_stream);
+
+/* Spectral derivatives of a real field (Section 3, g_x ~ i k_x g):
+ * fx = d f/dx, fy = d f/dy. Either output may be NULL. */
+sgn_status sgn_spectral_derivative(sgn_t ctx, const double* f, double* fx, double* fy);
+
+/* 2D real-to-complex DFT (unnormalised, e^{-i k x}): f [Ny][Nx] real ->
+ * fhat [Ny][Nx/2+1] complex, stored as interleaved (re, im) float64 pairs,
+ * i.e. 2*Ny*(Nx/2+1) doubles. Row ky holds kx = 0..Nx/2. */
+sgn_status sgn_fft2_r2c(sgn_t ctx, const double* f, double* fhat);
+
+/* Inverse of sgn_fft2_r2c including the 1/(Nx*Ny) factor. The imaginary parts
+ * of the kx = 0 and kx = Nx/2 entries after the y-transform are ignored. */
+sgn_status sgn_fft2_c2r(sgn_t ctx, const double* fhat, double* f);
+
+/* out = L[sigma] = 3 sigma/h^3 - d/dx(sigma_x/h) - d/dy(sigma_y/h)
+ * (Section 3, Eq. (sigmav)), unpreconditioned. Returns SGN_ECAVITATION /
+ * SGN_ENONFINITE if h is not positive and finite. */
+sgn_status sgn_elliptic_apply(sgn_t ctx, const double* h, const double* sigma, double* out);
+
+/* Solves L[sigma] = b by left-preconditioned restarted GMRES (Section 3;
+ * Saad & Schultz), sigma_inout is the initial guess on entry and the solution
+ * on exit. iters (may be NULL) receives the matvec count; relres (may be NULL)
+ * the final estimate of ||M^-1 r|| / ||M^-1 b||. SGN_ENOTCONV if maxit is hit. */
+sgn_status sgn_gmres_solve(sgn_t ctx, const double* h, const double* b,
+                           double* sigma_inout, int* iters, double* relres);
+
+/* One evaluation of the right-hand side (Section 2.2 Eq. (1), Section 3):
+ * solves Eq. (sigmav) for sigma from the guess in sigma_inout (written back),
+ * then ht = -div(h u), vxt, vyt = -grad F. With dealias = 1 the outputs are
+ * 2/3-masked. */
+sgn_status sgn_rhs(sgn_t ctx, const double* h, const double* vx, const double* vy,
+                   double* sigma_inout, double* ht, double* vxt, double* vyt);
+
+/* Advances (h, vx, vy) in place by nsteps classic RK4 steps of size dt
+ * (Section 3). Each stage's GMRES starts from the last computed sigma
+ * (sigma_inout on entry, the stage-4 sigma of the last step on exit). The
+ * state is held in spectral form between steps; the Krasny filter, when on,
+ * runs after every step. */
+sgn_status sgn_rk4_step(sgn_t ctx, double* h, double* vx, double* vy,
+                        double* sigma_inout, double dt, int nsteps);
+
+/* sgn_rk4_step on HOST arrays (pageable or pinned): copies the four fields
+ * to the device, steps, and copies them back before returning. */
+sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy,
+                             double* sigma_inout, double dt, int nsteps);
+
+/* Conserved quantities (Section 2.3, Eqs. (total_mass), (total_momentum),
+ * (total_energy)) by the rectangle rule with u = v - grad(sigma)/h:
+ * out[0] = mass sum(h - 1) dA, out[1..2] = momentum sum(h u) dA,
+ * out[3] = energy sum(h|u|^2/2 + 3 sigma^2/(2h^3) + g(h-1)^2/2) dA.
+ * out is a HOST array of 4 doubles; the call synchronises the stream. */
+sgn_status sgn_invariants(sgn_t ctx, const double* h, const double* vx,
+                          const double* vy, const double* sigma, double out[4]);
+
+/* Statistics of the last GMRES-using call: total matvecs, number of solves,
+ * the largest iteration count of one solve and the last relative residual. */
+typedef struct {
+  long long matvecs;
+  int solves;
+  int max_iters;
+  double last_relres;
+  int last_iters;
+} sgn_stats;
+sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out);
+
+/* Per-kernel-class timing with CUDA events on the handle's stream (off by
+ * default). Classes, in order: 0 coefficients of Eq. (sigmav) from h_hat,
+ * 1-3 the matvec passes (y-inverse, fused x-pass, y-forward + M^-1),
+ * 4-6 the RHS passes (y-inverse, fused x-pass, y-forward + RK4 update),
+ * 7 GMRES vector kernels and reductions, 8 conversions at call boundaries.
+ * sgn_set_profiling(ctx, 1) clears the counters; sgn_get_profile fills up to n
+ * entries of ms (summed milliseconds) and counts (timed launches) and
+ * *launches with the number of kernels launched since the last clear. */
+#define SGN_PROFILE_CLASSES 9
+sgn_status sgn_set_profiling(sgn_t ctx, int on);
+sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long long* launches);
+
+/* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
+const char* sgn_last_error(sgn_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGN_H */

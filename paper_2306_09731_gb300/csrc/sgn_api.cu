@@ -1,0 +1,648 @@
+// sgn_api.cu - C ABI (include/sgn.h) and host orchestration of the SGN hot path.
+//
+// The handle owns every device buffer. The RK4 state lives in spectral form
+// (half spectra of h, vx, vy) between steps; sigma_hat is the GMRES warm start
+// carried from stage to stage and step to step (Section 3: "started with the
+// last computed value"). One stage is:
+//   coefficients  h, 1/(2N h), 3/(2N h^3) from h_hat        (y-inverse + x-pass)
+//   GMRES         L sigma = b, b_hat = -(i kx vx + i ky vy) (Eq. (sigmav))
+//   RHS + update  K = (h_t, v_t) and the RK4 stage update  (3 fused passes)
+// The GMRES loop runs on the host: each Arnoldi step enqueues its kernels and
+// reads back one residual estimate (one stream synchronisation per step).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sgn.h"
+#include "sgn_internal.h"
+
+using namespace sgn;
+
+typedef cpx<double> C64;
+
+struct sgn_ctx {
+  Geom G{};
+  double g = 1.0;
+  sgn_options opt{};
+  cudaStream_t stream = 0;
+  int device = 0;
+  Tables<double> tb{};
+  C64* Un[3] = {};
+  C64* Us[3] = {};
+  C64* acc[3] = {};
+  C64* sig = nullptr;
+  C64* bh = nullptr;
+  C64* cvec = nullptr;
+  C64* w = nullptr;
+  C64* tmp[4] = {};
+  C64* V = nullptr;
+  double* h = nullptr;
+  double* cr = nullptr;
+  double* cc = nullptr;
+  double* phys[4] = {};  // staging for sgn_rk4_step_host / derivatives (lazy)
+  double* partials = nullptr;
+  double* scal = nullptr;  // small device scalars
+  GmresDev* gst = nullptr;
+  GmresReadback* rb_dev = nullptr;
+  GmresReadback* rb_host = nullptr;  // pinned
+  double* inv_host = nullptr;        // pinned, 4 doubles
+  int* flags = nullptr;
+  Prof prof;
+  std::vector<void*> allocs;
+  std::string err;
+  sgn_stats stats{};
+};
+
+static std::string g_create_error;
+
+namespace {
+
+struct Fail {
+  sgn_status st;
+};
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                              \
+      throw Fail{SGN_ECUDA};                                                                      \
+    }                                                                                             \
+  } while (0)
+
+sgn_status fail(sgn_ctx* ctx, sgn_status st, const std::string& msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// cos and sin of 2 pi k / n by reduction to the first octant (n power of 2).
+void cos_sin_2pi(long k, long n, double* c, double* s) {
+  k %= n;
+  if (k < 0) k += n;
+  const long q = k / (n / 4), kr = k % (n / 4);
+  const double two_pi = 6.283185307179586476925286766559;
+  double c0, s0;
+  if (kr <= n / 8) {
+    c0 = cos(two_pi * (double)kr / (double)n);
+    s0 = sin(two_pi * (double)kr / (double)n);
+  } else {
+    const long m = n / 4 - kr;
+    c0 = sin(two_pi * (double)m / (double)n);
+    s0 = cos(two_pi * (double)m / (double)n);
+  }
+  switch (q) {
+    case 0: *c = c0; *s = s0; break;
+    case 1: *c = -s0; *s = c0; break;
+    case 2: *c = -c0; *s = -s0; break;
+    default: *c = s0; *s = -c0; break;
+  }
+}
+
+template <typename P>
+P* dalloc(sgn_ctx* ctx, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(P));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    throw Fail{SGN_ENOMEM};
+  }
+  ctx->allocs.push_back(p);
+  return static_cast<P*>(p);
+}
+
+void free_all(sgn_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  if (ctx->rb_host) cudaFreeHost(ctx->rb_host);
+  if (ctx->inv_host) cudaFreeHost(ctx->inv_host);
+  ctx->rb_host = nullptr;
+  ctx->inv_host = nullptr;
+}
+
+void build_tables(sgn_ctx* ctx) {
+  const Geom& G = ctx->G;
+  std::vector<C64> tx(G.Nx), ty(G.Ny);
+  for (int k = 0; k < G.Nx; ++k) {
+    double c, s;
+    cos_sin_2pi(k, G.Nx, &c, &s);
+    tx[k].x = c;
+    tx[k].y = -s;
+  }
+  for (int k = 0; k < G.Ny; ++k) {
+    double c, s;
+    cos_sin_2pi(k, G.Ny, &c, &s);
+    ty[k].x = c;
+    ty[k].y = -s;
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> kx(G.Nxh), ky(G.Ny);
+  for (int k = 0; k < G.Nxh; ++k) kx[k] = (k == G.Nx / 2) ? 0.0 : two_pi * k / G.Lx;
+  for (int k = 0; k < G.Ny; ++k) {
+    const int m = k < G.Ny / 2 ? k : k - G.Ny;
+    ky[k] = (k == G.Ny / 2) ? 0.0 : two_pi * m / G.Ly;
+  }
+  ctx->tb.twx = dalloc<C64>(ctx, G.Nx);
+  ctx->tb.twy = dalloc<C64>(ctx, G.Ny);
+  ctx->tb.kx = dalloc<double>(ctx, G.Nxh);
+  ctx->tb.ky = dalloc<double>(ctx, G.Ny);
+  CK(cudaMemcpy(ctx->tb.twx, tx.data(), G.Nx * sizeof(C64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tb.twy, ty.data(), G.Ny * sizeof(C64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tb.kx, kx.data(), G.Nxh * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tb.ky, ky.data(), G.Ny * sizeof(double), cudaMemcpyHostToDevice));
+}
+
+Exec EX(sgn_ctx* ctx, int kind_override = -1) {
+  Exec e{ctx->stream, &ctx->prof};
+  e.kind_override = kind_override;
+  return e;
+}
+
+// ------------------------------------------------------------ transforms
+
+void fwd2(sgn_ctx* ctx, const double* const* f, int nf, C64* const* out) {
+  CK(launch_x_r2c<double>(ctx->G, ctx->tb, f, nf, out, EX(ctx)));
+  CK(launch_y_fft<double>(ctx->G, ctx->tb, false, (const C64* const*)out, nullptr, nf, out, EX(ctx)));
+}
+
+// physical out[i] = inverse 2D transform of (i kx)^dx (i ky)^dy in[i]; uses tmp[0..nf)
+void inv2(sgn_ctx* ctx, const C64* const* in, const int* dx, const int* dy, int nf, double* const* out) {
+  CK(launch_y_fft<double>(ctx->G, ctx->tb, true, in, dy, nf, ctx->tmp, EX(ctx)));
+  CK(launch_x_c2r<double>(ctx->G, ctx->tb, (const C64* const*)ctx->tmp, dx, nf, out,
+                          1.0 / (double)ctx->G.nphys(), EX(ctx)));
+}
+
+void sync_read(sgn_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->rb_host, ctx->rb_dev, sizeof(GmresReadback), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->prof.on) ctx->prof.harvest();
+}
+
+void check_flags(sgn_ctx* ctx, int flags) {
+  if (flags & FLAG_NONFINITE) {
+    ctx->err = "non-finite depth h";
+    throw Fail{SGN_ENONFINITE};
+  }
+  if (flags & FLAG_CAVITATION) {
+    ctx->err = "cavitation: h <= 0 somewhere";
+    throw Fail{SGN_ECAVITATION};
+  }
+}
+
+// coefficient fields from the spectral depth h_hat
+void coef_from_spectral(sgn_ctx* ctx, const C64* hh) {
+  CK(launch_y_fft<double>(ctx->G, ctx->tb, true, &hh, nullptr, 1, ctx->tmp, EX(ctx, PK_COEF)));
+  CK(launch_coef_x<double>(ctx->G, ctx->tb, ctx->tmp[0], ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+}
+
+// --------------------------------------------------------------- GMRES
+// Left-preconditioned restarted GMRES on A = M^-1 L, c = M^-1 b (Section 3).
+// Uses ctx->h/cr/cc, ctx->bh (b_hat); ctx->sig is the guess and the result.
+// Returns true if converged.
+bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
+  const Geom& G = ctx->G;
+  cudaStream_t s = ctx->stream;
+  const int m = ctx->opt.restart;
+  const size_t vs = G.nspec();
+  double* cnorm_d = ctx->scal + 0;
+  double* beta_d = ctx->scal + 1;
+  CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 1, cnorm_d, true, EX(ctx)));
+  CK(launch_readback_scalar(cnorm_d, ctx->flags, ctx->rb_dev, EX(ctx)));
+  sync_read(ctx);
+  check_flags(ctx, ctx->rb_host->flags);
+  const double cnorm = ctx->rb_host->scalar;
+  ctx->stats.solves++;
+  if (cnorm == 0.0) {
+    CK(launch_zero<double>(G, ctx->sig, EX(ctx)));
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    ctx->stats.last_iters = 0;
+    ctx->stats.last_relres = 0.0;
+    return true;
+  }
+  const double target = ctx->opt.tol * cnorm;
+  int its = 0;
+  bool conv = false;
+  double res = 0.0;
+  C64* const V = ctx->V;
+  for (;;) {
+    CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+    CK(launch_residual<double>(G, ctx->cvec, ctx->w, V, ctx->partials, EX(ctx)));
+    CK(launch_reduce(ctx->partials, 1, beta_d, true, EX(ctx)));
+    CK(launch_readback_scalar(beta_d, ctx->flags, ctx->rb_dev, EX(ctx)));
+    sync_read(ctx);
+    check_flags(ctx, ctx->rb_host->flags);
+    const double beta = ctx->rb_host->scalar;
+    res = beta;
+    if (!(beta > target)) {
+      conv = !(beta != beta);
+      break;
+    }
+    if (its >= ctx->opt.maxit) break;
+    CK(launch_scale<double>(G, V, beta_d, true, V, EX(ctx)));
+    CK(launch_gmres_start(ctx->gst, beta_d, EX(ctx)));
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      C64* Vj = V + (size_t)j * vs;
+      const int nv = j + 1;
+      CK(launch_matvec<double>(G, ctx->tb, Vj, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+      ++its;
+      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, EX(ctx)));
+      CK(launch_reduce(ctx->partials, nv, ctx->gst->h1, false, EX(ctx)));
+      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h1, ctx->w, ctx->partials, true, EX(ctx)));
+      CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, EX(ctx)));
+      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h2, ctx->w, ctx->partials, false, EX(ctx)));
+      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, EX(ctx)));
+      CK(launch_givens(ctx->gst, j, ctx->rb_dev, ctx->flags, EX(ctx)));
+      sync_read(ctx);
+      res = ctx->rb_host->res;
+      const double hnext = ctx->rb_host->hnext;
+      k = j + 1;
+      if (res <= target || its >= ctx->opt.maxit || !(hnext > 0.0) || res != res) break;
+      if (j + 1 < m) CK(launch_scale<double>(G, ctx->w, &ctx->gst->hnext, true, V + (size_t)(j + 1) * vs, EX(ctx)));
+    }
+    CK(launch_backsolve(ctx->gst, k, EX(ctx)));
+    CK(launch_axpy_multi<double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
+    if (res <= target) {
+      conv = true;
+      break;
+    }
+    if (res != res) break;
+  }
+  ctx->stats.matvecs += its;
+  if (its > ctx->stats.max_iters) ctx->stats.max_iters = its;
+  ctx->stats.last_iters = its;
+  ctx->stats.last_relres = res / cnorm;
+  if (iters_out) *iters_out = its;
+  if (relres_out) *relres_out = res / cnorm;
+  return conv;
+}
+
+// one RK4 stage (s = 1..4) or a plain RHS evaluation (mode RK_STORE_K)
+bool stage(sgn_ctx* ctx, int mode, double dt) {
+  C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
+  coef_from_spectral(ctx, U[0]);
+  if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
+  const bool conv = gmres(ctx, nullptr, nullptr);
+  RkArgs rk{};
+  rk.mode = mode;
+  rk.dt = dt;
+  rk.dealias = ctx->opt.dealias;
+  rk.krasny = ctx->opt.krasny;
+  rk.krasny_thr = ctx->opt.krasny_thr;
+  rk.g = ctx->g;
+  CK(launch_rhs<double>(ctx->G, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un, ctx->Us, ctx->acc,
+                        mode == RK_STORE_K ? nullptr : ctx->bh, rk, EX(ctx)));
+  return conv;
+}
+
+void reset_flags(sgn_ctx* ctx) { CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->stream)); }
+
+void ensure_phys(sgn_ctx* ctx) {
+  if (ctx->phys[0]) return;
+  for (int i = 0; i < 4; ++i) ctx->phys[i] = dalloc<double>(ctx, ctx->G.nphys());
+}
+
+void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
+                bool* conv_all) {
+  const double* f3[3] = {h, vx, vy};
+  reset_flags(ctx);
+  fwd2(ctx, f3, 3, ctx->Un);
+  const double* fs[1] = {sigma};
+  fwd2(ctx, fs, 1, &ctx->sig);
+  CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
+  bool conv = true;
+  for (int n = 0; n < nsteps; ++n) {
+    conv &= stage(ctx, RK_STAGE1, dt);
+    conv &= stage(ctx, RK_STAGE2, dt);
+    conv &= stage(ctx, RK_STAGE3, dt);
+    conv &= stage(ctx, RK_FINAL, dt);
+  }
+  double* o3[3] = {h, vx, vy};
+  inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o3);
+  double* os[1] = {sigma};
+  inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
+  *conv_all = conv;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+void sgn_default_options(sgn_options* o) {
+  if (!o) return;
+  o->precision = 0;
+  o->restart = 20;
+  o->maxit = 1000;
+  o->tol = 1e-10;
+  o->krasny = 0;
+  o->krasny_thr = 1e-12;
+  o->dealias = 0;
+  o->guess = 0;
+}
+
+sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_options* opt, sgn_t* out) {
+  if (!out) return fail(nullptr, SGN_EINVAL, "sgn_create: out is NULL");
+  *out = nullptr;
+  if (!pow2(Nx) || !pow2(Ny) || Nx < 8 || Ny < 8 || Nx > 2048 || Ny > 2048)
+    return fail(nullptr, SGN_EINVAL, "sgn_create: Nx, Ny must be powers of two in [8, 2048]");
+  if (!(Lx > 0.0) || !(Ly > 0.0) || !isfinite(Lx) || !isfinite(Ly) || !isfinite(g))
+    return fail(nullptr, SGN_EINVAL, "sgn_create: Lx, Ly must be positive and finite, g finite");
+  sgn_options o;
+  sgn_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != 0) return fail(nullptr, SGN_EINVAL, "sgn_create: only precision = 0 (FP64) is built");
+  if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
+  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || (o.guess != 0 && o.guess != 1))
+    return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr or guess");
+  sgn_ctx* ctx = new (std::nothrow) sgn_ctx();
+  if (!ctx) return fail(nullptr, SGN_ENOMEM, "sgn_create: host allocation failed");
+  ctx->opt = o;
+  ctx->g = g;
+  Geom& G = ctx->G;
+  G.Nx = Nx;
+  G.Ny = Ny;
+  G.lNx = ilog2(Nx);
+  G.lNy = ilog2(Ny);
+  G.Nxh = Nx / 2 + 1;
+  G.ldS = G.Nxh;
+  G.Lx = Lx;
+  G.Ly = Ly;
+  try {
+    CK(cudaGetDevice(&ctx->device));
+    init_kernel_attributes<double>();
+    build_tables(ctx);
+    const size_t ns = G.nspec();
+    for (int f = 0; f < 3; ++f) {
+      ctx->Un[f] = dalloc<C64>(ctx, ns);
+      ctx->Us[f] = dalloc<C64>(ctx, ns);
+      ctx->acc[f] = dalloc<C64>(ctx, ns);
+    }
+    ctx->sig = dalloc<C64>(ctx, ns);
+    ctx->bh = dalloc<C64>(ctx, ns);
+    ctx->cvec = dalloc<C64>(ctx, ns);
+    ctx->w = dalloc<C64>(ctx, ns);
+    for (int i = 0; i < 4; ++i) ctx->tmp[i] = dalloc<C64>(ctx, ns);
+    ctx->V = dalloc<C64>(ctx, ns * (size_t)(o.restart + 1));
+    ctx->h = dalloc<double>(ctx, G.nphys());
+    ctx->cr = dalloc<double>(ctx, G.nphys());
+    ctx->cc = dalloc<double>(ctx, G.nphys());
+    ctx->partials = dalloc<double>(ctx, (size_t)(MAXV + 1) * RED_BLOCKS);
+    ctx->scal = dalloc<double>(ctx, 16);
+    ctx->gst = dalloc<GmresDev>(ctx, 1);
+    ctx->rb_dev = dalloc<GmresReadback>(ctx, 1);
+    ctx->flags = dalloc<int>(ctx, 1);
+    CK(cudaMallocHost((void**)&ctx->rb_host, sizeof(GmresReadback)));
+    CK(cudaMallocHost((void**)&ctx->inv_host, 4 * sizeof(double)));
+    CK(cudaMemset(ctx->flags, 0, sizeof(int)));
+    CK(cudaMemset(ctx->gst, 0, sizeof(GmresDev)));
+    // spectra are zero-initialised so padding never holds garbage
+    for (int f = 0; f < 3; ++f) {
+      CK(cudaMemset(ctx->Un[f], 0, ns * sizeof(C64)));
+      CK(cudaMemset(ctx->Us[f], 0, ns * sizeof(C64)));
+      CK(cudaMemset(ctx->acc[f], 0, ns * sizeof(C64)));
+    }
+    CK(cudaMemset(ctx->sig, 0, ns * sizeof(C64)));
+    CK(cudaDeviceSynchronize());
+  } catch (Fail& f) {
+    g_create_error = ctx->err;
+    free_all(ctx);
+    delete ctx;
+    return f.st;
+  }
+  *out = ctx;
+  return SGN_OK;
+}
+
+sgn_status sgn_destroy(sgn_t ctx) {
+  if (!ctx) return SGN_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->prof.destroy();
+  free_all(ctx);
+  delete ctx;
+  return SGN_OK;
+}
+
+sgn_status sgn_set_stream(sgn_t ctx, void* stream) {
+  if (!ctx) return SGN_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return SGN_OK;
+}
+
+const char* sgn_last_error(sgn_t ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+sgn_status sgn_set_profiling(sgn_t ctx, int on) {
+  if (!ctx) return SGN_EINVAL;
+  if (on) {
+    ctx->prof.init();
+    ctx->prof.reset();
+  } else {
+    ctx->prof.harvest();
+  }
+  ctx->prof.on = on != 0;
+  return SGN_OK;
+}
+
+sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long long* launches) {
+  if (!ctx) return SGN_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->prof.harvest();
+  for (int k = 0; k < n && k < PK_COUNT; ++k) {
+    if (ms) ms[k] = ctx->prof.ms[k];
+    if (counts) counts[k] = ctx->prof.cnt[k];
+  }
+  if (launches) *launches = ctx->prof.launches;
+  return SGN_OK;
+}
+
+sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out) {
+  if (!ctx || !out) return SGN_EINVAL;
+  *out = ctx->stats;
+  return SGN_OK;
+}
+
+#define API_BEGIN                                                                                  \
+  if (!ctx) return SGN_EINVAL;                                                                     \
+  ctx->err.clear();                                                                                \
+  try {
+#define API_END                                                                                    \
+  }                                                                                                \
+  catch (Fail & f) {                                                                               \
+    return f.st;                                                                                   \
+  }
+
+sgn_status sgn_spectral_derivative(sgn_t ctx, const double* f, double* fx, double* fy) {
+  API_BEGIN
+  if (!f) return fail(ctx, SGN_EINVAL, "sgn_spectral_derivative: f is NULL");
+  const double* fi[1] = {f};
+  fwd2(ctx, fi, 1, &ctx->w);
+  const C64* in[1] = {ctx->w};
+  if (fx) {
+    int dx[1] = {1}, dy[1] = {0};
+    double* o[1] = {fx};
+    inv2(ctx, in, dx, dy, 1, o);
+  }
+  if (fy) {
+    int dx[1] = {0}, dy[1] = {1};
+    double* o[1] = {fy};
+    inv2(ctx, in, dx, dy, 1, o);
+  }
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_fft2_r2c(sgn_t ctx, const double* f, double* fhat) {
+  API_BEGIN
+  if (!f || !fhat) return fail(ctx, SGN_EINVAL, "sgn_fft2_r2c: NULL pointer");
+  const double* fi[1] = {f};
+  fwd2(ctx, fi, 1, &ctx->w);
+  const Geom& G = ctx->G;
+  CK(cudaMemcpy2DAsync(fhat, G.Nxh * sizeof(C64), ctx->w, G.ldS * sizeof(C64), G.Nxh * sizeof(C64), G.Ny,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_fft2_c2r(sgn_t ctx, const double* fhat, double* f) {
+  API_BEGIN
+  if (!f || !fhat) return fail(ctx, SGN_EINVAL, "sgn_fft2_c2r: NULL pointer");
+  const Geom& G = ctx->G;
+  CK(cudaMemcpy2DAsync(ctx->w, G.ldS * sizeof(C64), fhat, G.Nxh * sizeof(C64), G.Nxh * sizeof(C64), G.Ny,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  const C64* in[1] = {ctx->w};
+  double* o[1] = {f};
+  inv2(ctx, in, nullptr, nullptr, 1, o);
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_elliptic_apply(sgn_t ctx, const double* h, const double* sigma, double* out) {
+  API_BEGIN
+  if (!h || !sigma || !out) return fail(ctx, SGN_EINVAL, "sgn_elliptic_apply: NULL pointer");
+  reset_flags(ctx);
+  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+  const double* fi[1] = {sigma};
+  fwd2(ctx, fi, 1, &ctx->sig);
+  CK(launch_matvec<double>(ctx->G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, false, EX(ctx)));
+  const C64* in[1] = {ctx->w};
+  double* o[1] = {out};
+  inv2(ctx, in, nullptr, nullptr, 1, o);
+  CK(launch_readback_scalar(ctx->scal, ctx->flags, ctx->rb_dev, EX(ctx)));
+  sync_read(ctx);
+  check_flags(ctx, ctx->rb_host->flags);
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_gmres_solve(sgn_t ctx, const double* h, const double* b, double* sigma, int* iters,
+                           double* relres) {
+  API_BEGIN
+  if (!h || !b || !sigma) return fail(ctx, SGN_EINVAL, "sgn_gmres_solve: NULL pointer");
+  reset_flags(ctx);
+  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+  const double* fb[1] = {b};
+  fwd2(ctx, fb, 1, &ctx->bh);
+  const double* fs[1] = {sigma};
+  fwd2(ctx, fs, 1, &ctx->sig);
+  const bool conv = gmres(ctx, iters, relres);
+  const C64* in[1] = {ctx->sig};
+  double* o[1] = {sigma};
+  inv2(ctx, in, nullptr, nullptr, 1, o);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit before the tolerance");
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_rhs(sgn_t ctx, const double* h, const double* vx, const double* vy, double* sigma, double* ht,
+                   double* vxt, double* vyt) {
+  API_BEGIN
+  if (!h || !vx || !vy || !sigma || !ht || !vxt || !vyt) return fail(ctx, SGN_EINVAL, "sgn_rhs: NULL pointer");
+  reset_flags(ctx);
+  const double* f3[3] = {h, vx, vy};
+  fwd2(ctx, f3, 3, ctx->Un);
+  const double* fs[1] = {sigma};
+  fwd2(ctx, fs, 1, &ctx->sig);
+  CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
+  const bool conv = stage(ctx, RK_STORE_K, 0.0);
+  double* o3[3] = {ht, vxt, vyt};
+  inv2(ctx, (const C64* const*)ctx->acc, nullptr, nullptr, 3, o3);
+  double* os[1] = {sigma};
+  inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit before the tolerance");
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_rk4_step(sgn_t ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps) {
+  API_BEGIN
+  if (!h || !vx || !vy || !sigma) return fail(ctx, SGN_EINVAL, "sgn_rk4_step: NULL pointer");
+  if (nsteps < 0 || !isfinite(dt)) return fail(ctx, SGN_EINVAL, "sgn_rk4_step: bad dt or nsteps");
+  if (nsteps == 0) return SGN_OK;
+  bool conv = true;
+  rk4_device(ctx, h, vx, vy, sigma, dt, nsteps, &conv);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, double* sigma, double dt,
+                             int nsteps) {
+  API_BEGIN
+  if (!h || !vx || !vy || !sigma) return fail(ctx, SGN_EINVAL, "sgn_rk4_step_host: NULL pointer");
+  if (nsteps < 0 || !isfinite(dt)) return fail(ctx, SGN_EINVAL, "sgn_rk4_step_host: bad dt or nsteps");
+  ensure_phys(ctx);
+  const size_t bytes = ctx->G.nphys() * sizeof(double);
+  double* hv[4] = {h, vx, vy, sigma};
+  for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->phys[i], hv[i], bytes, cudaMemcpyHostToDevice, ctx->stream));
+  bool conv = true;
+  if (nsteps > 0) rk4_device(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
+  for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_invariants(sgn_t ctx, const double* h, const double* vx, const double* vy, const double* sigma,
+                          double out[4]) {
+  API_BEGIN
+  if (!h || !vx || !vy || !sigma || !out) return fail(ctx, SGN_EINVAL, "sgn_invariants: NULL pointer");
+  ensure_phys(ctx);
+  const double* fs[1] = {sigma};
+  fwd2(ctx, fs, 1, &ctx->w);
+  const C64* in[2] = {ctx->w, ctx->w};
+  int dx[2] = {1, 0}, dy[2] = {0, 1};
+  double* o[2] = {ctx->phys[0], ctx->phys[1]};
+  inv2(ctx, in, dx, dy, 2, o);
+  CK(launch_invariant_sums(ctx->G, h, vx, vy, sigma, ctx->phys[0], ctx->phys[1], ctx->g, ctx->partials,
+                           EX(ctx)));
+  CK(launch_reduce(ctx->partials, 4, ctx->scal + 4, false, EX(ctx)));
+  CK(cudaMemcpyAsync(ctx->inv_host, ctx->scal + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double dA = ctx->G.Lx * ctx->G.Ly / (double)ctx->G.nphys();
+  for (int q = 0; q < 4; ++q) out[q] = ctx->inv_host[q] * dA;
+  return SGN_OK;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// sgn_internal.h - host-side interface between the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace sgn {
+
+// Upper bound of the GMRES restart length (Krylov basis of MAXM+1 vectors).
+constexpr int MAXM = 32;
+constexpr int MAXV = MAXM + 1;
+// Blocks of the reduction kernels (a multiple of the 152 SMs of a GB300).
+constexpr int RED_BLOCKS = 304;
+
+// Grid geometry. Spectra are stored row-major [Ny][ldS] complex, row ky holds
+// kx = 0..Nx/2 (R2C half storage along x); ldS >= Nxh.
+struct Geom {
+  int Nx, Ny, lNx, lNy, Nxh, ldS;
+  double Lx, Ly;
+  __host__ __device__ size_t nphys() const { return (size_t)Nx * Ny; }
+  __host__ __device__ size_t nspec() const { return (size_t)Ny * ldS; }
+};
+
+// Device flags raised by the coefficient pass (OR-ed bits).
+enum : int { FLAG_CAVITATION = 1, FLAG_NONFINITE = 2 };
+
+// Epilogue modes of the RHS y-forward pass (the RK4 stage update, Section 3).
+enum RkMode : int {
+  RK_STORE_K = 0,  // write K = (h_t, vx_t, vy_t) spectra
+  RK_STAGE1 = 1,   // acc = K;       U_s = U_n + dt/2 K
+  RK_STAGE2 = 2,   // acc += 2K;     U_s = U_n + dt/2 K
+  RK_STAGE3 = 3,   // acc += 2K;     U_s = U_n + dt K
+  RK_FINAL = 4     // U_n += dt/6 (acc + K), then the Krasny filter if on
+};
+
+// Per-precision device tables.
+template <typename T>
+struct Tables {
+  cpx<T>* twx = nullptr;  // W_Nx^k, k < Nx
+  cpx<T>* twy = nullptr;  // W_Ny^k, k < Ny
+  T* kx = nullptr;        // 2 pi m / Lx, m = 0..Nx/2, Nyquist 0   [Nxh]
+  T* ky = nullptr;        // 2 pi m / Ly, m = 0..Ny/2-1, -Ny/2..-1, Nyquist 0 [Ny]
+};
+
+// GMRES scalars that live on the device (Hessenberg, rotations, residual).
+struct GmresDev {
+  double H[(MAXM + 1) * MAXM];  // column-major, H[i + j*(MAXM+1)]
+  double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
+  double h1[MAXV], h2[MAXV];  // the two classical Gram-Schmidt passes
+  double nrm2;                // squared norm of the orthogonalised vector
+  double hnext, inv_hnext;    // H[j+1][j] and its inverse
+  double res;                 // |g_{j+1}|
+};
+
+// What the host reads back after each Arnoldi step.
+struct GmresReadback {
+  double res;
+  double hnext;
+  double scalar;  // generic scalar (a norm) for other sync points
+  int flags;
+  int pad;
+};
+
+// ------------------------------------------------------------ profiling
+// Kernel classes timed with CUDA events when profiling is on.
+enum ProfKind : int {
+  PK_COEF = 0,     // y-inverse + x-pass of h (coefficients of Eq. (sigmav))
+  PK_MV_YINV,      // matvec: y-inverse of sigma_hat, i ky sigma_hat
+  PK_MV_X,         // matvec: fused x-pass
+  PK_MV_YFWD,      // matvec: y-forward + preconditioner
+  PK_RHS_YINV,     // RHS: y-inverse of vx, vy, sigma, i ky sigma
+  PK_RHS_X,        // RHS: fused x-pass
+  PK_RHS_YFWD,     // RHS: y-forward + RK4 update
+  PK_KRYLOV,       // GMRES vector kernels and reductions
+  PK_IO,           // physical <-> spectral conversions at call boundaries
+  PK_COUNT
+};
+
+struct Prof {
+  static constexpr int POOL = 512;
+  bool on = false;
+  bool ready = false;
+  cudaEvent_t ev[2 * POOL];
+  int kind[POOL];
+  int n = 0;
+  double ms[PK_COUNT] = {};
+  long long cnt[PK_COUNT] = {};
+  long long launches = 0;  // every kernel the library launched (profiling or not)
+
+  void init() {
+    if (ready) return;
+    for (int i = 0; i < 2 * POOL; ++i) cudaEventCreate(&ev[i]);
+    ready = true;
+  }
+  void destroy() {
+    if (!ready) return;
+    for (int i = 0; i < 2 * POOL; ++i) cudaEventDestroy(ev[i]);
+    ready = false;
+  }
+  // accumulates every recorded pair; waits for the last one
+  void harvest() {
+    if (!ready || n == 0) return;
+    cudaEventSynchronize(ev[2 * n - 1]);
+    for (int i = 0; i < n; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+        ms[kind[i]] += t;
+        cnt[kind[i]] += 1;
+      }
+    }
+    n = 0;
+  }
+  void reset() {
+    n = 0;
+    for (int k = 0; k < PK_COUNT; ++k) {
+      ms[k] = 0.0;
+      cnt[k] = 0;
+    }
+    launches = 0;
+  }
+};
+
+// Where and how a launcher enqueues: the stream, and the profiler (may be null).
+struct Exec {
+  cudaStream_t s;
+  Prof* p;
+  int kind_override = -1;  // time every launch of this call under one class
+  void begin(int k, int nlaunch = 1) const {
+    if (!p) return;
+    if (kind_override >= 0) k = kind_override;
+    p->launches += nlaunch;
+    if (!p->on || !p->ready) return;
+    if (p->n == Prof::POOL) p->harvest();
+    p->kind[p->n] = k;
+    cudaEventRecord(p->ev[2 * p->n], s);
+  }
+  void end() const {
+    if (!p || !p->on || !p->ready) return;
+    cudaEventRecord(p->ev[2 * p->n + 1], s);
+    p->n += 1;
+  }
+};
+
+// ------------------------------------------------------------ launchers
+// All launchers enqueue on ex.s and return cudaGetLastError().
+
+template <typename T>
+void init_kernel_attributes();
+
+// physical rows -> x-spectral half rows (R2C along x), nf fields
+template <typename T>
+cudaError_t launch_x_r2c(const Geom& G, const Tables<T>& tb, const double* const* f, int nf,
+                         cpx<T>* const* out, const Exec& ex);
+// x-spectral half rows (times i kx if deriv) -> physical rows, times scale
+template <typename T>
+cudaError_t launch_x_c2r(const Geom& G, const Tables<T>& tb, const cpx<T>* const* in, const int* deriv,
+                         int nf, double* const* out, double scale, const Exec& ex);
+// column transforms of nf spectra (in place allowed); inverse may pre-multiply by i ky
+template <typename T>
+cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const cpx<T>* const* in,
+                         const int* deriv, int nf, cpx<T>* const* out, const Exec& ex);
+
+// coefficient pass: from Hy = y-inverse of h_hat, write h, cr = 0.5/(N h), cc = 1.5/(N h^3)
+template <typename T>
+cudaError_t launch_coef_x(const Geom& G, const Tables<T>& tb, const cpx<T>* Hy, T* h, T* cr, T* cc,
+                          int* flags, const Exec& ex);
+// the same three arrays straight from a physical h (float64)
+template <typename T>
+cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T* cc, int* flags,
+                             const Exec& ex);
+
+// matvec w = M^-1 L sigma (precond) or L sigma (!precond), spectral in/out.
+// tmp: 4 spectra of scratch (S, Sy, C, By).
+template <typename T>
+cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
+                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex);
+
+// RHS of one stage from state U (3 spectra), sigma_hat, h, cr; K goes through
+// the RK epilogue. tmp: 4 spectra. Writes b_hat of the next stage state.
+struct RkArgs {
+  int mode;
+  double dt;
+  int dealias;
+  int krasny;
+  double krasny_thr;
+  double g;
+};
+template <typename T>
+cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, const cpx<T>* sig, const T* h,
+                       const T* cr, cpx<T>* const* tmp, cpx<T>* const* Un, cpx<T>* const* Unext,
+                       cpx<T>* const* acc, cpx<T>* bhat, const RkArgs& rk, const Exec& ex);
+
+// b_hat = -(i kx vx_hat + i ky vy_hat)
+template <typename T>
+cudaError_t launch_spec_div(const Geom& G, const Tables<T>& tb, const cpx<T>* vx, const cpx<T>* vy,
+                            cpx<T>* b, const Exec& ex);
+// out = M^-1 in (spectral), and the weighted squared norm into partials
+template <typename T>
+cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<T>* out,
+                           double* partials, const Exec& ex);
+
+// ---- Krylov vector kernels (spectral vectors, Parseval-weighted inner product)
+template <typename T>
+cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
+                        double* partials, const Exec& ex);
+// w -= sum_i coef[i] V_i; then partial dots of V_i with new w (want_dots) and its squared norm
+template <typename T>
+cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
+                              cpx<T>* w, double* partials, bool want_dots, const Exec& ex);
+// r = c - w, and partial squared norm of r
+template <typename T>
+cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
+                            const Exec& ex);
+// x *= (*factor) (device scalar) or y = x * factor
+template <typename T>
+cudaError_t launch_scale(const Geom& G, const cpx<T>* x, const double* factor, bool invert, cpx<T>* y,
+                         const Exec& ex);
+// x += sum_i coef[i] V_i
+template <typename T>
+cudaError_t launch_axpy_multi(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
+                              cpx<T>* x, const Exec& ex);
+template <typename T>
+cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex);
+
+// reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
+cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const Exec& ex);
+// GMRES scalar kernels (one thread)
+cudaError_t launch_gmres_start(GmresDev* st, const double* beta, const Exec& ex);
+cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int* flags, const Exec& ex);
+cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex);
+cudaError_t launch_readback_scalar(const double* x, const int* flags, GmresReadback* rb_dev, const Exec& ex);
+
+// invariants: physical pointwise sums (mass, px, py, energy) -> partials[RED_BLOCKS][4]
+cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* vx, const double* vy,
+                                  const double* sig, const double* sx, const double* sy, double g,
+                                  double* partials, const Exec& ex);
+
+}  // namespace sgn

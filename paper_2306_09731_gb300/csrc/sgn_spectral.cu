@@ -1,0 +1,836 @@
+// sgn_spectral.cu - spectral passes of the SGN hot path (Section 3).
+//
+// Every 2D transform is split into an x-pass over row PAIRS and a y-pass over
+// column tiles of the half spectrum [Ny][ldS]:
+//  * x-pass: rows y0 = 2p, y1 = 2p+1 travel together as one complex signal
+//    z = f(y0) + i f(y1). An inverse x-transform of two half spectra is one
+//    complex inverse FFT of length Nx; a forward one is a complex FFT followed by
+//    the split F0 = Z + conj(Z(-k)), F1 = -i (Z - conj(Z(-k))) (each 2x the
+//    half-spectrum of a real row).
+//  * y-pass: C neighbouring kx columns per block, interleaved in shared memory.
+// The pointwise work of the method is fused into these passes:
+//  * matvec (Eq. (sigmav) preconditioned): y-inverse of sigma_hat and i ky
+//    sigma_hat; x-pass forms sigma, sigma_x, sigma_y, a = 3 sigma/h^3,
+//    b = grad(sigma)/h, forward x and the combination a - i kx bx; y-forward,
+//    minus i ky by, times 1/(3 + kx^2 + ky^2).
+//  * RHS (Eq. (1) and the v-form of Eq. (2)): y-inverse of vx, vy, sigma,
+//    i ky sigma; x-pass forms q = h v - grad sigma (= h u) and
+//    F = |v|^2/2 - |grad sigma|^2/(2h^2) + g h - 9 sigma^2/(2 h^4), forward x;
+//    y-forward with -i k combinations and the RK4 stage update.
+#include <math.h>
+
+#include "sgn_internal.h"
+
+namespace sgn {
+
+// ------------------------------------------------------------------ helpers
+
+template <typename T>
+__device__ __forceinline__ cpx<T> ld(const cpx<T>* p) {
+  return *p;
+}
+
+// Packed full-length spectrum of two real rows from their half spectra:
+// Z[k] = G0[k] + i G1[k], G = (deriv ? i kx : 1) * S, extended by Hermitian
+// symmetry for k > N/2; the kx = 0 and kx = N/2 entries are taken real (the
+// C2R convention).
+template <typename T>
+__device__ __forceinline__ void load_packed(cpx<T> (&v)[8], const cpx<T>* S0, const cpx<T>* S1, bool deriv,
+                                            const T* __restrict__ kx, int t, int lN) {
+  const int N = 1 << lN, T_ = N >> 3, half = N >> 1;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int k = t + s * T_;
+    const int kk = (k <= half) ? k : N - k;
+    cpx<T> A = ld(S0 + kk), B = ld(S1 + kk);
+    if (deriv) {
+      const T kv = __ldg(kx + kk);
+      A = mul_ik(A, kv);
+      B = mul_ik(B, kv);
+    }
+    if (kk == 0 || kk == half) {
+      A.y = (T)0;
+      B.y = (T)0;
+    }
+    if (k > half) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    v[s] = mk(A.x - B.y, A.y + B.x);
+  }
+}
+
+// After a forward FFT of z = f0 + i f1 held in v: writes v to sm, syncs, and
+// returns for the thread's half-spectrum indices k = t + s*T_ (s < 4, plus
+// k = N/2 on t == 0) the values 2*F0[k] and 2*F1[k]. Leaves sm in use: the
+// caller syncs before reusing it.
+template <typename T>
+__device__ __forceinline__ void split_pair(const cpx<T> (&v)[8], cpx<T>* sm, int t, int lN, cpx<T> (&f0)[5],
+                                           cpx<T> (&f1)[5]) {
+  const int N = 1 << lN, T_ = N >> 3;
+  store_slots(v, sm, t, T_, 0);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int k = t + s * T_;
+    const cpx<T> P = v[s];
+    const cpx<T> Q = conjg(sm[pad_idx((N - k) & (N - 1))]);
+    f0[s] = P + Q;
+    f1[s] = mul_mi(P - Q);
+  }
+}
+
+__device__ __forceinline__ bool split_owns(int s, int t) { return s < 4 || t == 0; }
+
+// Block layout of the x-pass: P row pairs per block, T_ = Nx/8 threads each.
+struct XLayout {
+  int t, grp, pair, y0, y1;
+  bool valid;
+};
+__device__ __forceinline__ XLayout x_layout(const Geom& G) {
+  XLayout L;
+  const int lT = G.lNx - 3;
+  L.grp = threadIdx.x >> lT;
+  L.t = threadIdx.x & ((1 << lT) - 1);
+  const int P = blockDim.x >> lT;
+  int pair = blockIdx.x * P + L.grp;
+  L.valid = pair < (G.Ny >> 1);
+  if (!L.valid) pair = (G.Ny >> 1) - 1;
+  L.pair = pair;
+  L.y0 = 2 * pair;
+  L.y1 = L.y0 + 1;
+  return L;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T>* x_smem(const Geom& G, int grp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  return reinterpret_cast<cpx<T>*>(smraw) + grp * smem_elems(G.Nx);
+}
+
+// ------------------------------------------------------------ plain x-passes
+
+template <typename T>
+struct XR2CArgs {
+  const double* f[4];
+  cpx<T>* out[4];
+};
+
+template <typename T>
+__global__ void k_x_r2c(Geom G, const cpx<T>* __restrict__ tw, XR2CArgs<T> a) {
+  const XLayout L = x_layout(G);
+  cpx<T>* sm = x_smem<T>(G, L.grp);
+  const int N = G.Nx, T_ = N >> 3;
+  const double* f = a.f[blockIdx.y];
+  cpx<T> v[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    v[s] = mk((T)f[(size_t)L.y0 * N + x], (T)f[(size_t)L.y1 * N + x]);
+  }
+  fft_regs<false>(v, sm, tw, L.t, G.lNx);
+  cpx<T> f0[5], f1[5];
+  split_pair(v, sm, L.t, G.lNx, f0, f1);
+  if (!L.valid) return;
+  cpx<T>* o = a.out[blockIdx.y];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t)) continue;
+    const int k = L.t + s * T_;
+    o[(size_t)L.y0 * G.ldS + k] = scl(f0[s], (T)0.5);
+    o[(size_t)L.y1 * G.ldS + k] = scl(f1[s], (T)0.5);
+  }
+}
+
+template <typename T>
+struct XC2RArgs {
+  const cpx<T>* in[4];
+  double* out[4];
+  int deriv[4];
+};
+
+template <typename T>
+__global__ void k_x_c2r(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx, XC2RArgs<T> a,
+                        double scale) {
+  const XLayout L = x_layout(G);
+  cpx<T>* sm = x_smem<T>(G, L.grp);
+  const int N = G.Nx, T_ = N >> 3;
+  const int fi = blockIdx.y;
+  cpx<T> v[8];
+  load_packed(v, a.in[fi] + (size_t)L.y0 * G.ldS, a.in[fi] + (size_t)L.y1 * G.ldS, a.deriv[fi] != 0, kx,
+              L.t, G.lNx);
+  fft_regs<true>(v, sm, tw, L.t, G.lNx);
+  if (!L.valid) return;
+  double* o = a.out[fi];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    o[(size_t)L.y0 * N + x] = (double)v[s].x * scale;
+    o[(size_t)L.y1 * N + x] = (double)v[s].y * scale;
+  }
+}
+
+// ------------------------------------------------------ coefficient passes
+
+template <typename T>
+__device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, T* cc, size_t i, int* flags) {
+  if (!isfinite(hv)) {
+    atomicOr(flags, FLAG_NONFINITE);
+  } else if (!(hv > 0.0)) {
+    atomicOr(flags, FLAG_CAVITATION);
+  }
+  const double r = 1.0 / hv;
+  h[i] = (T)hv;
+  cr[i] = (T)(0.5 * invN * r);
+  cc[i] = (T)(1.5 * invN * r * r * r);
+}
+
+// Hy = y-inverse of h_hat; x-inverse gives N*h. Writes h, cr = 0.5/(N h),
+// cc = 1.5/(N h^3), the coefficients of Eq. (sigmav) with the factor 1/(2N)
+// of the matvec's packed transforms folded in.
+template <typename T>
+__global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx, const cpx<T>* Hy,
+                         T* h, T* cr, T* cc, int* flags) {
+  const XLayout L = x_layout(G);
+  cpx<T>* sm = x_smem<T>(G, L.grp);
+  const int N = G.Nx, T_ = N >> 3;
+  cpx<T> v[8];
+  load_packed(v, Hy + (size_t)L.y0 * G.ldS, Hy + (size_t)L.y1 * G.ldS, false, kx, L.t, G.lNx);
+  fft_regs<true>(v, sm, tw, L.t, G.lNx);
+  if (!L.valid) return;
+  const double invN = 1.0 / (double)G.nphys();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags);
+    coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags);
+  }
+}
+
+template <typename T>
+__global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, T* cc, int* flags) {
+  const double invN = 1.0 / (double)G.nphys();
+  const size_t n = G.nphys();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    coef_point<T>(hp[i], invN, h, cr, cc, i, flags);
+}
+
+// ---------------------------------------------------------- fused matvec x
+
+// S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
+// Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
+// reads only its own row pair before writing it: Cout/Byout may alias S/Sy.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+                                               const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
+                                               const T* __restrict__ cc, cpx<T>* Cout, cpx<T>* Byout) {
+  const XLayout L = x_layout(G);
+  cpx<T>* sm = x_smem<T>(G, L.grp);
+  const int N = G.Nx, T_ = N >> 3, lN = G.lNx;
+  const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
+  cpx<T> X[8], Y[8], Z[8];
+  load_packed(X, S + o0, S + o1, true, kx, L.t, lN);
+  fft_regs<true>(X, sm, tw, L.t, lN);
+  load_packed(Y, Sy + o0, Sy + o1, false, kx, L.t, lN);
+  fft_regs<true>(Y, sm, tw, L.t, lN);
+  load_packed(Z, S + o0, S + o1, false, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+  const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    const T r0 = cr[p0 + x], r1 = cr[p1 + x], c0 = cc[p0 + x], c1 = cc[p1 + x];
+    Z[s] = mk(c0 * Z[s].x, c1 * Z[s].y);
+    X[s] = mk(r0 * X[s].x, r1 * X[s].y);
+    Y[s] = mk(r0 * Y[s].x, r1 * Y[s].y);
+  }
+  cpx<T> a0[5], a1[5], b0[5], b1[5];
+  fft_regs<false>(Z, sm, tw, L.t, lN);
+  split_pair(Z, sm, L.t, lN, a0, a1);
+  __syncthreads();
+  fft_regs<false>(X, sm, tw, L.t, lN);
+  split_pair(X, sm, L.t, lN, b0, b1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t) || !L.valid) continue;
+    const int k = L.t + s * T_;
+    const T kv = __ldg(kx + k);
+    Cout[o0 + k] = a0[s] - mul_ik(b0[s], kv);
+    Cout[o1 + k] = a1[s] - mul_ik(b1[s], kv);
+  }
+  __syncthreads();
+  fft_regs<false>(Y, sm, tw, L.t, lN);
+  split_pair(Y, sm, L.t, lN, b0, b1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t) || !L.valid) continue;
+    const int k = L.t + s * T_;
+    Byout[o0 + k] = b0[s];
+    Byout[o1 + k] = b1[s];
+  }
+}
+
+// ------------------------------------------------------------- fused RHS x
+
+// Inputs (y-inverse outputs): Vx, Vy, S = sigma, Sy = i ky sigma. Writes
+// Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and Fh = F^x.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+                                                const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
+                                                const cpx<T>* Sy, const T* __restrict__ hh,
+                                                const T* __restrict__ cr, T g, cpx<T>* Cq, cpx<T>* Qy,
+                                                cpx<T>* Fh) {
+  const XLayout L = x_layout(G);
+  cpx<T>* sm = x_smem<T>(G, L.grp);
+  const int N = G.Nx, T_ = N >> 3, lN = G.lNx;
+  const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
+  const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
+  const T n = (T)(1.0 / (double)G.nphys());
+  const T twoN = (T)(2.0 * (double)G.nphys());
+  cpx<T> QX[8], QY[8], F[8], Z[8];
+  // grad sigma
+  load_packed(QX, S + o0, S + o1, true, kx, L.t, lN);
+  fft_regs<true>(QX, sm, tw, L.t, lN);
+  load_packed(QY, Sy + o0, Sy + o1, false, kx, L.t, lN);
+  fft_regs<true>(QY, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    const T r0 = cr[p0 + x] * twoN, r1 = cr[p1 + x] * twoN;
+    const T sx0 = QX[s].x * n, sx1 = QX[s].y * n, sy0 = QY[s].x * n, sy1 = QY[s].y * n;
+    QX[s] = mk(-sx0, -sx1);
+    QY[s] = mk(-sy0, -sy1);
+    F[s] = mk((T)-0.5 * r0 * r0 * (sx0 * sx0 + sy0 * sy0), (T)-0.5 * r1 * r1 * (sx1 * sx1 + sy1 * sy1));
+  }
+  // sigma: -9 sigma^2 / (2 h^4)
+  load_packed(Z, S + o0, S + o1, false, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    const T r0 = cr[p0 + x] * twoN, r1 = cr[p1 + x] * twoN;
+    const T s0 = Z[s].x * n, s1 = Z[s].y * n;
+    const T q0 = s0 * r0 * r0, q1 = s1 * r1 * r1;
+    F[s].x -= (T)4.5 * q0 * q0;
+    F[s].y -= (T)4.5 * q1 * q1;
+  }
+  // vx: h vx and |vx|^2/2
+  load_packed(Z, Vx + o0, Vx + o1, false, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    const T h0 = hh[p0 + x], h1 = hh[p1 + x];
+    const T v0 = Z[s].x * n, v1 = Z[s].y * n;
+    QX[s].x += h0 * v0;
+    QX[s].y += h1 * v1;
+    F[s].x += (T)0.5 * v0 * v0;
+    F[s].y += (T)0.5 * v1 * v1;
+  }
+  // vy: h vy, |vy|^2/2 and g h
+  load_packed(Z, Vy + o0, Vy + o1, false, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    const T h0 = hh[p0 + x], h1 = hh[p1 + x];
+    const T v0 = Z[s].x * n, v1 = Z[s].y * n;
+    QY[s].x += h0 * v0;
+    QY[s].y += h1 * v1;
+    F[s].x += (T)0.5 * v0 * v0 + g * h0;
+    F[s].y += (T)0.5 * v1 * v1 + g * h1;
+    // the split returns twice the half spectra: pre-scale by 1/2
+    QX[s] = scl(QX[s], (T)0.5);
+    QY[s] = scl(QY[s], (T)0.5);
+    F[s] = scl(F[s], (T)0.5);
+  }
+  cpx<T> f0[5], f1[5];
+  fft_regs<false>(QX, sm, tw, L.t, lN);
+  split_pair(QX, sm, L.t, lN, f0, f1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t) || !L.valid) continue;
+    const int k = L.t + s * T_;
+    const T kv = __ldg(kx + k);
+    Cq[o0 + k] = mul_ik(f0[s], -kv);
+    Cq[o1 + k] = mul_ik(f1[s], -kv);
+  }
+  __syncthreads();
+  fft_regs<false>(QY, sm, tw, L.t, lN);
+  split_pair(QY, sm, L.t, lN, f0, f1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t) || !L.valid) continue;
+    const int k = L.t + s * T_;
+    Qy[o0 + k] = f0[s];
+    Qy[o1 + k] = f1[s];
+  }
+  __syncthreads();
+  fft_regs<false>(F, sm, tw, L.t, lN);
+  split_pair(F, sm, L.t, lN, f0, f1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (!split_owns(s, L.t) || !L.valid) continue;
+    const int k = L.t + s * T_;
+    Fh[o0 + k] = f0[s];
+    Fh[o1 + k] = f1[s];
+  }
+}
+
+// ------------------------------------------------------------------ y-pass
+
+template <typename T, int NIN>
+struct YIn {
+  const cpx<T>* src[NIN];
+  int deriv[NIN];  // pre-multiply by i ky (inverse passes)
+};
+
+// Column tile: C = blockDim / (Ny/8) neighbouring kx columns, thread index
+// c + C*t. Each input column is transformed in registers; the epilogue gets
+// all NIN results of the thread's 8 rows.
+constexpr int ypass_threads(int nin) { return nin >= 3 ? 256 : 512; }
+
+template <typename T, bool INV, int NIN, class Epi>
+__global__ void __launch_bounds__(ypass_threads(NIN)) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
+                                                YIn<T, NIN> in, Epi epi) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
+  const int lN = G.lNy, T_ = G.Ny >> 3;
+  const int lC = __ffs(blockDim.x >> (lN - 3)) - 1;
+  const int c = threadIdx.x & ((1 << lC) - 1);
+  const int t = threadIdx.x >> lC;
+  int col = (blockIdx.x << lC) + c;
+  const bool valid = col < G.Nxh;
+  if (!valid) col = G.Nxh - 1;
+  cpx<T> r[NIN][8];
+#pragma unroll
+  for (int i = 0; i < NIN; ++i) {
+    const cpx<T>* src = in.src[i];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int row = t + s * T_;
+      cpx<T> z = ld(src + (size_t)row * G.ldS + col);
+      if (in.deriv[i]) z = mul_ik(z, __ldg(ky + row));
+      r[i][s] = z;
+    }
+    fft_regs<INV>(r[i], smb + c, tw, t, lN, lC);
+  }
+  epi(r, col, t, T_, valid, G, ky);
+}
+
+template <typename T, int NIN>
+struct EpiStore {
+  cpx<T>* dst[NIN];
+  __device__ __forceinline__ void operator()(cpx<T> (&r)[NIN][8], int col, int t, int T_, bool valid,
+                                             const Geom& G, const T* ky) const {
+    if (!valid) return;
+#pragma unroll
+    for (int i = 0; i < NIN; ++i)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) dst[i][(size_t)(t + s * T_) * G.ldS + col] = r[i][s];
+  }
+};
+
+// w = [M^-1] (C - i ky By), M = 3 + kx^2 + ky^2 (Section 3 preconditioner)
+template <typename T>
+struct EpiMatvec {
+  cpx<T>* w;
+  const T* kx;
+  int precond;
+  __device__ __forceinline__ void operator()(cpx<T> (&r)[2][8], int col, int t, int T_, bool valid,
+                                             const Geom& G, const T* ky) const {
+    if (!valid) return;
+    const T kxv = __ldg(kx + col);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int row = t + s * T_;
+      const T kyv = __ldg(ky + row);
+      cpx<T> z = r[0][s] - mul_ik(r[1][s], kyv);
+      if (precond) z = scl(z, (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+      w[(size_t)row * G.ldS + col] = z;
+    }
+  }
+};
+
+// K = (h_t, vx_t, vy_t) from r0 = Cq^y, r1 = Qy^y, r2 = F^y, then the RK4
+// stage update and b_hat = -(i kx vx + i ky vy) of the next stage state.
+template <typename T>
+struct EpiRHS {
+  cpx<T>* K[3];      // RK_STORE_K output
+  cpx<T>* Un[3];     // step-start state (RK_FINAL: updated in place)
+  cpx<T>* Unext[3];  // next stage state (stages 1-3)
+  cpx<T>* acc[3];    // running sum of b_s K_s
+  cpx<T>* b;         // next b_hat (may be null)
+  const T* kx;
+  RkArgs rk;
+  __device__ __forceinline__ void operator()(cpx<T> (&r)[3][8], int col, int t, int T_, bool valid,
+                                             const Geom& G, const T* ky) const {
+    if (!valid) return;
+    const T kxv = __ldg(kx + col);
+    const bool keepx = !rk.dealias || 3 * col <= G.Nx;
+    const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int row = t + s * T_;
+      const T kyv = __ldg(ky + row);
+      const size_t e = (size_t)row * G.ldS + col;
+      cpx<T> k0 = r[0][s] - mul_ik(r[1][s], kyv);
+      cpx<T> k1 = mul_ik(r[2][s], -kxv);
+      cpx<T> k2 = mul_ik(r[2][s], -kyv);
+      if (rk.dealias) {
+        const int my = row <= (G.Ny >> 1) ? row : G.Ny - row;
+        if (!keepx || 3 * my > G.Ny) {
+          k0 = mk((T)0, (T)0);
+          k1 = k0;
+          k2 = k0;
+        }
+      }
+      cpx<T> kk[3] = {k0, k1, k2};
+      if (rk.mode == RK_STORE_K) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) K[f][e] = kk[f];
+        continue;
+      }
+      cpx<T> u[3];
+      if (rk.mode == RK_FINAL) {
+        const T c6 = (T)(rk.dt / 6.0);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          cpx<T> z = Un[f][e] + scl(acc[f][e] + kk[f], c6);
+          if (rk.krasny && (double)z.x * z.x + (double)z.y * z.y < thr2) z = mk((T)0, (T)0);
+          Un[f][e] = z;
+          u[f] = z;
+        }
+      } else {
+        const T cdt = (T)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          acc[f][e] = (rk.mode == RK_STAGE1) ? kk[f] : acc[f][e] + scl(kk[f], (T)2);
+          u[f] = Un[f][e] + scl(kk[f], cdt);
+          Unext[f][e] = u[f];
+        }
+      }
+      if (b) b[e] = mul_ik(u[1], -kxv) - mul_ik(u[2], kyv);
+    }
+  }
+};
+
+// ------------------------------------------------------------ launchers
+
+template <typename T>
+static inline int x_pairs_per_block(const Geom& G) {
+  int Tn = G.Nx >> 3;
+  int P = Tn >= 256 ? 1 : 256 / Tn;
+  int half = G.Ny >> 1;
+  if (P > half) P = half;
+  return P;
+}
+template <typename T>
+static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int nf) {
+  const int P = x_pairs_per_block<T>(G);
+  block = dim3((G.Nx >> 3) * P);
+  grid = dim3((G.Ny / 2 + P - 1) / P, nf);
+  smem = (size_t)P * smem_elems(G.Nx) * sizeof(cpx<T>);
+}
+template <typename T>
+static inline void y_config(const Geom& G, int nin, dim3& grid, dim3& block, size_t& smem) {
+  const int Tn = G.Ny >> 3;
+  const int tpb = ypass_threads(nin);
+  int C = tpb / Tn;
+  if (C < 1) C = 1;
+  if (C > 64) C = 64;
+  block = dim3(Tn * C);
+  grid = dim3((G.Nxh + C - 1) / C);
+  smem = (size_t)C * smem_elems(G.Ny) * sizeof(cpx<T>);
+}
+
+static constexpr int kMaxDynSmem = 160 * 1024;
+
+template <typename T>
+static void set_smem(const void* fn) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+template <typename T>
+void init_kernel_attributes() {
+  set_smem<T>((const void*)k_x_r2c<T>);
+  set_smem<T>((const void*)k_x_c2r<T>);
+  set_smem<T>((const void*)k_coef_x<T>);
+  set_smem<T>((const void*)k_mv_x<T>);
+  set_smem<T>((const void*)k_rhs_x<T>);
+  set_smem<T>((const void*)k_ypass<T, false, 1, EpiStore<T, 1>>);
+  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>>);
+  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>>);
+  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>>);
+  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>>);
+  set_smem<T>((const void*)k_ypass<T, false, 3, EpiRHS<T>>);
+  cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_x_r2c(const Geom& G, const Tables<T>& tb, const double* const* f, int nf,
+                         cpx<T>* const* out, const Exec& ex) {
+  XR2CArgs<T> a{};
+  for (int i = 0; i < nf; ++i) {
+    a.f[i] = f[i];
+    a.out[i] = out[i];
+  }
+  dim3 grid, block;
+  size_t smem;
+  x_config<T>(G, grid, block, smem, nf);
+  ex.begin(PK_IO);
+  k_x_r2c<T><<<grid, block, smem, ex.s>>>(G, tb.twx, a);
+  ex.end();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_x_c2r(const Geom& G, const Tables<T>& tb, const cpx<T>* const* in, const int* deriv,
+                         int nf, double* const* out, double scale, const Exec& ex) {
+  XC2RArgs<T> a{};
+  for (int i = 0; i < nf; ++i) {
+    a.in[i] = in[i];
+    a.out[i] = out[i];
+    a.deriv[i] = deriv ? deriv[i] : 0;
+  }
+  dim3 grid, block;
+  size_t smem;
+  x_config<T>(G, grid, block, smem, nf);
+  ex.begin(PK_IO);
+  k_x_c2r<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, a, scale);
+  ex.end();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const cpx<T>* const* in,
+                         const int* deriv, int nf, cpx<T>* const* out, const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  y_config<T>(G, 1, grid, block, smem);
+  for (int i = 0; i < nf; ++i) {
+    YIn<T, 1> yi{};
+    yi.src[0] = in[i];
+    yi.deriv[0] = deriv ? deriv[i] : 0;
+    EpiStore<T, 1> ep{};
+    ep.dst[0] = out[i];
+    if (inverse) {
+      ex.begin(PK_IO);
+      k_ypass<T, true, 1, EpiStore<T, 1>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      ex.end();
+    }
+    else {
+      ex.begin(PK_IO);
+      k_ypass<T, false, 1, EpiStore<T, 1>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      ex.end();
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coef_x(const Geom& G, const Tables<T>& tb, const cpx<T>* Hy, T* h, T* cr, T* cc, int* flags,
+                          const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  x_config<T>(G, grid, block, smem, 1);
+  ex.begin(PK_COEF);
+  k_coef_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, Hy, h, cr, cc, flags);
+  ex.end();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T* cc, int* flags,
+                             const Exec& ex) {
+  ex.begin(PK_COEF);
+  k_coef_phys<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, hphys, h, cr, cc, flags);
+  ex.end();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
+                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  // y-inverse of sigma_hat and i ky sigma_hat
+  {
+    y_config<T>(G, 2, grid, block, smem);
+    YIn<T, 2> yi{};
+    yi.src[0] = sig;
+    yi.src[1] = sig;
+    yi.deriv[0] = 0;
+    yi.deriv[1] = 1;
+    EpiStore<T, 2> ep{};
+    ep.dst[0] = tmp[0];
+    ep.dst[1] = tmp[1];
+    ex.begin(PK_MV_YINV);
+    k_ypass<T, true, 2, EpiStore<T, 2>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  }
+  {
+    x_config<T>(G, grid, block, smem, 1);
+    ex.begin(PK_MV_X);
+    k_mv_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
+    ex.end();
+  }
+  {
+    y_config<T>(G, 2, grid, block, smem);
+    YIn<T, 2> yi{};
+    yi.src[0] = tmp[0];
+    yi.src[1] = tmp[1];
+    EpiMatvec<T> ep{w, tb.kx, precond ? 1 : 0};
+    ex.begin(PK_MV_YFWD);
+    k_ypass<T, false, 2, EpiMatvec<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, const cpx<T>* sig, const T* h,
+                       const T* cr, cpx<T>* const* tmp, cpx<T>* const* Un, cpx<T>* const* Unext,
+                       cpx<T>* const* acc, cpx<T>* bhat, const RkArgs& rk, const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  {
+    y_config<T>(G, 4, grid, block, smem);
+    YIn<T, 4> yi{};
+    yi.src[0] = U[1];
+    yi.src[1] = U[2];
+    yi.src[2] = sig;
+    yi.src[3] = sig;
+    yi.deriv[3] = 1;
+    EpiStore<T, 4> ep{};
+    for (int i = 0; i < 4; ++i) ep.dst[i] = tmp[i];
+    ex.begin(PK_RHS_YINV);
+    k_ypass<T, true, 4, EpiStore<T, 4>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  }
+  {
+    // each block reads only its own row pair before writing it, so the
+    // outputs may overwrite the inputs
+    x_config<T>(G, grid, block, smem, 1);
+    ex.begin(PK_RHS_X);
+    k_rhs_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], tmp[2], tmp[3], h, cr, (T)rk.g,
+                                         tmp[0], tmp[1], tmp[2]);
+    ex.end();
+  }
+  {
+    y_config<T>(G, 3, grid, block, smem);
+    YIn<T, 3> yi{};
+    yi.src[0] = tmp[0];
+    yi.src[1] = tmp[1];
+    yi.src[2] = tmp[2];
+    EpiRHS<T> ep{};
+    for (int f = 0; f < 3; ++f) {
+      ep.K[f] = acc[f];
+      ep.Un[f] = Un[f];
+      ep.Unext[f] = Unext ? Unext[f] : nullptr;
+      ep.acc[f] = acc[f];
+    }
+    ep.b = bhat;
+    ep.kx = tb.kx;
+    ep.rk = rk;
+    ex.begin(PK_RHS_YFWD);
+    k_ypass<T, false, 3, EpiRHS<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ spectral pointwise kernels
+
+template <typename T>
+__global__ void k_spec_div(Geom G, const T* __restrict__ kx, const T* __restrict__ ky, const cpx<T>* vx,
+                           const cpx<T>* vy, cpx<T>* b) {
+  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
+    const T kyv = __ldg(ky + row);
+    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
+      const size_t e = (size_t)row * G.ldS + col;
+      b[e] = mul_ik(vx[e], -__ldg(kx + col)) - mul_ik(vy[e], kyv);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_spec_div(const Geom& G, const Tables<T>& tb, const cpx<T>* vx, const cpx<T>* vy, cpx<T>* b,
+                            const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_spec_div<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, tb.kx, tb.ky, vx, vy, b);
+  ex.end();
+  return cudaGetLastError();
+}
+
+// Parseval weight of a half-spectrum column: kx = 0 and kx = Nx/2 count once.
+__device__ __forceinline__ double col_weight(const Geom& G, int col) {
+  return (col == 0 || col == (G.Nx >> 1)) ? 1.0 : 2.0;
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+  return tot;
+}
+
+template <typename T>
+__global__ void k_precond(Geom G, const T* __restrict__ kx, const T* __restrict__ ky, const cpx<T>* in,
+                          cpx<T>* out, double* partials) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
+    const T kyv = __ldg(ky + row);
+    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
+      const size_t e = (size_t)row * G.ldS + col;
+      const T kxv = __ldg(kx + col);
+      const cpx<T> z = scl(in[e], (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+      out[e] = z;
+      acc += col_weight(G, col) * ((double)z.x * z.x + (double)z.y * z.y);
+    }
+  }
+  const double tot = block_sum<T>(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+template <typename T>
+cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<T>* out, double* partials,
+                           const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_precond<T><<<RED_BLOCKS, 256, 0, ex.s>>>(G, tb.kx, tb.ky, in, out, partials);
+  ex.end();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- instantiations
+#define SGN_INST(T)                                                                                          \
+  template void init_kernel_attributes<T>();                                                                 \
+  template cudaError_t launch_x_r2c<T>(const Geom&, const Tables<T>&, const double* const*, int,             \
+                                       cpx<T>* const*, const Exec&);                                        \
+  template cudaError_t launch_x_c2r<T>(const Geom&, const Tables<T>&, const cpx<T>* const*, const int*, int, \
+                                       double* const*, double, const Exec&);                                \
+  template cudaError_t launch_y_fft<T>(const Geom&, const Tables<T>&, bool, const cpx<T>* const*,            \
+                                       const int*, int, cpx<T>* const*, const Exec&);                       \
+  template cudaError_t launch_coef_x<T>(const Geom&, const Tables<T>&, const cpx<T>*, T*, T*, T*, int*,      \
+                                        const Exec&);                                                       \
+  template cudaError_t launch_coef_phys<T>(const Geom&, const double*, T*, T*, T*, int*, const Exec&);      \
+  template cudaError_t launch_matvec<T>(const Geom&, const Tables<T>&, const cpx<T>*, const T*, const T*,    \
+                                        cpx<T>*, cpx<T>* const*, bool, const Exec&);                        \
+  template cudaError_t launch_rhs<T>(const Geom&, const Tables<T>&, cpx<T>* const*, const cpx<T>*,          \
+                                     const T*, const T*, cpx<T>* const*, cpx<T>* const*, cpx<T>* const*,    \
+                                     cpx<T>* const*, cpx<T>*, const RkArgs&, const Exec&);                  \
+  template cudaError_t launch_spec_div<T>(const Geom&, const Tables<T>&, const cpx<T>*, const cpx<T>*,      \
+                                          cpx<T>*, const Exec&);                                            \
+  template cudaError_t launch_precond<T>(const Geom&, const Tables<T>&, const cpx<T>*, cpx<T>*, double*,    \
+                                         const Exec&);
+
+SGN_INST(double)
+
+}  // namespace sgn

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libsgn.so (include/sgn.h): argument marshalling only.
+
+Functions keep the C names (``sgn_create``, ``sgn_rhs``, ...). Field arguments
+are CUDA tensors (float64, contiguous, shape (Ny, Nx)) or raw integer device
+pointers; every computation runs in the library's CUDA kernels. The library is
+loaded on first use and a missing or unloadable library raises: there is no
+CPU fallback.
+
+``Solver`` wraps a handle for convenient use from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SGN_OK, SGN_EINVAL, SGN_ENOTCONV, SGN_ECAVITATION, SGN_ENONFINITE, SGN_ECUDA, SGN_ENOMEM = range(7)
+STATUS_NAMES = {0: "SGN_OK", 1: "SGN_EINVAL", 2: "SGN_ENOTCONV", 3: "SGN_ECAVITATION",
+                4: "SGN_ENONFINITE", 5: "SGN_ECUDA", 6: "SGN_ENOMEM"}
+
+# every symbol include/sgn.h declares
+EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
+           "sgn_spectral_derivative", "sgn_fft2_r2c", "sgn_fft2_c2r", "sgn_elliptic_apply",
+           "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
+           "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_last_error"]
+
+PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io"]
+
+
+class SGNError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sgn_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("tol", ctypes.c_double), ("krasny", ctypes.c_int), ("krasny_thr", ctypes.c_double),
+                ("dealias", ctypes.c_int), ("guess", ctypes.c_int)]
+
+
+class sgn_stats(ctypes.Structure):
+    _fields_ = [("matvecs", ctypes.c_longlong), ("solves", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("last_relres", ctypes.c_double), ("last_iters", ctypes.c_int)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def load_library(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libsgn.so (building it in-tree first if it is absent or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if path is None:
+        path = _build.lib_path()
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsgn.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "sgn_default_options": (None, [ctypes.POINTER(sgn_options)]),
+        "sgn_create": (_I, [_I, _I, _D, _D, _D, ctypes.POINTER(sgn_options), ctypes.POINTER(_P)]),
+        "sgn_destroy": (_I, [_P]),
+        "sgn_set_stream": (_I, [_P, _P]),
+        "sgn_spectral_derivative": (_I, [_P, _P, _P, _P]),
+        "sgn_fft2_r2c": (_I, [_P, _P, _P]),
+        "sgn_fft2_c2r": (_I, [_P, _P, _P]),
+        "sgn_elliptic_apply": (_I, [_P, _P, _P, _P]),
+        "sgn_gmres_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+        "sgn_rhs": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+        "sgn_rk4_step": (_I, [_P, _P, _P, _P, _P, _D, _I]),
+        "sgn_rk4_step_host": (_I, [_P, _P, _P, _P, _P, _D, _I]),
+        "sgn_invariants": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
+        "sgn_get_stats": (_I, [_P, ctypes.POINTER(sgn_stats)]),
+        "sgn_set_profiling": (_I, [_P, _I]),
+        "sgn_get_profile": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I,
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+        "sgn_last_error": (ctypes.c_char_p, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_cuda or x.dtype.itemsize != 8 or not x.is_contiguous():
+            raise ValueError("expected a contiguous CUDA float64 tensor")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy array (host variants only)
+        if x.dtype.itemsize != 8 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(handle, status):
+    if status != SGN_OK:
+        msg = load_library().sgn_last_error(handle)
+        raise SGNError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ C-named calls
+
+def sgn_default_options() -> sgn_options:
+    o = sgn_options()
+    load_library().sgn_default_options(ctypes.byref(o))
+    return o
+
+
+def sgn_create(Nx, Ny, Lx, Ly, g=1.0, opt: sgn_options | None = None):
+    h = _P()
+    st = load_library().sgn_create(int(Nx), int(Ny), float(Lx), float(Ly), float(g),
+                                   ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def sgn_destroy(handle):
+    _check(handle, load_library().sgn_destroy(handle))
+
+
+def sgn_set_stream(handle, stream):
+    _check(handle, load_library().sgn_set_stream(handle, int(stream) if stream else None))
+
+
+def sgn_spectral_derivative(handle, f, fx, fy):
+    _check(handle, load_library().sgn_spectral_derivative(handle, _ptr(f), _ptr(fx), _ptr(fy)))
+
+
+def sgn_fft2_r2c(handle, f, fhat):
+    _check(handle, load_library().sgn_fft2_r2c(handle, _ptr(f), _ptr(fhat)))
+
+
+def sgn_fft2_c2r(handle, fhat, f):
+    _check(handle, load_library().sgn_fft2_c2r(handle, _ptr(fhat), _ptr(f)))
+
+
+def sgn_elliptic_apply(handle, h, sigma, out):
+    _check(handle, load_library().sgn_elliptic_apply(handle, _ptr(h), _ptr(sigma), _ptr(out)))
+
+
+def sgn_gmres_solve(handle, h, b, sigma):
+    it = _I(0)
+    rr = _D(0.0)
+    st = load_library().sgn_gmres_solve(handle, _ptr(h), _ptr(b), _ptr(sigma), ctypes.byref(it),
+                                        ctypes.byref(rr))
+    if st not in (SGN_OK, SGN_ENOTCONV):
+        _check(handle, st)
+    return st, it.value, rr.value
+
+
+def sgn_rhs(handle, h, vx, vy, sigma, ht, vxt, vyt):
+    _check(handle, load_library().sgn_rhs(handle, _ptr(h), _ptr(vx), _ptr(vy), _ptr(sigma), _ptr(ht),
+                                          _ptr(vxt), _ptr(vyt)))
+
+
+def sgn_rk4_step(handle, h, vx, vy, sigma, dt, nsteps=1):
+    _check(handle, load_library().sgn_rk4_step(handle, _ptr(h), _ptr(vx), _ptr(vy), _ptr(sigma),
+                                               float(dt), int(nsteps)))
+
+
+def sgn_rk4_step_host(handle, h, vx, vy, sigma, dt, nsteps=1):
+    _check(handle, load_library().sgn_rk4_step_host(handle, _ptr(h), _ptr(vx), _ptr(vy), _ptr(sigma),
+                                                    float(dt), int(nsteps)))
+
+
+def sgn_invariants(handle, h, vx, vy, sigma):
+    out = (_D * 4)()
+    _check(handle, load_library().sgn_invariants(handle, _ptr(h), _ptr(vx), _ptr(vy), _ptr(sigma), out))
+    return [out[i] for i in range(4)]
+
+
+def sgn_get_stats(handle) -> dict:
+    s = sgn_stats()
+    _check(handle, load_library().sgn_get_stats(handle, ctypes.byref(s)))
+    return dict(matvecs=s.matvecs, solves=s.solves, max_iters=s.max_iters,
+                last_relres=s.last_relres, last_iters=s.last_iters)
+
+
+def sgn_set_profiling(handle, on: bool):
+    _check(handle, load_library().sgn_set_profiling(handle, 1 if on else 0))
+
+
+def sgn_get_profile(handle) -> dict:
+    n = len(PROFILE_CLASSES)
+    ms = (_D * n)()
+    cnt = (ctypes.c_longlong * n)()
+    launches = ctypes.c_longlong(0)
+    _check(handle, load_library().sgn_get_profile(handle, ms, cnt, n, ctypes.byref(launches)))
+    return dict(ms={k: ms[i] for i, k in enumerate(PROFILE_CLASSES)},
+                counts={k: cnt[i] for i, k in enumerate(PROFILE_CLASSES)}, launches=launches.value)
+
+
+def sgn_last_error(handle) -> str:
+    m = load_library().sgn_last_error(handle)
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------------ wrapper
+
+class Solver:
+    """One grid + options; methods take and return CUDA float64 tensors (Ny, Nx)."""
+
+    def __init__(self, Nx, Ny, Lx, Ly, g=1.0, **opts):
+        import torch
+        o = sgn_default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.Nx, self.Ny, self.Lx, self.Ly, self.g = Nx, Ny, Lx, Ly, g
+        self.options = o
+        self.handle = sgn_create(Nx, Ny, Lx, Ly, g, o)
+        self._torch = torch
+        sgn_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    def close(self):
+        if self.handle:
+            sgn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _new(self):
+        return self._torch.empty((self.Ny, self.Nx), dtype=self._torch.float64, device="cuda")
+
+    def set_stream(self, stream):
+        sgn_set_stream(self.handle, stream.cuda_stream)
+
+    def derivative(self, f):
+        fx, fy = self._new(), self._new()
+        sgn_spectral_derivative(self.handle, f, fx, fy)
+        return fx, fy
+
+    def fft2(self, f):
+        out = self._torch.empty((self.Ny, self.Nx // 2 + 1), dtype=self._torch.complex128, device="cuda")
+        _check(self.handle, load_library().sgn_fft2_r2c(self.handle, _ptr(f), out.data_ptr()))
+        return out
+
+    def ifft2(self, fhat):
+        f = self._new()
+        _check(self.handle, load_library().sgn_fft2_c2r(self.handle, fhat.contiguous().data_ptr(), _ptr(f)))
+        return f
+
+    def elliptic_apply(self, h, sigma):
+        out = self._new()
+        sgn_elliptic_apply(self.handle, h, sigma, out)
+        return out
+
+    def gmres_solve(self, h, b, sigma0=None):
+        sigma = self._torch.zeros_like(b) if sigma0 is None else sigma0.clone()
+        st, its, rr = sgn_gmres_solve(self.handle, h, b, sigma)
+        return sigma, its, rr, st == SGN_OK
+
+    def rhs(self, h, vx, vy, sigma):
+        ht, vxt, vyt = self._new(), self._new(), self._new()
+        sgn_rhs(self.handle, h, vx, vy, sigma, ht, vxt, vyt)
+        return ht, vxt, vyt
+
+    def rk4_step(self, h, vx, vy, sigma, dt, nsteps=1):
+        sgn_rk4_step(self.handle, h, vx, vy, sigma, dt, nsteps)
+
+    def invariants(self, h, vx, vy, sigma):
+        return sgn_invariants(self.handle, h, vx, vy, sigma)
+
+    def stats(self):
+        return sgn_get_stats(self.handle)
+
+    def set_profiling(self, on=True):
+        sgn_set_profiling(self.handle, on)
+
+    def profile(self):
+        return sgn_get_profile(self.handle)

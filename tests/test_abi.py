@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/sgn.h declares.
+
+These tests run without a GPU: they make no compute call, only argument
+validation that the library performs before touching the device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_09731_gb300 import build as B
+from paper_2306_09731_gb300 import sgn as S
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sgn.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgn_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load_library()
+
+
+def test_header_and_binding_agree():
+    assert declared_symbols() == sorted(S.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_default_options(lib):
+    o = S.sgn_default_options()
+    assert (o.precision, o.restart, o.maxit, o.tol, o.krasny, o.krasny_thr, o.dealias, o.guess) == \
+        (0, 20, 1000, 1e-10, 0, 1e-12, 0, 0)
+
+
+@pytest.mark.parametrize("Nx,Ny", [(12, 16), (16, 4), (4096, 16), (0, 8), (16, -8)])
+def test_create_rejects_bad_sizes(lib, Nx, Ny):
+    h = ctypes.c_void_p()
+    st = lib.sgn_create(Nx, Ny, 1.0, 1.0, 1.0, None, ctypes.byref(h))
+    assert st == S.SGN_EINVAL and not h.value
+    assert b"power" in lib.sgn_last_error(None)
+
+
+def test_create_rejects_bad_options(lib):
+    o = S.sgn_default_options()
+    o.restart = 0
+    h = ctypes.c_void_p()
+    assert lib.sgn_create(16, 16, 1.0, 1.0, 1.0, ctypes.byref(o), ctypes.byref(h)) == S.SGN_EINVAL
+    o = S.sgn_default_options()
+    o.precision = 7
+    assert lib.sgn_create(16, 16, 1.0, 1.0, 1.0, ctypes.byref(o), ctypes.byref(h)) == S.SGN_EINVAL
+    assert lib.sgn_create(16, 16, -1.0, 1.0, 1.0, None, ctypes.byref(h)) == S.SGN_EINVAL
+
+
+def test_null_handle_is_einval(lib):
+    assert lib.sgn_rk4_step(None, None, None, None, None, 1e-3, 1) == S.SGN_EINVAL
+    assert lib.sgn_destroy(None) == S.SGN_EINVAL

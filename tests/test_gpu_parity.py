@@ -1,0 +1,275 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar (FP64 path): relative L2 <= 1e-10 per field against the oracle on the same
+seeded inputs, GMRES run to 1e-13 on both sides where the two solvers' stopping
+points would otherwise differ by up to kappa * tol. Transforms and the operator
+are compared at 1e-12 (pure rounding).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2306_09731_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09731_gb300 import sgn
+    sgn.load_library()
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def solver(Nx, Ny, Lx, Ly, **kw):
+    from paper_2306_09731_gb300.sgn import Solver
+    return Solver(Nx, Ny, Lx, Ly, **kw)
+
+
+# grids: tiny, ragged aspect ratios, the line-soliton grid, and the largest size
+GRIDS = [(8, 8, 1.0, 1.0), (16, 8, 3.0, 2.0), (8, 64, 1.0, 7.0), (32, 64, 5.0, 9.0),
+         (256, 16, 80.0, 10.0), (128, 128, 10.0, 10.0), (2048, 16, 100.0, 5.0), (16, 2048, 5.0, 100.0)]
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS)
+def test_fft2_matches_dft(Nx, Ny, Lx, Ly):
+    f = np.random.default_rng(Nx * 7 + Ny).standard_normal((Ny, Nx))
+    s = solver(Nx, Ny, Lx, Ly)
+    F = s.fft2(dev(f)).cpu().numpy()
+    ref = np.fft.rfft2(f)
+    assert rel(F, ref) < 1e-13
+    back = host(s.ifft2(torch.tensor(F, device="cuda")))
+    assert rel(back, f) < 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS)
+def test_derivative_parity(Nx, Ny, Lx, Ly):
+    f = np.random.default_rng(Nx + 3 * Ny).standard_normal((Ny, Nx))
+    s = solver(Nx, Ny, Lx, Ly)
+    fx, fy = s.derivative(dev(f))
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    assert rel(host(fx), O.dx(G, f)) < 1e-12
+    assert rel(host(fy), O.dy(G, f)) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS)
+def test_elliptic_apply_parity(Nx, Ny, Lx, Ly):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + Ny)
+    s = solver(Nx, Ny, Lx, Ly)
+    out = host(s.elliptic_apply(dev(st.h), dev(st.sigma)))
+    ref = O.elliptic_apply(O.Grid(Nx, Ny, Lx, Ly), st.h, st.sigma)
+    assert rel(out, ref) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS[:6])
+def test_gmres_parity(Nx, Ny, Lx, Ly):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=2 * Nx + Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    b = O.divergence_rhs(G, st.vx, st.vy)
+    s = solver(Nx, Ny, Lx, Ly, tol=1e-13, restart=20)
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), dev(b), dev(np.zeros_like(b)))
+    ref, rits, rrr, rconv = O.gmres(G, st.h, b, np.zeros_like(b), tol=1e-13)
+    assert conv and rconv and rr <= 1e-13
+    assert rel(host(sig), ref) < 1e-10
+    assert abs(its - rits) <= 2
+    s.close()
+
+
+def test_gmres_soliton_closed_form():
+    st = I.soliton_256x16()
+    G = O.Grid(st.Nx, st.Ny, st.Lx, st.Ly)
+    b = O.divergence_rhs(G, st.vx, st.vy)
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly, tol=1e-13)
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), dev(b), dev(np.zeros_like(b)))
+    assert conv
+    assert rel(host(sig), st.sigma) < 1e-9  # Eq. (sol): sigma = m (h^2)'/6
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS[:6])
+@pytest.mark.parametrize("dealias", [0, 1])
+def test_rhs_parity(Nx, Ny, Lx, Ly, dealias):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 5 * Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    s = solver(Nx, Ny, Lx, Ly, tol=1e-13, dealias=dealias)
+    sg = dev(st.sigma)
+    ht, vxt, vyt = s.rhs(dev(st.h), dev(st.vx), dev(st.vy), sg)
+    rht, rvxt, rvyt, rsg, info = O.rhs(G, st.h, st.vx, st.vy, st.sigma, tol=1e-13, dealias=bool(dealias))
+    assert rel(host(ht), rht) < 1e-10
+    assert rel(host(vxt), rvxt) < 1e-10
+    assert rel(host(vyt), rvyt) < 1e-10
+    assert rel(host(sg), rsg) < 1e-10
+    s.close()
+
+
+def test_rhs_soliton_travelling_wave():
+    st = I.soliton_256x16()
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly, tol=1e-13)
+    ht, vxt, vyt = s.rhs(dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma))
+    f, c = st.meta["fields"], st.meta["c"]
+    ones = np.ones((st.Ny, 1))
+    assert rel(host(ht), ones * (-c * f["h_xi"])) < 1e-8
+    assert rel(host(vxt), ones * (-c * f["v_xi"])) < 1e-8
+    assert np.abs(host(vyt)).max() < 1e-12
+    s.close()
+
+
+def test_rk4_parity_soliton_and_exact():
+    st = I.soliton_256x16()
+    G = O.Grid(st.Nx, st.Ny, st.Lx, st.Ly)
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly)
+    h, vx, vy, sg = dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)
+    s.rk4_step(h, vx, vy, sg, 5e-3, 10)
+    oh, ovx, ovy, osg = O.rk4_step(G, st.h, st.vx, st.vy, st.sigma, 5e-3, 10)
+    assert rel(host(h), oh) < 1e-10
+    assert rel(host(vx), ovx) < 1e-10
+    assert np.abs(host(vy)).max() < 1e-12
+    # continue to t = 0.5 (100 steps in total) and compare with the exact soliton
+    s.rk4_step(h, vx, vy, sg, 5e-3, 90)
+    ex = I.soliton_256x16(t=0.5)
+    assert rel(host(h), ex.h) < 1e-8
+    assert rel(host(vx), ex.vx) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,L,krasny", [(32, 32, 6.0, 0), (64, 16, 8.0, 1), (16, 64, 4.0, 0)])
+def test_rk4_parity_random(Nx, Ny, L, krasny):
+    st = I.random_state(Nx, Ny, L, L, seed=Nx * Ny)
+    G = O.Grid(Nx, Ny, L, L)
+    phi = I.random_smooth(Nx, Ny, L, L, seed=17, kmax=4)
+    vx, vy = O.dx(G, phi), O.dy(G, phi)
+    s = solver(Nx, Ny, L, L, tol=1e-13, krasny=krasny)
+    h_, vx_, vy_, sg_ = dev(st.h), dev(vx), dev(vy), dev(np.zeros_like(vx))
+    s.rk4_step(h_, vx_, vy_, sg_, 2e-3, 5)
+    oh, ovx, ovy, osg = O.rk4_step(G, st.h, vx, vy, np.zeros_like(vx), 2e-3, 5, tol=1e-13,
+                                   krasny_on=bool(krasny))
+    assert rel(host(h_), oh) < 1e-10
+    assert rel(host(vx_), ovx) < 1e-10
+    assert rel(host(vy_), ovy) < 1e-10
+    assert rel(host(sg_), osg) < 1e-10
+    s.close()
+
+
+def test_krasny_zeroes_small_coefficients():
+    st = I.soliton_256x16()
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly, krasny=1, krasny_thr=1e-12)
+    h = dev(st.h)
+    vx, vy, sg = dev(st.vx), dev(st.vy), dev(st.sigma)
+    s.rk4_step(h, vx, vy, sg, 5e-3, 3)
+    F = np.abs(s.fft2(h).cpu().numpy()) / (st.Nx * st.Ny)
+    # every surviving coefficient is either above the threshold or rounding noise of a zero
+    assert np.all((F >= 1e-12 * (1 - 1e-6)) | (F < 1e-15))
+    assert np.count_nonzero(F < 1e-15) > 0
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS[:6])
+def test_invariants_parity(Nx, Ny, Lx, Ly):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=3 * Nx + Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    s = solver(Nx, Ny, Lx, Ly)
+    inv = np.array(s.invariants(dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)))
+    ref = O.invariants(G, st.h, st.vx, st.vy, st.sigma)
+    scale = np.abs(ref).max()
+    assert np.abs(inv - ref).max() < 1e-12 * scale
+    s.close()
+
+
+def test_cavitation_reported_and_context_survives():
+    from paper_2306_09731_gb300.sgn import SGNError, SGN_ECAVITATION, SGN_ENONFINITE
+    st = I.random_state(32, 32, 6.0, 6.0, seed=1)
+    s = solver(32, 32, 6.0, 6.0)
+    bad = st.h.copy()
+    bad[3, 5] = -0.1
+    with pytest.raises(SGNError) as e:
+        s.elliptic_apply(dev(bad), dev(st.sigma))
+    assert e.value.status == SGN_ECAVITATION
+    nan = st.h.copy()
+    nan[0, 0] = np.nan
+    with pytest.raises(SGNError) as e:
+        s.rk4_step(dev(nan), dev(st.vx), dev(st.vy), dev(st.sigma), 1e-3, 1)
+    assert e.value.status == SGN_ENONFINITE
+    out = host(s.elliptic_apply(dev(st.h), dev(st.sigma)))
+    assert rel(out, O.elliptic_apply(O.Grid(32, 32, 6.0, 6.0), st.h, st.sigma)) < 1e-12
+    s.close()
+
+
+def test_gmres_maxit_and_zero_rhs():
+    from paper_2306_09731_gb300.sgn import SGN_ENOTCONV
+    st = I.random_state(32, 16, 6.0, 3.0, seed=4)
+    G = O.Grid(32, 16, 6.0, 3.0)
+    b = O.divergence_rhs(G, st.vx, st.vy)
+    s = solver(32, 16, 6.0, 3.0, tol=1e-15, maxit=3, restart=2)
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), dev(b))
+    assert not conv and its == 3
+    ref, rits, rrr, rconv = O.gmres(G, st.h, b, np.zeros_like(b), tol=1e-15, restart=2, maxit=3)
+    assert not rconv and rits == 3
+    assert abs(rr - rrr) < 1e-8 * max(rrr, 1e-30)
+    z = dev(np.zeros_like(b))
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), z, dev(np.ones_like(b)))
+    assert conv and its == 0 and float(sig.abs().max()) == 0.0
+    s.close()
+
+
+def test_rk4_step_host_matches_device():
+    st = I.soliton_256x16()
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly)
+    from paper_2306_09731_gb300.sgn import sgn_rk4_step_host
+    hh = [np.ascontiguousarray(a.copy()) for a in (st.h, st.vx, st.vy, st.sigma)]
+    sgn_rk4_step_host(s.handle, *hh, 5e-3, 3)
+    d = [dev(a) for a in (st.h, st.vx, st.vy, st.sigma)]
+    s.rk4_step(*d, 5e-3, 3)
+    for a, b in zip(hh, d):
+        assert np.array_equal(a, host(b))
+    s.close()
+
+
+def test_full_size_gaussian_2048():
+    """The 2048^2 Gaussian-hump workload in the launch configuration the benchmark uses.
+
+    Elliptic operator element by element against the oracle; one RK4 step
+    checked by properties that hold at any size: the x <-> y mirror symmetry of
+    the radial data, x -> -x reflection, and mass conservation to roundoff.
+    """
+    st = I.gaussian_hump(2048, 100.0, 0.5)
+    N, L = 2048, 100.0
+    G = O.Grid(N, N, L, L)
+    s = solver(N, N, L, L)
+    sig = I.random_smooth(N, N, L, L, seed=5, kmax=3)
+    out = host(s.elliptic_apply(dev(st.h), dev(sig)))
+    assert rel(out, O.elliptic_apply(G, st.h, sig)) < 1e-12
+    h, vx, vy, sg = dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)
+    m0 = s.invariants(h, vx, vy, sg)
+    s.rk4_step(h, vx, vy, sg, 1e-3, 2)
+    H, VX, VY = host(h), host(vx), host(vy)
+    assert np.abs(H - H.T).max() < 1e-12
+    assert np.abs(VX - VY.T).max() < 1e-12
+    # x -> -x about x = 0 (grid index j -> N - j): h even, vx odd
+    Hr = np.roll(H[:, ::-1], 1, axis=1)
+    assert np.abs(H - Hr).max() < 1e-12
+    m1 = s.invariants(h, vx, vy, sg)
+    assert abs(m1[0] - m0[0]) < 1e-12 * abs(m0[0])
+    st2 = s.stats()
+    assert st2["solves"] > 0
+    s.close()
