@@ -269,7 +269,9 @@ def test_full_size_gaussian_2048():
     Hr = np.roll(H[:, ::-1], 1, axis=1)
     assert np.abs(H - Hr).max() < 1e-12
     m1 = s.invariants(h, vx, vy, sg)
-    assert abs(m1[0] - m0[0]) < 1e-12 * abs(m0[0])
+    # the mean depth 1 sits in the DC coefficient (sum h ~ 4e6, ulp ~ 1e-9), so
+    # roundoff of the mass is relative to the total volume L^2, not to the anomaly
+    assert abs(m1[0] - m0[0]) < 1e-14 * L * L
     st2 = s.stats()
     assert st2["solves"] > 0
     s.close()
