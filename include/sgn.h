@@ -149,6 +149,34 @@ sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out);
 sgn_status sgn_set_profiling(sgn_t ctx, int on);
 sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long long* launches);
 
+/* Allocation-free L[sigma]. The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, e.g. a host application whose
+ * own pool or caching allocator already holds the GPU's memory budget, a
+ * plugin that must not allocate behind its framework's back, or a
+ * latency-sensitive loop that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree.
+ * Computes out = L[sigma] exactly as sgn_elliptic_apply does (same kernels,
+ * device field pointers in the same layout), without a handle: every
+ * intermediate lives in one static device array sized for
+ * SGN_NOALLOC_MAX_POINTS grid points (about 4 MB), held on every GPU that
+ * loads the library until the process exits. The call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).
+ *  - Nx*Ny > SGN_NOALLOC_MAX_POINTS, or a size sgn_create would refuse, returns
+ *    SGN_EINVAL with a message in sgn_last_error(NULL); so do NULL pointers.
+ *  - The first call on a device sets up (looks up the static array's device
+ *    address with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call uses the same array and leaves its contents behind: calls
+ *    that overlap on the GPU (other streams, other host threads) race. Calls
+ *    on one stream, one after another, are safe.
+ *  - Enqueued on cuda_stream (a cudaStream_t, NULL for the legacy default
+ *    stream); the call synchronises that stream before returning its status
+ *    (SGN_ECAVITATION / SGN_ENONFINITE as in sgn_elliptic_apply). */
+#define SGN_NOALLOC_MAX_POINTS 65536
+sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly,
+                                      const double* h, const double* sigma, double* out,
+                                      void* cuda_stream);
+
 /* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
 const char* sgn_last_error(sgn_t ctx);
 

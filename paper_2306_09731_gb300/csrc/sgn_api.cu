@@ -57,7 +57,7 @@ struct sgn_ctx {
   sgn_stats stats{};
 };
 
-static std::string g_create_error;
+std::string g_create_error;  // also written by sgn_elliptic_apply_noalloc
 
 namespace {
 

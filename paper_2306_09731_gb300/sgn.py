@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "SGN_OK", 1: "SGN_EINVAL", 2: "SGN_ENOTCONV", 3: "SGN_ECAVITA
 EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_spectral_derivative", "sgn_fft2_r2c", "sgn_fft2_c2r", "sgn_elliptic_apply",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
-           "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_last_error"]
+           "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
+           "sgn_last_error"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io"]
 
@@ -81,6 +82,7 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         "sgn_set_profiling": (_I, [_P, _I]),
         "sgn_get_profile": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I,
                                  ctypes.POINTER(ctypes.c_longlong)]),
+        "sgn_elliptic_apply_noalloc": (_I, [_I, _I, _D, _D, _P, _P, _P, _P]),
         "sgn_last_error": (ctypes.c_char_p, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +205,13 @@ def sgn_get_profile(handle) -> dict:
     _check(handle, load_library().sgn_get_profile(handle, ms, cnt, n, ctypes.byref(launches)))
     return dict(ms={k: ms[i] for i, k in enumerate(PROFILE_CLASSES)},
                 counts={k: cnt[i] for i, k in enumerate(PROFILE_CLASSES)}, launches=launches.value)
+
+
+def sgn_elliptic_apply_noalloc(Nx, Ny, Lx, Ly, h, sigma, out, stream=None):
+    """L[sigma] with no device allocation; see include/sgn.h."""
+    st = load_library().sgn_elliptic_apply_noalloc(int(Nx), int(Ny), float(Lx), float(Ly), _ptr(h),
+                                                     _ptr(sigma), _ptr(out), int(stream) if stream else None)
+    _check(None, st)
 
 
 def sgn_last_error(handle) -> str:
