@@ -221,7 +221,7 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   double* cnorm_d = ctx->scal + 0;
   double* beta_d = ctx->scal + 1;
   CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
-  CK(launch_reduce(ctx->partials, 1, cnorm_d, true, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 1, cnorm_d, true, nullptr, EX(ctx)));
   CK(launch_readback_scalar(cnorm_d, ctx->flags, ctx->rb_dev, EX(ctx)));
   sync_read(ctx);
   check_flags(ctx, ctx->rb_host->flags);
@@ -243,7 +243,7 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   for (;;) {
     CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
     CK(launch_residual<double>(G, ctx->cvec, ctx->w, V, ctx->partials, EX(ctx)));
-    CK(launch_reduce(ctx->partials, 1, beta_d, true, EX(ctx)));
+    CK(launch_reduce(ctx->partials, 1, beta_d, true, nullptr, EX(ctx)));
     CK(launch_readback_scalar(beta_d, ctx->flags, ctx->rb_dev, EX(ctx)));
     sync_read(ctx);
     check_flags(ctx, ctx->rb_host->flags);
@@ -262,12 +262,17 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
       const int nv = j + 1;
       CK(launch_matvec<double>(G, ctx->tb, Vj, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
       ++its;
-      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, EX(ctx)));
-      CK(launch_reduce(ctx->partials, nv, ctx->gst->h1, false, EX(ctx)));
-      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h1, ctx->w, ctx->partials, true, EX(ctx)));
-      CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, EX(ctx)));
-      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h2, ctx->w, ctx->partials, false, EX(ctx)));
-      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, EX(ctx)));
+      // classical Gram-Schmidt, second pass only if the DGKS test asks for it
+      const int* gate = &ctx->gst->reorth;
+      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, nullptr, EX(ctx)));
+      CK(launch_reduce(ctx->partials, nv + 1, ctx->gst->h1, false, nullptr, EX(ctx)));
+      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h1, ctx->w, ctx->partials, nullptr, EX(ctx)));
+      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, nullptr, EX(ctx)));
+      CK(launch_reorth_decide(ctx->gst, nv, EX(ctx)));
+      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, gate, EX(ctx)));
+      CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, gate, EX(ctx)));
+      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h2, ctx->w, ctx->partials, gate, EX(ctx)));
+      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, gate, EX(ctx)));
       CK(launch_givens(ctx->gst, j, ctx->rb_dev, ctx->flags, EX(ctx)));
       sync_read(ctx);
       res = ctx->rb_host->res;
@@ -404,7 +409,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->h = dalloc<double>(ctx, G.nphys());
     ctx->cr = dalloc<double>(ctx, G.nphys());
     ctx->cc = dalloc<double>(ctx, G.nphys());
-    ctx->partials = dalloc<double>(ctx, (size_t)(MAXV + 1) * RED_BLOCKS);
+    ctx->partials = dalloc<double>(ctx, (size_t)(MAXV + 2) * NBLK);
     ctx->scal = dalloc<double>(ctx, 16);
     ctx->gst = dalloc<GmresDev>(ctx, 1);
     ctx->rb_dev = dalloc<GmresReadback>(ctx, 1);
@@ -636,7 +641,7 @@ sgn_status sgn_invariants(sgn_t ctx, const double* h, const double* vx, const do
   inv2(ctx, in, dx, dy, 2, o);
   CK(launch_invariant_sums(ctx->G, h, vx, vy, sigma, ctx->phys[0], ctx->phys[1], ctx->g, ctx->partials,
                            EX(ctx)));
-  CK(launch_reduce(ctx->partials, 4, ctx->scal + 4, false, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 4, ctx->scal + 4, false, nullptr, EX(ctx)));
   CK(cudaMemcpyAsync(ctx->inv_host, ctx->scal + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const double dA = ctx->G.Lx * ctx->G.Ly / (double)ctx->G.nphys();

@@ -11,8 +11,8 @@ namespace sgn {
 // Upper bound of the GMRES restart length (Krylov basis of MAXM+1 vectors).
 constexpr int MAXM = 32;
 constexpr int MAXV = MAXM + 1;
-// Blocks of the reduction kernels (a multiple of the 152 SMs of a GB300).
-constexpr int RED_BLOCKS = 304;
+// Blocks of the vector and reduction kernels (8 per SM of a GB300's 152).
+constexpr int NBLK = 1216;
 
 // Grid geometry. Spectra are stored row-major [Ny][ldS] complex, row ky holds
 // kx = 0..Nx/2 (R2C half storage along x); ldS >= Nxh.
@@ -48,8 +48,10 @@ struct Tables {
 struct GmresDev {
   double H[(MAXM + 1) * MAXM];  // column-major, H[i + j*(MAXM+1)]
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
-  double h1[MAXV], h2[MAXV];  // the two classical Gram-Schmidt passes
+  double h1[MAXV + 1], h2[MAXV + 1];  // Gram-Schmidt passes; slot nv holds |w|^2
   double nrm2;                // squared norm of the orthogonalised vector
+  int reorth;                 // second pass needed (DGKS test)
+  int pad_;
   double hnext, inv_hnext;    // H[j+1][j] and its inverse
   double res;                 // |g_{j+1}|
 };
@@ -202,13 +204,14 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
                            double* partials, const Exec& ex);
 
 // ---- Krylov vector kernels (spectral vectors, Parseval-weighted inner product)
+// partial <V_i, w> (slots 0..nv-1) and |w|^2 (slot nv); gate: run only if *gate != 0 (may be null)
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const Exec& ex);
-// w -= sum_i coef[i] V_i; then partial dots of V_i with new w (want_dots) and its squared norm
+                        double* partials, const int* gate, const Exec& ex);
+// w -= sum_i coef[i] V_i and partial |w_new|^2 (slot 0); gated like launch_dots
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* w, double* partials, bool want_dots, const Exec& ex);
+                              cpx<T>* w, double* partials, const int* gate, const Exec& ex);
 // r = c - w, and partial squared norm of r
 template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
@@ -225,14 +228,17 @@ template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex);
 
 // reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
-cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const Exec& ex);
+cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
+                          const Exec& ex);
+// second Gram-Schmidt pass needed? (sets st->reorth, zeroes h2 if not)
+cudaError_t launch_reorth_decide(GmresDev* st, int nv, const Exec& ex);
 // GMRES scalar kernels (one thread)
 cudaError_t launch_gmres_start(GmresDev* st, const double* beta, const Exec& ex);
 cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int* flags, const Exec& ex);
 cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex);
 cudaError_t launch_readback_scalar(const double* x, const int* flags, GmresReadback* rb_dev, const Exec& ex);
 
-// invariants: physical pointwise sums (mass, px, py, energy) -> partials[RED_BLOCKS][4]
+// invariants: physical pointwise sums (mass, px, py, energy) -> partials[4][NBLK]
 cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* vx, const double* vy,
                                   const double* sig, const double* sx, const double* sy, double g,
                                   double* partials, const Exec& ex);

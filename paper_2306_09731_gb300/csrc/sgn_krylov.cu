@@ -7,113 +7,99 @@
 // Nx*Ny times the Euclidean inner product of the physical fields; relative
 // residuals are therefore the same as for unknowns in physical space.
 //
-// Orthogonalisation is classical Gram-Schmidt applied twice (CGS2): one pass
-// forms all dot products, and each update pass w -= sum h_i V_i also forms the
-// dot products (or the norm) of the updated vector in the same sweep. All
-// reductions accumulate in FP64, per block with warp shuffles, then over the
-// RED_BLOCKS block partials in a fixed order (deterministic).
+// Orthogonalisation is classical Gram-Schmidt with selective
+// reorthogonalisation (the DGKS test): one pass forms all dot products and
+// |w|^2, one pass applies w -= sum h_i V_i and forms |w'|^2; a second
+// (dots, update) pair runs only when |w'|^2 < |w|^2 / 2, decided on the device
+// (the second-pass kernels are gated by a device flag). All reductions
+// accumulate in FP64, per block with warp shuffles, then over the NBLK block
+// partials in a fixed order (deterministic). On a GB300 these BLAS-1 kernels
+// are FP64-issue bound, not HBM bound (4 DFMA per 16-byte entry against an
+// FP64:HBM balance below 1 DFMA per byte), so each entry's Parseval weight is
+// folded into w once rather than into every dot product.
 #include <math.h>
 
 #include "sgn_internal.h"
+#include "vec_common.cuh"
 
 namespace sgn {
 
-__device__ __forceinline__ double col_weight_k(const Geom& G, int col) {
-  return (col == 0 || col == (G.Nx >> 1)) ? 1.0 : 2.0;
-}
+constexpr int DOT_CHUNK = 8;  // dot products per block row of the grid (blockIdx.y)
 
-template <typename T>
-__device__ __forceinline__ double wdot(cpx<T> a, cpx<T> b) {
-  return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-}
-
-// Sum v over the block into red (one slot per warp); result valid on thread 0.
-__device__ __forceinline__ double block_reduce(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double tot = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
-  __syncthreads();
-  return tot;
-}
-
-// partials[i * RED_BLOCKS + block] = sum over the block's rows of <V_i, w>
+// partials[i * NBLK + b] = block b's share of <V_i, w> for the chunk
+// i = 8*blockIdx.y .. +7 (i < nv); chunk 0 also writes |w|^2 to slot nv.
+// gate (may be null): the kernel does nothing unless *gate != 0.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                                              double* partials) {
+                                              double* partials, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[32];
-  double acc[MAXV];
+  const int i0 = blockIdx.y * DOT_CHUNK;
+  const int nc = min(DOT_CHUNK, nv - i0);
+  double acc[DOT_CHUNK];
 #pragma unroll
-  for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      const double wt = col_weight_k(G, col);
-      const cpx<T> we = w[e];
+  for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = 0.0;
+  double nrm = 0.0;
+  const cpx<T>* Vc = V + (size_t)i0 * vstride;
+  for (Walk it(G); it.ok(); it.next()) {
+    const cpx<T> we = w[it.e];
+    const double wt = col_weight_k(G, it.col);
+    const double wx = wt * (double)we.x, wy = wt * (double)we.y;
+    cpx<T> v[DOT_CHUNK];
 #pragma unroll
-      for (int i = 0; i < MAXV; ++i)
-        if (i < nv) acc[i] += wt * wdot(V[i * vstride + e], we);
-    }
+    for (int i = 0; i < DOT_CHUNK; ++i)
+      if (i < nc) v[i] = Vc[i * vstride + it.e];
+#pragma unroll
+    for (int i = 0; i < DOT_CHUNK; ++i)
+      if (i < nc) acc[i] += wx * (double)v[i].x + wy * (double)v[i].y;
+    nrm += wx * (double)we.x + wy * (double)we.y;
   }
 #pragma unroll
-  for (int i = 0; i < MAXV; ++i) {
-    if (i < nv) {
+  for (int i = 0; i < DOT_CHUNK; ++i) {
+    if (i < nc) {
       const double tot = block_reduce(acc[i], red);
-      if (threadIdx.x == 0) partials[(size_t)i * RED_BLOCKS + blockIdx.x] = tot;
+      if (threadIdx.x == 0) partials[(size_t)(i0 + i) * NBLK + blockIdx.x] = tot;
     }
+  }
+  if (blockIdx.y == 0) {
+    const double tot = block_reduce(nrm, red);
+    if (threadIdx.x == 0) partials[(size_t)nv * NBLK + blockIdx.x] = tot;
   }
 }
 
-// w -= sum_i coef[i] V_i, then either the dots <V_i, w_new> (i < nv) and
-// |w_new|^2 (slot nv), or only |w_new|^2 (slot 0).
+// w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, size_t vstride, int nv,
                                                     const double* __restrict__ coef, cpx<T>* w, double* partials,
-                                                    int want_dots) {
+                                                    const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[32];
   __shared__ double cf[MAXV];
   if (threadIdx.x < MAXV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
   __syncthreads();
-  double acc[MAXV + 1];
-#pragma unroll
-  for (int i = 0; i <= MAXV; ++i) acc[i] = 0.0;
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      const double wt = col_weight_k(G, col);
-      double zx = (double)w[e].x, zy = (double)w[e].y;
-#pragma unroll
-      for (int i = 0; i < MAXV; ++i) {
-        if (i < nv) {
-          const cpx<T> v = V[i * vstride + e];
-          zx -= cf[i] * (double)v.x;
-          zy -= cf[i] * (double)v.y;
-        }
-      }
-      const cpx<T> z = mk((T)zx, (T)zy);
-      w[e] = z;
-      if (want_dots) {
-#pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-          if (i < nv) acc[i] += wt * wdot(V[i * vstride + e], z);
-      }
-      acc[MAXV] += wt * wdot(z, z);
+  double nrm = 0.0;
+  for (Walk it(G); it.ok(); it.next()) {
+    const cpx<T> we = w[it.e];
+    double zx = (double)we.x, zy = (double)we.y;
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      const cpx<T> v0 = V[(size_t)(i + 0) * vstride + it.e], v1 = V[(size_t)(i + 1) * vstride + it.e];
+      const cpx<T> v2 = V[(size_t)(i + 2) * vstride + it.e], v3 = V[(size_t)(i + 3) * vstride + it.e];
+      zx -= cf[i] * (double)v0.x + cf[i + 1] * (double)v1.x + cf[i + 2] * (double)v2.x + cf[i + 3] * (double)v3.x;
+      zy -= cf[i] * (double)v0.y + cf[i + 1] * (double)v1.y + cf[i + 2] * (double)v2.y + cf[i + 3] * (double)v3.y;
     }
-  }
-  if (want_dots) {
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) {
-      if (i < nv) {
-        const double tot = block_reduce(acc[i], red);
-        if (threadIdx.x == 0) partials[(size_t)i * RED_BLOCKS + blockIdx.x] = tot;
-      }
+    for (; i < nv; ++i) {
+      const cpx<T> v0 = V[(size_t)i * vstride + it.e];
+      zx -= cf[i] * (double)v0.x;
+      zy -= cf[i] * (double)v0.y;
     }
+    const cpx<T> z = mk((T)zx, (T)zy);
+    w[it.e] = z;
+    const double wt = col_weight_k(G, it.col);
+    nrm += wt * ((double)z.x * (double)z.x + (double)z.y * (double)z.y);
   }
-  const double tot = block_reduce(acc[MAXV], red);
-  if (threadIdx.x == 0) partials[(size_t)(want_dots ? nv : 0) * RED_BLOCKS + blockIdx.x] = tot;
+  const double tot = block_reduce(nrm, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 template <typename T>
@@ -121,13 +107,10 @@ __global__ void __launch_bounds__(256) k_residual(Geom G, const cpx<T>* c, const
                                                   double* partials) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      const cpx<T> z = c[e] - w[e];
-      r[e] = z;
-      acc += col_weight_k(G, col) * wdot(z, z);
-    }
+  for (Walk it(G); it.ok(); it.next()) {
+    const cpx<T> z = c[it.e] - w[it.e];
+    r[it.e] = z;
+    acc += col_weight_k(G, it.col) * wdot(z, z);
   }
   const double tot = block_reduce(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -137,11 +120,7 @@ template <typename T>
 __global__ void k_scale(Geom G, const cpx<T>* x, const double* factor, int invert, cpx<T>* y) {
   const double f0 = *factor;
   const T f = (T)(invert ? 1.0 / f0 : f0);
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x)
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      y[e] = scl(x[e], f);
-    }
+  for (Walk it(G); it.ok(); it.next()) y[it.e] = scl(x[it.e], f);
 }
 
 template <typename T>
@@ -150,34 +129,44 @@ __global__ void k_axpy_multi(Geom G, const cpx<T>* V, size_t vstride, int nv, co
   __shared__ double cf[MAXV];
   if (threadIdx.x < MAXV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
   __syncthreads();
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x)
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      double zx = (double)x[e].x, zy = (double)x[e].y;
-      for (int i = 0; i < nv; ++i) {
-        const cpx<T> v = V[i * vstride + e];
-        zx += cf[i] * (double)v.x;
-        zy += cf[i] * (double)v.y;
-      }
-      x[e] = mk((T)zx, (T)zy);
+  for (Walk it(G); it.ok(); it.next()) {
+    double zx = (double)x[it.e].x, zy = (double)x[it.e].y;
+    for (int i = 0; i < nv; ++i) {
+      const cpx<T> v = V[(size_t)i * vstride + it.e];
+      zx += cf[i] * (double)v.x;
+      zy += cf[i] * (double)v.y;
     }
+    x[it.e] = mk((T)zx, (T)zy);
+  }
 }
 
 template <typename T>
 __global__ void k_zero(Geom G, cpx<T>* x) {
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x)
-    for (int col = threadIdx.x; col < G.ldS; col += blockDim.x) x[(size_t)row * G.ldS + col] = mk((T)0, (T)0);
+  for (Walk it(G); it.ok(); it.next()) x[it.e] = mk((T)0, (T)0);
 }
 
-// out[i] = sum_b partials[i*RED_BLOCKS + b] (fixed order), i < n
-__global__ void k_reduce(const double* partials, int n, double* out, int sqrt_out) {
+// out[i] = sum_b partials[i*NBLK + b] (fixed order), i < n. Gated.
+__global__ void k_reduce(const double* partials, int n, double* out, int sqrt_out, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[32];
   for (int i = 0; i < n; ++i) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) v += partials[(size_t)i * RED_BLOCKS + b];
+    for (int b = threadIdx.x; b < NBLK; b += blockDim.x) v += partials[(size_t)i * NBLK + b];
     const double tot = block_reduce(v, red);
     if (threadIdx.x == 0) out[i] = sqrt_out ? sqrt(tot) : tot;
   }
+}
+
+// DGKS test after the first Gram-Schmidt pass: reorthogonalise when the
+// update removed more than half of |w|^2 (|w'| < |w|/sqrt 2); otherwise the
+// second-pass coefficients are zero.
+__global__ void k_reorth_decide(GmresDev* st, int nv) {
+  if (threadIdx.x != 0) return;
+  const double nw = st->h1[nv];
+  const int need = (st->nrm2 < 0.5 * nw) ? 1 : 0;
+  st->reorth = need;
+  if (!need)
+    for (int i = 0; i < MAXV; ++i) st->h2[i] = 0.0;
 }
 
 // ---------------------------------------------------------- scalar kernels
@@ -241,7 +230,7 @@ __global__ void k_readback_scalar(const double* x, const int* flags, GmresReadba
 
 // ----------------------------------------------------------- invariants
 
-// partials[q*RED_BLOCKS + b], q = mass, px, py, energy (Section 2.3)
+// partials[q*NBLK + b], q = mass, px, py, energy (Section 2.3)
 __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h, const double* vx,
                                                         const double* vy, const double* sig, const double* sx,
                                                         const double* sy, double g, double* partials) {
@@ -260,7 +249,7 @@ __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h,
   double vals[4] = {m, px, py, en};
   for (int q = 0; q < 4; ++q) {
     const double tot = block_reduce(vals[q], red);
-    if (threadIdx.x == 0) partials[(size_t)q * RED_BLOCKS + blockIdx.x] = tot;
+    if (threadIdx.x == 0) partials[(size_t)q * NBLK + blockIdx.x] = tot;
   }
 }
 
@@ -268,17 +257,19 @@ __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h,
 
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const Exec& ex) {
+                        double* partials, const int* gate, const Exec& ex) {
+  dim3 grid(NBLK, (nv + DOT_CHUNK - 1) / DOT_CHUNK);
+  if (grid.y == 0) grid.y = 1;
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<RED_BLOCKS, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials);
+  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate);
   ex.end();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* w, double* partials, bool want_dots, const Exec& ex) {
+                              cpx<T>* w, double* partials, const int* gate, const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_cgs_update<T><<<RED_BLOCKS, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, want_dots ? 1 : 0);
+  k_cgs_update<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate);
   ex.end();
   return cudaGetLastError();
 }
@@ -286,7 +277,7 @@ template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
                             const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_residual<T><<<RED_BLOCKS, 256, 0, ex.s>>>(G, c, w, r, partials);
+  k_residual<T><<<NBLK, 256, 0, ex.s>>>(G, c, w, r, partials);
   ex.end();
   return cudaGetLastError();
 }
@@ -294,7 +285,7 @@ template <typename T>
 cudaError_t launch_scale(const Geom& G, const cpx<T>* x, const double* factor, bool invert, cpx<T>* y,
                          const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_scale<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y);
+  k_scale<T><<<NBLK, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y);
   ex.end();
   return cudaGetLastError();
 }
@@ -302,21 +293,28 @@ template <typename T>
 cudaError_t launch_axpy_multi(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* x, const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_axpy_multi<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x);
+  k_axpy_multi<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x);
   ex.end();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_zero<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, x);
+  k_zero<T><<<NBLK, 256, 0, ex.s>>>(G, x);
   ex.end();
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const Exec& ex) {
+cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
+                          const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_reduce<<<1, 256, 0, ex.s>>>(partials, n, out, sqrt_out ? 1 : 0);
+  k_reduce<<<1, 256, 0, ex.s>>>(partials, n, out, sqrt_out ? 1 : 0, gate);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_reorth_decide(GmresDev* st, int nv, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_reorth_decide<<<1, 32, 0, ex.s>>>(st, nv);
   ex.end();
   return cudaGetLastError();
 }
@@ -348,16 +346,16 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
                                   const double* sig, const double* sx, const double* sy, double g,
                                   double* partials, const Exec& ex) {
   ex.begin(PK_IO);
-  k_invariant_sums<<<RED_BLOCKS, 256, 0, ex.s>>>(G, h, vx, vy, sig, sx, sy, g, partials);
+  k_invariant_sums<<<NBLK, 256, 0, ex.s>>>(G, h, vx, vy, sig, sx, sy, g, partials);
   ex.end();
   return cudaGetLastError();
 }
 
 #define SGN_KRYLOV_INST(T)                                                                                   \
   template cudaError_t launch_dots<T>(const Geom&, const cpx<T>*, size_t, int, const cpx<T>*, double*,       \
-                                      const Exec&);                                                         \
+                                      const int*, const Exec&);                                             \
   template cudaError_t launch_cgs_update<T>(const Geom&, const cpx<T>*, size_t, int, const double*, cpx<T>*, \
-                                            double*, bool, const Exec&);                                    \
+                                            double*, const int*, const Exec&);                              \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
   template cudaError_t launch_scale<T>(const Geom&, const cpx<T>*, const double*, bool, cpx<T>*,            \

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "sgn_internal.h"
+#include "vec_common.cuh"
 
 namespace sgn {
 
@@ -644,7 +645,7 @@ template <typename T>
 cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T* cc, int* flags,
                              const Exec& ex) {
   ex.begin(PK_COEF);
-  k_coef_phys<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, hphys, h, cr, cc, flags);
+  k_coef_phys<T><<<NBLK, 256, 0, ex.s>>>(G, hphys, h, cr, cc, flags);
   ex.end();
   return cudaGetLastError();
 }
@@ -745,12 +746,9 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, con
 template <typename T>
 __global__ void k_spec_div(Geom G, const T* __restrict__ kx, const T* __restrict__ ky, const cpx<T>* vx,
                            const cpx<T>* vy, cpx<T>* b) {
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
-    const T kyv = __ldg(ky + row);
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      b[e] = mul_ik(vx[e], -__ldg(kx + col)) - mul_ik(vy[e], kyv);
-    }
+  for (Walk it(G); it.ok(); it.next()) {
+    const T kxv = it.col < G.Nxh ? __ldg(kx + it.col) : (T)0;
+    b[it.e] = mul_ik(vx[it.e], -kxv) - mul_ik(vy[it.e], __ldg(ky + it.row));
   }
 }
 
@@ -758,45 +756,24 @@ template <typename T>
 cudaError_t launch_spec_div(const Geom& G, const Tables<T>& tb, const cpx<T>* vx, const cpx<T>* vy, cpx<T>* b,
                             const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_spec_div<T><<<RED_BLOCKS * 2, 256, 0, ex.s>>>(G, tb.kx, tb.ky, vx, vy, b);
+  k_spec_div<T><<<NBLK, 256, 0, ex.s>>>(G, tb.kx, tb.ky, vx, vy, b);
   ex.end();
   return cudaGetLastError();
 }
 
-// Parseval weight of a half-spectrum column: kx = 0 and kx = Nx/2 count once.
-__device__ __forceinline__ double col_weight(const Geom& G, int col) {
-  return (col == 0 || col == (G.Nx >> 1)) ? 1.0 : 2.0;
-}
-
 template <typename T>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double tot = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
-  return tot;
-}
-
-template <typename T>
-__global__ void k_precond(Geom G, const T* __restrict__ kx, const T* __restrict__ ky, const cpx<T>* in,
-                          cpx<T>* out, double* partials) {
+__global__ void __launch_bounds__(256) k_precond(Geom G, const T* __restrict__ kx, const T* __restrict__ ky,
+                                                 const cpx<T>* in, cpx<T>* out, double* partials) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (int row = blockIdx.x; row < G.Ny; row += gridDim.x) {
-    const T kyv = __ldg(ky + row);
-    for (int col = threadIdx.x; col < G.Nxh; col += blockDim.x) {
-      const size_t e = (size_t)row * G.ldS + col;
-      const T kxv = __ldg(kx + col);
-      const cpx<T> z = scl(in[e], (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
-      out[e] = z;
-      acc += col_weight(G, col) * ((double)z.x * z.x + (double)z.y * z.y);
-    }
+  for (Walk it(G); it.ok(); it.next()) {
+    const T kxv = it.col < G.Nxh ? __ldg(kx + it.col) : (T)0;
+    const T kyv = __ldg(ky + it.row);
+    const cpx<T> z = scl(in[it.e], (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+    out[it.e] = z;
+    acc += col_weight_k(G, it.col) * ((double)z.x * z.x + (double)z.y * z.y);
   }
-  const double tot = block_sum<T>(acc, red);
+  const double tot = block_reduce(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
@@ -804,7 +781,7 @@ template <typename T>
 cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<T>* out, double* partials,
                            const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_precond<T><<<RED_BLOCKS, 256, 0, ex.s>>>(G, tb.kx, tb.ky, in, out, partials);
+  k_precond<T><<<NBLK, 256, 0, ex.s>>>(G, tb.kx, tb.ky, in, out, partials);
   ex.end();
   return cudaGetLastError();
 }
