@@ -104,6 +104,24 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank: float, seconds_local: float, world: int):
+    """Whole-job units/s: all ranks' units over the slowest rank's time."""
+    t = max_over_ranks(seconds_local, world)
+    return world * units_per_rank / t, t
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -185,11 +203,8 @@ def run_ours(args, rank, world, local_rank):
     prof = s.profile()
     stats1 = s.stats()
     s.set_profiling(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1000.0)
+    value, t_max = throughput(args.steps, ms / 1000.0, world)
+    ms_max = t_max * 1000.0
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, args.steps // 4)
@@ -206,10 +221,8 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(e2e_steps):
             sgn_rk4_step_host(s.handle, *hh, DT, 1)
         w1 = time.perf_counter()
-        te = torch.tensor([w1 - w0], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * e2e_steps / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e_value, _ = throughput(e2e_steps, w1 - w0, world)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
 

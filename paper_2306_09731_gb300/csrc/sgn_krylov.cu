@@ -24,13 +24,15 @@
 
 namespace sgn {
 
-constexpr int DOT_CHUNK = 8;  // dot products per block row of the grid (blockIdx.y)
+constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockIdx.y)
 
 // partials[i * NBLK + b] = block b's share of <V_i, w> for the chunk
-// i = 8*blockIdx.y .. +7 (i < nv); chunk 0 also writes |w|^2 to slot nv.
+// i = 4*blockIdx.y .. +3 (i < nv); chunk 0 also writes |w|^2 to slot nv.
+// Four accumulators keep registers low enough for 4 blocks per SM: the
+// kernel is latency bound at lower occupancy.
 // gate (may be null): the kernel does nothing unless *gate != 0.
 template <typename T>
-__global__ void __launch_bounds__(256) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
+__global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                                               double* partials, const int* gate) {
   if (gate && *gate == 0) return;
   __shared__ double red[32];
