@@ -41,13 +41,17 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="grid points per side (default 2048)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
+                    help="headline is the mixed path when it runs; both also times plain FP64")
     return ap.parse_args()
 
 
-def config(n):
+def config(n, fp32=False):
     return {"workload": f"gaussian_hump_{n}x{n}", "grid": [n, n], "box": [-L_DEFAULT / 2, L_DEFAULT / 2],
             "h0": f"1+{ALPHA}*exp(-(x^2+y^2))", "v0": "0", "dt": DT, "gmres_restart": 20, "gmres_tol": 1e-10,
-            "precision": "fp64", "l2": "inputs larger than L2 (state + Krylov basis ~1.3 GB), no flush"}
+            "precision": ("fp32 transforms/pointwise/inner GMRES, fp64 state, dots, Givens and refinement "
+                          "residual" if fp32 else "fp64"),
+            "l2": "inputs larger than L2 (state + Krylov basis, 0.9-1.3 GB), no flush"}
 
 
 class ClockSampler:
@@ -139,30 +143,120 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 MEASURED_TRAFFIC = {
     ("mv_x", "fp64", 2048): {"bytes": 134.508544e6 + 23.561472e6,
                              "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
+    ("ref_x", "fp64", 2048): {"bytes": 134.508544e6 + 23.561472e6,
+                              "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
 }
 
 # kernel classes that are one kernel each (candidates for the roofline line)
-SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs_yfwd")
+SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs_yfwd", "ref_yinv", "ref_x",
+                         "ref_yfwd")
 
 
-def mv_x_flops(n):
-    """Algorithmic flops of one launch of the fused matvec x-pass at n x n.
+def kernel_work(cls, n, tbytes):
+    """Algorithmic (flops, DRAM bytes) of one launch of a kernel class at n x n.
 
-    Per row: 3 inverse and 3 forward real FFTs of length n (2.5 n log2 n each),
-    plus the pointwise products (6 per point) and the a - i kx b combination
-    (4 per half-spectrum entry).
+    tbytes: bytes per real of the pass (8 FP64, 4 FP32); the RK4 state, sigma
+    and b stay FP64 (8) in both modes. FFT flops: 5 m log2 m per complex
+    transform of length m, 2.5 m log2 m per real one.
     """
     import math
-    rows = n
-    return rows * (6 * 2.5 * n * math.log2(n) + 6 * n + 4 * (n // 2 + 1))
+    nxh = n // 2 + 1
+    spec = n * nxh * 2 * tbytes       # one half spectrum of the pass's type
+    spec_s = n * nxh * 2 * 8          # one FP64 half spectrum (state)
+    phys = n * n * tbytes
+    col = 5 * n * math.log2(n)        # one complex column FFT
+    row = 2.5 * n * math.log2(n)      # one real row FFT
+    if cls in ("mv_yinv", "ref_yinv"):
+        return 2 * nxh * col, 3 * spec
+    if cls in ("mv_x", "ref_x"):
+        return n * (6 * row + 6 * n + 4 * nxh), 4 * spec + 2 * phys
+    if cls in ("mv_yfwd", "ref_yfwd"):
+        return 2 * nxh * col + 10 * n * nxh, 3 * spec
+    if cls == "rhs_yinv":
+        return 4 * nxh * col, 3 * spec_s + 4 * spec
+    if cls == "rhs_x":
+        return n * (8 * row + 30 * n + 6 * nxh), 4 * spec + 2 * phys + 3 * spec
+    if cls == "rhs_yfwd":
+        return 3 * nxh * col + 40 * n * nxh, 3 * spec + 13 * spec_s
+    return None, None
 
 
-def mv_x_bytes(n):
-    """Algorithmic DRAM bytes of one launch: read S, Sy (2 half spectra) and the
-    two coefficient fields, write C, By (2 half spectra), FP64."""
-    spec = n * (n // 2 + 1) * 16
-    phys = n * n * 8
-    return 4 * spec + 2 * phys
+KERNEL_NAMES = {"mv_yinv": "k_ypass<inv,2> (matvec y-inverse)", "mv_x": "k_mv_x (fused matvec x-pass)",
+                "mv_yfwd": "k_ypass<fwd,EpiMatvec> (matvec y-forward + M^-1)",
+                "rhs_yinv": "k_ypass<inv,4> (RHS y-inverse)", "rhs_x": "k_rhs_x (fused RHS x-pass)",
+                "rhs_yfwd": "k_ypass<fwd,EpiRHS> (RHS y-forward + RK4 update)",
+                "ref_yinv": "k_ypass<inv,2> FP64 (refinement matvec y-inverse)",
+                "ref_x": "k_mv_x FP64 (refinement matvec x-pass)",
+                "ref_yfwd": "k_ypass<fwd,EpiMatvec> FP64 (refinement matvec y-forward)"}
+
+
+def class_roofline(cls, n, fp32, prof, peaks):
+    """Live roofline of one kernel class from the library's event timers."""
+    cnt = prof["counts"].get(cls, 0)
+    if not cnt:
+        return None
+    avg_ms = prof["ms"][cls] / cnt
+    is32 = fp32 and not cls.startswith("ref")
+    flops, nbytes = kernel_work(cls, n, 4 if is32 else 8)
+    if flops is None:
+        return None
+    if is32:
+        ach = nbytes / (avg_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        ach = flops / (avg_ms / 1e3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": ach / FP64_PEAK_TFLOPS,
+               "peak_source": "derived FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    out.update({"kernel": KERNEL_NAMES.get(cls, cls) + (" FP32" if is32 else " FP64"),
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "avg_launch_ms": avg_ms, "launches": cnt})
+    tr = MEASURED_TRAFFIC.get((cls, "fp32" if is32 else "fp64", n))
+    out["traffic"] = tr["bytes"] if tr else None
+    out["traffic_source"] = tr["source"] if tr else None
+    return out
+
+
+def time_path(precision, args, st, n, world):
+    """W warm-up steps, then K timed RK4 steps of one path; returns its record."""
+    import torch
+
+    from paper_2306_09731_gb300.sgn import Solver
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+    s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10, precision=precision)
+    stream = torch.cuda.current_stream()
+    if args.warmup > 0:
+        s.rk4_step(*f, DT, args.warmup)
+    torch.cuda.synchronize()
+    s.set_profiling(True)
+    st0 = s.stats()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.rk4_step(*f, DT, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    st1 = s.stats()
+    s.set_profiling(False)
+    value, t_max = throughput(args.steps, ms / 1000.0, world)
+    solves = st1["solves"] - st0["solves"]
+    rec = {"value": value, "ms_per_step": t_max * 1e3 / args.steps,
+           "gmres": {"inner_matvecs_per_step": (st1["matvecs"] - st0["matvecs"]) / args.steps,
+                     "solves": solves,
+                     "iters_per_stage": (st1["matvecs"] - st0["matvecs"]) / max(solves, 1),
+                     "fp64_refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1)},
+           "prof": prof}
+    return s, f, rec
 
 
 def run_ours(args, rank, world, local_rank):
@@ -170,41 +264,28 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_2306_09731_gb300 import inputs as I
-    from paper_2306_09731_gb300.sgn import Solver, sgn_rk4_step_host
+    from paper_2306_09731_gb300.sgn import sgn_rk4_step_host
 
     torch.cuda.set_device(local_rank)
     n = args.n
     st = I.gaussian_hump(n, L_DEFAULT, ALPHA)
-    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
-    h, vx, vy, sg = dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)
-    s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10)
-    stream = torch.cuda.current_stream()
-    if args.warmup > 0:
-        s.rk4_step(h, vx, vy, sg, DT, args.warmup)
-    torch.cuda.synchronize()
-    s.set_profiling(True)
-    stats0 = s.stats()
+    peaks, _ = measured_peaks()
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.4)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.rk4_step(h, vx, vy, sg, DT, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    paths = {}
+    fields = {}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        if args.path != "both" and args.path != name:
+            continue
+        s, f, rec = time_path(prec, args, st, n, world)
+        fields[name] = [x.cpu().numpy() for x in f[:3]]
+        if name == ("mixed" if args.path in ("both", "mixed") else "fp64"):
+            head_solver, head_rec, head_prec = s, rec, prec
+        else:
+            s.close()
+        paths[name] = rec
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = s.profile()
-    stats1 = s.stats()
-    s.set_profiling(False)
-    value, t_max = throughput(args.steps, ms / 1000.0, world)
-    ms_max = t_max * 1000.0
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, args.steps // 4)
@@ -213,59 +294,55 @@ def run_ours(args, rank, world, local_rank):
     if e2e_steps > 0:
         pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory().numpy()
         hh = [pin(st.h), pin(st.vx), pin(st.vy), pin(st.sigma)]
-        sgn_rk4_step_host(s.handle, *hh, DT, 1)  # warm
+        sgn_rk4_step_host(head_solver.handle, *hh, DT, 1)  # warm
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(e2e_steps):
-            sgn_rk4_step_host(s.handle, *hh, DT, 1)
+            sgn_rk4_step_host(head_solver.handle, *hh, DT, 1)
         w1 = time.perf_counter()
         e2e_value, _ = throughput(e2e_steps, w1 - w0, world)
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
+    head_solver.close()
 
-    # roofline of the dominant kernel class
-    cls = max(SINGLE_KERNEL_CLASSES, key=lambda k: prof["ms"][k])
-    launches_dom = prof["counts"][cls]
-    avg_ms = prof["ms"][cls] / max(launches_dom, 1)
-    peaks, src = measured_peaks()
-    if cls == "mv_x":
-        achieved = mv_x_flops(n) / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": "k_mv_x (fused matvec x-pass)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": (MEASURED_TRAFFIC.get(("mv_x", "fp64", n)) or {}).get("bytes"),
-                "traffic_source": (MEASURED_TRAFFIC.get(("mv_x", "fp64", n)) or {}).get("source"),
-                "algorithmic_bytes_per_launch": mv_x_bytes(n),
-                "achieved_gbs": mv_x_bytes(n) / (avg_ms / 1e3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                "peak_source": "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)",
-                "avg_launch_ms": avg_ms, "launches": launches_dom}
-    else:
-        roof = {"kernel": cls, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
-
-    matvecs = stats1["matvecs"] - stats0["matvecs"]
-    solves = stats1["solves"] - stats0["solves"]
+    fp32 = head_prec == 1
+    prof = head_rec["prof"]
+    rooflines = {c: class_roofline(c, n, fp32, prof, peaks) for c in SINGLE_KERNEL_CLASSES}
+    dom = max((c for c in rooflines if rooflines[c]), key=lambda c: prof["ms"][c])
     total_prof = sum(prof["ms"].values())
-    gmres_ms = sum(prof["ms"][k] for k in ("mv_yinv", "mv_x", "mv_yfwd", "krylov"))
+    gmres_ms = sum(prof["ms"][k] for k in ("mv_yinv", "mv_x", "mv_yfwd", "krylov", "ref_yinv", "ref_x",
+                                           "ref_yfwd"))
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(config(n), parallelism=f"replicas{world}" if world > 1 else "single"),
-        "path": "plain FP64",
-        "gmres": {"matvecs_per_step": matvecs / args.steps, "solves": solves,
-                  "iters_per_stage": matvecs / max(solves, 1)},
-        "time_share": {k: v / total_prof for k, v in prof["ms"].items()},
+        "metric": METRIC, "value": head_rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head_rec["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+        "config": dict(config(n, fp32), parallelism=f"replicas{world}" if world > 1 else "single"),
+        "path": "mixed: FP32 bulk + FP64 refinement to the FP64 tolerance" if fp32 else "plain FP64",
+        "gmres": head_rec["gmres"],
+        "time_share": {k: v / total_prof for k, v in prof["ms"].items() if v > 0},
         "gmres_share": gmres_ms / total_prof if total_prof else None,
         "gpu_launches": prof["launches"],
-        "roofline": roof,
+        "roofline": rooflines[dom],
+        "roofline_by_kernel": {c: {"frac": r["frac"], "bound": r["bound"], "achieved": r["achieved"],
+                                   "unit": r["unit"], "avg_launch_ms": r["avg_launch_ms"]}
+                               for c, r in rooflines.items() if r},
         "e2e": e2e,
         "clocks": clk,
     }
-    s.close()
+    if "fp64" in paths and "mixed" in paths:
+        f64 = paths["fp64"]
+        out["fp64_plain"] = {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+                             "gmres": f64["gmres"]}
+        out["speedup_mixed_vs_fp64"] = head_rec["value"] / f64["value"]
+        errs = {}
+        for i, nm in enumerate(("h", "vx", "vy")):
+            a, b = fields["mixed"][i], fields["fp64"][i]
+            errs[nm] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        out["mixed_vs_fp64_rel_l2"] = errs
+        out["mixed_vs_fp64_after_steps"] = args.warmup + args.steps
     return out
 
 
@@ -304,7 +381,7 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(config(n), parallelism="single"),
+            "config": dict(config(n, True), parallelism="single"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -329,7 +406,7 @@ def main():
         t, it = oracle_stage_sample(args.n)
         v = 1.0 / (4.0 * t)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"one RK4 stage (stage 2 of step 1, {it} GMRES iterations) of the "
+                               "sample": f"one RK4 stage (stage 2 of step 1, {it} GMRES iterations, FP64) of the "
                                          f"{args.n}x{args.n} workload, x4 for a step; numpy FFT, 1 thread"}
     if rank == 0:
         print(json.dumps(out))

@@ -46,7 +46,9 @@ typedef enum {
 } sgn_status;
 
 typedef struct {
-  int precision;      /* 0 = FP64 throughout (the only mode built so far) */
+  int precision;      /* 0 = FP64 throughout; 1 = FP32 transforms, pointwise work and
+                         inner GMRES, with FP64 state, dot products, Givens and an
+                         FP64 refinement residual (same FP64 tolerance test) */
   int restart;        /* GMRES restart length m, 1..64 (default 20) */
   int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
   double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */
@@ -129,11 +131,12 @@ sgn_status sgn_invariants(sgn_t ctx, const double* h, const double* vx,
 /* Statistics of the last GMRES-using call: total matvecs, number of solves,
  * the largest iteration count of one solve and the last relative residual. */
 typedef struct {
-  long long matvecs;
+  long long matvecs;      /* Arnoldi matvecs (FP32 ones in precision 1) */
   int solves;
   int max_iters;
   double last_relres;
   int last_iters;
+  long long refinements;  /* FP64 residual evaluations of precision 1 */
 } sgn_stats;
 sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out);
 
@@ -141,11 +144,13 @@ sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out);
  * default). Classes, in order: 0 coefficients of Eq. (sigmav) from h_hat,
  * 1-3 the matvec passes (y-inverse, fused x-pass, y-forward + M^-1),
  * 4-6 the RHS passes (y-inverse, fused x-pass, y-forward + RK4 update),
- * 7 GMRES vector kernels and reductions, 8 conversions at call boundaries.
+ * 7 GMRES vector kernels and reductions, 8 conversions at call boundaries,
+ * 9-11 the FP64 refinement matvec passes of precision 1 (the matvec classes
+ * 1-3 then count only its FP32 inner matvecs).
  * sgn_set_profiling(ctx, 1) clears the counters; sgn_get_profile fills up to n
  * entries of ms (summed milliseconds) and counts (timed launches) and
  * *launches with the number of kernels launched since the last clear. */
-#define SGN_PROFILE_CLASSES 9
+#define SGN_PROFILE_CLASSES 12
 sgn_status sgn_set_profiling(sgn_t ctx, int on);
 sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long long* launches);
 

@@ -23,6 +23,17 @@
 using namespace sgn;
 
 typedef cpx<double> C64;
+typedef cpx<float> C32;
+
+// Mixed precision (precision = 1): the inner FP32 GMRES stops once it has
+// reduced its residual estimate by kInnerRel (below that the FP32 estimate
+// stops tracking the true residual), and its estimate is trusted as the final
+// FP64 residual only when kFp32Trust * beta, a bound on the gap between the
+// FP32 estimate and the true residual for a sweep that started at residual
+// beta, is below half the tolerance. Otherwise the next sweep recomputes the
+// residual in FP64.
+constexpr double kInnerRel = 1e-6;
+constexpr double kFp32Trust = 1e-5;
 
 struct sgn_ctx {
   Geom G{};
@@ -43,6 +54,15 @@ struct sgn_ctx {
   double* h = nullptr;
   double* cr = nullptr;
   double* cc = nullptr;
+  // mixed precision (precision = 1)
+  Tables<float> tb32{};
+  C32* V32 = nullptr;
+  C32* w32 = nullptr;
+  C32* tmp32[4] = {};
+  float* h32 = nullptr;
+  float* cr32 = nullptr;
+  float* cc32 = nullptr;
+  C64* r64 = nullptr;
   double* phys[4] = {};  // staging for sgn_rk4_step_host / derivatives (lazy)
   double* partials = nullptr;
   double* scal = nullptr;  // small device scalars
@@ -65,11 +85,11 @@ struct Fail {
   sgn_status st;
 };
 
-#define CK(call)                                                                                  \
+#define CK(...)                                                                                   \
   do {                                                                                            \
-    cudaError_t e_ = (call);                                                                      \
+    cudaError_t e_ = (__VA_ARGS__);                                                               \
     if (e_ != cudaSuccess) {                                                                      \
-      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                              \
+      ctx->err = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_);                       \
       throw Fail{SGN_ECUDA};                                                                      \
     }                                                                                             \
   } while (0)
@@ -164,11 +184,42 @@ void build_tables(sgn_ctx* ctx) {
   CK(cudaMemcpy(ctx->tb.twy, ty.data(), G.Ny * sizeof(C64), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.kx, kx.data(), G.Nxh * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.ky, ky.data(), G.Ny * sizeof(double), cudaMemcpyHostToDevice));
+  if (ctx->opt.precision == 1) {
+    std::vector<C32> fx(G.Nx), fy(G.Ny);
+    for (int k = 0; k < G.Nx; ++k) fx[k] = C32{(float)tx[k].x, (float)tx[k].y};
+    for (int k = 0; k < G.Ny; ++k) fy[k] = C32{(float)ty[k].x, (float)ty[k].y};
+    std::vector<float> kxf(kx.begin(), kx.end()), kyf(ky.begin(), ky.end());
+    ctx->tb32.twx = dalloc<C32>(ctx, G.Nx);
+    ctx->tb32.twy = dalloc<C32>(ctx, G.Ny);
+    ctx->tb32.kx = dalloc<float>(ctx, G.Nxh);
+    ctx->tb32.ky = dalloc<float>(ctx, G.Ny);
+    CK(cudaMemcpy(ctx->tb32.twx, fx.data(), G.Nx * sizeof(C32), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tb32.twy, fy.data(), G.Ny * sizeof(C32), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tb32.kx, kxf.data(), G.Nxh * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tb32.ky, kyf.data(), G.Ny * sizeof(float), cudaMemcpyHostToDevice));
+  }
+}
+
+CoefCopy coef_copy(sgn_ctx* ctx) {
+  CoefCopy cp;
+  if (ctx->opt.precision == 1) {
+    cp.h = ctx->h32;
+    cp.cr = ctx->cr32;
+    cp.cc = ctx->cc32;
+  }
+  return cp;
 }
 
 Exec EX(sgn_ctx* ctx, int kind_override = -1) {
   Exec e{ctx->stream, &ctx->prof};
   e.kind_override = kind_override;
+  return e;
+}
+
+// launches of the FP64 refinement residual of precision 1
+Exec EX_REFINE(sgn_ctx* ctx) {
+  Exec e = EX(ctx);
+  e.refine = true;
   return e;
 }
 
@@ -206,14 +257,15 @@ void check_flags(sgn_ctx* ctx, int flags) {
 // coefficient fields from the spectral depth h_hat
 void coef_from_spectral(sgn_ctx* ctx, const C64* hh) {
   CK(launch_y_fft<double>(ctx->G, ctx->tb, true, &hh, nullptr, 1, ctx->tmp, EX(ctx, PK_COEF)));
-  CK(launch_coef_x<double>(ctx->G, ctx->tb, ctx->tmp[0], ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+  CK(launch_coef_x<double>(ctx->G, ctx->tb, ctx->tmp[0], ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx),
+                            EX(ctx)));
 }
 
 // --------------------------------------------------------------- GMRES
 // Left-preconditioned restarted GMRES on A = M^-1 L, c = M^-1 b (Section 3).
 // Uses ctx->h/cr/cc, ctx->bh (b_hat); ctx->sig is the guess and the result.
 // Returns true if converged.
-bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
+bool gmres_fp64(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   const Geom& G = ctx->G;
   cudaStream_t s = ctx->stream;
   const int m = ctx->opt.restart;
@@ -254,7 +306,7 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
       break;
     }
     if (its >= ctx->opt.maxit) break;
-    CK(launch_scale<double>(G, V, beta_d, true, V, EX(ctx)));
+    CK(launch_scale<double, double>(G, V, beta_d, true, V, EX(ctx)));
     CK(launch_gmres_start(ctx->gst, beta_d, EX(ctx)));
     int k = 0;
     for (int j = 0; j < m; ++j) {
@@ -279,10 +331,10 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
       const double hnext = ctx->rb_host->hnext;
       k = j + 1;
       if (res <= target || its >= ctx->opt.maxit || !(hnext > 0.0) || res != res) break;
-      if (j + 1 < m) CK(launch_scale<double>(G, ctx->w, &ctx->gst->hnext, true, V + (size_t)(j + 1) * vs, EX(ctx)));
+      if (j + 1 < m) CK(launch_scale<double, double>(G, ctx->w, &ctx->gst->hnext, true, V + (size_t)(j + 1) * vs, EX(ctx)));
     }
     CK(launch_backsolve(ctx->gst, k, EX(ctx)));
-    CK(launch_axpy_multi<double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
+    CK(launch_axpy_multi<double, double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
     if (res <= target) {
       conv = true;
       break;
@@ -298,6 +350,115 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   return conv;
 }
 
+// One Arnoldi step of the inner or outer GMRES on the basis V (type T):
+// w = A V_j, classical Gram-Schmidt with DGKS reorthogonalisation, Givens.
+// Returns the residual estimate and H[j+1][j] through the readback.
+template <typename T>
+void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, cpx<T>* V, cpx<T>* w,
+                  cpx<T>* const* tmp, int j) {
+  const Geom& G = ctx->G;
+  const size_t vs = G.nspec();
+  const int nv = j + 1;
+  CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx)));
+  const int* gate = &ctx->gst->reorth;
+  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, EX(ctx)));
+  CK(launch_reduce(ctx->partials, nv + 1, ctx->gst->h1, false, nullptr, EX(ctx)));
+  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, nullptr, EX(ctx)));
+  CK(launch_reorth_decide(ctx->gst, nv, EX(ctx)));
+  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, EX(ctx)));
+  CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, gate, EX(ctx)));
+  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, gate, EX(ctx)));
+  CK(launch_givens(ctx->gst, j, ctx->rb_dev, ctx->flags, EX(ctx)));
+  sync_read(ctx);
+}
+
+// Mixed-precision GMRES (precision = 1), iterative refinement: each sweep
+// computes the residual r = c - A sigma with the FP64 matvec, then solves the
+// correction equation A d = r by GMRES with FP32 matvecs and FP32 Krylov
+// vectors (FP64 dot products, Givens rotations and sigma += d). The
+// tolerance test is the FP64 one of gmres_fp64.
+bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
+  const Geom& G = ctx->G;
+  const int m = ctx->opt.restart;
+  const size_t vs = G.nspec();
+  double* cnorm_d = ctx->scal + 0;
+  double* beta_d = ctx->scal + 1;
+  CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
+  CK(launch_reduce(ctx->partials, 1, cnorm_d, true, nullptr, EX(ctx)));
+  CK(launch_readback_scalar(cnorm_d, ctx->flags, ctx->rb_dev, EX(ctx)));
+  sync_read(ctx);
+  check_flags(ctx, ctx->rb_host->flags);
+  const double cnorm = ctx->rb_host->scalar;
+  ctx->stats.solves++;
+  if (cnorm == 0.0) {
+    CK(launch_zero<double>(G, ctx->sig, EX(ctx)));
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    ctx->stats.last_iters = 0;
+    ctx->stats.last_relres = 0.0;
+    return true;
+  }
+  const double target = ctx->opt.tol * cnorm;
+  int its = 0;
+  bool conv = false;
+  double res = 0.0;
+  for (;;) {
+    CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX_REFINE(ctx)));
+    CK(launch_residual<double>(G, ctx->cvec, ctx->w, ctx->r64, ctx->partials, EX(ctx)));
+    CK(launch_reduce(ctx->partials, 1, beta_d, true, nullptr, EX(ctx)));
+    CK(launch_readback_scalar(beta_d, ctx->flags, ctx->rb_dev, EX(ctx)));
+    sync_read(ctx);
+    check_flags(ctx, ctx->rb_host->flags);
+    ctx->stats.refinements++;
+    const double beta = ctx->rb_host->scalar;
+    res = beta;
+    if (!(beta > target)) {
+      conv = !(beta != beta);
+      break;
+    }
+    if (its >= ctx->opt.maxit) break;
+    C32* const V = ctx->V32;
+    CK(launch_scale<double, float>(G, ctx->r64, beta_d, true, V, EX(ctx)));
+    CK(launch_gmres_start(ctx->gst, beta_d, EX(ctx)));
+    const double inner_target = fmax(0.5 * target, kInnerRel * beta);
+    double res_in = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      arnoldi_step<float>(ctx, ctx->tb32, ctx->cr32, ctx->cc32, V, ctx->w32, ctx->tmp32, j);
+      ++its;
+      res_in = ctx->rb_host->res;
+      const double hnext = ctx->rb_host->hnext;
+      k = j + 1;
+      if (res_in <= inner_target || its >= ctx->opt.maxit || !(hnext > 0.0) || res_in != res_in) break;
+      if (j + 1 < m) CK(launch_scale<float, float>(G, ctx->w32, &ctx->gst->hnext, true, V + (size_t)(j + 1) * vs, EX(ctx)));
+    }
+    CK(launch_backsolve(ctx->gst, k, EX(ctx)));
+    CK(launch_axpy_multi<float, double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
+    if (res_in != res_in) {
+      res = res_in;
+      break;
+    }
+    if (res_in <= target && kFp32Trust * beta <= 0.5 * target) {
+      res = res_in;
+      conv = true;
+      break;
+    }
+  }
+  ctx->stats.matvecs += its;
+  if (its > ctx->stats.max_iters) ctx->stats.max_iters = its;
+  ctx->stats.last_iters = its;
+  ctx->stats.last_relres = res / cnorm;
+  if (iters_out) *iters_out = its;
+  if (relres_out) *relres_out = res / cnorm;
+  return conv;
+}
+
+bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
+  return ctx->opt.precision == 1 ? gmres_mixed(ctx, iters_out, relres_out) : gmres_fp64(ctx, iters_out, relres_out);
+}
+
 // one RK4 stage (s = 1..4) or a plain RHS evaluation (mode RK_STORE_K)
 bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
@@ -311,8 +472,13 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   rk.krasny = ctx->opt.krasny;
   rk.krasny_thr = ctx->opt.krasny_thr;
   rk.g = ctx->g;
-  CK(launch_rhs<double>(ctx->G, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un, ctx->Us, ctx->acc,
-                        mode == RK_STORE_K ? nullptr : ctx->bh, rk, EX(ctx)));
+  C64* bnext = mode == RK_STORE_K ? nullptr : ctx->bh;
+  if (ctx->opt.precision == 1)
+    CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32, ctx->Un,
+                                  ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
+  else
+    CK((launch_rhs<double, double>(ctx->G, ctx->tb, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
+                                   ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
   return conv;
 }
 
@@ -373,7 +539,8 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   sgn_options o;
   sgn_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != 0) return fail(nullptr, SGN_EINVAL, "sgn_create: only precision = 0 (FP64) is built");
+  if (o.precision != 0 && o.precision != 1)
+    return fail(nullptr, SGN_EINVAL, "sgn_create: precision must be 0 (FP64) or 1 (FP32 + FP64 refinement)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
   if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || (o.guess != 0 && o.guess != 1))
     return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr or guess");
@@ -393,6 +560,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   try {
     CK(cudaGetDevice(&ctx->device));
     init_kernel_attributes<double>();
+    if (o.precision == 1) init_kernel_attributes<float>();
     build_tables(ctx);
     const size_t ns = G.nspec();
     for (int f = 0; f < 3; ++f) {
@@ -405,7 +573,17 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->cvec = dalloc<C64>(ctx, ns);
     ctx->w = dalloc<C64>(ctx, ns);
     for (int i = 0; i < 4; ++i) ctx->tmp[i] = dalloc<C64>(ctx, ns);
-    ctx->V = dalloc<C64>(ctx, ns * (size_t)(o.restart + 1));
+    if (o.precision == 1) {
+      ctx->V32 = dalloc<C32>(ctx, ns * (size_t)(o.restart + 1));
+      ctx->w32 = dalloc<C32>(ctx, ns);
+      for (int i = 0; i < 4; ++i) ctx->tmp32[i] = dalloc<C32>(ctx, ns);
+      ctx->h32 = dalloc<float>(ctx, G.nphys());
+      ctx->cr32 = dalloc<float>(ctx, G.nphys());
+      ctx->cc32 = dalloc<float>(ctx, G.nphys());
+      ctx->r64 = dalloc<C64>(ctx, ns);
+    } else {
+      ctx->V = dalloc<C64>(ctx, ns * (size_t)(o.restart + 1));
+    }
     ctx->h = dalloc<double>(ctx, G.nphys());
     ctx->cr = dalloc<double>(ctx, G.nphys());
     ctx->cc = dalloc<double>(ctx, G.nphys());
@@ -542,7 +720,7 @@ sgn_status sgn_elliptic_apply(sgn_t ctx, const double* h, const double* sigma, d
   API_BEGIN
   if (!h || !sigma || !out) return fail(ctx, SGN_EINVAL, "sgn_elliptic_apply: NULL pointer");
   reset_flags(ctx);
-  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
   const double* fi[1] = {sigma};
   fwd2(ctx, fi, 1, &ctx->sig);
   CK(launch_matvec<double>(ctx->G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, false, EX(ctx)));
@@ -561,7 +739,7 @@ sgn_status sgn_gmres_solve(sgn_t ctx, const double* h, const double* b, double* 
   API_BEGIN
   if (!h || !b || !sigma) return fail(ctx, SGN_EINVAL, "sgn_gmres_solve: NULL pointer");
   reset_flags(ctx);
-  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, EX(ctx)));
+  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
   const double* fb[1] = {b};
   fwd2(ctx, fb, 1, &ctx->bh);
   const double* fs[1] = {sigma};

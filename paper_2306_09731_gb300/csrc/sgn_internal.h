@@ -77,6 +77,9 @@ enum ProfKind : int {
   PK_RHS_YFWD,     // RHS: y-forward + RK4 update
   PK_KRYLOV,       // GMRES vector kernels and reductions
   PK_IO,           // physical <-> spectral conversions at call boundaries
+  PK_REF_YINV,     // FP64 refinement matvec of precision 1: y-inverse
+  PK_REF_X,        //   fused x-pass
+  PK_REF_YFWD,     //   y-forward + M^-1
   PK_COUNT
 };
 
@@ -129,9 +132,11 @@ struct Exec {
   cudaStream_t s;
   Prof* p;
   int kind_override = -1;  // time every launch of this call under one class
+  bool refine = false;     // matvec passes count as the FP64 refinement classes
   void begin(int k, int nlaunch = 1) const {
     if (!p) return;
     if (kind_override >= 0) k = kind_override;
+    if (refine && k >= PK_MV_YINV && k <= PK_MV_YFWD) k += PK_REF_YINV - PK_MV_YINV;
     p->launches += nlaunch;
     if (!p->on || !p->ready) return;
     if (p->n == Prof::POOL) p->harvest();
@@ -164,14 +169,21 @@ template <typename T>
 cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const cpx<T>* const* in,
                          const int* deriv, int nf, cpx<T>* const* out, const Exec& ex);
 
+// Optional FP32 copies of the coefficient fields (all null: none written).
+struct CoefCopy {
+  float* h = nullptr;
+  float* cr = nullptr;
+  float* cc = nullptr;
+};
+
 // coefficient pass: from Hy = y-inverse of h_hat, write h, cr = 0.5/(N h), cc = 1.5/(N h^3)
 template <typename T>
 cudaError_t launch_coef_x(const Geom& G, const Tables<T>& tb, const cpx<T>* Hy, T* h, T* cr, T* cc,
-                          int* flags, const Exec& ex);
+                          int* flags, const CoefCopy& cp, const Exec& ex);
 // the same three arrays straight from a physical h (float64)
 template <typename T>
 cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T* cc, int* flags,
-                             const Exec& ex);
+                             const CoefCopy& cp, const Exec& ex);
 
 // matvec w = M^-1 L sigma (precond) or L sigma (!precond), spectral in/out.
 // tmp: 4 spectra of scratch (S, Sy, C, By).
@@ -189,10 +201,13 @@ struct RkArgs {
   double krasny_thr;
   double g;
 };
-template <typename T>
-cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, const cpx<T>* sig, const T* h,
-                       const T* cr, cpx<T>* const* tmp, cpx<T>* const* Un, cpx<T>* const* Unext,
-                       cpx<T>* const* acc, cpx<T>* bhat, const RkArgs& rk, const Exec& ex);
+// T: compute type of the passes (tmp, h, cr); S: storage type of the state,
+// sigma_hat and b_hat (FP64 in both modes).
+template <typename T, typename S>
+cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs, cpx<S>* const* U,
+                       const cpx<S>* sig, const T* h, const T* cr, cpx<T>* const* tmp, cpx<S>* const* Un,
+                       cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk,
+                       const Exec& ex);
 
 // b_hat = -(i kx vx_hat + i ky vy_hat)
 template <typename T>
@@ -216,14 +231,14 @@ cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, in
 template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
                             const Exec& ex);
-// x *= (*factor) (device scalar) or y = x * factor
-template <typename T>
-cudaError_t launch_scale(const Geom& G, const cpx<T>* x, const double* factor, bool invert, cpx<T>* y,
+// y = x * f, f = *factor or 1 / *factor (device scalar); may change precision
+template <typename TI, typename TO>
+cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, bool invert, cpx<TO>* y,
                          const Exec& ex);
-// x += sum_i coef[i] V_i
-template <typename T>
-cudaError_t launch_axpy_multi(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* x, const Exec& ex);
+// x += sum_i coef[i] V_i (V in TV, x in TX, FP64 arithmetic)
+template <typename TV, typename TX>
+cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
+                              cpx<TX>* x, const Exec& ex);
 template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex);
 

@@ -118,27 +118,30 @@ __global__ void __launch_bounds__(256) k_residual(Geom G, const cpx<T>* c, const
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-template <typename T>
-__global__ void k_scale(Geom G, const cpx<T>* x, const double* factor, int invert, cpx<T>* y) {
+template <typename TI, typename TO>
+__global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int invert, cpx<TO>* y) {
   const double f0 = *factor;
-  const T f = (T)(invert ? 1.0 / f0 : f0);
-  for (Walk it(G); it.ok(); it.next()) y[it.e] = scl(x[it.e], f);
+  const double f = invert ? 1.0 / f0 : f0;
+  for (Walk it(G); it.ok(); it.next()) {
+    const cpx<TI> v = x[it.e];
+    y[it.e] = mk((TO)((double)v.x * f), (TO)((double)v.y * f));
+  }
 }
 
-template <typename T>
-__global__ void k_axpy_multi(Geom G, const cpx<T>* V, size_t vstride, int nv, const double* __restrict__ coef,
-                             cpx<T>* x) {
+template <typename TV, typename TX>
+__global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, const double* __restrict__ coef,
+                             cpx<TX>* x) {
   __shared__ double cf[MAXV];
   if (threadIdx.x < MAXV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
   __syncthreads();
   for (Walk it(G); it.ok(); it.next()) {
     double zx = (double)x[it.e].x, zy = (double)x[it.e].y;
     for (int i = 0; i < nv; ++i) {
-      const cpx<T> v = V[(size_t)i * vstride + it.e];
+      const cpx<TV> v = V[(size_t)i * vstride + it.e];
       zx += cf[i] * (double)v.x;
       zy += cf[i] * (double)v.y;
     }
-    x[it.e] = mk((T)zx, (T)zy);
+    x[it.e] = mk((TX)zx, (TX)zy);
   }
 }
 
@@ -283,19 +286,19 @@ cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx
   ex.end();
   return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_scale(const Geom& G, const cpx<T>* x, const double* factor, bool invert, cpx<T>* y,
+template <typename TI, typename TO>
+cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, bool invert, cpx<TO>* y,
                          const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_scale<T><<<NBLK, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y);
+  k_scale<TI, TO><<<NBLK, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y);
   ex.end();
   return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_axpy_multi(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* x, const Exec& ex) {
+template <typename TV, typename TX>
+cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
+                              cpx<TX>* x, const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_axpy_multi<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x);
+  k_axpy_multi<TV, TX><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x);
   ex.end();
   return cudaGetLastError();
 }
@@ -360,12 +363,19 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
                                             double*, const int*, const Exec&);                              \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
-  template cudaError_t launch_scale<T>(const Geom&, const cpx<T>*, const double*, bool, cpx<T>*,            \
-                                       const Exec&);                                                        \
-  template cudaError_t launch_axpy_multi<T>(const Geom&, const cpx<T>*, size_t, int, const double*, cpx<T>*, \
-                                            const Exec&);                                                   \
   template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&);
 
 SGN_KRYLOV_INST(double)
+SGN_KRYLOV_INST(float)
+template cudaError_t launch_scale<double, double>(const Geom&, const cpx<double>*, const double*, bool,
+                                                  cpx<double>*, const Exec&);
+template cudaError_t launch_scale<double, float>(const Geom&, const cpx<double>*, const double*, bool,
+                                                 cpx<float>*, const Exec&);
+template cudaError_t launch_scale<float, float>(const Geom&, const cpx<float>*, const double*, bool,
+                                                cpx<float>*, const Exec&);
+template cudaError_t launch_axpy_multi<double, double>(const Geom&, const cpx<double>*, size_t, int,
+                                                       const double*, cpx<double>*, const Exec&);
+template cudaError_t launch_axpy_multi<float, double>(const Geom&, const cpx<float>*, size_t, int,
+                                                      const double*, cpx<double>*, const Exec&);
 
 }  // namespace sgn

@@ -136,7 +136,7 @@ extern "C" sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, doub
   e = cudaGetLastError();
   // the flags keep the previous call's value: clear them first
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), stream);
-  if (e == cudaSuccess) e = launch_coef_phys<double>(G, h, hh, cr, cc, flags, ex);
+  if (e == cudaSuccess) e = launch_coef_phys<double>(G, h, hh, cr, cc, flags, CoefCopy{}, ex);
   const double* fin[1] = {sigma};
   cpx<double>* sg[1] = {sig};
   if (e == cudaSuccess) e = launch_x_r2c<double>(G, tb, fin, 1, sg, ex);

@@ -174,16 +174,23 @@ __global__ void k_x_c2r(Geom G, const cpx<T>* __restrict__ tw, const T* __restri
 // ------------------------------------------------------ coefficient passes
 
 template <typename T>
-__device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, T* cc, size_t i, int* flags) {
+__device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, T* cc, size_t i, int* flags,
+                                           const CoefCopy& cp) {
   if (!isfinite(hv)) {
     atomicOr(flags, FLAG_NONFINITE);
   } else if (!(hv > 0.0)) {
     atomicOr(flags, FLAG_CAVITATION);
   }
   const double r = 1.0 / hv;
+  const double vr = 0.5 * invN * r, vc = 1.5 * invN * r * r * r;
   h[i] = (T)hv;
-  cr[i] = (T)(0.5 * invN * r);
-  cc[i] = (T)(1.5 * invN * r * r * r);
+  cr[i] = (T)vr;
+  cc[i] = (T)vc;
+  if (cp.h) {
+    cp.h[i] = (float)hv;
+    cp.cr[i] = (float)vr;
+    cp.cc[i] = (float)vc;
+  }
 }
 
 // Hy = y-inverse of h_hat; x-inverse gives N*h. Writes h, cr = 0.5/(N h),
@@ -191,7 +198,7 @@ __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, 
 // of the matvec's packed transforms folded in.
 template <typename T>
 __global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx, const cpx<T>* Hy,
-                         T* h, T* cr, T* cc, int* flags) {
+                         T* h, T* cr, T* cc, int* flags, CoefCopy cp) {
   const XLayout L = x_layout(G);
   cpx<T>* sm = x_smem<T>(G, L.grp);
   const int N = G.Nx, T_ = N >> 3;
@@ -203,17 +210,17 @@ __global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restr
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags);
-    coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags);
+    coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
+    coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
   }
 }
 
 template <typename T>
-__global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, T* cc, int* flags) {
+__global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, T* cc, int* flags, CoefCopy cp) {
   const double invN = 1.0 / (double)G.nphys();
   const size_t n = G.nphys();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    coef_point<T>(hp[i], invN, h, cr, cc, i, flags);
+    coef_point<T>(hp[i], invN, h, cr, cc, i, flags, cp);
 }
 
 // ---------------------------------------------------------- fused matvec x
@@ -380,20 +387,26 @@ __global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict_
 
 // ------------------------------------------------------------------ y-pass
 
-template <typename T, int NIN>
+template <typename T, int NIN, typename S = T>
 struct YIn {
-  const cpx<T>* src[NIN];
-  int deriv[NIN];  // pre-multiply by i ky (inverse passes)
+  const cpx<S>* src[NIN];  // storage type S, converted to the compute type T on load
+  int deriv[NIN];          // pre-multiply by i ky (inverse passes)
 };
+
+template <typename T, typename S>
+__device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
+  const cpx<S> v = *p;
+  return mk((T)v.x, (T)v.y);
+}
 
 // Column tile: C = blockDim / (Ny/8) neighbouring kx columns, thread index
 // c + C*t. Each input column is transformed in registers; the epilogue gets
 // all NIN results of the thread's 8 rows.
 constexpr int ypass_threads(int nin) { return nin >= 3 ? 256 : 512; }
 
-template <typename T, bool INV, int NIN, class Epi>
+template <typename T, bool INV, int NIN, class Epi, typename S = T>
 __global__ void __launch_bounds__(ypass_threads(NIN)) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
-                                                YIn<T, NIN> in, Epi epi) {
+                                                YIn<T, NIN, S> in, Epi epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
   const int lN = G.lNy, T_ = G.Ny >> 3;
@@ -406,11 +419,11 @@ __global__ void __launch_bounds__(ypass_threads(NIN)) k_ypass(Geom G, const cpx<
   cpx<T> r[NIN][8];
 #pragma unroll
   for (int i = 0; i < NIN; ++i) {
-    const cpx<T>* src = in.src[i];
+    const cpx<S>* src = in.src[i];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
-      cpx<T> z = ld(src + (size_t)row * G.ldS + col);
+      cpx<T> z = ld_as<T, S>(src + (size_t)row * G.ldS + col);
       if (in.deriv[i]) z = mul_ik(z, __ldg(ky + row));
       r[i][s] = z;
     }
@@ -455,19 +468,24 @@ struct EpiMatvec {
 
 // K = (h_t, vx_t, vy_t) from r0 = Cq^y, r1 = Qy^y, r2 = F^y, then the RK4
 // stage update and b_hat = -(i kx vx + i ky vy) of the next stage state.
-template <typename T>
+// K is formed in the compute type T; the state (Un, Unext, acc, b) is stored
+// and updated in S (FP64 in both precision modes).
+template <typename T, typename S = T>
 struct EpiRHS {
-  cpx<T>* K[3];      // RK_STORE_K output
-  cpx<T>* Un[3];     // step-start state (RK_FINAL: updated in place)
-  cpx<T>* Unext[3];  // next stage state (stages 1-3)
-  cpx<T>* acc[3];    // running sum of b_s K_s
-  cpx<T>* b;         // next b_hat (may be null)
+  cpx<S>* K[3];      // RK_STORE_K output
+  cpx<S>* Un[3];     // step-start state (RK_FINAL: updated in place)
+  cpx<S>* Unext[3];  // next stage state (stages 1-3)
+  cpx<S>* acc[3];    // running sum of b_s K_s
+  cpx<S>* b;         // next b_hat (may be null)
   const T* kx;
+  const S* kxs;      // wavenumbers in the state type
+  const S* kys;
   RkArgs rk;
   __device__ __forceinline__ void operator()(cpx<T> (&r)[3][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
     const T kxv = __ldg(kx + col);
+    const S kxs_v = __ldg(kxs + col);
     const bool keepx = !rk.dealias || 3 * col <= G.Nx;
     const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
 #pragma unroll
@@ -486,32 +504,32 @@ struct EpiRHS {
           k2 = k0;
         }
       }
-      cpx<T> kk[3] = {k0, k1, k2};
+      cpx<S> kk[3] = {mk((S)k0.x, (S)k0.y), mk((S)k1.x, (S)k1.y), mk((S)k2.x, (S)k2.y)};
       if (rk.mode == RK_STORE_K) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) K[f][e] = kk[f];
         continue;
       }
-      cpx<T> u[3];
+      cpx<S> u[3];
       if (rk.mode == RK_FINAL) {
-        const T c6 = (T)(rk.dt / 6.0);
+        const S c6 = (S)(rk.dt / 6.0);
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-          cpx<T> z = Un[f][e] + scl(acc[f][e] + kk[f], c6);
-          if (rk.krasny && (double)z.x * z.x + (double)z.y * z.y < thr2) z = mk((T)0, (T)0);
+          cpx<S> z = Un[f][e] + scl(acc[f][e] + kk[f], c6);
+          if (rk.krasny && (double)z.x * z.x + (double)z.y * z.y < thr2) z = mk((S)0, (S)0);
           Un[f][e] = z;
           u[f] = z;
         }
       } else {
-        const T cdt = (T)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
+        const S cdt = (S)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-          acc[f][e] = (rk.mode == RK_STAGE1) ? kk[f] : acc[f][e] + scl(kk[f], (T)2);
+          acc[f][e] = (rk.mode == RK_STAGE1) ? kk[f] : acc[f][e] + scl(kk[f], (S)2);
           u[f] = Un[f][e] + scl(kk[f], cdt);
           Unext[f][e] = u[f];
         }
       }
-      if (b) b[e] = mul_ik(u[1], -kxv) - mul_ik(u[2], kyv);
+      if (b) b[e] = mul_ik(u[1], -kxs_v) - mul_ik(u[2], __ldg(kys + row));
     }
   }
 };
@@ -565,6 +583,9 @@ void init_kernel_attributes() {
   set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>>);
   set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>>);
   set_smem<T>((const void*)k_ypass<T, false, 3, EpiRHS<T>>);
+  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>, double>);
+  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>, double>);
+  set_smem<T>((const void*)k_ypass<T, false, 3, EpiRHS<T, double>>);
   cudaGetLastError();
 }
 
@@ -631,21 +652,21 @@ cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const
 
 template <typename T>
 cudaError_t launch_coef_x(const Geom& G, const Tables<T>& tb, const cpx<T>* Hy, T* h, T* cr, T* cc, int* flags,
-                          const Exec& ex) {
+                          const CoefCopy& cp, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
   x_config<T>(G, grid, block, smem, 1);
   ex.begin(PK_COEF);
-  k_coef_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, Hy, h, cr, cc, flags);
+  k_coef_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, Hy, h, cr, cc, flags, cp);
   ex.end();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T* cc, int* flags,
-                             const Exec& ex) {
+                             const CoefCopy& cp, const Exec& ex) {
   ex.begin(PK_COEF);
-  k_coef_phys<T><<<NBLK, 256, 0, ex.s>>>(G, hphys, h, cr, cc, flags);
+  k_coef_phys<T><<<NBLK, 256, 0, ex.s>>>(G, hphys, h, cr, cc, flags, cp);
   ex.end();
   return cudaGetLastError();
 }
@@ -689,15 +710,15 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, const cpx<T>* sig, const T* h,
-                       const T* cr, cpx<T>* const* tmp, cpx<T>* const* Un, cpx<T>* const* Unext,
-                       cpx<T>* const* acc, cpx<T>* bhat, const RkArgs& rk, const Exec& ex) {
+template <typename T, typename S>
+cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs, cpx<S>* const* U,
+                       const cpx<S>* sig, const T* h, const T* cr, cpx<T>* const* tmp, cpx<S>* const* Un,
+                       cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
   {
     y_config<T>(G, 4, grid, block, smem);
-    YIn<T, 4> yi{};
+    YIn<T, 4, S> yi{};
     yi.src[0] = U[1];
     yi.src[1] = U[2];
     yi.src[2] = sig;
@@ -706,7 +727,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, con
     EpiStore<T, 4> ep{};
     for (int i = 0; i < 4; ++i) ep.dst[i] = tmp[i];
     ex.begin(PK_RHS_YINV);
-    k_ypass<T, true, 4, EpiStore<T, 4>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, true, 4, EpiStore<T, 4>, S><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   }
   {
@@ -715,7 +736,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, con
     x_config<T>(G, grid, block, smem, 1);
     ex.begin(PK_RHS_X);
     k_rhs_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], tmp[2], tmp[3], h, cr, (T)rk.g,
-                                         tmp[0], tmp[1], tmp[2]);
+                                            tmp[0], tmp[1], tmp[2]);
     ex.end();
   }
   {
@@ -724,7 +745,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, con
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
     yi.src[2] = tmp[2];
-    EpiRHS<T> ep{};
+    EpiRHS<T, S> ep{};
     for (int f = 0; f < 3; ++f) {
       ep.K[f] = acc[f];
       ep.Un[f] = Un[f];
@@ -733,9 +754,11 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, cpx<T>* const* U, con
     }
     ep.b = bhat;
     ep.kx = tb.kx;
+    ep.kxs = tbs.kx;
+    ep.kys = tbs.ky;
     ep.rk = rk;
     ex.begin(PK_RHS_YFWD);
-    k_ypass<T, false, 3, EpiRHS<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, false, 3, EpiRHS<T, S>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   }
   return cudaGetLastError();
@@ -796,18 +819,30 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
   template cudaError_t launch_y_fft<T>(const Geom&, const Tables<T>&, bool, const cpx<T>* const*,            \
                                        const int*, int, cpx<T>* const*, const Exec&);                       \
   template cudaError_t launch_coef_x<T>(const Geom&, const Tables<T>&, const cpx<T>*, T*, T*, T*, int*,      \
-                                        const Exec&);                                                       \
-  template cudaError_t launch_coef_phys<T>(const Geom&, const double*, T*, T*, T*, int*, const Exec&);      \
+                                        const CoefCopy&, const Exec&);                                      \
+  template cudaError_t launch_coef_phys<T>(const Geom&, const double*, T*, T*, T*, int*, const CoefCopy&,   \
+                                           const Exec&);                                                    \
   template cudaError_t launch_matvec<T>(const Geom&, const Tables<T>&, const cpx<T>*, const T*, const T*,    \
                                         cpx<T>*, cpx<T>* const*, bool, const Exec&);                        \
-  template cudaError_t launch_rhs<T>(const Geom&, const Tables<T>&, cpx<T>* const*, const cpx<T>*,          \
-                                     const T*, const T*, cpx<T>* const*, cpx<T>* const*, cpx<T>* const*,    \
-                                     cpx<T>* const*, cpx<T>*, const RkArgs&, const Exec&);                  \
   template cudaError_t launch_spec_div<T>(const Geom&, const Tables<T>&, const cpx<T>*, const cpx<T>*,      \
                                           cpx<T>*, const Exec&);                                            \
   template cudaError_t launch_precond<T>(const Geom&, const Tables<T>&, const cpx<T>*, cpx<T>*, double*,    \
                                          const Exec&);
 
 SGN_INST(double)
+
+template void init_kernel_attributes<float>();
+template cudaError_t launch_matvec<float>(const Geom&, const Tables<float>&, const cpx<float>*, const float*,
+                                          const float*, cpx<float>*, cpx<float>* const*, bool, const Exec&);
+template cudaError_t launch_rhs<double, double>(const Geom&, const Tables<double>&, const Tables<double>&,
+                                                cpx<double>* const*, const cpx<double>*, const double*,
+                                                const double*, cpx<double>* const*, cpx<double>* const*,
+                                                cpx<double>* const*, cpx<double>* const*, cpx<double>*,
+                                                const RkArgs&, const Exec&);
+template cudaError_t launch_rhs<float, double>(const Geom&, const Tables<float>&, const Tables<double>&,
+                                               cpx<double>* const*, const cpx<double>*, const float*,
+                                               const float*, cpx<float>* const*, cpx<double>* const*,
+                                               cpx<double>* const*, cpx<double>* const*, cpx<double>*,
+                                               const RkArgs&, const Exec&);
 
 }  // namespace sgn

@@ -26,7 +26,8 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
            "sgn_last_error"]
 
-PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io"]
+PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
+                   "ref_yinv", "ref_x", "ref_yfwd"]
 
 
 class SGNError(RuntimeError):
@@ -43,7 +44,8 @@ class sgn_options(ctypes.Structure):
 
 class sgn_stats(ctypes.Structure):
     _fields_ = [("matvecs", ctypes.c_longlong), ("solves", ctypes.c_int), ("max_iters", ctypes.c_int),
-                ("last_relres", ctypes.c_double), ("last_iters", ctypes.c_int)]
+                ("last_relres", ctypes.c_double), ("last_iters", ctypes.c_int),
+                ("refinements", ctypes.c_longlong)]
 
 
 _LIB = None
@@ -190,7 +192,7 @@ def sgn_get_stats(handle) -> dict:
     s = sgn_stats()
     _check(handle, load_library().sgn_get_stats(handle, ctypes.byref(s)))
     return dict(matvecs=s.matvecs, solves=s.solves, max_iters=s.max_iters,
-                last_relres=s.last_relres, last_iters=s.last_iters)
+                last_relres=s.last_relres, last_iters=s.last_iters, refinements=s.refinements)
 
 
 def sgn_set_profiling(handle, on: bool):

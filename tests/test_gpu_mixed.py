@@ -1,0 +1,126 @@
+"""Mixed precision (precision = 1): FP32 transforms, pointwise work and inner
+GMRES with FP64 state, dot products, Givens and an FP64 refinement residual.
+
+Bar: relative L2 <= 1e-5 against the FP64 oracle on the same inputs, and every
+GMRES solve meets the same FP64 tolerance test as the FP64 path, checked here
+by recomputing ||M^-1 (b - L sigma)|| / ||M^-1 b|| with the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2306_09731_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def solver(*a, **kw):
+    from paper_2306_09731_gb300.sgn import Solver
+    return Solver(*a, precision=1, **kw)
+
+
+def fp64_relres(G, h, b, sigma):
+    c = O.precond_solve(G, b)
+    r = c - O.precond_solve(G, O.elliptic_apply(G, h, sigma))
+    return float(np.linalg.norm(r) / np.linalg.norm(c))
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly,tol", [(64, 32, 8.0, 5.0, 1e-10), (128, 128, 10.0, 10.0, 1e-10),
+                                            (256, 16, 80.0, 10.0, 1e-12), (32, 256, 4.0, 30.0, 1e-9)])
+def test_mixed_gmres_meets_fp64_tolerance(Nx, Ny, Lx, Ly, tol):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 7 * Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    b = O.divergence_rhs(G, st.vx, st.vy)
+    s = solver(Nx, Ny, Lx, Ly, tol=tol)
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), dev(b), dev(np.zeros_like(b)))
+    assert conv and rr <= tol
+    sg = host(sig)
+    assert fp64_relres(G, st.h, b, sg) <= 2 * tol
+    ref, _, _, _ = O.gmres(G, st.h, b, np.zeros_like(b), tol=1e-13)
+    assert rel(sg, ref) < 1e-7
+    assert s.stats()["refinements"] >= 1
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", [(64, 32, 8.0, 5.0), (256, 16, 80.0, 10.0), (128, 128, 10.0, 10.0)])
+def test_mixed_rhs_parity(Nx, Ny, Lx, Ly):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 11 * Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    s = solver(Nx, Ny, Lx, Ly)
+    sg = dev(st.sigma)
+    ht, vxt, vyt = s.rhs(dev(st.h), dev(st.vx), dev(st.vy), sg)
+    rht, rvxt, rvyt, rsg, _ = O.rhs(G, st.h, st.vx, st.vy, st.sigma, tol=1e-13)
+    for a, b in ((ht, rht), (vxt, rvxt), (vyt, rvyt)):
+        assert rel(host(a), b) < 1e-5
+    assert rel(host(sg), rsg) < 1e-8
+    s.close()
+
+
+def test_mixed_rk4_soliton_against_oracle_and_exact():
+    st = I.soliton_256x16()
+    G = O.Grid(st.Nx, st.Ny, st.Lx, st.Ly)
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly)
+    h, vx, vy, sg = dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)
+    s.rk4_step(h, vx, vy, sg, 5e-3, 10)
+    oh, ovx, _, _ = O.rk4_step(G, st.h, st.vx, st.vy, st.sigma, 5e-3, 10)
+    assert rel(host(h), oh) < 1e-5 and rel(host(vx), ovx) < 1e-5
+    s.rk4_step(h, vx, vy, sg, 5e-3, 90)
+    ex = I.soliton_256x16(t=0.5)
+    assert rel(host(h), ex.h) < 1e-5 and rel(host(vx), ex.vx) < 1e-5
+    s.close()
+
+
+def test_mixed_rk4_random_against_oracle():
+    Nx, Ny, L = 64, 64, 8.0
+    st = I.random_state(Nx, Ny, L, L, seed=31)
+    G = O.Grid(Nx, Ny, L, L)
+    phi = I.random_smooth(Nx, Ny, L, L, seed=32, kmax=4)
+    vx, vy = O.dx(G, phi), O.dy(G, phi)
+    z = np.zeros_like(vx)
+    s = solver(Nx, Ny, L, L, dealias=1)
+    a = [dev(st.h), dev(vx), dev(vy), dev(z)]
+    s.rk4_step(*a, 2e-3, 8)
+    ref = O.rk4_step(G, st.h, vx, vy, z, 2e-3, 8, tol=1e-13, dealias=True)
+    for x, r in zip(a[:3], ref[:3]):
+        assert rel(host(x), r) < 1e-5
+    s.close()
+
+
+def test_mixed_gaussian_2048_close_to_fp64_path():
+    """The benchmark workload: two steps of the mixed path stay within 1e-5 of
+    the FP64 path and conserve mass to the FP64 rounding of the DC mode."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.gaussian_hump(2048, 100.0, 0.5)
+    runs = []
+    for prec in (1, 0):
+        s = Solver(2048, 2048, 100.0, 100.0, precision=prec)
+        f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+        m0 = s.invariants(*f)[0]
+        s.rk4_step(*f, 1e-3, 2)
+        m1 = s.invariants(*f)[0]
+        assert abs(m1 - m0) < 1e-14 * 100.0 * 100.0
+        runs.append([host(x) for x in f[:3]])
+        s.close()
+    for a, b in zip(runs[0], runs[1]):
+        if np.linalg.norm(b) > 0:
+            assert rel(a, b) < 1e-5
