@@ -11,6 +11,7 @@
 // reads back one residual estimate (one stream synchronisation per step).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -72,6 +73,7 @@ struct sgn_ctx {
   double* inv_host = nullptr;        // pinned, 4 doubles
   int* flags = nullptr;
   Prof prof;
+  bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
   std::vector<void*> allocs;
   std::string err;
   sgn_stats stats{};
@@ -272,6 +274,7 @@ bool gmres_fp64(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   const size_t vs = G.nspec();
   double* cnorm_d = ctx->scal + 0;
   double* beta_d = ctx->scal + 1;
+  CK(launch_hermitian_fix<double>(G, ctx->bh, EX(ctx)));
   CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
   CK(launch_reduce(ctx->partials, 1, cnorm_d, true, nullptr, EX(ctx)));
   CK(launch_readback_scalar(cnorm_d, ctx->flags, ctx->rb_dev, EX(ctx)));
@@ -385,6 +388,7 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   const size_t vs = G.nspec();
   double* cnorm_d = ctx->scal + 0;
   double* beta_d = ctx->scal + 1;
+  CK(launch_hermitian_fix<double>(G, ctx->bh, EX(ctx)));
   CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
   CK(launch_reduce(ctx->partials, 1, cnorm_d, true, nullptr, EX(ctx)));
   CK(launch_readback_scalar(cnorm_d, ctx->flags, ctx->rb_dev, EX(ctx)));
@@ -436,6 +440,9 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
     }
     CK(launch_backsolve(ctx->gst, k, EX(ctx)));
     CK(launch_axpy_multi<float, double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
+    if (ctx->trace)
+      fprintf(stderr, "[sgn] mixed sweep: beta/|c| %.3e, inner its %d, inner estimate/|c| %.3e, total its %d\n",
+              beta / cnorm, k, res_in / cnorm, its);
     if (res_in != res_in) {
       res = res_in;
       break;
@@ -548,6 +555,10 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   if (!ctx) return fail(nullptr, SGN_ENOMEM, "sgn_create: host allocation failed");
   ctx->opt = o;
   ctx->g = g;
+  {
+    const char* tr = getenv("SGN_TRACE");
+    ctx->trace = tr && tr[0] == '1';
+  }
   Geom& G = ctx->G;
   G.Nx = Nx;
   G.Ny = Ny;

@@ -176,7 +176,7 @@ struct CoefCopy {
   float* cc = nullptr;
 };
 
-// coefficient pass: from Hy = y-inverse of h_hat, write h, cr = 0.5/(N h), cc = 1.5/(N h^3)
+// coefficient pass: from Hy = y-inverse of h_hat, write h - 1, cr = 0.5/(N h), cc = 1.5/(N h^3)
 template <typename T>
 cudaError_t launch_coef_x(const Geom& G, const Tables<T>& tb, const cpx<T>* Hy, T* h, T* cr, T* cc,
                           int* flags, const CoefCopy& cp, const Exec& ex);
@@ -213,6 +213,9 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
 template <typename T>
 cudaError_t launch_spec_div(const Geom& G, const Tables<T>& tb, const cpx<T>* vx, const cpx<T>* vy,
                             cpx<T>* b, const Exec& ex);
+// project the kx = 0 and kx = Nx/2 columns onto their Hermitian part (in place)
+template <typename T>
+cudaError_t launch_hermitian_fix(const Geom& G, cpx<T>* x, const Exec& ex);
 // out = M^-1 in (spectral), and the weighted squared norm into partials
 template <typename T>
 cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<T>* out,

@@ -183,19 +183,19 @@ __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, 
   }
   const double r = 1.0 / hv;
   const double vr = 0.5 * invN * r, vc = 1.5 * invN * r * r * r;
-  h[i] = (T)hv;
+  h[i] = (T)(hv - 1.0);  // the depth anomaly h - h_inf (exact in FP64 near h = 1)
   cr[i] = (T)vr;
   cc[i] = (T)vc;
   if (cp.h) {
-    cp.h[i] = (float)hv;
+    cp.h[i] = (float)(hv - 1.0);
     cp.cr[i] = (float)vr;
     cp.cc[i] = (float)vc;
   }
 }
 
-// Hy = y-inverse of h_hat; x-inverse gives N*h. Writes h, cr = 0.5/(N h),
-// cc = 1.5/(N h^3), the coefficients of Eq. (sigmav) with the factor 1/(2N)
-// of the matvec's packed transforms folded in.
+// Hy = y-inverse of h_hat; x-inverse gives N*h. Writes the anomaly h - 1,
+// cr = 0.5/(N h) and cc = 1.5/(N h^3): the coefficients of Eq. (sigmav) with
+// the factor 1/(2N) of the matvec's packed transforms folded in.
 template <typename T>
 __global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx, const cpx<T>* Hy,
                          T* h, T* cr, T* cc, int* flags, CoefCopy cp) {
@@ -280,8 +280,9 @@ __global__ void __launch_bounds__(256) k_mv_x(Geom G, const cpx<T>* __restrict__
 
 // ------------------------------------------------------------- fused RHS x
 
-// Inputs (y-inverse outputs): Vx, Vy, S = sigma, Sy = i ky sigma. Writes
-// Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and Fh = F^x.
+// Inputs (y-inverse outputs): Vx, Vy, S = sigma, Sy = i ky sigma, and the
+// depth anomaly hh = h - 1. Writes Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and
+// Fh = F^x with F = |v|^2/2 - |grad sigma|^2/(2h^2) + g (h - 1) - 9 sigma^2/(2h^4).
 template <typename T>
 __global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                 const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
@@ -328,10 +329,10 @@ __global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict_
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    const T h0 = hh[p0 + x], h1 = hh[p1 + x];
+    const T a0 = hh[p0 + x], a1 = hh[p1 + x];  // h - 1
     const T v0 = Z[s].x * n, v1 = Z[s].y * n;
-    QX[s].x += h0 * v0;
-    QX[s].y += h1 * v1;
+    QX[s].x += v0 + a0 * v0;
+    QX[s].y += v1 + a1 * v1;
     F[s].x += (T)0.5 * v0 * v0;
     F[s].y += (T)0.5 * v1 * v1;
   }
@@ -341,12 +342,14 @@ __global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict_
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    const T h0 = hh[p0 + x], h1 = hh[p1 + x];
+    const T a0 = hh[p0 + x], a1 = hh[p1 + x];  // h - 1
     const T v0 = Z[s].x * n, v1 = Z[s].y * n;
-    QY[s].x += h0 * v0;
-    QY[s].y += h1 * v1;
-    F[s].x += (T)0.5 * v0 * v0 + g * h0;
-    F[s].y += (T)0.5 * v1 * v1 + g * h1;
+    QY[s].x += v0 + a0 * v0;
+    QY[s].y += v1 + a1 * v1;
+    // g (h - h_inf): the constant g h_inf of the Bernoulli equation (2) has no
+    // gradient; leaving it out keeps F's rounding relative to its variation
+    F[s].x += (T)0.5 * v0 * v0 + g * a0;
+    F[s].y += (T)0.5 * v1 * v1 + g * a1;
     // the split returns twice the half spectra: pre-scale by 1/2
     QX[s] = scl(QX[s], (T)0.5);
     QY[s] = scl(QY[s], (T)0.5);
@@ -533,6 +536,41 @@ struct EpiRHS {
     }
   }
 };
+
+// The kx = 0 and kx = Nx/2 columns of the half spectrum of a real field are
+// Hermitian in ky: x(-ky) = conj(x(ky)), real at ky = 0 and ky = Ny/2. The
+// inverse transforms read only that part, so an anti-Hermitian remainder (FP32
+// rounding of RK4 increments leaves one in the state) lies in the null space
+// of the discrete operator; left in b_hat it would stall GMRES at its size.
+// This projects both columns onto their Hermitian part, in place.
+template <typename T>
+__global__ void k_hermitian_fix(Geom G, cpx<T>* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // 0 .. Ny/2 for each of the 2 columns
+  const int half = G.Ny >> 1;
+  if (i > 2 * half + 1) return;
+  const int col = (i <= half) ? 0 : (G.Nx >> 1);
+  const int ky = (i <= half) ? i : i - half - 1;
+  const int kn = (G.Ny - ky) & (G.Ny - 1);
+  cpx<T>* a = x + (size_t)ky * G.ldS + col;
+  cpx<T>* b = x + (size_t)kn * G.ldS + col;
+  if (ky == kn) {
+    a->y = (T)0;
+  } else {
+    const cpx<T> va = *a, vb = *b;
+    const cpx<T> h = mk((T)0.5 * (va.x + vb.x), (T)0.5 * (va.y - vb.y));
+    *a = h;
+    *b = conjg(h);
+  }
+}
+
+template <typename T>
+cudaError_t launch_hermitian_fix(const Geom& G, cpx<T>* x, const Exec& ex) {
+  const int n = 2 * ((G.Ny >> 1) + 1);
+  ex.begin(PK_KRYLOV);
+  k_hermitian_fix<T><<<(n + 127) / 128, 128, 0, ex.s>>>(G, x);
+  ex.end();
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------------ launchers
 
@@ -827,7 +865,8 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
   template cudaError_t launch_spec_div<T>(const Geom&, const Tables<T>&, const cpx<T>*, const cpx<T>*,      \
                                           cpx<T>*, const Exec&);                                            \
   template cudaError_t launch_precond<T>(const Geom&, const Tables<T>&, const cpx<T>*, cpx<T>*, double*,    \
-                                         const Exec&);
+                                         const Exec&);                                                      \
+  template cudaError_t launch_hermitian_fix<T>(const Geom&, cpx<T>*, const Exec&);
 
 SGN_INST(double)
 
