@@ -55,7 +55,10 @@ typedef struct {
   int krasny;         /* 1: Krasny filter after every RK4 step (Section 3); default 0 */
   double krasny_thr;  /* zero DFT coefficients with |c|/(Nx*Ny) < thr (default 1e-12) */
   int dealias;        /* 1: 2/3-rule mask on the RHS spectra (not in the paper); default 0 */
-  int guess;          /* GMRES start: 0 = the last computed sigma (Section 3), 1 = zero */
+  int guess;          /* GMRES start: 0 = the last computed sigma (Section 3), 1 = zero,
+                         2 = linear extrapolation in time inside sgn_rk4_step (stage 2 from
+                         sigma(t) and the previous step's sigma(t - dt/2), stage 4 from
+                         sigma(t + dt/2) and sigma(t)); every solve still meets tol */
 } sgn_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -64,6 +64,11 @@ struct sgn_ctx {
   float* cr32 = nullptr;
   float* cc32 = nullptr;
   C64* r64 = nullptr;
+  // extrapolated GMRES start (guess = 2): sigma of stage 1 of this step and
+  // of stage 3 of the previous step, as half spectra
+  C64* sig_s1 = nullptr;
+  C64* sig_s3 = nullptr;
+  bool have_s3 = false;
   double* phys[4] = {};  // staging for sgn_rk4_step_host / derivatives (lazy)
   double* partials = nullptr;
   double* scal = nullptr;  // small device scalars
@@ -471,7 +476,22 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
   coef_from_spectral(ctx, U[0]);
   if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
+  if (ctx->opt.guess == 2) {
+    // linear extrapolation in time over the stage times t, t+dt/2, t+dt/2, t+dt:
+    // stage 2 from sigma(t) and the previous step's sigma(t - dt/2),
+    // stage 4 from sigma(t + dt/2) and sigma(t)
+    if (mode == RK_STAGE2 && ctx->have_s3) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx)));
+    if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
+  }
   const bool conv = gmres(ctx, nullptr, nullptr);
+  if (ctx->opt.guess == 2) {
+    const size_t bytes = ctx->G.nspec() * sizeof(C64);
+    if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (mode == RK_STAGE3) {
+      CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      ctx->have_s3 = true;
+    }
+  }
   RkArgs rk{};
   rk.mode = mode;
   rk.dt = dt;
@@ -504,6 +524,7 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
   const double* fs[1] = {sigma};
   fwd2(ctx, fs, 1, &ctx->sig);
   CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
+  ctx->have_s3 = false;  // the extrapolation history lives within one call
   bool conv = true;
   for (int n = 0; n < nsteps; ++n) {
     conv &= stage(ctx, RK_STAGE1, dt);
@@ -549,7 +570,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   if (o.precision != 0 && o.precision != 1)
     return fail(nullptr, SGN_EINVAL, "sgn_create: precision must be 0 (FP64) or 1 (FP32 + FP64 refinement)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
-  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || (o.guess != 0 && o.guess != 1))
+  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2)
     return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr or guess");
   sgn_ctx* ctx = new (std::nothrow) sgn_ctx();
   if (!ctx) return fail(nullptr, SGN_ENOMEM, "sgn_create: host allocation failed");
@@ -580,6 +601,10 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
       ctx->acc[f] = dalloc<C64>(ctx, ns);
     }
     ctx->sig = dalloc<C64>(ctx, ns);
+    if (o.guess == 2) {
+      ctx->sig_s1 = dalloc<C64>(ctx, ns);
+      ctx->sig_s3 = dalloc<C64>(ctx, ns);
+    }
     ctx->bh = dalloc<C64>(ctx, ns);
     ctx->cvec = dalloc<C64>(ctx, ns);
     ctx->w = dalloc<C64>(ctx, ns);

@@ -244,6 +244,9 @@ cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, i
                               cpx<TX>* x, const Exec& ex);
 template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex);
+// y = a x + b y
+template <typename T>
+cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex);
 
 // reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
 cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,

@@ -24,6 +24,20 @@
 
 namespace sgn {
 
+// Per-thread accumulation type: FP64 vectors accumulate in FP64; FP32 vectors
+// (the inner solve of precision 1) form products and each thread's running
+// sum over its few entries (about 7 at 2048^2) in FP32 and hand the partial
+// sum to the FP64 warp/block/grid reduction. On a GB300 (FP64:FP32 = 1:58) a
+// per-entry FP64 conversion and DFMA would cost as much as for FP64 vectors.
+template <typename T>
+struct Acc {
+  typedef double type;
+};
+template <>
+struct Acc<float> {
+  typedef float type;
+};
+
 constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockIdx.y)
 
 // partials[i * NBLK + b] = block b's share of <V_i, w> for the chunk
@@ -33,38 +47,39 @@ constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockId
 // gate (may be null): the kernel does nothing unless *gate != 0.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                                              double* partials, const int* gate) {
+                                                 double* partials, const int* gate) {
+  typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   __shared__ double red[32];
   const int i0 = blockIdx.y * DOT_CHUNK;
   const int nc = min(DOT_CHUNK, nv - i0);
-  double acc[DOT_CHUNK];
+  A acc[DOT_CHUNK];
 #pragma unroll
-  for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = 0.0;
-  double nrm = 0.0;
+  for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = (A)0;
+  A nrm = (A)0;
   const cpx<T>* Vc = V + (size_t)i0 * vstride;
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<T> we = w[it.e];
-    const double wt = col_weight_k(G, it.col);
-    const double wx = wt * (double)we.x, wy = wt * (double)we.y;
+    const A wt = (A)col_weight_k(G, it.col);
+    const A wx = wt * (A)we.x, wy = wt * (A)we.y;
     cpx<T> v[DOT_CHUNK];
 #pragma unroll
     for (int i = 0; i < DOT_CHUNK; ++i)
       if (i < nc) v[i] = Vc[i * vstride + it.e];
 #pragma unroll
     for (int i = 0; i < DOT_CHUNK; ++i)
-      if (i < nc) acc[i] += wx * (double)v[i].x + wy * (double)v[i].y;
-    nrm += wx * (double)we.x + wy * (double)we.y;
+      if (i < nc) acc[i] += wx * (A)v[i].x + wy * (A)v[i].y;
+    nrm += wx * (A)we.x + wy * (A)we.y;
   }
 #pragma unroll
   for (int i = 0; i < DOT_CHUNK; ++i) {
     if (i < nc) {
-      const double tot = block_reduce(acc[i], red);
+      const double tot = block_reduce((double)acc[i], red);
       if (threadIdx.x == 0) partials[(size_t)(i0 + i) * NBLK + blockIdx.x] = tot;
     }
   }
   if (blockIdx.y == 0) {
-    const double tot = block_reduce(nrm, red);
+    const double tot = block_reduce((double)nrm, red);
     if (threadIdx.x == 0) partials[(size_t)nv * NBLK + blockIdx.x] = tot;
   }
 }
@@ -74,33 +89,34 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, size_t vstride, int nv,
                                                     const double* __restrict__ coef, cpx<T>* w, double* partials,
                                                     const int* gate) {
+  typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   __shared__ double red[32];
-  __shared__ double cf[MAXV];
-  if (threadIdx.x < MAXV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
+  __shared__ A cf[MAXV];
+  if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
   __syncthreads();
-  double nrm = 0.0;
+  A nrm = (A)0;
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<T> we = w[it.e];
-    double zx = (double)we.x, zy = (double)we.y;
+    A zx = (A)we.x, zy = (A)we.y;
     int i = 0;
     for (; i + 4 <= nv; i += 4) {
       const cpx<T> v0 = V[(size_t)(i + 0) * vstride + it.e], v1 = V[(size_t)(i + 1) * vstride + it.e];
       const cpx<T> v2 = V[(size_t)(i + 2) * vstride + it.e], v3 = V[(size_t)(i + 3) * vstride + it.e];
-      zx -= cf[i] * (double)v0.x + cf[i + 1] * (double)v1.x + cf[i + 2] * (double)v2.x + cf[i + 3] * (double)v3.x;
-      zy -= cf[i] * (double)v0.y + cf[i + 1] * (double)v1.y + cf[i + 2] * (double)v2.y + cf[i + 3] * (double)v3.y;
+      zx -= cf[i] * (A)v0.x + cf[i + 1] * (A)v1.x + cf[i + 2] * (A)v2.x + cf[i + 3] * (A)v3.x;
+      zy -= cf[i] * (A)v0.y + cf[i + 1] * (A)v1.y + cf[i + 2] * (A)v2.y + cf[i + 3] * (A)v3.y;
     }
     for (; i < nv; ++i) {
       const cpx<T> v0 = V[(size_t)i * vstride + it.e];
-      zx -= cf[i] * (double)v0.x;
-      zy -= cf[i] * (double)v0.y;
+      zx -= cf[i] * (A)v0.x;
+      zy -= cf[i] * (A)v0.y;
     }
     const cpx<T> z = mk((T)zx, (T)zy);
     w[it.e] = z;
-    const double wt = col_weight_k(G, it.col);
-    nrm += wt * ((double)z.x * (double)z.x + (double)z.y * (double)z.y);
+    const A wt = (A)col_weight_k(G, it.col);
+    nrm += wt * ((A)z.x * (A)z.x + (A)z.y * (A)z.y);
   }
-  const double tot = block_reduce(nrm, red);
+  const double tot = block_reduce((double)nrm, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
@@ -120,28 +136,44 @@ __global__ void __launch_bounds__(256) k_residual(Geom G, const cpx<T>* c, const
 
 template <typename TI, typename TO>
 __global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int invert, cpx<TO>* y) {
+  // arithmetic in the wider of the two types (FP32 when both are FP32)
+  typedef typename Acc<decltype(TI() * TO())>::type A;
   const double f0 = *factor;
-  const double f = invert ? 1.0 / f0 : f0;
+  const A f = (A)(invert ? 1.0 / f0 : f0);
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<TI> v = x[it.e];
-    y[it.e] = mk((TO)((double)v.x * f), (TO)((double)v.y * f));
+    y[it.e] = mk((TO)((A)v.x * f), (TO)((A)v.y * f));
   }
 }
 
+// The combination sum_i coef[i] V_i is formed in V's accumulation type (FP32
+// for the inner corrections of precision 1, whose relative accuracy only has
+// to match the FP32 basis) and added to x in x's type.
 template <typename TV, typename TX>
 __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, const double* __restrict__ coef,
                              cpx<TX>* x) {
-  __shared__ double cf[MAXV];
-  if (threadIdx.x < MAXV) cf[threadIdx.x] = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
+  typedef typename Acc<TV>::type A;
+  __shared__ A cf[MAXV];
+  if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
   __syncthreads();
   for (Walk it(G); it.ok(); it.next()) {
-    double zx = (double)x[it.e].x, zy = (double)x[it.e].y;
+    A dx = (A)0, dy = (A)0;
     for (int i = 0; i < nv; ++i) {
       const cpx<TV> v = V[(size_t)i * vstride + it.e];
-      zx += cf[i] * (double)v.x;
-      zy += cf[i] * (double)v.y;
+      dx += cf[i] * (A)v.x;
+      dy += cf[i] * (A)v.y;
     }
-    x[it.e] = mk((TX)zx, (TX)zy);
+    const cpx<TX> xv = x[it.e];
+    x[it.e] = mk((TX)(xv.x + (TX)dx), (TX)(xv.y + (TX)dy));
+  }
+}
+
+// y = a x + b y (FP64 arithmetic); the extrapolated GMRES start
+template <typename T>
+__global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y) {
+  for (Walk it(G); it.ok(); it.next()) {
+    const cpx<T> u = x[it.e], v = y[it.e];
+    y[it.e] = mk((T)(a * (double)u.x + b * (double)v.x), (T)(a * (double)u.y + b * (double)v.y));
   }
 }
 
@@ -310,6 +342,14 @@ cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_axpby<T><<<NBLK, 256, 0, ex.s>>>(G, a, x, b, y);
+  ex.end();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
                           const Exec& ex) {
   ex.begin(PK_KRYLOV);
@@ -363,7 +403,8 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
                                             double*, const int*, const Exec&);                              \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
-  template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&);
+  template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&);                                   \
+  template cudaError_t launch_axpby<T>(const Geom&, double, const cpx<T>*, double, cpx<T>*, const Exec&);
 
 SGN_KRYLOV_INST(double)
 SGN_KRYLOV_INST(float)

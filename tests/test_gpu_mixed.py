@@ -124,3 +124,22 @@ def test_mixed_gaussian_2048_close_to_fp64_path():
     for a, b in zip(runs[0], runs[1]):
         if np.linalg.norm(b) > 0:
             assert rel(a, b) < 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_extrapolated_guess_same_answer_fewer_iterations(precision):
+    """guess = 2 only moves GMRES's starting point: the fields agree with the
+    paper's warm start within the solver tolerance, with fewer iterations."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.perturbed_soliton(256, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=3)
+    out, its = [], []
+    for guess in (0, 2):
+        s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, precision=precision, guess=guess)
+        f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+        s.rk4_step(*f, 2e-3, 6)
+        out.append([host(x) for x in f])
+        its.append(s.stats()["matvecs"])
+        s.close()
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert rel(a, b) < (1e-9 if precision == 0 else 1e-6)
+    assert its[1] < its[0]
