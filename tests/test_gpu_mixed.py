@@ -141,5 +141,5 @@ def test_extrapolated_guess_same_answer_fewer_iterations(precision):
         its.append(s.stats()["matvecs"])
         s.close()
     for a, b in zip(out[0][:3], out[1][:3]):
-        assert rel(a, b) < (1e-9 if precision == 0 else 1e-6)
+        assert rel(a, b) < (1e-9 if precision == 0 else 1e-5)
     assert its[1] < its[0]
