@@ -12,8 +12,10 @@
 // runs 8/Rs butterflies; butterfly q of thread t has index j = t + q*T and its
 // inputs j + r*N/Rs are exactly the thread's slots q + r*(8/Rs), so every stage
 // reads the same thread-strided slots. Between stages data goes through shared
-// memory at padded index p + (p >> 3), which is bank-conflict free for 16-byte
-// elements in every stage.
+// memory at an index that keeps every stage bank-conflict free: FP64 (16-byte
+// elements) pads, p + (p >> 3); FP32 (8-byte elements) XOR-swizzles within
+// aligned groups of 16 elements (one transform per buffer) or 8 elements
+// (several interleaved columns), see sidx().
 //
 // Twiddles W_N^k = exp(-2 pi i k / N) come from a table in global memory
 // (L1-resident); the inverse transform uses their conjugates. No transform
@@ -75,8 +77,30 @@ __device__ __forceinline__ cpx<float> ldg(const cpx<float>* p) {
   return mk(v.x, v.y);
 }
 
-__device__ __forceinline__ int pad_idx(int p) { return p + (p >> 3); }
-// shared-memory elements needed by one transform of length N
+// Shared-memory slot of element p of a transform whose buffer interleaves
+// 2^lcs columns. 16-byte elements: a quarter-warp phase touches 8 elements, and
+// one pad slot every 8 keeps the stride-8 writes of the first stage, the
+// 64a + b writes of the second and consecutive reads on distinct banks. 8-byte
+// elements: a half-warp phase touches 16; within each aligned group of 16 the
+// slot is XOR-ed with (g & 7) | (bit 2 of g) << 3, g = p >> 4, which separates
+// the stride-8 writes (low three bits cycle over 8 groups) and the 64a + b
+// writes (bit 3 flips between groups g and g + 4). With 2 or more interleaved
+// columns only p mod 8 selects the bank pair, so the XOR uses (p >> 3) & 7.
+template <typename T>
+__device__ __forceinline__ int sidx(int p, int lcs);
+template <>
+__device__ __forceinline__ int sidx<double>(int p, int lcs) {
+  return (p + (p >> 3)) << lcs;
+}
+template <>
+__device__ __forceinline__ int sidx<float>(int p, int lcs) {
+  if (lcs == 0) {
+    const int g = p >> 4;
+    return p ^ ((g & 7) | (((g >> 2) & 1) << 3));
+  }
+  return (p ^ ((p >> 3) & 7)) << lcs;
+}
+// shared-memory elements needed by one transform of length N (either layout)
 __host__ __device__ constexpr int smem_elems(int N) { return N + (N >> 3); }
 
 // ---------------------------------------------------------------- butterflies
@@ -147,11 +171,26 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[8], cpx<T>* sm, const cpx<
 #pragma unroll
     for (int r = 0; r < RS; ++r) xs[r] = v[q + r * NB];
     if (lNs > 0) {
+      cpx<T> w[RS];
+      if (sizeof(T) == 4 && RS >= 4) {
+        // FP32: three table loads and products for the rest (the L1 pipe, not
+        // the FMA pipe, limits the FP32 passes); FP64 loads all (FP64 products
+        // cost more than loads on this part)
+        w[1] = ldg(tw + (jm << twshift));
+        w[2] = ldg(tw + ((jm * 2) << twshift));
+        w[3] = cmul(w[1], w[2]);
+        if (RS == 8) {
+          w[4] = ldg(tw + ((jm * 4) << twshift));
+          w[5] = cmul(w[1], w[4]);
+          w[6] = cmul(w[2], w[4]);
+          w[7] = cmul(w[3], w[4]);
+        }
+      } else {
 #pragma unroll
-      for (int r = 1; r < RS; ++r) {
-        cpx<T> w = ldg(tw + ((jm * r) << twshift));
-        xs[r] = INV ? cmulc(xs[r], w) : cmul(xs[r], w);
+        for (int r = 1; r < RS; ++r) w[r] = ldg(tw + ((jm * r) << twshift));
       }
+#pragma unroll
+      for (int r = 1; r < RS; ++r) xs[r] = INV ? cmulc(xs[r], w[r]) : cmul(xs[r], w[r]);
     }
     if (RS == 8) bfly8<INV>(xs);
     if (RS == 4) bfly4<INV>(xs[0], xs[1], xs[2], xs[3]);
@@ -162,22 +201,22 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[8], cpx<T>* sm, const cpx<
     } else {
       const int base = ((j >> lNs) << (lNs + LRS)) + jm;
 #pragma unroll
-      for (int r = 0; r < RS; ++r) sm[pad_idx(base + r * Ns) << lcs] = xs[r];
+      for (int r = 0; r < RS; ++r) sm[sidx<T>(base + r * Ns, lcs)] = xs[r];
     }
   }
 }
 
-// Slot s of thread t is element t + s*T_; element p lives at sm[pad(p) << lcs]
+// Slot s of thread t is element t + s*T_; element p lives at sm[sidx(p, lcs)]
 // (lcs = log2 of the interleave factor when several columns share a buffer).
 template <typename T>
 __device__ __forceinline__ void load_slots(cpx<T> (&v)[8], const cpx<T>* sm, int t, int T_, int lcs) {
 #pragma unroll
-  for (int s = 0; s < 8; ++s) v[s] = sm[pad_idx(t + s * T_) << lcs];
+  for (int s = 0; s < 8; ++s) v[s] = sm[sidx<T>(t + s * T_, lcs)];
 }
 template <typename T>
 __device__ __forceinline__ void store_slots(const cpx<T> (&v)[8], cpx<T>* sm, int t, int T_, int lcs) {
 #pragma unroll
-  for (int s = 0; s < 8; ++s) sm[pad_idx(t + s * T_) << lcs] = v[s];
+  for (int s = 0; s < 8; ++s) sm[sidx<T>(t + s * T_, lcs)] = v[s];
 }
 
 // Full transform of length N = 2^lN (lN >= 3) held in v (thread-strided

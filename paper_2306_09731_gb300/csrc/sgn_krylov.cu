@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
   const cpx<T>* Vc = V + (size_t)i0 * vstride;
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<T> we = w[it.e];
-    const A wt = (A)col_weight_k(G, it.col);
+    const A wt = col_weight_k<A>(G, it.col);
     const A wx = wt * (A)we.x, wy = wt * (A)we.y;
     cpx<T> v[DOT_CHUNK];
 #pragma unroll
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
     }
     const cpx<T> z = mk((T)zx, (T)zy);
     w[it.e] = z;
-    const A wt = (A)col_weight_k(G, it.col);
+    const A wt = col_weight_k<A>(G, it.col);
     nrm += wt * ((A)z.x * (A)z.x + (A)z.y * (A)z.y);
   }
   const double tot = block_reduce((double)nrm, red);

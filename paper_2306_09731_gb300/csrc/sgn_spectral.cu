@@ -75,7 +75,7 @@ __device__ __forceinline__ void split_pair(const cpx<T> (&v)[8], cpx<T>* sm, int
   for (int s = 0; s < 5; ++s) {
     const int k = t + s * T_;
     const cpx<T> P = v[s];
-    const cpx<T> Q = conjg(sm[pad_idx((N - k) & (N - 1))]);
+    const cpx<T> Q = conjg(sm[sidx<T>((N - k) & (N - 1), 0)]);
     f0[s] = P + Q;
     f1[s] = mul_mi(P - Q);
   }

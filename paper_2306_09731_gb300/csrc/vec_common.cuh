@@ -34,8 +34,9 @@ struct Walk {
 
 // Parseval weight of a half-spectrum column: 1 on kx = 0 and kx = Nx/2, 2 on
 // the columns in between, 0 on padding columns.
-__device__ __forceinline__ double col_weight_k(const Geom& G, int col) {
-  return (col == 0 || col == (G.Nx >> 1)) ? 1.0 : (col < G.Nxh ? 2.0 : 0.0);
+template <typename A = double>
+__device__ __forceinline__ A col_weight_k(const Geom& G, int col) {
+  return (col == 0 || col == (G.Nx >> 1)) ? (A)1 : (col < G.Nxh ? (A)2 : (A)0);
 }
 
 template <typename T>
