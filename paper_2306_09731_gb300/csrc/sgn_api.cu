@@ -77,6 +77,7 @@ struct sgn_ctx {
   GmresReadback* rb_host = nullptr;  // pinned
   double* inv_host = nullptr;        // pinned, 4 doubles
   int* flags = nullptr;
+  unsigned* counters = nullptr;  // last-block reduction tickets (zeroed, self-resetting)
   Prof prof;
   bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
   std::vector<void*> allocs;
@@ -268,6 +269,27 @@ void coef_from_spectral(sgn_ctx* ctx, const C64* hh) {
                             EX(ctx)));
 }
 
+// One Arnoldi step of the inner or outer GMRES on the basis V (type T):
+// w = A V_j, classical Gram-Schmidt with DGKS reorthogonalisation, Givens.
+// Returns the residual estimate and H[j+1][j] through the readback.
+template <typename T>
+void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, cpx<T>* V, cpx<T>* w,
+                  cpx<T>* const* tmp, int j) {
+  const Geom& G = ctx->G;
+  const size_t vs = G.nspec();
+  const int nv = j + 1;
+  CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx)));
+  const int* gate = &ctx->gst->reorth;
+  unsigned* cnt = ctx->counters;
+  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx)));
+  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, j, 1, cnt + 1,
+                          ctx->rb_dev, ctx->flags, EX(ctx)));
+  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx)));
+  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, j, 2, cnt + 3,
+                          ctx->rb_dev, ctx->flags, EX(ctx)));
+  sync_read(ctx);
+}
+
 // --------------------------------------------------------------- GMRES
 // Left-preconditioned restarted GMRES on A = M^-1 L, c = M^-1 b (Section 3).
 // Uses ctx->h/cr/cc, ctx->bh (b_hat); ctx->sig is the guess and the result.
@@ -318,23 +340,8 @@ bool gmres_fp64(sgn_ctx* ctx, int* iters_out, double* relres_out) {
     CK(launch_gmres_start(ctx->gst, beta_d, EX(ctx)));
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      C64* Vj = V + (size_t)j * vs;
-      const int nv = j + 1;
-      CK(launch_matvec<double>(G, ctx->tb, Vj, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+      arnoldi_step<double>(ctx, ctx->tb, ctx->cr, ctx->cc, V, ctx->w, ctx->tmp, j);
       ++its;
-      // classical Gram-Schmidt, second pass only if the DGKS test asks for it
-      const int* gate = &ctx->gst->reorth;
-      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, nullptr, EX(ctx)));
-      CK(launch_reduce(ctx->partials, nv + 1, ctx->gst->h1, false, nullptr, EX(ctx)));
-      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h1, ctx->w, ctx->partials, nullptr, EX(ctx)));
-      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, nullptr, EX(ctx)));
-      CK(launch_reorth_decide(ctx->gst, nv, EX(ctx)));
-      CK(launch_dots<double>(G, V, vs, nv, ctx->w, ctx->partials, gate, EX(ctx)));
-      CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, gate, EX(ctx)));
-      CK(launch_cgs_update<double>(G, V, vs, nv, ctx->gst->h2, ctx->w, ctx->partials, gate, EX(ctx)));
-      CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, gate, EX(ctx)));
-      CK(launch_givens(ctx->gst, j, ctx->rb_dev, ctx->flags, EX(ctx)));
-      sync_read(ctx);
       res = ctx->rb_host->res;
       const double hnext = ctx->rb_host->hnext;
       k = j + 1;
@@ -356,30 +363,6 @@ bool gmres_fp64(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   if (iters_out) *iters_out = its;
   if (relres_out) *relres_out = res / cnorm;
   return conv;
-}
-
-// One Arnoldi step of the inner or outer GMRES on the basis V (type T):
-// w = A V_j, classical Gram-Schmidt with DGKS reorthogonalisation, Givens.
-// Returns the residual estimate and H[j+1][j] through the readback.
-template <typename T>
-void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, cpx<T>* V, cpx<T>* w,
-                  cpx<T>* const* tmp, int j) {
-  const Geom& G = ctx->G;
-  const size_t vs = G.nspec();
-  const int nv = j + 1;
-  CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx)));
-  const int* gate = &ctx->gst->reorth;
-  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, EX(ctx)));
-  CK(launch_reduce(ctx->partials, nv + 1, ctx->gst->h1, false, nullptr, EX(ctx)));
-  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, EX(ctx)));
-  CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, nullptr, EX(ctx)));
-  CK(launch_reorth_decide(ctx->gst, nv, EX(ctx)));
-  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, EX(ctx)));
-  CK(launch_reduce(ctx->partials, nv, ctx->gst->h2, false, gate, EX(ctx)));
-  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, EX(ctx)));
-  CK(launch_reduce(ctx->partials, 1, &ctx->gst->nrm2, false, gate, EX(ctx)));
-  CK(launch_givens(ctx->gst, j, ctx->rb_dev, ctx->flags, EX(ctx)));
-  sync_read(ctx);
 }
 
 // Mixed-precision GMRES (precision = 1), iterative refinement: each sweep
@@ -628,6 +611,8 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->gst = dalloc<GmresDev>(ctx, 1);
     ctx->rb_dev = dalloc<GmresReadback>(ctx, 1);
     ctx->flags = dalloc<int>(ctx, 1);
+    ctx->counters = dalloc<unsigned>(ctx, 8);
+    CK(cudaMemset(ctx->counters, 0, 8 * sizeof(unsigned)));
     CK(cudaMallocHost((void**)&ctx->rb_host, sizeof(GmresReadback)));
     CK(cudaMallocHost((void**)&ctx->inv_host, 4 * sizeof(double)));
     CK(cudaMemset(ctx->flags, 0, sizeof(int)));

@@ -222,14 +222,19 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
                            double* partials, const Exec& ex);
 
 // ---- Krylov vector kernels (spectral vectors, Parseval-weighted inner product)
-// partial <V_i, w> (slots 0..nv-1) and |w|^2 (slot nv); gate: run only if *gate != 0 (may be null)
+// out[i] = <V_i, w> (i < nv) and out[nv] = |w|^2, reduced by the last block
+// to finish; gate: run only if *gate != 0 (may be null). counter: a zeroed
+// device word private to this call site (left zeroed).
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const int* gate, const Exec& ex);
-// w -= sum_i coef[i] V_i and partial |w_new|^2 (slot 0); gated like launch_dots
+                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex);
+// Gram-Schmidt update w -= sum_i coef[i] V_i of Arnoldi step j; the last block
+// stores |w'|^2, takes the DGKS decision (pass 1) and runs the Givens step once
+// the orthogonalisation is final (pass 1 without reorthogonalisation, or pass 2).
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* w, double* partials, const int* gate, const Exec& ex);
+                              cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
+                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex);
 // r = c - w, and partial squared norm of r
 template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,

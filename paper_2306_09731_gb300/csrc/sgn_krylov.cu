@@ -24,6 +24,60 @@
 
 namespace sgn {
 
+// Givens update of column j of the Hessenberg matrix (one thread): the column
+// from the two Gram-Schmidt passes and |w|, previous rotations, a new rotation
+// zeroing H[j+1][j], and the residual estimate |g_{j+1}| into the readback.
+__device__ void givens_step(GmresDev* st, int j, GmresReadback* rb, const int* flags) {
+  const int ld = MAXM + 1;
+  double* Hj = st->H + (size_t)j * ld;
+  for (int i = 0; i <= j; ++i) Hj[i] = st->h1[i] + st->h2[i];
+  const double hn = sqrt(st->nrm2);
+  Hj[j + 1] = hn;
+  st->hnext = hn;
+  st->inv_hnext = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double a = Hj[i], b = Hj[i + 1];
+    Hj[i] = st->cs[i] * a + st->sn[i] * b;
+    Hj[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+  }
+  const double d = hypot(Hj[j], Hj[j + 1]);
+  const double c = d > 0.0 ? Hj[j] / d : 1.0;
+  const double s = d > 0.0 ? Hj[j + 1] / d : 0.0;
+  st->cs[j] = c;
+  st->sn[j] = s;
+  Hj[j] = d;
+  Hj[j + 1] = 0.0;
+  st->g[j + 1] = -s * st->g[j];
+  st->g[j] = c * st->g[j];
+  st->res = fabs(st->g[j + 1]);
+  rb->res = st->res;
+  rb->hnext = hn;
+  rb->flags = flags ? *flags : 0;
+}
+
+// True (in every thread) in the block that finishes last; it then sees every
+// other block's partials. Resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y;
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == total - 1) ? 1 : 0;
+    if (s_last) *counter = 0u;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Fixed-order sum over the NBLK block partials of one slot (valid on thread 0).
+__device__ __forceinline__ double reduce_slot(const double* partials, int slot, double* red) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < NBLK; b += blockDim.x) v += __ldcg(partials + (size_t)slot * NBLK + b);
+  return block_reduce(v, red);
+}
+
 // Per-thread accumulation type: FP64 vectors accumulate in FP64; FP32 vectors
 // (the inner solve of precision 1) form products and each thread's running
 // sum over its few entries (about 7 at 2048^2) in FP32 and hand the partial
@@ -47,7 +101,8 @@ constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockId
 // gate (may be null): the kernel does nothing unless *gate != 0.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                                                 double* partials, const int* gate) {
+                                                 double* partials, const int* gate, double* out,
+                                                 unsigned* counter) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   __shared__ double red[32];
@@ -82,13 +137,21 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
     const double tot = block_reduce((double)nrm, red);
     if (threadIdx.x == 0) partials[(size_t)nv * NBLK + blockIdx.x] = tot;
   }
+  // the last block combines all partials: out[i] = <V_i, w>, out[nv] = |w|^2
+  if (last_block(counter)) {
+    for (int i = 0; i <= nv; ++i) {
+      const double tot = reduce_slot(partials, i, red);
+      if (threadIdx.x == 0) out[i] = tot;
+    }
+  }
 }
 
 // w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, size_t vstride, int nv,
                                                     const double* __restrict__ coef, cpx<T>* w, double* partials,
-                                                    const int* gate) {
+                                                    const int* gate, GmresDev* st, int j, int pass,
+                                                    unsigned* counter, GmresReadback* rb, const int* flags) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   __shared__ double red[32];
@@ -118,6 +181,24 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
   }
   const double tot = block_reduce((double)nrm, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  // the last block: |w'|^2, then (first pass) the DGKS test, and the Givens
+  // step once the orthogonalisation is final
+  if (last_block(counter)) {
+    const double n2 = reduce_slot(partials, 0, red);
+    if (threadIdx.x == 0) {
+      st->nrm2 = n2;
+      bool final_pass = (pass == 2);
+      if (pass == 1) {
+        const int need = (n2 < 0.5 * st->h1[nv]) ? 1 : 0;
+        st->reorth = need;
+        if (!need) {
+          for (int i = 0; i <= MAXV; ++i) st->h2[i] = 0.0;
+          final_pass = true;
+        }
+      }
+      if (final_pass) givens_step(st, j, rb, flags);
+    }
+  }
 }
 
 template <typename T>
@@ -221,31 +302,7 @@ __global__ void k_gmres_start(GmresDev* st, const double* beta) {
 // estimate |g_{j+1}|.
 __global__ void k_givens(GmresDev* st, int j, GmresReadback* rb, const int* flags) {
   if (threadIdx.x != 0) return;
-  const int ld = MAXM + 1;
-  double* Hj = st->H + (size_t)j * ld;
-  for (int i = 0; i <= j; ++i) Hj[i] = st->h1[i] + st->h2[i];
-  const double hn = sqrt(st->nrm2);
-  Hj[j + 1] = hn;
-  st->hnext = hn;
-  st->inv_hnext = hn > 0.0 ? 1.0 / hn : 0.0;
-  for (int i = 0; i < j; ++i) {
-    const double a = Hj[i], b = Hj[i + 1];
-    Hj[i] = st->cs[i] * a + st->sn[i] * b;
-    Hj[i + 1] = -st->sn[i] * a + st->cs[i] * b;
-  }
-  const double d = hypot(Hj[j], Hj[j + 1]);
-  const double c = d > 0.0 ? Hj[j] / d : 1.0;
-  const double s = d > 0.0 ? Hj[j + 1] / d : 0.0;
-  st->cs[j] = c;
-  st->sn[j] = s;
-  Hj[j] = d;
-  Hj[j + 1] = 0.0;
-  st->g[j + 1] = -s * st->g[j];
-  st->g[j] = c * st->g[j];
-  st->res = fabs(st->g[j + 1]);
-  rb->res = st->res;
-  rb->hnext = hn;
-  rb->flags = flags ? *flags : 0;
+  givens_step(st, j, rb, flags);
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution
@@ -294,19 +351,21 @@ __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h,
 
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const int* gate, const Exec& ex) {
+                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex) {
   dim3 grid(NBLK, (nv + DOT_CHUNK - 1) / DOT_CHUNK);
   if (grid.y == 0) grid.y = 1;
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate);
+  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter);
   ex.end();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
-                              cpx<T>* w, double* partials, const int* gate, const Exec& ex) {
+                              cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
+                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_cgs_update<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate);
+  k_cgs_update<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate, st, j, pass, counter, rb,
+                                         flags);
   ex.end();
   return cudaGetLastError();
 }
@@ -398,9 +457,10 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
 
 #define SGN_KRYLOV_INST(T)                                                                                   \
   template cudaError_t launch_dots<T>(const Geom&, const cpx<T>*, size_t, int, const cpx<T>*, double*,       \
-                                      const int*, const Exec&);                                             \
+                                      const int*, double*, unsigned*, const Exec&);                         \
   template cudaError_t launch_cgs_update<T>(const Geom&, const cpx<T>*, size_t, int, const double*, cpx<T>*, \
-                                            double*, const int*, const Exec&);                              \
+                                            double*, const int*, GmresDev*, int, int, unsigned*,            \
+                                            GmresReadback*, const int*, const Exec&);                       \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
   template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&);                                   \

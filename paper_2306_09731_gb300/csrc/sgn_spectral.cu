@@ -225,11 +225,19 @@ __global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, 
 
 // ---------------------------------------------------------- fused matvec x
 
+// Resident 256-thread blocks per SM the x-passes ask the compiler for: the
+// FP32 passes are latency bound and need the warps; the FP64 ones are
+// FP64-issue bound and keep their registers.
+template <typename T>
+constexpr int mv_min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+template <typename T>
+constexpr int rhs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
+
 // S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
 // Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
 // reads only its own row pair before writing it: Cout/Byout may alias S/Sy.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+__global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
                                                const T* __restrict__ cc, cpx<T>* Cout, cpx<T>* Byout) {
   const XLayout L = x_layout(G);
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(256) k_mv_x(Geom G, const cpx<T>* __restrict__
 // depth anomaly hh = h - 1. Writes Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and
 // Fh = F^x with F = |v|^2/2 - |grad sigma|^2/(2h^2) + g (h - 1) - 9 sigma^2/(2h^4).
 template <typename T>
-__global__ void __launch_bounds__(256) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+__global__ void __launch_bounds__(256, rhs_min_blocks<T>()) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                 const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
                                                 const cpx<T>* Sy, const T* __restrict__ hh,
                                                 const T* __restrict__ cr, T g, cpx<T>* Cq, cpx<T>* Qy,
