@@ -201,6 +201,19 @@ struct RkArgs {
   double krasny_thr;
   double g;
 };
+// Arguments of the RK4 stage-update kernel.
+template <typename T, typename S>
+struct RkK {
+  const cpx<T>* K[3];
+  cpx<S>* Un[3];
+  cpx<S>* Unext[3];
+  cpx<S>* acc[3];
+  cpx<S>* b;
+  const S* kxs;
+  const S* kys;
+  RkArgs rk;
+};
+
 // T: compute type of the passes (tmp, h, cr); S: storage type of the state,
 // sigma_hat and b_hat (FP64 in both modes).
 template <typename T, typename S>

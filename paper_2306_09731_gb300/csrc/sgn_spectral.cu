@@ -413,10 +413,13 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // Column tile: C = blockDim / (Ny/8) neighbouring kx columns, thread index
 // c + C*t. Each input column is transformed in registers; the epilogue gets
 // all NIN results of the thread's 8 rows.
-constexpr int ypass_threads(int nin) { return nin >= 3 ? 256 : 512; }
+// Threads of a y-pass block: FP64 passes with 3 or 4 transforms per thread need
+// the registers of 256-thread blocks; FP32 ones fit 512 (two columns per block,
+// twice the bytes per row segment).
+constexpr int ypass_threads(int nin, int tbytes) { return (nin >= 3 && tbytes == 8) ? 256 : 512; }
 
 template <typename T, bool INV, int NIN, class Epi, typename S = T>
-__global__ void __launch_bounds__(ypass_threads(NIN)) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
+__global__ void __launch_bounds__(ypass_threads(NIN, sizeof(T))) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
                                                 YIn<T, NIN, S> in, Epi epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
@@ -477,28 +480,21 @@ struct EpiMatvec {
   }
 };
 
-// K = (h_t, vx_t, vy_t) from r0 = Cq^y, r1 = Qy^y, r2 = F^y, then the RK4
-// stage update and b_hat = -(i kx vx + i ky vy) of the next stage state.
-// K is formed in the compute type T; the state (Un, Unext, acc, b) is stored
-// and updated in S (FP64 in both precision modes).
-template <typename T, typename S = T>
-struct EpiRHS {
-  cpx<S>* K[3];      // RK_STORE_K output
-  cpx<S>* Un[3];     // step-start state (RK_FINAL: updated in place)
-  cpx<S>* Unext[3];  // next stage state (stages 1-3)
-  cpx<S>* acc[3];    // running sum of b_s K_s
-  cpx<S>* b;         // next b_hat (may be null)
+// K = (h_t, vx_t, vy_t) from r0 = Cq^y, r1 = Qy^y, r2 = F^y:
+// h_t = -i kx (h u_x)^ - i ky (h u_y)^, v_t = -i k F^ (2/3-masked if asked).
+// Stored in the pass's type; the RK4 stage update is a separate flat kernel
+// (k_rk_update) so that the FP64 state is read and written with coalesced rows
+// rather than in the column layout of this pass.
+template <typename T>
+struct EpiK {
+  cpx<T>* K[3];
   const T* kx;
-  const S* kxs;      // wavenumbers in the state type
-  const S* kys;
-  RkArgs rk;
+  int dealias;
   __device__ __forceinline__ void operator()(cpx<T> (&r)[3][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
     const T kxv = __ldg(kx + col);
-    const S kxs_v = __ldg(kxs + col);
-    const bool keepx = !rk.dealias || 3 * col <= G.Nx;
-    const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
+    const bool keepx = !dealias || 3 * col <= G.Nx;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
@@ -507,7 +503,7 @@ struct EpiRHS {
       cpx<T> k0 = r[0][s] - mul_ik(r[1][s], kyv);
       cpx<T> k1 = mul_ik(r[2][s], -kxv);
       cpx<T> k2 = mul_ik(r[2][s], -kyv);
-      if (rk.dealias) {
+      if (dealias) {
         const int my = row <= (G.Ny >> 1) ? row : G.Ny - row;
         if (!keepx || 3 * my > G.Ny) {
           k0 = mk((T)0, (T)0);
@@ -515,35 +511,57 @@ struct EpiRHS {
           k2 = k0;
         }
       }
-      cpx<S> kk[3] = {mk((S)k0.x, (S)k0.y), mk((S)k1.x, (S)k1.y), mk((S)k2.x, (S)k2.y)};
-      if (rk.mode == RK_STORE_K) {
-#pragma unroll
-        for (int f = 0; f < 3; ++f) K[f][e] = kk[f];
-        continue;
-      }
-      cpx<S> u[3];
-      if (rk.mode == RK_FINAL) {
-        const S c6 = (S)(rk.dt / 6.0);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-          cpx<S> z = Un[f][e] + scl(acc[f][e] + kk[f], c6);
-          if (rk.krasny && (double)z.x * z.x + (double)z.y * z.y < thr2) z = mk((S)0, (S)0);
-          Un[f][e] = z;
-          u[f] = z;
-        }
-      } else {
-        const S cdt = (S)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-          acc[f][e] = (rk.mode == RK_STAGE1) ? kk[f] : acc[f][e] + scl(kk[f], (S)2);
-          u[f] = Un[f][e] + scl(kk[f], cdt);
-          Unext[f][e] = u[f];
-        }
-      }
-      if (b) b[e] = mul_ik(u[1], -kxs_v) - mul_ik(u[2], __ldg(kys + row));
+      K[0][e] = k0;
+      K[1][e] = k1;
+      K[2][e] = k2;
     }
   }
 };
+
+// RK4 stage update (Section 3) on the state type S from K in type T, then
+// b_hat = -(i kx vx + i ky vy) of the next stage state:
+//   stage 1: acc = K,    U_s = U_n + dt/2 K;   stage 2: acc += 2K, U_s = U_n + dt/2 K
+//   stage 3: acc += 2K,  U_s = U_n + dt K;     final:   U_n += dt/6 (acc + K), Krasny
+//   RK_STORE_K: acc = K (one RHS evaluation)
+template <typename T, typename S>
+__global__ void k_rk_update(Geom G, RkK<T, S> a) {
+  const RkArgs rk = a.rk;
+  const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
+  const S c6 = (S)(rk.dt / 6.0);
+  const S cdt = (S)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
+  for (Walk it(G); it.ok(); it.next()) {
+    const size_t e = it.e;
+    cpx<S> kk[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) kk[f] = mk((S)a.K[f][e].x, (S)a.K[f][e].y);
+    if (rk.mode == RK_STORE_K) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) a.acc[f][e] = kk[f];
+      continue;
+    }
+    cpx<S> u[3];
+    if (rk.mode == RK_FINAL) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        cpx<S> z = a.Un[f][e] + scl(a.acc[f][e] + kk[f], c6);
+        if (rk.krasny && (double)z.x * z.x + (double)z.y * z.y < thr2) z = mk((S)0, (S)0);
+        a.Un[f][e] = z;
+        u[f] = z;
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        a.acc[f][e] = (rk.mode == RK_STAGE1) ? kk[f] : a.acc[f][e] + scl(kk[f], (S)2);
+        u[f] = a.Un[f][e] + scl(kk[f], cdt);
+        a.Unext[f][e] = u[f];
+      }
+    }
+    if (a.b) {
+      const S kxv = it.col < G.Nxh ? __ldg(a.kxs + it.col) : (S)0;
+      a.b[e] = mul_ik(u[1], -kxv) - mul_ik(u[2], __ldg(a.kys + it.row));
+    }
+  }
+}
 
 // The kx = 0 and kx = Nx/2 columns of the half spectrum of a real field are
 // Hermitian in ky: x(-ky) = conj(x(ky)), real at ky = 0 and ky = Ny/2. The
@@ -600,7 +618,7 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
 template <typename T>
 static inline void y_config(const Geom& G, int nin, dim3& grid, dim3& block, size_t& smem) {
   const int Tn = G.Ny >> 3;
-  const int tpb = ypass_threads(nin);
+  const int tpb = ypass_threads(nin, sizeof(T));
   int C = tpb / Tn;
   if (C < 1) C = 1;
   if (C > 64) C = 64;
@@ -628,10 +646,9 @@ void init_kernel_attributes() {
   set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>>);
   set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>>);
   set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>>);
-  set_smem<T>((const void*)k_ypass<T, false, 3, EpiRHS<T>>);
+  set_smem<T>((const void*)k_ypass<T, false, 3, EpiK<T>>);
   set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>, double>);
   set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>, double>);
-  set_smem<T>((const void*)k_ypass<T, false, 3, EpiRHS<T, double>>);
   cudaGetLastError();
 }
 
@@ -791,20 +808,30 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
     yi.src[2] = tmp[2];
-    EpiRHS<T, S> ep{};
-    for (int f = 0; f < 3; ++f) {
-      ep.K[f] = acc[f];
-      ep.Un[f] = Un[f];
-      ep.Unext[f] = Unext ? Unext[f] : nullptr;
-      ep.acc[f] = acc[f];
-    }
-    ep.b = bhat;
+    // K overwrites the three inputs column by column (each block reads its
+    // columns completely before writing them)
+    EpiK<T> ep{};
+    for (int f = 0; f < 3; ++f) ep.K[f] = tmp[f];
     ep.kx = tb.kx;
-    ep.kxs = tbs.kx;
-    ep.kys = tbs.ky;
-    ep.rk = rk;
+    ep.dealias = rk.dealias;
     ex.begin(PK_RHS_YFWD);
-    k_ypass<T, false, 3, EpiRHS<T, S>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, false, 3, EpiK<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  }
+  {
+    RkK<T, S> a{};
+    for (int f = 0; f < 3; ++f) {
+      a.K[f] = tmp[f];
+      a.Un[f] = Un[f];
+      a.Unext[f] = Unext ? Unext[f] : nullptr;
+      a.acc[f] = acc[f];
+    }
+    a.b = bhat;
+    a.kxs = tbs.kx;
+    a.kys = tbs.ky;
+    a.rk = rk;
+    ex.begin(PK_RHS_YFWD);
+    k_rk_update<T, S><<<NBLK, 256, 0, ex.s>>>(G, a);
     ex.end();
   }
   return cudaGetLastError();
