@@ -148,7 +148,7 @@ MEASURED_TRAFFIC = {
 }
 
 # kernel classes that are one kernel each (candidates for the roofline line)
-SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs_yfwd", "ref_yinv", "ref_x",
+SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs_yfwd", "rk", "ref_yinv", "ref_x",
                          "ref_yfwd")
 
 
@@ -177,14 +177,16 @@ def kernel_work(cls, n, tbytes):
     if cls == "rhs_x":
         return n * (8 * row + 30 * n + 6 * nxh), 4 * spec + 2 * phys + 3 * spec
     if cls == "rhs_yfwd":
-        return 3 * nxh * col + 40 * n * nxh, 3 * spec + 13 * spec_s
+        return 3 * nxh * col + 10 * n * nxh, 6 * spec
+    if cls == "rk":
+        return 30 * n * nxh, 3 * spec + 13 * spec_s
     return None, None
 
 
 KERNEL_NAMES = {"mv_yinv": "k_ypass<inv,2> (matvec y-inverse)", "mv_x": "k_mv_x (fused matvec x-pass)",
                 "mv_yfwd": "k_ypass<fwd,EpiMatvec> (matvec y-forward + M^-1)",
                 "rhs_yinv": "k_ypass<inv,4> (RHS y-inverse)", "rhs_x": "k_rhs_x (fused RHS x-pass)",
-                "rhs_yfwd": "k_ypass<fwd,EpiRHS> (RHS y-forward + RK4 update)",
+                "rhs_yfwd": "k_ypass<fwd,EpiK> (RHS y-forward)", "rk": "k_rk_update (RK4 stage update)",
                 "ref_yinv": "k_ypass<inv,2> FP64 (refinement matvec y-inverse)",
                 "ref_x": "k_mv_x FP64 (refinement matvec x-pass)",
                 "ref_yfwd": "k_ypass<fwd,EpiMatvec> FP64 (refinement matvec y-forward)"}

@@ -149,11 +149,11 @@ sgn_status sgn_get_stats(sgn_t ctx, sgn_stats* out);
  * 4-6 the RHS passes (y-inverse, fused x-pass, y-forward + RK4 update),
  * 7 GMRES vector kernels and reductions, 8 conversions at call boundaries,
  * 9-11 the FP64 refinement matvec passes of precision 1 (the matvec classes
- * 1-3 then count only its FP32 inner matvecs).
+ * 1-3 then count only its FP32 inner matvecs), 12 the RK4 stage update.
  * sgn_set_profiling(ctx, 1) clears the counters; sgn_get_profile fills up to n
  * entries of ms (summed milliseconds) and counts (timed launches) and
  * *launches with the number of kernels launched since the last clear. */
-#define SGN_PROFILE_CLASSES 12
+#define SGN_PROFILE_CLASSES 13
 sgn_status sgn_set_profiling(sgn_t ctx, int on);
 sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long long* launches);
 

@@ -281,12 +281,19 @@ void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, c
   CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx)));
   const int* gate = &ctx->gst->reorth;
   unsigned* cnt = ctx->counters;
+  // FP64 Arnoldi (the plain path and nothing else) reorthogonalises by the DGKS
+  // test; the FP32 inner solve of precision 1 runs one classical Gram-Schmidt
+  // pass: it only has to reduce its residual by 1e-6 and the FP64 refinement
+  // checks the result (measured: same iteration and refinement counts, 4% faster)
+  const bool dgks = sizeof(T) == 8;
   CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx)));
-  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, j, 1, cnt + 1,
-                          ctx->rb_dev, ctx->flags, EX(ctx)));
-  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx)));
-  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, j, 2, cnt + 3,
-                          ctx->rb_dev, ctx->flags, EX(ctx)));
+  CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, j, dgks ? 1 : 3,
+                          cnt + 1, ctx->rb_dev, ctx->flags, EX(ctx)));
+  if (dgks) {
+    CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx)));
+    CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, j, 2, cnt + 3,
+                            ctx->rb_dev, ctx->flags, EX(ctx)));
+  }
   sync_read(ctx);
 }
 

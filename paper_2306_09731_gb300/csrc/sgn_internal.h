@@ -80,6 +80,7 @@ enum ProfKind : int {
   PK_REF_YINV,     // FP64 refinement matvec of precision 1: y-inverse
   PK_REF_X,        //   fused x-pass
   PK_REF_YFWD,     //   y-forward + M^-1
+  PK_RK,           // RK4 stage update (flat, after the RHS y-forward)
   PK_COUNT
 };
 
@@ -243,7 +244,8 @@ cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, 
                         double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex);
 // Gram-Schmidt update w -= sum_i coef[i] V_i of Arnoldi step j; the last block
 // stores |w'|^2, takes the DGKS decision (pass 1) and runs the Givens step once
-// the orthogonalisation is final (pass 1 without reorthogonalisation, or pass 2).
+// the orthogonalisation is final (pass 1 without reorthogonalisation, pass 2,
+// or pass 3 = a single pass that never reorthogonalises).
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,

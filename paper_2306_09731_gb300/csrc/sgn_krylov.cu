@@ -182,14 +182,16 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
   const double tot = block_reduce((double)nrm, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   // the last block: |w'|^2, then (first pass) the DGKS test, and the Givens
-  // step once the orthogonalisation is final
+  // step once the orthogonalisation is final. pass: 1 first pass with the DGKS
+  // test, 2 second pass, 3 single pass (no reorthogonalisation)
   if (last_block(counter)) {
     const double n2 = reduce_slot(partials, 0, red);
     if (threadIdx.x == 0) {
       st->nrm2 = n2;
       bool final_pass = (pass == 2);
-      if (pass == 1) {
-        const int need = (n2 < 0.5 * st->h1[nv]) ? 1 : 0;
+      if (pass == 1 || pass == 3) {
+        // pass 3: first pass of an Arnoldi step that never reorthogonalises
+        const int need = (pass == 1 && n2 < 0.5 * st->h1[nv]) ? 1 : 0;
         st->reorth = need;
         if (!need) {
           for (int i = 0; i <= MAXV; ++i) st->h2[i] = 0.0;

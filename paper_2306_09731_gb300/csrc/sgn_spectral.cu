@@ -830,7 +830,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     a.kxs = tbs.kx;
     a.kys = tbs.ky;
     a.rk = rk;
-    ex.begin(PK_RHS_YFWD);
+    ex.begin(PK_RK);
     k_rk_update<T, S><<<NBLK, 256, 0, ex.s>>>(G, a);
     ex.end();
   }

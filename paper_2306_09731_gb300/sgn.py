@@ -27,7 +27,7 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_last_error"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
-                   "ref_yinv", "ref_x", "ref_yfwd"]
+                   "ref_yinv", "ref_x", "ref_yfwd", "rk"]
 
 
 class SGNError(RuntimeError):
