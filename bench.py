@@ -141,10 +141,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # is now, with the summary that holds the command; set to None when the kernel
 # changes.
 MEASURED_TRAFFIC = {
-    ("mv_x", "fp64", 2048): {"bytes": 134.508544e6 + 23.561472e6,
+    ("mv_x", "fp64", 2048): {"bytes": 134.483712e6 + 25.482752e6,
                              "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
-    ("ref_x", "fp64", 2048): {"bytes": 134.508544e6 + 23.561472e6,
+    ("ref_x", "fp64", 2048): {"bytes": 134.483712e6 + 25.482752e6,
                               "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
+    ("mv_x", "fp32", 2048): {"bytes": 67.233024e6 + 1.019904e6,
+                             "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
+    ("ref_yinv", "fp64", 2048): {"bytes": 34.86208e6 + 14.923776e6,
+                                 "source": "profiles/k_ypass_inv2_fp64_gaussian2048.md"},
+    ("mv_yinv", "fp64", 2048): {"bytes": 34.86208e6 + 14.923776e6,
+                                "source": "profiles/k_ypass_inv2_fp64_gaussian2048.md"},
 }
 
 # kernel classes that are one kernel each (candidates for the roofline line)
