@@ -339,6 +339,9 @@ def run_ours(args, rank, world, local_rank):
         "gmres": head_rec["gmres"],
         "time_share": {k: v / total_prof for k, v in prof["ms"].items() if v > 0},
         "gmres_share": gmres_ms / total_prof if total_prof else None,
+        # kernel time summed from the event timers: the rest of ms_per_step is
+        # launch gaps and the per-Arnoldi-step host synchronisation
+        "kernel_ms_per_step": total_prof / args.steps,
         "gpu_launches": prof["launches"],
         "roofline": rooflines[dom],
         "roofline_by_kernel": {c: {"frac": r["frac"], "bound": r["bound"], "achieved": r["achieved"],

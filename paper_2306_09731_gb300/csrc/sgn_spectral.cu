@@ -19,6 +19,8 @@
 //    y-forward with -i k combinations and the RK4 stage update.
 #include <math.h>
 
+#include <type_traits>
+
 #include "sgn_internal.h"
 #include "vec_common.cuh"
 
@@ -88,9 +90,13 @@ struct XLayout {
   int t, grp, pair, y0, y1;
   bool valid;
 };
+// LN > 0: the row length 2^LN is a compile-time constant (the common sizes of
+// the FP32 passes), so the stage loops unroll and every index shift folds; 0:
+// read it from G.
+template <int LN = 0>
 __device__ __forceinline__ XLayout x_layout(const Geom& G) {
   XLayout L;
-  const int lT = G.lNx - 3;
+  const int lT = (LN > 0 ? LN : G.lNx) - 3;
   L.grp = threadIdx.x >> lT;
   L.t = threadIdx.x & ((1 << lT) - 1);
   const int P = blockDim.x >> lT;
@@ -236,13 +242,14 @@ constexpr int rhs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 // S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
 // Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
 // reads only its own row pair before writing it: Cout/Byout may alias S/Sy.
-template <typename T>
+template <typename T, int LN = 0>
 __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
                                                const T* __restrict__ cc, cpx<T>* Cout, cpx<T>* Byout) {
-  const XLayout L = x_layout(G);
+  const XLayout L = x_layout<LN>(G);
   cpx<T>* sm = x_smem<T>(G, L.grp);
-  const int N = G.Nx, T_ = N >> 3, lN = G.lNx;
+  const int lN = LN > 0 ? LN : G.lNx;
+  const int N = 1 << lN, T_ = N >> 3;
   const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
   cpx<T> X[8], Y[8], Z[8];
   load_packed(X, S + o0, S + o1, true, kx, L.t, lN);
@@ -291,15 +298,16 @@ __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const 
 // Inputs (y-inverse outputs): Vx, Vy, S = sigma, Sy = i ky sigma, and the
 // depth anomaly hh = h - 1. Writes Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and
 // Fh = F^x with F = |v|^2/2 - |grad sigma|^2/(2h^2) + g (h - 1) - 9 sigma^2/(2h^4).
-template <typename T>
+template <typename T, int LN = 0>
 __global__ void __launch_bounds__(256, rhs_min_blocks<T>()) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                 const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
                                                 const cpx<T>* Sy, const T* __restrict__ hh,
                                                 const T* __restrict__ cr, T g, cpx<T>* Cq, cpx<T>* Qy,
                                                 cpx<T>* Fh) {
-  const XLayout L = x_layout(G);
+  const XLayout L = x_layout<LN>(G);
   cpx<T>* sm = x_smem<T>(G, L.grp);
-  const int N = G.Nx, T_ = N >> 3, lN = G.lNx;
+  const int lN = LN > 0 ? LN : G.lNx;
+  const int N = 1 << lN, T_ = N >> 3;
   const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
   const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
   const T n = (T)(1.0 / (double)G.nphys());
@@ -418,13 +426,24 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // twice the bytes per row segment).
 constexpr int ypass_threads(int nin, int tbytes) { return (nin >= 3 && tbytes == 8) ? 256 : 512; }
 
-template <typename T, bool INV, int NIN, class Epi, typename S = T>
+// LN > 0: compile-time column length 2^LN; the interleave 2^LC of the block's
+// columns then follows from the block size the launcher uses.
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+template <int LN, int NIN, int TB>
+constexpr int ypass_lc() {
+  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads(NIN, TB)) - (LN - 3), 0, 6);
+}
+
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
 __global__ void __launch_bounds__(ypass_threads(NIN, sizeof(T))) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
                                                 YIn<T, NIN, S> in, Epi epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
-  const int lN = G.lNy, T_ = G.Ny >> 3;
-  const int lC = __ffs(blockDim.x >> (lN - 3)) - 1;
+  const int lN = LN > 0 ? LN : G.lNy;
+  const int T_ = 1 << (lN - 3);
+  constexpr int LCc = ypass_lc<LN, NIN, sizeof(T)>();
+  const int lC = LCc >= 0 ? LCc : __ffs(blockDim.x >> (lN - 3)) - 1;
   const int c = threadIdx.x & ((1 << lC) - 1);
   const int t = threadIdx.x >> lC;
   int col = (blockIdx.x << lC) + c;
@@ -600,6 +619,22 @@ cudaError_t launch_hermitian_fix(const Geom& G, cpx<T>* x, const Exec& ex) {
 
 // ------------------------------------------------------------ launchers
 
+// Calls f(std::integral_constant<int, LN>) with LN = lN for the sizes that have
+// compile-time FP32 kernels (256..2048 points), LN = 0 (runtime size) otherwise.
+template <typename T, class F>
+static inline void dispatch_ln(int lN, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    switch (lN) {
+      case 8: f(std::integral_constant<int, 8>()); return;
+      case 9: f(std::integral_constant<int, 9>()); return;
+      case 10: f(std::integral_constant<int, 10>()); return;
+      case 11: f(std::integral_constant<int, 11>()); return;
+      default: break;
+    }
+  }
+  f(std::integral_constant<int, 0>());
+}
+
 template <typename T>
 static inline int x_pairs_per_block(const Geom& G) {
   int Tn = G.Nx >> 3;
@@ -634,8 +669,24 @@ static void set_smem(const void* fn) {
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
+template <typename T, int L>
+static void set_attrs_ln() {
+  set_smem<T>((const void*)k_mv_x<T, L>);
+  set_smem<T>((const void*)k_rhs_x<T, L>);
+  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>, T, L>);
+  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>, T, L>);
+  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>, double, L>);
+  set_smem<T>((const void*)k_ypass<T, false, 3, EpiK<T>, T, L>);
+}
+
 template <typename T>
 void init_kernel_attributes() {
+  if constexpr (sizeof(T) == 4) {
+    set_attrs_ln<T, 8>();
+    set_attrs_ln<T, 9>();
+    set_attrs_ln<T, 10>();
+    set_attrs_ln<T, 11>();
+  }
   set_smem<T>((const void*)k_x_r2c<T>);
   set_smem<T>((const void*)k_x_c2r<T>);
   set_smem<T>((const void*)k_coef_x<T>);
@@ -740,8 +791,9 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
   dim3 grid, block;
   size_t smem;
   // y-inverse of sigma_hat and i ky sigma_hat
-  {
-    y_config<T>(G, 2, grid, block, smem);
+  y_config<T>(G, 2, grid, block, smem);
+  dispatch_ln<T>(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     YIn<T, 2> yi{};
     yi.src[0] = sig;
     yi.src[1] = sig;
@@ -751,25 +803,27 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
     ep.dst[0] = tmp[0];
     ep.dst[1] = tmp[1];
     ex.begin(PK_MV_YINV);
-    k_ypass<T, true, 2, EpiStore<T, 2>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, true, 2, EpiStore<T, 2>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
-  }
-  {
-    x_config<T>(G, grid, block, smem, 1);
+  });
+  x_config<T>(G, grid, block, smem, 1);
+  dispatch_ln<T>(G.lNx, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     ex.begin(PK_MV_X);
-    k_mv_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
+    k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
     ex.end();
-  }
-  {
-    y_config<T>(G, 2, grid, block, smem);
+  });
+  y_config<T>(G, 2, grid, block, smem);
+  dispatch_ln<T>(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     YIn<T, 2> yi{};
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
     EpiMatvec<T> ep{w, tb.kx, precond ? 1 : 0};
     ex.begin(PK_MV_YFWD);
-    k_ypass<T, false, 2, EpiMatvec<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, false, 2, EpiMatvec<T>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
-  }
+  });
   return cudaGetLastError();
 }
 
@@ -779,8 +833,9 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                        cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  {
-    y_config<T>(G, 4, grid, block, smem);
+  y_config<T>(G, 4, grid, block, smem);
+  dispatch_ln<T>(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     YIn<T, 4, S> yi{};
     yi.src[0] = U[1];
     yi.src[1] = U[2];
@@ -790,20 +845,22 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     EpiStore<T, 4> ep{};
     for (int i = 0; i < 4; ++i) ep.dst[i] = tmp[i];
     ex.begin(PK_RHS_YINV);
-    k_ypass<T, true, 4, EpiStore<T, 4>, S><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, true, 4, EpiStore<T, 4>, S, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
-  }
-  {
-    // each block reads only its own row pair before writing it, so the
-    // outputs may overwrite the inputs
-    x_config<T>(G, grid, block, smem, 1);
+  });
+  // each block reads only its own row pair before writing it, so the outputs
+  // may overwrite the inputs
+  x_config<T>(G, grid, block, smem, 1);
+  dispatch_ln<T>(G.lNx, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     ex.begin(PK_RHS_X);
-    k_rhs_x<T><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], tmp[2], tmp[3], h, cr, (T)rk.g,
-                                            tmp[0], tmp[1], tmp[2]);
+    k_rhs_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], tmp[2], tmp[3], h, cr,
+                                               (T)rk.g, tmp[0], tmp[1], tmp[2]);
     ex.end();
-  }
-  {
-    y_config<T>(G, 3, grid, block, smem);
+  });
+  y_config<T>(G, 3, grid, block, smem);
+  dispatch_ln<T>(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
     YIn<T, 3> yi{};
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
@@ -815,9 +872,9 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     ep.kx = tb.kx;
     ep.dealias = rk.dealias;
     ex.begin(PK_RHS_YFWD);
-    k_ypass<T, false, 3, EpiK<T>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, false, 3, EpiK<T>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
-  }
+  });
   {
     RkK<T, S> a{};
     for (int f = 0; f < 3; ++f) {

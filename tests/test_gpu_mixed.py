@@ -62,7 +62,9 @@ def test_mixed_gmres_meets_fp64_tolerance(Nx, Ny, Lx, Ly, tol):
     s.close()
 
 
-@pytest.mark.parametrize("Nx,Ny,Lx,Ly", [(64, 32, 8.0, 5.0), (256, 16, 80.0, 10.0), (128, 128, 10.0, 10.0)])
+# sizes cover the runtime-sized kernels and the compile-time FP32 sizes 2^8..2^10
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", [(64, 32, 8.0, 5.0), (256, 16, 80.0, 10.0), (128, 128, 10.0, 10.0),
+                                         (512, 1024, 40.0, 60.0)])
 def test_mixed_rhs_parity(Nx, Ny, Lx, Ly):
     st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 11 * Ny)
     G = O.Grid(Nx, Ny, Lx, Ly)
