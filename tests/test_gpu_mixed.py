@@ -46,7 +46,8 @@ def fp64_relres(G, h, b, sigma):
 
 
 @pytest.mark.parametrize("Nx,Ny,Lx,Ly,tol", [(64, 32, 8.0, 5.0, 1e-10), (128, 128, 10.0, 10.0, 1e-10),
-                                            (256, 16, 80.0, 10.0, 1e-12), (32, 256, 4.0, 30.0, 1e-9)])
+                                            (256, 16, 80.0, 10.0, 1e-12), (32, 256, 4.0, 30.0, 1e-9),
+                                            (512, 1024, 40.0, 60.0, 1e-10)])
 def test_mixed_gmres_meets_fp64_tolerance(Nx, Ny, Lx, Ly, tol):
     st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 7 * Ny)
     G = O.Grid(Nx, Ny, Lx, Ly)
@@ -62,10 +63,16 @@ def test_mixed_gmres_meets_fp64_tolerance(Nx, Ny, Lx, Ly, tol):
     s.close()
 
 
-# sizes cover the runtime-sized kernels and the compile-time FP32 sizes 2^8..2^10
-@pytest.mark.parametrize("Nx,Ny,Lx,Ly", [(64, 32, 8.0, 5.0), (256, 16, 80.0, 10.0), (128, 128, 10.0, 10.0),
-                                         (512, 1024, 40.0, 60.0)])
-def test_mixed_rhs_parity(Nx, Ny, Lx, Ly):
+# Sizes cover the runtime-sized kernels and the compile-time FP32 sizes 2^8..2^10.
+# One RHS evaluation in FP32 carries rounding eps32 ~ 6e-8 amplified by spectral
+# differentiation by about k_max / k_signal: ~10-40 on the first three grids,
+# ~500 on the over-resolved 512 x 1024 one (band-limited data with |m| <= 6 on
+# 512 x 1024 points; a plain FP32 numpy evaluation of the same formula is off by
+# up to 3e-4 there). States after RK4 steps, where the RHS error is multiplied by
+# dt, meet 1e-5 (the tests below).
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly,bound", [(64, 32, 8.0, 5.0, 1e-5), (256, 16, 80.0, 10.0, 1e-5),
+                                               (128, 128, 10.0, 10.0, 1e-5), (512, 1024, 40.0, 60.0, 1e-4)])
+def test_mixed_rhs_parity(Nx, Ny, Lx, Ly, bound):
     st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 11 * Ny)
     G = O.Grid(Nx, Ny, Lx, Ly)
     s = solver(Nx, Ny, Lx, Ly)
@@ -73,7 +80,7 @@ def test_mixed_rhs_parity(Nx, Ny, Lx, Ly):
     ht, vxt, vyt = s.rhs(dev(st.h), dev(st.vx), dev(st.vy), sg)
     rht, rvxt, rvyt, rsg, _ = O.rhs(G, st.h, st.vx, st.vy, st.sigma, tol=1e-13)
     for a, b in ((ht, rht), (vxt, rvxt), (vyt, rvyt)):
-        assert rel(host(a), b) < 1e-5
+        assert rel(host(a), b) < bound
     assert rel(host(sg), rsg) < 1e-8
     s.close()
 
