@@ -184,6 +184,12 @@ void build_tables(sgn_ctx* ctx) {
     const int m = k < G.Ny / 2 ? k : k - G.Ny;
     ky[k] = (k == G.Ny / 2) ? 0.0 : two_pi * m / G.Ly;
   }
+  // M^-1 = 1/(3 + kx^2 + ky^2) for the FP64 passes (Section 3 preconditioner)
+  std::vector<double> minv((size_t)G.Ny * G.ldS, 0.0);
+  for (int r = 0; r < G.Ny; ++r)
+    for (int c = 0; c < G.Nxh; ++c) minv[(size_t)r * G.ldS + c] = 1.0 / (3.0 + kx[c] * kx[c] + ky[r] * ky[r]);
+  ctx->tb.minv = dalloc<double>(ctx, minv.size());
+  CK(cudaMemcpy(ctx->tb.minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
   ctx->tb.twx = dalloc<C64>(ctx, G.Nx);
   ctx->tb.twy = dalloc<C64>(ctx, G.Ny);
   ctx->tb.kx = dalloc<double>(ctx, G.Nxh);

@@ -42,6 +42,7 @@ struct Tables {
   cpx<T>* twy = nullptr;  // W_Ny^k, k < Ny
   T* kx = nullptr;        // 2 pi m / Lx, m = 0..Nx/2, Nyquist 0   [Nxh]
   T* ky = nullptr;        // 2 pi m / Ly, m = 0..Ny/2-1, -Ny/2..-1, Nyquist 0 [Ny]
+  T* minv = nullptr;      // 1 / (3 + kx^2 + ky^2) per half-spectrum entry [Ny][ldS] (FP64 only)
 };
 
 // GMRES scalars that live on the device (Hessenberg, rotations, residual).

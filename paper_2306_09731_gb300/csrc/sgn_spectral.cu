@@ -179,6 +179,20 @@ __global__ void k_x_c2r(Geom G, const cpx<T>* __restrict__ tw, const T* __restri
 
 // ------------------------------------------------------ coefficient passes
 
+// 1/h in FP64 by the Newton-Raphson iteration r <- r + r (1 - h r) from an FP32
+// reciprocal seed: each step squares the relative error (1e-7 -> 1e-14 ->
+// rounding), for a handful of FMAs instead of a full FP64 division, which costs
+// about 25 FP64 instructions on a part with a 1:58 FP64:FP32 rate. Depths
+// outside the FP32 range take the plain division.
+__device__ __forceinline__ double recip_nr(double h) {
+  if (!(h > 1e-30 && h < 1e30)) return 1.0 / h;
+  double r = (double)(1.0f / (float)h);
+  double e = fma(-h, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-h, r, 1.0);
+  return fma(r, e, r);
+}
+
 template <typename T>
 __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, T* cc, size_t i, int* flags,
                                            const CoefCopy& cp) {
@@ -187,7 +201,7 @@ __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, 
   } else if (!(hv > 0.0)) {
     atomicOr(flags, FLAG_CAVITATION);
   }
-  const double r = 1.0 / hv;
+  const double r = recip_nr(hv);
   const double vr = 0.5 * invN * r, vc = 1.5 * invN * r * r * r;
   h[i] = (T)(hv - 1.0);  // the depth anomaly h - h_inf (exact in FP64 near h = 1)
   cr[i] = (T)vr;
@@ -479,11 +493,14 @@ struct EpiStore {
 };
 
 // w = [M^-1] (C - i ky By), M = 3 + kx^2 + ky^2 (Section 3 preconditioner)
+// minv (may be null): the FP64 path reads M^-1 from a table, because a division
+// costs about 25 FP64 instructions here; FP32 divides (cheap) on the fly.
 template <typename T>
 struct EpiMatvec {
   cpx<T>* w;
   const T* kx;
   int precond;
+  const T* minv;
   __device__ __forceinline__ void operator()(cpx<T> (&r)[2][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
@@ -492,9 +509,10 @@ struct EpiMatvec {
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
       const T kyv = __ldg(ky + row);
+      const size_t e = (size_t)row * G.ldS + col;
       cpx<T> z = r[0][s] - mul_ik(r[1][s], kyv);
-      if (precond) z = scl(z, (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
-      w[(size_t)row * G.ldS + col] = z;
+      if (precond) z = scl(z, minv ? __ldg(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+      w[e] = z;
     }
   }
 };
@@ -819,7 +837,7 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
     YIn<T, 2> yi{};
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
-    EpiMatvec<T> ep{w, tb.kx, precond ? 1 : 0};
+    EpiMatvec<T> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
     ex.begin(PK_MV_YFWD);
     k_ypass<T, false, 2, EpiMatvec<T>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
@@ -916,13 +934,15 @@ cudaError_t launch_spec_div(const Geom& G, const Tables<T>& tb, const cpx<T>* vx
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_precond(Geom G, const T* __restrict__ kx, const T* __restrict__ ky,
-                                                 const cpx<T>* in, cpx<T>* out, double* partials) {
+                                                 const T* __restrict__ minv, const cpx<T>* in, cpx<T>* out,
+                                                 double* partials) {
   __shared__ double red[32];
   double acc = 0.0;
   for (Walk it(G); it.ok(); it.next()) {
     const T kxv = it.col < G.Nxh ? __ldg(kx + it.col) : (T)0;
     const T kyv = __ldg(ky + it.row);
-    const cpx<T> z = scl(in[it.e], (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+    const T m = minv ? __ldg(minv + it.e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv);
+    const cpx<T> z = scl(in[it.e], m);
     out[it.e] = z;
     acc += col_weight_k(G, it.col) * ((double)z.x * z.x + (double)z.y * z.y);
   }
@@ -934,7 +954,7 @@ template <typename T>
 cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<T>* out, double* partials,
                            const Exec& ex) {
   ex.begin(PK_KRYLOV);
-  k_precond<T><<<NBLK, 256, 0, ex.s>>>(G, tb.kx, tb.ky, in, out, partials);
+  k_precond<T><<<NBLK, 256, 0, ex.s>>>(G, tb.kx, tb.ky, tb.minv, in, out, partials);
   ex.end();
   return cudaGetLastError();
 }
