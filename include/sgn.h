@@ -49,7 +49,7 @@ typedef struct {
   int precision;      /* 0 = FP64 throughout; 1 = FP32 transforms, pointwise work and
                          inner GMRES, with FP64 state, dot products, Givens and an
                          FP64 refinement residual (same FP64 tolerance test) */
-  int restart;        /* GMRES restart length m, 1..64 (default 20) */
+  int restart;        /* GMRES restart length m, 1..32 (default 20) */
   int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
   double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */
   int krasny;         /* 1: Krasny filter after every RK4 step (Section 3); default 0 */
@@ -59,6 +59,14 @@ typedef struct {
                          2 = linear extrapolation in time inside sgn_rk4_step (stage 2 from
                          sigma(t) and the previous step's sigma(t - dt/2), stage 4 from
                          sigma(t + dt/2) and sigma(t)); every solve still meets tol */
+  int graph;          /* 1: sgn_rk4_step and sgn_rk4_step_host run each RK4 step as one
+                         CUDA graph whose GMRES loops are conditional WHILE nodes driven
+                         by device-side tests (no host synchronisation inside the call;
+                         cavitation and non-finite h are reported when the call ends);
+                         the graph is built on the first call and rebuilt when dt
+                         changes. 0 (default): the host-driven loop, one stream
+                         synchronisation per Arnoldi step. Profiling (sgn_set_profiling)
+                         always takes the host-driven loop. */
 } sgn_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -79,7 +79,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = lib_path() + ".tmp"
-    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+    # -z defs: a declared but never defined launcher fails here, not at load time
+    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xlinker", "-z,defs"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + r.stdout.decode(errors="replace"))

@@ -7,8 +7,11 @@
 //   coefficients  h, 1/(2N h), 3/(2N h^3) from h_hat        (y-inverse + x-pass)
 //   GMRES         L sigma = b, b_hat = -(i kx vx + i ky vy) (Eq. (sigmav))
 //   RHS + update  K = (h_t, v_t) and the RK4 stage update  (3 fused passes)
-// The GMRES loop runs on the host: each Arnoldi step enqueues its kernels and
-// reads back one residual estimate (one stream synchronisation per step).
+// By default the GMRES loop runs on the host: each Arnoldi step enqueues its
+// kernels and reads back one residual estimate (one stream synchronisation per
+// step). With opt.graph = 1 one RK4 step is a CUDA graph instead: the restart
+// cycles and Arnoldi steps are conditional WHILE nodes, and one-thread control
+// kernels take the host loop's decisions on the device.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -26,15 +29,6 @@ using namespace sgn;
 typedef cpx<double> C64;
 typedef cpx<float> C32;
 
-// Mixed precision (precision = 1): the inner FP32 GMRES stops once it has
-// reduced its residual estimate by kInnerRel (below that the FP32 estimate
-// stops tracking the true residual), and its estimate is trusted as the final
-// FP64 residual only when kFp32Trust * beta, a bound on the gap between the
-// FP32 estimate and the true residual for a sweep that started at residual
-// beta, is below half the tolerance. Otherwise the next sweep recomputes the
-// residual in FP64.
-constexpr double kInnerRel = 1e-6;
-constexpr double kFp32Trust = 1e-5;
 
 struct sgn_ctx {
   Geom G{};
@@ -79,6 +73,15 @@ struct sgn_ctx {
   int* flags = nullptr;
   unsigned* counters = nullptr;  // last-block reduction tickets (zeroed, self-resetting)
   Prof prof;
+  // graph mode (opt.graph = 1): one RK4 step as an instantiated graph
+  cudaStream_t cap = nullptr;  // private stream the step is captured on
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  double graph_dt = 0.0;
+  // kernels per step outside the loops, per restart cycle / sweep, per Arnoldi step
+  long long graph_fixed = 0, graph_per_sweep = 0, graph_per_step = 0;
+  GmresDev* gst_host = nullptr;  // pinned
+  std::vector<cudaGraph_t> sweep_bodies, step_bodies;  // owned by their conditional nodes
   bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
   std::vector<void*> allocs;
   std::string err;
@@ -153,13 +156,27 @@ P* dalloc(sgn_ctx* ctx, size_t count) {
   return static_cast<P*>(p);
 }
 
+void free_graph(sgn_ctx* ctx) {
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  ctx->sweep_bodies.clear();
+  ctx->step_bodies.clear();
+}
+
 void free_all(sgn_ctx* ctx) {
+  free_graph(ctx);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  ctx->cap = nullptr;
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   if (ctx->rb_host) cudaFreeHost(ctx->rb_host);
   if (ctx->inv_host) cudaFreeHost(ctx->inv_host);
+  if (ctx->gst_host) cudaFreeHost(ctx->gst_host);
   ctx->rb_host = nullptr;
   ctx->inv_host = nullptr;
+  ctx->gst_host = nullptr;
 }
 
 void build_tables(sgn_ctx* ctx) {
@@ -535,6 +552,315 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
   *conv_all = conv;
 }
 
+
+// ------------------------------------------------------------ graph mode
+// One RK4 step as a CUDA graph. Straight-line work is stream-captured into
+// the graph; each GMRES solve becomes
+//   ... c = M^-1 b, |c|, k_ctl_begin, [sigma = 0 if c = 0]
+//   WHILE (h_sweep) {                       restart cycle / refinement sweep
+//     A sigma (FP64), r = c - A sigma, |r|, k_ctl_sweep, V_0 = r/|r|
+//     WHILE (h_step) { Arnoldi step j (j read from the device), V_{j+1} }
+//     y = H^-1 g, sigma += V y, k_ctl_after
+//   }
+// where the Givens step of the last Gram-Schmidt kernel and the control
+// kernels set the two conditions with the tests of gmres_fp64 / gmres_mixed.
+
+// Captures stretches of launches on ctx->cap into graph g after the nodes in
+// tail, and appends conditional WHILE nodes.
+struct GraphSeg {
+  sgn_ctx* ctx;
+  cudaGraph_t g;
+  std::vector<cudaGraphNode_t> tail;
+
+  void open() {
+    CK(cudaStreamBeginCaptureToGraph(ctx->cap, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(),
+                                     cudaStreamCaptureModeThreadLocal));
+  }
+  void close() {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+    std::vector<cudaGraphNode_t> t(deps, deps + nd);
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(ctx->cap, &out));
+    tail = t;
+  }
+  cudaGraphConditionalHandle handle() {
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    return h;
+  }
+  // WHILE node after the tail; returns its body graph
+  cudaGraph_t add_while(cudaGraphConditionalHandle h) {
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &p));
+    tail.assign(1, node);
+    return p.conditional.phGraph_out[0];
+  }
+};
+
+// Kernels enqueued by f (counted through the profiler's launch counter).
+template <typename F>
+long long count_launches(sgn_ctx* ctx, F&& f) {
+  const long long before = ctx->prof.launches;
+  f();
+  const long long n = ctx->prof.launches - before;
+  ctx->prof.launches = before;
+  return n;
+}
+
+// One Arnoldi step with device-side j: the body of the inner WHILE node.
+template <typename T>
+void graph_arnoldi(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, cpx<T>* V, cpx<T>* w,
+                   cpx<T>* const* tmp, const GraphCtl& ctl) {
+  const Geom& G = ctx->G;
+  const size_t vs = G.nspec();
+  const int m = ctx->opt.restart;
+  const int* jd = &ctx->gst->j;
+  const int* gate = &ctx->gst->reorth;
+  unsigned* cnt = ctx->counters;
+  const bool dgks = sizeof(T) == 8;
+  CK(launch_matvec<T>(G, tb, V, cr, cc, w, tmp, true, EX(ctx), jd, vs));
+  CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx), jd));
+  CK(launch_cgs_update<T>(G, V, vs, m, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, 0, dgks ? 1 : 3, cnt + 1,
+                          ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl));
+  if (dgks) {
+    CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx), jd));
+    CK(launch_cgs_update<T>(G, V, vs, m, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, 0, 2, cnt + 3,
+                            ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl));
+  }
+  // V_{j+1} = w / H[j+1][j]; j has already advanced (index m is the spare slot)
+  CK(launch_scale<T, T>(G, w, &ctx->gst->hnext, true, V, EX(ctx), jd, vs));
+}
+
+// One GMRES solve (FP64 or mixed) appended to the top-level segment.
+void graph_gmres(sgn_ctx* ctx, GraphSeg& top) {
+  const Geom& G = ctx->G;
+  const bool mixed = ctx->opt.precision == 1;
+  const size_t vs = G.nspec();
+  double* cnorm_d = ctx->scal + 0;
+  double* beta_d = ctx->scal + 1;
+  GraphCtl ctl{};
+  ctl.tol = ctx->opt.tol;
+  ctl.m = ctx->opt.restart;
+  ctl.maxit = ctx->opt.maxit;
+  ctl.mixed = mixed ? 1 : 0;
+  ctl.enabled = 1;
+  // the handle is made while no capture into the graph is open
+  top.close();
+  ctl.h_sweep = top.handle();
+  top.open();
+  long long fixed = count_launches(ctx, [&] {
+    CK(launch_hermitian_fix<double>(G, ctx->bh, EX(ctx)));
+    CK(launch_precond<double>(G, ctx->tb, ctx->bh, ctx->cvec, ctx->partials, EX(ctx)));
+    CK(launch_reduce(ctx->partials, 1, cnorm_d, true, nullptr, EX(ctx)));
+    CK(launch_ctl_begin(ctx->gst, cnorm_d, ctl, EX(ctx)));
+    CK(launch_zero<double>(G, ctx->sig, EX(ctx), &ctx->gst->zero_sigma));
+  });
+  top.close();
+  GraphSeg sweep{ctx, top.add_while(ctl.h_sweep), {}};
+  ctl.h_step = sweep.handle();
+  sweep.open();
+  long long per_sweep = count_launches(ctx, [&] {
+    CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+    C64* r = mixed ? ctx->r64 : ctx->V;
+    CK(launch_residual<double>(G, ctx->cvec, ctx->w, r, ctx->partials, EX(ctx)));
+    CK(launch_reduce(ctx->partials, 1, beta_d, true, nullptr, EX(ctx)));
+    CK(launch_ctl_sweep(ctx->gst, beta_d, ctl, EX(ctx)));
+    if (mixed)
+      CK((launch_scale<double, float>(G, r, beta_d, true, ctx->V32, EX(ctx))));
+    else
+      CK((launch_scale<double, double>(G, r, beta_d, true, ctx->V, EX(ctx))));
+  });
+  sweep.close();
+  ctx->sweep_bodies.push_back(sweep.g);
+  GraphSeg step{ctx, sweep.add_while(ctl.h_step), {}};
+  ctx->step_bodies.push_back(step.g);
+  step.open();
+  long long per_step = count_launches(ctx, [&] {
+    if (mixed)
+      graph_arnoldi<float>(ctx, ctx->tb32, ctx->cr32, ctx->cc32, ctx->V32, ctx->w32, ctx->tmp32, ctl);
+    else
+      graph_arnoldi<double>(ctx, ctx->tb, ctx->cr, ctx->cc, ctx->V, ctx->w, ctx->tmp, ctl);
+  });
+  step.close();
+  sweep.open();
+  per_sweep += count_launches(ctx, [&] {
+    CK(launch_backsolve(ctx->gst, 0, EX(ctx), &ctx->gst->k));
+    if (mixed)
+      CK((launch_axpy_multi<float, double>(G, ctx->V32, vs, 0, ctx->gst->y, ctx->sig, EX(ctx), &ctx->gst->k)));
+    else
+      CK((launch_axpy_multi<double, double>(G, ctx->V, vs, 0, ctx->gst->y, ctx->sig, EX(ctx), &ctx->gst->k)));
+    CK(launch_ctl_after(ctx->gst, ctl, EX(ctx)));
+  });
+  sweep.close();
+  top.open();
+  ctx->graph_fixed += fixed;
+  ctx->graph_per_sweep = per_sweep;
+  ctx->graph_per_step = per_step;
+}
+
+// One RK4 stage appended to the top-level segment (open on entry and exit).
+void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
+  C64* const* U = mode == RK_STAGE1 ? ctx->Un : ctx->Us;
+  const size_t bytes = ctx->G.nspec() * sizeof(C64);
+  ctx->graph_fixed += count_launches(ctx, [&] {
+    coef_from_spectral(ctx, U[0]);
+    if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
+    if (ctx->opt.guess == 2) {
+      if (mode == RK_STAGE2)
+        CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx), &ctx->gst->have_s3));
+      if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
+    }
+  });
+  graph_gmres(ctx, top);
+  ctx->graph_fixed += count_launches(ctx, [&] {
+    if (ctx->opt.guess == 2) {
+      if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (mode == RK_STAGE3) {
+        CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(launch_set_int(&ctx->gst->have_s3, 1, EX(ctx)));
+      }
+    }
+    RkArgs rk{};
+    rk.mode = mode;
+    rk.dt = dt;
+    rk.dealias = ctx->opt.dealias;
+    rk.krasny = ctx->opt.krasny;
+    rk.krasny_thr = ctx->opt.krasny_thr;
+    rk.g = ctx->g;
+    if (ctx->opt.precision == 1)
+      CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32,
+                                    ctx->Un, ctx->Us, ctx->acc, ctx->bh, rk, EX(ctx))));
+    else
+      CK((launch_rhs<double, double>(ctx->G, ctx->tb, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
+                                     ctx->Us, ctx->acc, ctx->bh, rk, EX(ctx))));
+  });
+}
+
+// Kernel and conditional nodes of a graph (not of its bodies).
+void count_nodes(sgn_ctx* ctx, cudaGraph_t g, long long* kernels, long long* conds, long long* others) {
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  *kernels = *conds = *others = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel)
+      ++*kernels;
+    else if (t == cudaGraphNodeTypeConditional)
+      ++*conds;
+    else
+      ++*others;
+  }
+}
+
+// The loops end only through their control kernels, so before the first
+// launch the built graph is checked against what was enqueued: four WHILE
+// nodes at the top, each sweep body holding its kernels (k_ctl_sweep and
+// k_ctl_after among them) and one nested WHILE node, each Arnoldi body its
+// kernels (the Gram-Schmidt kernel with the Givens controller among them).
+void check_step_graph(sgn_ctx* ctx) {
+  long long k, c, o;
+  count_nodes(ctx, ctx->step_graph, &k, &c, &o);
+  bool ok = c == 4 && ctx->sweep_bodies.size() == 4 && ctx->step_bodies.size() == 4;
+  for (size_t i = 0; ok && i < ctx->sweep_bodies.size(); ++i) {
+    count_nodes(ctx, ctx->sweep_bodies[i], &k, &c, &o);
+    ok = k == ctx->graph_per_sweep && c == 1 && o == 0;
+    if (!ok) break;
+    count_nodes(ctx, ctx->step_bodies[i], &k, &c, &o);
+    ok = k == ctx->graph_per_step && c == 0 && o == 0;
+  }
+  if (!ok) {
+    ctx->err = "graph mode: the captured step graph does not have the expected loop structure";
+    throw Fail{SGN_ECUDA};
+  }
+}
+
+// Builds and instantiates the step graph for time step dt. Every launch goes
+// to ctx->cap while it is built (ctx->stream is swapped and restored) with
+// profiling off, so the Exec of each launcher only counts kernels.
+void build_step_graph(sgn_ctx* ctx, double dt) {
+  free_graph(ctx);
+  if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+  if (!ctx->gst_host) CK(cudaMallocHost((void**)&ctx->gst_host, sizeof(GmresDev)));
+  CK(cudaGraphCreate(&ctx->step_graph, 0));
+  const cudaStream_t saved = ctx->stream;
+  const bool prof_on = ctx->prof.on;
+  ctx->stream = ctx->cap;
+  ctx->prof.on = false;
+  ctx->graph_fixed = 0;
+  GraphSeg top{ctx, ctx->step_graph, {}};
+  bool capturing = false;
+  try {
+    top.open();
+    capturing = true;
+    graph_stage(ctx, top, RK_STAGE1, dt);
+    graph_stage(ctx, top, RK_STAGE2, dt);
+    graph_stage(ctx, top, RK_STAGE3, dt);
+    graph_stage(ctx, top, RK_FINAL, dt);
+    capturing = false;
+    top.close();
+    check_step_graph(ctx);
+    CK(cudaGraphInstantiate(&ctx->step_exec, ctx->step_graph, 0));
+  } catch (Fail&) {
+    if (capturing) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(ctx->cap, &junk);
+      if (junk && junk != ctx->step_graph) cudaGraphDestroy(junk);
+    }
+    cudaGetLastError();
+    ctx->stream = saved;
+    ctx->prof.on = prof_on;
+    free_graph(ctx);
+    throw;
+  }
+  ctx->stream = saved;
+  ctx->prof.on = prof_on;
+  ctx->graph_dt = dt;
+}
+
+// rk4_device with each step replayed from the step graph. The GMRES
+// statistics and the depth flags are read once, after the last step.
+void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
+                      bool* conv_all) {
+  if (!ctx->step_exec || ctx->graph_dt != dt) build_step_graph(ctx, dt);
+  const double* f3[3] = {h, vx, vy};
+  reset_flags(ctx);
+  CK(cudaMemsetAsync(ctx->gst, 0, sizeof(GmresDev), ctx->stream));
+  fwd2(ctx, f3, 3, ctx->Un);
+  const double* fs[1] = {sigma};
+  fwd2(ctx, fs, 1, &ctx->sig);
+  CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
+  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
+  double* o3[3] = {h, vx, vy};
+  inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o3);
+  double* os[1] = {sigma};
+  inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
+  CK(cudaMemcpyAsync(ctx->gst_host, ctx->gst, sizeof(GmresDev), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(launch_readback_scalar(ctx->scal, ctx->flags, ctx->rb_dev, EX(ctx)));
+  sync_read(ctx);
+  const GmresDev& st = *ctx->gst_host;
+  ctx->stats.solves += (int)st.tot_solves;
+  ctx->stats.matvecs += st.tot_its;
+  if (ctx->opt.precision == 1) ctx->stats.refinements += st.tot_sweeps;
+  if (st.max_its > ctx->stats.max_iters) ctx->stats.max_iters = st.max_its;
+  ctx->stats.last_iters = st.last_its;
+  ctx->stats.last_relres = st.last_relres;
+  ctx->prof.launches += (long long)nsteps * ctx->graph_fixed + st.tot_sweeps * ctx->graph_per_sweep +
+                        st.tot_its * ctx->graph_per_step;
+  check_flags(ctx, ctx->rb_host->flags);
+  *conv_all = st.notconv == 0;
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -551,6 +877,7 @@ void sgn_default_options(sgn_options* o) {
   o->krasny_thr = 1e-12;
   o->dealias = 0;
   o->guess = 0;
+  o->graph = 0;
 }
 
 sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_options* opt, sgn_t* out) {
@@ -566,8 +893,9 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   if (o.precision != 0 && o.precision != 1)
     return fail(nullptr, SGN_EINVAL, "sgn_create: precision must be 0 (FP64) or 1 (FP32 + FP64 refinement)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
-  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2)
-    return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr or guess");
+  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2 ||
+      (o.graph != 0 && o.graph != 1))
+    return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr, guess or graph");
   sgn_ctx* ctx = new (std::nothrow) sgn_ctx();
   if (!ctx) return fail(nullptr, SGN_ENOMEM, "sgn_create: host allocation failed");
   ctx->opt = o;
@@ -815,7 +1143,10 @@ sgn_status sgn_rk4_step(sgn_t ctx, double* h, double* vx, double* vy, double* si
   if (nsteps < 0 || !isfinite(dt)) return fail(ctx, SGN_EINVAL, "sgn_rk4_step: bad dt or nsteps");
   if (nsteps == 0) return SGN_OK;
   bool conv = true;
-  rk4_device(ctx, h, vx, vy, sigma, dt, nsteps, &conv);
+  if (ctx->opt.graph && !ctx->prof.on)
+    rk4_device_graph(ctx, h, vx, vy, sigma, dt, nsteps, &conv);
+  else
+    rk4_device(ctx, h, vx, vy, sigma, dt, nsteps, &conv);
   CK(cudaStreamSynchronize(ctx->stream));
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
   return SGN_OK;
@@ -832,7 +1163,10 @@ sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, doubl
   double* hv[4] = {h, vx, vy, sigma};
   for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->phys[i], hv[i], bytes, cudaMemcpyHostToDevice, ctx->stream));
   bool conv = true;
-  if (nsteps > 0) rk4_device(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
+  if (nsteps > 0 && ctx->opt.graph && !ctx->prof.on)
+    rk4_device_graph(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
+  else if (nsteps > 0)
+    rk4_device(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
   for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");

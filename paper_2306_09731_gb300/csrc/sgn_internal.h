@@ -55,6 +55,39 @@ struct GmresDev {
   int pad_;
   double hnext, inv_hnext;    // H[j+1][j] and its inverse
   double res;                 // |g_{j+1}|
+  // device-side control of graph mode (see GraphCtl): the solve's state and
+  // counters that the host reads after a graph launch
+  double cnorm, target, beta, res_in, inner_target;
+  int j;             // next Arnoldi step of the current cycle
+  int k;             // Arnoldi steps completed in the current cycle
+  int its;           // matvecs of the current solve
+  int conv;          // current solve converged
+  int zero_sigma;    // right-hand side is zero: sigma = 0
+  int have_s3;       // extrapolated start: sigma of stage 3 is available
+  int notconv;       // some solve since the last reset missed the tolerance
+  int sweeps;        // residual evaluations of the current solve
+  int last_its, max_its;
+  int pad2_;
+  long long tot_its, tot_sweeps, tot_solves;
+  double last_relres;
+};
+
+// Mixed precision (precision = 1): the inner FP32 GMRES stops once it has
+// reduced its residual estimate by kInnerRel (below that the FP32 estimate
+// stops tracking the true residual), and its estimate is trusted as the final
+// FP64 residual only when kFp32Trust * beta, a bound on the gap between the
+// FP32 estimate and the true residual for a sweep that started at residual
+// beta, is below half the tolerance. Otherwise the next sweep recomputes the
+// residual in FP64.
+constexpr double kInnerRel = 1e-6;
+constexpr double kFp32Trust = 1e-5;
+
+// Constants and conditional-node handles of the graph-mode GMRES control.
+struct GraphCtl {
+  unsigned long long h_sweep;  // WHILE over restart cycles / refinement sweeps
+  unsigned long long h_step;   // WHILE over the Arnoldi steps of a cycle
+  double tol;
+  int m, maxit, mixed, enabled;
 };
 
 // What the host reads back after each Arnoldi step.
@@ -189,9 +222,12 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
 
 // matvec w = M^-1 L sigma (precond) or L sigma (!precond), spectral in/out.
 // tmp: 4 spectra of scratch (S, Sy, C, By).
+// jsel (may be null): the input is sig + (*jsel) * jstride (graph mode: the
+// Arnoldi step index lives on the device)
 template <typename T>
 cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
-                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex);
+                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex,
+                          const int* jsel = nullptr, size_t jstride = 0);
 
 // RHS of one stage from state U (3 spectra), sigma_hat, h, cr; K goes through
 // the RK epilogue. tmp: 4 spectra. Writes b_hat of the next stage state.
@@ -240,34 +276,44 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
 // out[i] = <V_i, w> (i < nv) and out[nv] = |w|^2, reduced by the last block
 // to finish; gate: run only if *gate != 0 (may be null). counter: a zeroed
 // device word private to this call site (left zeroed).
+// jdev (may be null): nv = *jdev + 1 read on the device (graph mode); nv is then
+// the largest value it can take (for the grid size).
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex);
+                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
+                        const int* jdev = nullptr);
 // Gram-Schmidt update w -= sum_i coef[i] V_i of Arnoldi step j; the last block
 // stores |w'|^2, takes the DGKS decision (pass 1) and runs the Givens step once
 // the orthogonalisation is final (pass 1 without reorthogonalisation, pass 2,
 // or pass 3 = a single pass that never reorthogonalises).
+// jdev (may be null): j and nv = j + 1 read on the device; ctl.enabled: after
+// the Givens step the last block advances the graph-mode control (its, k, j,
+// the Arnoldi loop condition).
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
-                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex);
+                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex,
+                              const int* jdev = nullptr, const GraphCtl* ctl = nullptr);
 // r = c - w, and partial squared norm of r
 template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
                             const Exec& ex);
-// y = x * f, f = *factor or 1 / *factor (device scalar); may change precision
+// y = x * f, f = *factor or 1 / *factor (device scalar); may change precision.
+// ysel (may be null): y += (*ysel) * ystride (graph mode).
 template <typename TI, typename TO>
 cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, bool invert, cpx<TO>* y,
-                         const Exec& ex);
-// x += sum_i coef[i] V_i (V in TV, x in TX, FP64 arithmetic)
+                         const Exec& ex, const int* ysel = nullptr, size_t ystride = 0);
+// x += sum_i coef[i] V_i (V in TV, x in TX); ndev (may be null): nv = *ndev
 template <typename TV, typename TX>
 cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
-                              cpx<TX>* x, const Exec& ex);
+                              cpx<TX>* x, const Exec& ex, const int* ndev = nullptr);
+// x = 0; gate (may be null): only if *gate != 0
 template <typename T>
-cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex);
-// y = a x + b y
+cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex, const int* gate = nullptr);
+// y = a x + b y; gate (may be null): only if *gate != 0
 template <typename T>
-cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex);
+cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex,
+                         const int* gate = nullptr);
 
 // reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
 cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
@@ -277,7 +323,12 @@ cudaError_t launch_reorth_decide(GmresDev* st, int nv, const Exec& ex);
 // GMRES scalar kernels (one thread)
 cudaError_t launch_gmres_start(GmresDev* st, const double* beta, const Exec& ex);
 cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int* flags, const Exec& ex);
-cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex);
+cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex, const int* kdev = nullptr);
+// graph-mode control kernels (one thread); see csrc/sgn_krylov.cu
+cudaError_t launch_ctl_begin(GmresDev* st, const double* cnorm, GraphCtl ctl, const Exec& ex);
+cudaError_t launch_ctl_sweep(GmresDev* st, const double* beta, GraphCtl ctl, const Exec& ex);
+cudaError_t launch_ctl_after(GmresDev* st, GraphCtl ctl, const Exec& ex);
+cudaError_t launch_set_int(int* p, int v, const Exec& ex);
 cudaError_t launch_readback_scalar(const double* x, const int* flags, GmresReadback* rb_dev, const Exec& ex);
 
 // invariants: physical pointwise sums (mass, px, py, energy) -> partials[4][NBLK]

@@ -102,29 +102,35 @@ constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockId
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                                                  double* partials, const int* gate, double* out,
-                                                 unsigned* counter) {
+                                                 unsigned* counter, const int* jdev) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
+  if (jdev) nv = *jdev + 1;
   __shared__ double red[32];
   const int i0 = blockIdx.y * DOT_CHUNK;
   const int nc = min(DOT_CHUNK, nv - i0);
+  const bool chunk0 = blockIdx.y == 0;
   A acc[DOT_CHUNK];
 #pragma unroll
   for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = (A)0;
   A nrm = (A)0;
   const cpx<T>* Vc = V + (size_t)i0 * vstride;
-  for (Walk it(G); it.ok(); it.next()) {
-    const cpx<T> we = w[it.e];
-    const A wt = col_weight_k<A>(G, it.col);
-    const A wx = wt * (A)we.x, wy = wt * (A)we.y;
-    cpx<T> v[DOT_CHUNK];
+  // chunks past nv (graph mode sizes the grid for the largest nv) only take part
+  // in the last-block ticket
+  if (nc > 0 || chunk0) {
+    for (Walk it(G); it.ok(); it.next()) {
+      const cpx<T> we = w[it.e];
+      const A wt = col_weight_k<A>(G, it.col);
+      const A wx = wt * (A)we.x, wy = wt * (A)we.y;
+      cpx<T> v[DOT_CHUNK];
 #pragma unroll
-    for (int i = 0; i < DOT_CHUNK; ++i)
-      if (i < nc) v[i] = Vc[i * vstride + it.e];
+      for (int i = 0; i < DOT_CHUNK; ++i)
+        if (i < nc) v[i] = Vc[i * vstride + it.e];
 #pragma unroll
-    for (int i = 0; i < DOT_CHUNK; ++i)
-      if (i < nc) acc[i] += wx * (A)v[i].x + wy * (A)v[i].y;
-    nrm += wx * (A)we.x + wy * (A)we.y;
+      for (int i = 0; i < DOT_CHUNK; ++i)
+        if (i < nc) acc[i] += wx * (A)v[i].x + wy * (A)v[i].y;
+      if (chunk0) nrm += wx * (A)we.x + wy * (A)we.y;
+    }
   }
 #pragma unroll
   for (int i = 0; i < DOT_CHUNK; ++i) {
@@ -147,13 +153,32 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
 }
 
 // w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
+// After the final Givens step of Arnoldi step j (graph mode): count the matvec,
+// record the residual estimate, and keep the Arnoldi loop running unless the
+// cycle is done (the eager host loop's test).
+__device__ __forceinline__ void ctl_step(GmresDev* st, int j, const GraphCtl& ctl) {
+  st->its += 1;
+  st->tot_its += 1;
+  st->k = j + 1;
+  st->j = j + 1;
+  st->res_in = st->res;
+  const bool stop = !(st->res > st->inner_target) || st->its >= ctl.maxit || !(st->hnext > 0.0) ||
+                    st->k >= ctl.m || st->res != st->res;
+  cudaGraphSetConditional(ctl.h_step, stop ? 0u : 1u);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, size_t vstride, int nv,
                                                     const double* __restrict__ coef, cpx<T>* w, double* partials,
                                                     const int* gate, GmresDev* st, int j, int pass,
-                                                    unsigned* counter, GmresReadback* rb, const int* flags) {
+                                                    unsigned* counter, GmresReadback* rb, const int* flags,
+                                                    const int* jdev, GraphCtl ctl) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
+  if (jdev) {
+    j = *jdev;
+    nv = j + 1;
+  }
   __shared__ double red[32];
   __shared__ A cf[MAXV];
   if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
@@ -198,7 +223,12 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
           final_pass = true;
         }
       }
-      if (final_pass) givens_step(st, j, rb, flags);
+      // graph mode: the Arnoldi loop continues only if the final pass re-arms it
+      if (ctl.enabled) cudaGraphSetConditional(ctl.h_step, 0u);
+      if (final_pass) {
+        givens_step(st, j, rb, flags);
+        if (ctl.enabled) ctl_step(st, j, ctl);
+      }
     }
   }
 }
@@ -218,7 +248,9 @@ __global__ void __launch_bounds__(256) k_residual(Geom G, const cpx<T>* c, const
 }
 
 template <typename TI, typename TO>
-__global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int invert, cpx<TO>* y) {
+__global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int invert, cpx<TO>* y, const int* ysel,
+                        size_t ystride) {
+  if (ysel) y += (size_t)(*ysel) * ystride;
   // arithmetic in the wider of the two types (FP32 when both are FP32)
   typedef typename Acc<decltype(TI() * TO())>::type A;
   const double f0 = *factor;
@@ -234,8 +266,10 @@ __global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int inve
 // to match the FP32 basis) and added to x in x's type.
 template <typename TV, typename TX>
 __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, const double* __restrict__ coef,
-                             cpx<TX>* x) {
+                             cpx<TX>* x, const int* ndev) {
   typedef typename Acc<TV>::type A;
+  if (ndev) nv = *ndev;
+  if (nv <= 0) return;
   __shared__ A cf[MAXV];
   if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
   __syncthreads();
@@ -253,7 +287,8 @@ __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, c
 
 // y = a x + b y (FP64 arithmetic); the extrapolated GMRES start
 template <typename T>
-__global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y) {
+__global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y, const int* gate) {
+  if (gate && *gate == 0) return;
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<T> u = x[it.e], v = y[it.e];
     y[it.e] = mk((T)(a * (double)u.x + b * (double)v.x), (T)(a * (double)u.y + b * (double)v.y));
@@ -261,7 +296,8 @@ __global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y) 
 }
 
 template <typename T>
-__global__ void k_zero(Geom G, cpx<T>* x) {
+__global__ void k_zero(Geom G, cpx<T>* x, const int* gate) {
+  if (gate && *gate == 0) return;
   for (Walk it(G); it.ok(); it.next()) x[it.e] = mk((T)0, (T)0);
 }
 
@@ -308,14 +344,94 @@ __global__ void k_givens(GmresDev* st, int j, GmresReadback* rb, const int* flag
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution
-__global__ void k_backsolve(GmresDev* st, int k) {
+__global__ void k_backsolve(GmresDev* st, int k, const int* kdev) {
   if (threadIdx.x != 0) return;
+  if (kdev) k = *kdev;
   const int ld = MAXM + 1;
   for (int i = k - 1; i >= 0; --i) {
     double s = st->g[i];
     for (int l = i + 1; l < k; ++l) s -= st->H[i + (size_t)l * ld] * st->y[l];
     st->y[i] = s / st->H[i + (size_t)i * ld];
   }
+}
+
+// ---------------------------------------------------- graph-mode control
+// One thread each. They make on the device the decisions the eager host loop
+// makes after its stream synchronisations.
+
+// end of a solve: its statistics
+__device__ void ctl_finish(GmresDev* st, bool conv, double relres) {
+  st->conv = conv ? 1 : 0;
+  if (!conv) st->notconv = 1;
+  st->last_relres = relres;
+  st->last_its = st->its;
+  st->max_its = max(st->max_its, st->its);
+}
+
+// after c = M^-1 b and |c|: a zero right-hand side gives sigma = 0 and no cycle
+__global__ void k_ctl_begin(GmresDev* st, const double* cnorm_d, GraphCtl ctl) {
+  if (threadIdx.x != 0) return;
+  const double cn = *cnorm_d;
+  st->cnorm = cn;
+  st->target = ctl.tol * cn;
+  st->its = 0;
+  st->sweeps = 0;
+  st->k = 0;
+  st->j = 0;
+  st->zero_sigma = (cn == 0.0) ? 1 : 0;
+  st->tot_solves += 1;
+  if (cn == 0.0) ctl_finish(st, true, 0.0);
+  cudaGraphSetConditional(ctl.h_sweep, cn == 0.0 ? 0u : 1u);
+}
+
+// after the residual beta of a restart cycle / refinement sweep: stop, or
+// start a cycle on V_0 = r / beta
+__global__ void k_ctl_sweep(GmresDev* st, const double* beta_d, GraphCtl ctl) {
+  if (threadIdx.x != 0) return;
+  const double beta = *beta_d;
+  st->beta = beta;
+  st->k = 0;
+  st->j = 0;
+  st->sweeps += 1;
+  st->tot_sweeps += 1;
+  const bool done = !(beta > st->target);
+  // every cycle takes at least one Arnoldi step, so its bounds the sweeps;
+  // the second test only guards the loop itself
+  const bool capped = st->its >= ctl.maxit || st->sweeps > ctl.maxit + 1;
+  if (done || capped) {
+    ctl_finish(st, done && beta == beta, beta / st->cnorm);
+    cudaGraphSetConditional(ctl.h_sweep, 0u);
+    cudaGraphSetConditional(ctl.h_step, 0u);
+    return;
+  }
+  st->inner_target = ctl.mixed ? fmax(0.5 * st->target, kInnerRel * beta) : st->target;
+  for (int i = 0; i <= MAXM; ++i) st->g[i] = 0.0;
+  st->g[0] = beta;
+  st->res = beta;
+  st->res_in = beta;
+  cudaGraphSetConditional(ctl.h_step, 1u);
+}
+
+// after a cycle's update sigma += V y: converged (mixed precision: only when
+// the FP32 estimate can be trusted), NaN, or another cycle / sweep
+__global__ void k_ctl_after(GmresDev* st, GraphCtl ctl) {
+  if (threadIdx.x != 0) return;
+  if (st->k == 0) return;  // the sweep stopped before the cycle
+  const double r = st->res_in;
+  if (r != r) {
+    ctl_finish(st, false, r);
+    cudaGraphSetConditional(ctl.h_sweep, 0u);
+    return;
+  }
+  const bool conv = ctl.mixed ? (r <= st->target && kFp32Trust * st->beta <= 0.5 * st->target) : (r <= st->target);
+  if (conv) {
+    ctl_finish(st, true, r / st->cnorm);
+    cudaGraphSetConditional(ctl.h_sweep, 0u);
+  }
+}
+
+__global__ void k_set_int(int* p, int v) {
+  if (threadIdx.x == 0) *p = v;
 }
 
 __global__ void k_readback_scalar(const double* x, const int* flags, GmresReadback* rb) {
@@ -353,21 +469,25 @@ __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h,
 
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
-                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex) {
+                        double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
+                        const int* jdev) {
   dim3 grid(NBLK, (nv + DOT_CHUNK - 1) / DOT_CHUNK);
   if (grid.y == 0) grid.y = 1;
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter);
+  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
   ex.end();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
-                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex) {
+                              unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex,
+                              const int* jdev, const GraphCtl* ctl) {
+  GraphCtl c{};
+  if (ctl) c = *ctl;
   ex.begin(PK_KRYLOV);
   k_cgs_update<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate, st, j, pass, counter, rb,
-                                         flags);
+                                         flags, jdev, c);
   ex.end();
   return cudaGetLastError();
 }
@@ -381,32 +501,33 @@ cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx
 }
 template <typename TI, typename TO>
 cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, bool invert, cpx<TO>* y,
-                         const Exec& ex) {
+                         const Exec& ex, const int* ysel, size_t ystride) {
   ex.begin(PK_KRYLOV);
-  k_scale<TI, TO><<<NBLK, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y);
+  k_scale<TI, TO><<<NBLK, 256, 0, ex.s>>>(G, x, factor, invert ? 1 : 0, y, ysel, ystride);
   ex.end();
   return cudaGetLastError();
 }
 template <typename TV, typename TX>
 cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
-                              cpx<TX>* x, const Exec& ex) {
+                              cpx<TX>* x, const Exec& ex, const int* ndev) {
   ex.begin(PK_KRYLOV);
-  k_axpy_multi<TV, TX><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x);
+  k_axpy_multi<TV, TX><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x, ndev);
   ex.end();
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex) {
+cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex, const int* gate) {
   ex.begin(PK_KRYLOV);
-  k_zero<T><<<NBLK, 256, 0, ex.s>>>(G, x);
+  k_zero<T><<<NBLK, 256, 0, ex.s>>>(G, x, gate);
   ex.end();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex) {
+cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex,
+                         const int* gate) {
   ex.begin(PK_KRYLOV);
-  k_axpby<T><<<NBLK, 256, 0, ex.s>>>(G, a, x, b, y);
+  k_axpby<T><<<NBLK, 256, 0, ex.s>>>(G, a, x, b, y, gate);
   ex.end();
   return cudaGetLastError();
 }
@@ -436,12 +557,37 @@ cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int*
   ex.end();
   return cudaGetLastError();
 }
-cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex) {
+cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex, const int* kdev) {
   ex.begin(PK_KRYLOV);
-  k_backsolve<<<1, 32, 0, ex.s>>>(st, k);
+  k_backsolve<<<1, 32, 0, ex.s>>>(st, k, kdev);
   ex.end();
   return cudaGetLastError();
 }
+cudaError_t launch_ctl_begin(GmresDev* st, const double* cnorm, GraphCtl ctl, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ctl_begin<<<1, 32, 0, ex.s>>>(st, cnorm, ctl);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_ctl_sweep(GmresDev* st, const double* beta, GraphCtl ctl, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ctl_sweep<<<1, 32, 0, ex.s>>>(st, beta, ctl);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_ctl_after(GmresDev* st, GraphCtl ctl, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ctl_after<<<1, 32, 0, ex.s>>>(st, ctl);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_set_int(int* p, int v, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_set_int<<<1, 32, 0, ex.s>>>(p, v);
+  ex.end();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_readback_scalar(const double* x, const int* flags, GmresReadback* rb_dev, const Exec& ex) {
   ex.begin(PK_KRYLOV);
   k_readback_scalar<<<1, 32, 0, ex.s>>>(x, flags, rb_dev);
@@ -459,26 +605,28 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
 
 #define SGN_KRYLOV_INST(T)                                                                                   \
   template cudaError_t launch_dots<T>(const Geom&, const cpx<T>*, size_t, int, const cpx<T>*, double*,       \
-                                      const int*, double*, unsigned*, const Exec&);                         \
+                                      const int*, double*, unsigned*, const Exec&, const int*);             \
   template cudaError_t launch_cgs_update<T>(const Geom&, const cpx<T>*, size_t, int, const double*, cpx<T>*, \
                                             double*, const int*, GmresDev*, int, int, unsigned*,            \
-                                            GmresReadback*, const int*, const Exec&);                       \
+                                            GmresReadback*, const int*, const Exec&, const int*,            \
+                                            const GraphCtl*);                                               \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
-  template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&);                                   \
-  template cudaError_t launch_axpby<T>(const Geom&, double, const cpx<T>*, double, cpx<T>*, const Exec&);
+  template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&, const int*);                       \
+  template cudaError_t launch_axpby<T>(const Geom&, double, const cpx<T>*, double, cpx<T>*, const Exec&,     \
+                                       const int*);
 
 SGN_KRYLOV_INST(double)
 SGN_KRYLOV_INST(float)
 template cudaError_t launch_scale<double, double>(const Geom&, const cpx<double>*, const double*, bool,
-                                                  cpx<double>*, const Exec&);
+                                                  cpx<double>*, const Exec&, const int*, size_t);
 template cudaError_t launch_scale<double, float>(const Geom&, const cpx<double>*, const double*, bool,
-                                                 cpx<float>*, const Exec&);
+                                                 cpx<float>*, const Exec&, const int*, size_t);
 template cudaError_t launch_scale<float, float>(const Geom&, const cpx<float>*, const double*, bool,
-                                                cpx<float>*, const Exec&);
+                                                cpx<float>*, const Exec&, const int*, size_t);
 template cudaError_t launch_axpy_multi<double, double>(const Geom&, const cpx<double>*, size_t, int,
-                                                       const double*, cpx<double>*, const Exec&);
+                                                       const double*, cpx<double>*, const Exec&, const int*);
 template cudaError_t launch_axpy_multi<float, double>(const Geom&, const cpx<float>*, size_t, int,
-                                                      const double*, cpx<double>*, const Exec&);
+                                                      const double*, cpx<double>*, const Exec&, const int*);
 
 }  // namespace sgn

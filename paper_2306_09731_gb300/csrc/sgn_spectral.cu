@@ -424,6 +424,8 @@ template <typename T, int NIN, typename S = T>
 struct YIn {
   const cpx<S>* src[NIN];  // storage type S, converted to the compute type T on load
   int deriv[NIN];          // pre-multiply by i ky (inverse passes)
+  const int* sel;          // may be null: every src is offset by (*sel) * sel_stride
+  size_t sel_stride;
 };
 
 template <typename T, typename S>
@@ -464,9 +466,10 @@ __global__ void __launch_bounds__(ypass_threads(NIN, sizeof(T))) k_ypass(Geom G,
   const bool valid = col < G.Nxh;
   if (!valid) col = G.Nxh - 1;
   cpx<T> r[NIN][8];
+  const size_t soff = in.sel ? (size_t)(*in.sel) * in.sel_stride : 0;
 #pragma unroll
   for (int i = 0; i < NIN; ++i) {
-    const cpx<S>* src = in.src[i];
+    const cpx<S>* src = in.src[i] + soff;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
@@ -805,7 +808,8 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
 
 template <typename T>
 cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
-                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex) {
+                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
+                          size_t jstride) {
   dim3 grid, block;
   size_t smem;
   // y-inverse of sigma_hat and i ky sigma_hat
@@ -817,6 +821,8 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
     yi.src[1] = sig;
     yi.deriv[0] = 0;
     yi.deriv[1] = 1;
+    yi.sel = jsel;
+    yi.sel_stride = jstride;
     EpiStore<T, 2> ep{};
     ep.dst[0] = tmp[0];
     ep.dst[1] = tmp[1];
@@ -973,7 +979,7 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
   template cudaError_t launch_coef_phys<T>(const Geom&, const double*, T*, T*, T*, int*, const CoefCopy&,   \
                                            const Exec&);                                                    \
   template cudaError_t launch_matvec<T>(const Geom&, const Tables<T>&, const cpx<T>*, const T*, const T*,    \
-                                        cpx<T>*, cpx<T>* const*, bool, const Exec&);                        \
+                                        cpx<T>*, cpx<T>* const*, bool, const Exec&, const int*, size_t);    \
   template cudaError_t launch_spec_div<T>(const Geom&, const Tables<T>&, const cpx<T>*, const cpx<T>*,      \
                                           cpx<T>*, const Exec&);                                            \
   template cudaError_t launch_precond<T>(const Geom&, const Tables<T>&, const cpx<T>*, cpx<T>*, double*,    \
@@ -984,7 +990,8 @@ SGN_INST(double)
 
 template void init_kernel_attributes<float>();
 template cudaError_t launch_matvec<float>(const Geom&, const Tables<float>&, const cpx<float>*, const float*,
-                                          const float*, cpx<float>*, cpx<float>* const*, bool, const Exec&);
+                                          const float*, cpx<float>*, cpx<float>* const*, bool, const Exec&,
+                                          const int*, size_t);
 template cudaError_t launch_rhs<double, double>(const Geom&, const Tables<double>&, const Tables<double>&,
                                                 cpx<double>* const*, const cpx<double>*, const double*,
                                                 const double*, cpx<double>* const*, cpx<double>* const*,

@@ -39,7 +39,7 @@ class SGNError(RuntimeError):
 class sgn_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("tol", ctypes.c_double), ("krasny", ctypes.c_int), ("krasny_thr", ctypes.c_double),
-                ("dealias", ctypes.c_int), ("guess", ctypes.c_int)]
+                ("dealias", ctypes.c_int), ("guess", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class sgn_stats(ctypes.Structure):
