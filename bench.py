@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="grid points per side (default 2048)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--no-graph", action="store_true", help="skip the graph-mode arm")
+    ap.add_argument("--no-graph", action="store_true", help="skip the graph-mode arms")
+    ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
                     help="headline is the mixed path when it runs; both also times plain FP64")
     return ap.parse_args()
@@ -137,6 +138,13 @@ def measured_peaks():
 
 # FP64 rate of a GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz max clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Double-float passes (precision 2) are bound by FP32 issue: 152 SMs x 128 FP32
+# lanes x 2.07 GHz instructions per second, divided by the FP32 instructions
+# one FP64-equivalent flop of a radix-8 FFT costs in this double-float
+# arithmetic: (52 adds x 11 + 4 products x 7 + 7 complex twiddle products x 38)
+# / (52 + 4 + 7 x 6) = 8.8.
+DF_INSTR_PER_FLOP = (52 * 11 + 4 * 7 + 7 * 38) / (52 + 4 + 7 * 6)
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_INSTR_PER_FLOP / 1e12
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # is now, with the summary that holds the command; set to None when the kernel
@@ -199,17 +207,24 @@ KERNEL_NAMES = {"mv_yinv": "k_ypass<inv,2> (matvec y-inverse)", "mv_x": "k_mv_x 
                 "ref_yfwd": "k_ypass<fwd,EpiMatvec> FP64 (refinement matvec y-forward)"}
 
 
-def class_roofline(cls, n, fp32, prof, peaks):
+def class_roofline(cls, n, prec, prof, peaks):
     """Live roofline of one kernel class from the library's event timers."""
     cnt = prof["counts"].get(cls, 0)
     if not cnt:
         return None
     avg_ms = prof["ms"][cls] / cnt
-    is32 = fp32 and not cls.startswith("ref")
+    is32 = prec >= 1 and not cls.startswith("ref")
+    isdf = prec == 2 and cls.startswith("ref")
     flops, nbytes = kernel_work(cls, n, 4 if is32 else 8)
     if flops is None:
         return None
-    if is32:
+    if isdf:
+        ach = flops / (avg_ms / 1e3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": ach / DF_PEAK_TFLOPS,
+               "peak_source": "derived double-float rate: 152 SMs x 128 FP32 lanes x 2.07 GHz / "
+                              f"{DF_INSTR_PER_FLOP:.1f} FP32 instructions per FP64-equivalent FFT flop"}
+    elif is32:
         ach = nbytes / (avg_ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -219,10 +234,10 @@ def class_roofline(cls, n, fp32, prof, peaks):
         out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                "frac": ach / FP64_PEAK_TFLOPS,
                "peak_source": "derived FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
-    out.update({"kernel": KERNEL_NAMES.get(cls, cls) + (" FP32" if is32 else " FP64"),
+    out.update({"kernel": KERNEL_NAMES.get(cls, cls) + (" FP32" if is32 else (" double-float" if isdf else " FP64")),
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                 "avg_launch_ms": avg_ms, "launches": cnt})
-    tr = MEASURED_TRAFFIC.get((cls, "fp32" if is32 else "fp64", n))
+    tr = MEASURED_TRAFFIC.get((cls, "fp32" if is32 else ("df" if isdf else "fp64"), n))
     out["traffic"] = tr["bytes"] if tr else None
     out["traffic_source"] = tr["source"] if tr else None
     return out
@@ -294,10 +309,13 @@ def run_ours(args, rank, world, local_rank):
     fields = {}
     # mixed: FP32 bulk + FP64 refinement, GMRES started by linear extrapolation in
     # time, host-driven loop with per-launch timers (the per-kernel rooflines);
-    # mixed_graph: the same kernels with each RK4 step replayed as a CUDA graph;
-    # fp64: the paper's method (FP64, start from the last sigma); mixed_paper_start:
-    # the mixed path with the paper's start, for attribution
-    plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0))
+    # mixed_df: the same with the refinement matvec and the coefficient pass in
+    # double-float arithmetic (precision 2); *_graph: the same kernels with each
+    # RK4 step replayed as a CUDA graph; fp64: the paper's method (FP64, start
+    # from the last sigma); mixed_paper_start: precision 1 with the paper's
+    # start, for attribution
+    plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
+            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0))
     solvers = {}
     for name, prec, guess, graph in plan:
         if args.path == "mixed" and not name.startswith("mixed"):
@@ -306,17 +324,24 @@ def run_ours(args, rank, world, local_rank):
             continue
         if args.no_graph and graph:
             continue
+        if args.no_df and prec == 2:
+            continue
         s, f, rec = time_path(prec, guess, args, st, n, world, graph)
+        rec["precision"] = prec
         fields[name] = [x.cpu().numpy() for x in f[:3]]
         solvers[name] = s
         paths[name] = rec
-    prof_name = "fp64" if args.path == "fp64" else "mixed"
-    # the headline is the faster execution of the headline path
-    head_name = prof_name
-    if prof_name == "mixed" and "mixed_graph" in paths and paths["mixed_graph"]["value"] > paths["mixed"]["value"]:
-        head_name = "mixed_graph"
+    # headline: the fastest arm of the headline path (all of them meet the same
+    # FP64 tolerance test in every solve); its per-kernel figures come from the
+    # host-driven arm of the same precision
+    if args.path == "fp64":
+        head_name = "fp64"
+    else:
+        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph") if k in paths]
+        head_name = max(cands, key=lambda k: paths[k]["value"])
+    prof_name = head_name[:-len("_graph")] if head_name.endswith("_graph") else head_name
     head_solver, head_rec = solvers[head_name], paths[head_name]
-    head_prec = 1 if prof_name == "mixed" else 0
+    head_prec = head_rec["precision"]
     for name, s in solvers.items():
         if name != head_name:
             s.close()
@@ -343,9 +368,9 @@ def run_ours(args, rank, world, local_rank):
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
     head_solver.close()
 
-    fp32 = head_prec == 1
+    fp32 = head_prec >= 1
     prof = paths[prof_name]["prof"]
-    rooflines = {c: class_roofline(c, n, fp32, prof, peaks) for c in SINGLE_KERNEL_CLASSES}
+    rooflines = {c: class_roofline(c, n, head_prec, prof, peaks) for c in SINGLE_KERNEL_CLASSES}
     dom = max((c for c in rooflines if rooflines[c]), key=lambda c: prof["ms"][c])
     total_prof = sum(prof["ms"].values())
     gmres_ms = sum(prof["ms"][k] for k in ("mv_yinv", "mv_x", "mv_yfwd", "krylov", "ref_yinv", "ref_x",
@@ -355,9 +380,15 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": head_rec["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
         "config": dict(config(n, fp32), parallelism=f"replicas{world}" if world > 1 else "single"),
-        "path": ("mixed: FP32 bulk + FP64 refinement to the FP64 tolerance, GMRES start extrapolated in time"
-                 if fp32 else "plain FP64") + (", each RK4 step one CUDA graph with device-side GMRES control"
-                                                if head_name.endswith("_graph") else ", host-driven GMRES loop"),
+        "path": ({0: "plain FP64",
+                  1: "mixed: FP32 bulk + FP64 refinement to the FP64 tolerance, GMRES start extrapolated in time",
+                  2: "mixed: FP32 bulk + double-float refinement matvec and coefficients to the FP64 tolerance, "
+                     "GMRES start extrapolated in time"}[head_prec])
+                + (", each RK4 step one CUDA graph with device-side GMRES control"
+                   if head_name.endswith("_graph") else ", host-driven GMRES loop"),
+        "arms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "precision": v["precision"],
+                     "graph": k.endswith("_graph"), "iters_per_stage": v["gmres"]["iters_per_stage"]}
+                 for k, v in paths.items()},
         "gmres": head_rec["gmres"],
         "time_share": {k: v / total_prof for k, v in prof["ms"].items() if v > 0},
         "gmres_share": gmres_ms / total_prof if total_prof else None,
@@ -376,24 +407,24 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "clocks": clk,
     }
-    if "fp64" in paths and "mixed" in paths:
+    if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]
         out["fp64_plain"] = {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
                              "gmres": f64["gmres"]}
-        out["speedup_mixed_vs_fp64"] = head_rec["value"] / f64["value"]
+        out["speedup_vs_fp64"] = head_rec["value"] / f64["value"]
         errs = {}
         for i, nm in enumerate(("h", "vx", "vy")):
-            a, b = fields["mixed"][i], fields["fp64"][i]
+            a, b = fields[head_name][i], fields["fp64"][i]
             errs[nm] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-        out["mixed_vs_fp64_rel_l2"] = errs
-        out["mixed_vs_fp64_after_steps"] = args.warmup + args.steps
-    if "mixed_graph" in paths and "mixed" in paths:
-        mg, mh = paths["mixed_graph"], paths["mixed"]
-        out["graph_vs_host_loop"] = {"graph": mg["value"], "host_loop": mh["value"], "unit": UNIT,
-                                     "ratio": mg["value"] / mh["value"],
-                                     "fields_bitwise_equal": all(
-                                         bool(np.array_equal(a, b))
-                                         for a, b in zip(fields["mixed_graph"], fields["mixed"]))}
+        out["headline_vs_fp64_rel_l2"] = errs
+        out["headline_vs_fp64_after_steps"] = args.warmup + args.steps
+    for base in ("mixed", "mixed_df"):
+        if base + "_graph" in paths and base in paths:
+            mg, mh = paths[base + "_graph"], paths[base]
+            out.setdefault("graph_vs_host_loop", {})[base] = {
+                "graph": mg["value"], "host_loop": mh["value"], "unit": UNIT, "ratio": mg["value"] / mh["value"],
+                "fields_bitwise_equal": all(bool(np.array_equal(a, b))
+                                            for a, b in zip(fields[base + "_graph"], fields[base]))}
     if "mixed_paper_start" in paths:
         mp = paths["mixed_paper_start"]
         out["mixed_paper_start"] = {"value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms_per_step"],

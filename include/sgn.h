@@ -48,7 +48,12 @@ typedef enum {
 typedef struct {
   int precision;      /* 0 = FP64 throughout; 1 = FP32 transforms, pointwise work and
                          inner GMRES, with FP64 state, dot products, Givens and an
-                         FP64 refinement residual (same FP64 tolerance test) */
+                         FP64 refinement residual (same FP64 tolerance test);
+                         2 = as 1, but the refinement residual's matvec and the
+                         coefficient pass run in double-float arithmetic (a value is
+                         the sum of two FP32 numbers: 48-bit significand, FP32
+                         exponent range, so 1/h^3 must stay below ~3e38); the
+                         tolerance test is unchanged */
   int restart;        /* GMRES restart length m, 1..32 (default 20) */
   int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
   double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */
@@ -100,8 +105,9 @@ sgn_status sgn_fft2_r2c(sgn_t ctx, const double* f, double* fhat);
 sgn_status sgn_fft2_c2r(sgn_t ctx, const double* fhat, double* f);
 
 /* out = L[sigma] = 3 sigma/h^3 - d/dx(sigma_x/h) - d/dy(sigma_y/h)
- * (Section 3, Eq. (sigmav)), unpreconditioned. Returns SGN_ECAVITATION /
- * SGN_ENONFINITE if h is not positive and finite. */
+ * (Section 3, Eq. (sigmav)), unpreconditioned, in the arithmetic of the
+ * handle's refinement residual (double-float for precision 2, else FP64).
+ * Returns SGN_ECAVITATION / SGN_ENONFINITE if h is not positive and finite. */
 sgn_status sgn_elliptic_apply(sgn_t ctx, const double* h, const double* sigma, double* out);
 
 /* Solves L[sigma] = b by left-preconditioned restarted GMRES (Section 3;

@@ -1,0 +1,141 @@
+// dfloat.cuh - double-float arithmetic for the refinement passes.
+//
+// A dfl is the unevaluated sum hi + lo of two FP32 numbers with |lo| at most
+// about half an ulp of hi: a 48-bit significand with the FP32 exponent range.
+// On a part whose FP32 rate is 58 times its FP64 rate, an FFT in this format
+// costs about ten FP32 instructions per FP64 operation it replaces and still
+// resolves relative errors near 1e-14, far below what the GMRES tolerance test
+// of the refinement residual needs.
+//
+// Building blocks (error-free transformations of two FP32 numbers):
+//   two_sum       Knuth's TwoSum: s + e == a + b exactly, any magnitudes
+//   fast_two_sum  Dekker's FastTwoSum: the same when |a| >= |b| (or a == 0)
+//   product       a*b - fl(a*b) is exact through one FMA (TwoProd)
+// Addition is Dekker's add2 (TwoSum of the high parts, the low parts added in
+// FP32, one renormalisation): its absolute error is a small multiple of
+// u^2 (|a| + |b|), u = 2^-24. That is the normwise bound the error analysis of
+// an FFT uses, and it holds under cancellation, where the relative error does
+// not. Multiplication is the FMA form of Dekker's mul2 (relative error a few
+// u^2). Every step uses explicit round-to-nearest intrinsics, so the compiler
+// can neither contract a product into an addition nor reorder an error term.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft_core.cuh"
+
+namespace sgn {
+
+struct __align__(8) dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfl(float v) : hi(v), lo(0.0f) {}
+  __host__ __device__ constexpr dfl(int v) : hi((float)v), lo((float)((double)v - (double)(float)v)) {}
+  // nearest split of an FP64 value (folded at compile time for constants)
+  __host__ __device__ constexpr dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi; }
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfl(s, e);
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const dfl s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
+
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+// product with a plain FP32 factor
+__device__ __forceinline__ dfl mul_f(dfl a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return fast_two_sum(p, e);
+}
+// exact scaling by a power of two (no overflow or underflow assumed)
+__device__ __forceinline__ dfl scale_pow2(dfl a, float s) { return dfl(__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)); }
+
+// 1/b: FP32 reciprocal r0, then one Newton step r0 + r0 (1 - b r0). The
+// residual 1 - b.hi r0 is exact through the FMA (it is below 2^-23 in size
+// and has no bits below 2^-48), so the step doubles the 24 correct bits.
+__device__ __forceinline__ dfl recip(dfl b) {
+  const float r0 = __frcp_rn(b.hi);
+  const float e = __fmaf_rn(-b.lo, r0, __fmaf_rn(-b.hi, r0, 1.0f));
+  return fast_two_sum(r0, __fmul_rn(r0, e));
+}
+// a/b: quotient of the high parts, corrected by the df remainder a - b q1
+__device__ __forceinline__ dfl operator/(dfl a, dfl b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const dfl r = a - mul_f(b, q1);
+  return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// --------------------------------------------------- complex and memory
+// a*b + SGN*c*d with the two exact high products gathered before one TwoSum:
+// 19 instructions, against 25 for two products and a sum. The error terms
+// (product errors and the cross products with the low parts) are summed in
+// FP32, so the absolute error stays a few u^2 (|a b| + |c d|).
+template <int SGN>
+__device__ __forceinline__ dfl dot2_df(dfl a, dfl b, dfl c, dfl d) {
+  const float ch = SGN > 0 ? c.hi : -c.hi;
+  const float cl = SGN > 0 ? c.lo : -c.lo;
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float q = __fmul_rn(ch, d.hi);
+  const float ep = __fmaf_rn(a.hi, b.hi, -p);
+  const float eq = __fmaf_rn(ch, d.hi, -q);
+  float e = __fadd_rn(ep, eq);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  e = __fmaf_rn(ch, d.lo, e);
+  e = __fmaf_rn(cl, d.hi, e);
+  const dfl s = two_sum(p, q);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, e));
+}
+
+template <>
+__device__ __forceinline__ cpx<dfl> cmul(cpx<dfl> a, cpx<dfl> b) {
+  return mk(dot2_df<-1>(a.x, b.x, a.y, b.y), dot2_df<1>(a.x, b.y, a.y, b.x));
+}
+// a * conj(b)
+template <>
+__device__ __forceinline__ cpx<dfl> cmulc(cpx<dfl> a, cpx<dfl> b) {
+  return mk(dot2_df<1>(a.x, b.x, a.y, b.y), dot2_df<-1>(a.y, b.x, a.x, b.y));
+}
+
+template <>
+__device__ __forceinline__ cpx<dfl> ldg(const cpx<dfl>* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return mk(dfl(v.x, v.y), dfl(v.z, v.w));
+}
+template <>
+__device__ __forceinline__ dfl ldr(const dfl* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return dfl(v.x, v.y);
+}
+
+// 16-byte elements: the FP64 padding layout
+template <>
+__device__ __forceinline__ int sidx<dfl>(int p, int lcs) {
+  return (p + (p >> 3)) << lcs;
+}
+
+}  // namespace sgn

@@ -77,6 +77,12 @@ __device__ __forceinline__ cpx<float> ldg(const cpx<float>* p) {
   return mk(v.x, v.y);
 }
 
+// read-only scalar load (wavenumbers, M^-1); the double-float type overloads it
+template <typename T>
+__device__ __forceinline__ T ldr(const T* p) {
+  return __ldg(p);
+}
+
 // Shared-memory slot of element p of a transform whose buffer interleaves
 // 2^lcs columns. 16-byte elements: a quarter-warp phase touches 8 elements, and
 // one pad slot every 8 keeps the stride-8 writes of the first stage, the

@@ -28,6 +28,7 @@ using namespace sgn;
 
 typedef cpx<double> C64;
 typedef cpx<float> C32;
+typedef cpx<dfl> CDF;
 
 
 struct sgn_ctx {
@@ -49,7 +50,7 @@ struct sgn_ctx {
   double* h = nullptr;
   double* cr = nullptr;
   double* cc = nullptr;
-  // mixed precision (precision = 1)
+  // mixed precision (precision = 1 and 2)
   Tables<float> tb32{};
   C32* V32 = nullptr;
   C32* w32 = nullptr;
@@ -58,6 +59,10 @@ struct sgn_ctx {
   float* cr32 = nullptr;
   float* cc32 = nullptr;
   C64* r64 = nullptr;
+  // precision 2: double-float tables and matvec coefficients
+  Tables<dfl> tbd{};
+  dfl* crd = nullptr;
+  dfl* ccd = nullptr;
   // extrapolated GMRES start (guess = 2): sigma of stage 1 of this step and
   // of stage 3 of the previous step, as half spectra
   C64* sig_s1 = nullptr;
@@ -215,7 +220,24 @@ void build_tables(sgn_ctx* ctx) {
   CK(cudaMemcpy(ctx->tb.twy, ty.data(), G.Ny * sizeof(C64), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.kx, kx.data(), G.Nxh * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.ky, ky.data(), G.Ny * sizeof(double), cudaMemcpyHostToDevice));
-  if (ctx->opt.precision == 1) {
+  if (ctx->opt.precision == 2) {
+    // double-float copies: nearest FP32 pair of each FP64 entry
+    std::vector<CDF> dx(G.Nx), dy(G.Ny);
+    for (int k = 0; k < G.Nx; ++k) dx[k] = CDF{dfl(tx[k].x), dfl(tx[k].y)};
+    for (int k = 0; k < G.Ny; ++k) dy[k] = CDF{dfl(ty[k].x), dfl(ty[k].y)};
+    std::vector<dfl> kxd(kx.begin(), kx.end()), kyd(ky.begin(), ky.end()), md(minv.begin(), minv.end());
+    ctx->tbd.twx = dalloc<CDF>(ctx, G.Nx);
+    ctx->tbd.twy = dalloc<CDF>(ctx, G.Ny);
+    ctx->tbd.kx = dalloc<dfl>(ctx, G.Nxh);
+    ctx->tbd.ky = dalloc<dfl>(ctx, G.Ny);
+    ctx->tbd.minv = dalloc<dfl>(ctx, md.size());
+    CK(cudaMemcpy(ctx->tbd.twx, dx.data(), G.Nx * sizeof(CDF), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.twy, dy.data(), G.Ny * sizeof(CDF), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.kx, kxd.data(), G.Nxh * sizeof(dfl), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.ky, kyd.data(), G.Ny * sizeof(dfl), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.minv, md.data(), md.size() * sizeof(dfl), cudaMemcpyHostToDevice));
+  }
+  if (ctx->opt.precision >= 1) {
     std::vector<C32> fx(G.Nx), fy(G.Ny);
     for (int k = 0; k < G.Nx; ++k) fx[k] = C32{(float)tx[k].x, (float)tx[k].y};
     for (int k = 0; k < G.Ny; ++k) fy[k] = C32{(float)ty[k].x, (float)ty[k].y};
@@ -233,7 +255,7 @@ void build_tables(sgn_ctx* ctx) {
 
 CoefCopy coef_copy(sgn_ctx* ctx) {
   CoefCopy cp;
-  if (ctx->opt.precision == 1) {
+  if (ctx->opt.precision >= 1) {
     cp.h = ctx->h32;
     cp.cr = ctx->cr32;
     cp.cc = ctx->cc32;
@@ -247,11 +269,31 @@ Exec EX(sgn_ctx* ctx, int kind_override = -1) {
   return e;
 }
 
-// launches of the FP64 refinement residual of precision 1
+// launches of the refinement residual of precision 1 and 2
 Exec EX_REFINE(sgn_ctx* ctx) {
   Exec e = EX(ctx);
   e.refine = true;
   return e;
+}
+
+CDF* const* tmp_df(sgn_ctx* ctx) { return reinterpret_cast<CDF* const*>(ctx->tmp); }
+
+// w = [M^-1] L sigma_hat in the handle's refinement arithmetic: double-float
+// for precision 2, FP64 otherwise
+void refine_matvec(sgn_ctx* ctx, bool precond, const Exec& ex) {
+  if (ctx->opt.precision == 2)
+    CK((launch_matvec_io<dfl, double>(ctx->G, ctx->tbd, ctx->sig, ctx->crd, ctx->ccd, ctx->w, tmp_df(ctx), precond,
+                                      ex)));
+  else
+    CK(launch_matvec<double>(ctx->G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, precond, ex));
+}
+
+// coefficient fields from a physical depth h
+void coef_phys(sgn_ctx* ctx, const double* h) {
+  if (ctx->opt.precision == 2)
+    CK(launch_coef_phys<dfl>(ctx->G, h, nullptr, ctx->crd, ctx->ccd, ctx->flags, coef_copy(ctx), EX(ctx)));
+  else
+    CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
 }
 
 // ------------------------------------------------------------ transforms
@@ -287,6 +329,12 @@ void check_flags(sgn_ctx* ctx, int flags) {
 
 // coefficient fields from the spectral depth h_hat
 void coef_from_spectral(sgn_ctx* ctx, const C64* hh) {
+  if (ctx->opt.precision == 2) {
+    CK(launch_y_inv64<dfl>(ctx->G, ctx->tbd, hh, tmp_df(ctx)[0], EX(ctx, PK_COEF)));
+    CK(launch_coef_x<dfl>(ctx->G, ctx->tbd, tmp_df(ctx)[0], nullptr, ctx->crd, ctx->ccd, ctx->flags,
+                          coef_copy(ctx), EX(ctx)));
+    return;
+  }
   CK(launch_y_fft<double>(ctx->G, ctx->tb, true, &hh, nullptr, 1, ctx->tmp, EX(ctx, PK_COEF)));
   CK(launch_coef_x<double>(ctx->G, ctx->tb, ctx->tmp[0], ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx),
                             EX(ctx)));
@@ -427,7 +475,7 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   bool conv = false;
   double res = 0.0;
   for (;;) {
-    CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX_REFINE(ctx)));
+    refine_matvec(ctx, true, EX_REFINE(ctx));
     CK(launch_residual<double>(G, ctx->cvec, ctx->w, ctx->r64, ctx->partials, EX(ctx)));
     CK(launch_reduce(ctx->partials, 1, beta_d, true, nullptr, EX(ctx)));
     CK(launch_readback_scalar(beta_d, ctx->flags, ctx->rb_dev, EX(ctx)));
@@ -481,7 +529,7 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
 }
 
 bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
-  return ctx->opt.precision == 1 ? gmres_mixed(ctx, iters_out, relres_out) : gmres_fp64(ctx, iters_out, relres_out);
+  return ctx->opt.precision >= 1 ? gmres_mixed(ctx, iters_out, relres_out) : gmres_fp64(ctx, iters_out, relres_out);
 }
 
 // one RK4 stage (s = 1..4) or a plain RHS evaluation (mode RK_STORE_K)
@@ -513,7 +561,7 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   rk.krasny_thr = ctx->opt.krasny_thr;
   rk.g = ctx->g;
   C64* bnext = mode == RK_STORE_K ? nullptr : ctx->bh;
-  if (ctx->opt.precision == 1)
+  if (ctx->opt.precision >= 1)
     CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32, ctx->Un,
                                   ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
   else
@@ -642,7 +690,7 @@ void graph_arnoldi(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, 
 // One GMRES solve (FP64 or mixed) appended to the top-level segment.
 void graph_gmres(sgn_ctx* ctx, GraphSeg& top) {
   const Geom& G = ctx->G;
-  const bool mixed = ctx->opt.precision == 1;
+  const bool mixed = ctx->opt.precision >= 1;
   const size_t vs = G.nspec();
   double* cnorm_d = ctx->scal + 0;
   double* beta_d = ctx->scal + 1;
@@ -668,7 +716,7 @@ void graph_gmres(sgn_ctx* ctx, GraphSeg& top) {
   ctl.h_step = sweep.handle();
   sweep.open();
   long long per_sweep = count_launches(ctx, [&] {
-    CK(launch_matvec<double>(G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+    refine_matvec(ctx, true, EX(ctx));
     C64* r = mixed ? ctx->r64 : ctx->V;
     CK(launch_residual<double>(G, ctx->cvec, ctx->w, r, ctx->partials, EX(ctx)));
     CK(launch_reduce(ctx->partials, 1, beta_d, true, nullptr, EX(ctx)));
@@ -735,7 +783,7 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
     rk.krasny = ctx->opt.krasny;
     rk.krasny_thr = ctx->opt.krasny_thr;
     rk.g = ctx->g;
-    if (ctx->opt.precision == 1)
+    if (ctx->opt.precision >= 1)
       CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32,
                                     ctx->Un, ctx->Us, ctx->acc, ctx->bh, rk, EX(ctx))));
     else
@@ -851,7 +899,7 @@ void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* s
   const GmresDev& st = *ctx->gst_host;
   ctx->stats.solves += (int)st.tot_solves;
   ctx->stats.matvecs += st.tot_its;
-  if (ctx->opt.precision == 1) ctx->stats.refinements += st.tot_sweeps;
+  if (ctx->opt.precision >= 1) ctx->stats.refinements += st.tot_sweeps;
   if (st.max_its > ctx->stats.max_iters) ctx->stats.max_iters = st.max_its;
   ctx->stats.last_iters = st.last_its;
   ctx->stats.last_relres = st.last_relres;
@@ -890,8 +938,10 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   sgn_options o;
   sgn_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != 0 && o.precision != 1)
-    return fail(nullptr, SGN_EINVAL, "sgn_create: precision must be 0 (FP64) or 1 (FP32 + FP64 refinement)");
+  if (o.precision < 0 || o.precision > 2)
+    return fail(nullptr, SGN_EINVAL,
+                "sgn_create: precision must be 0 (FP64), 1 (FP32 + FP64 refinement) or 2 (FP32 + double-float "
+                "refinement)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
   if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2 ||
       (o.graph != 0 && o.graph != 1))
@@ -916,7 +966,8 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   try {
     CK(cudaGetDevice(&ctx->device));
     init_kernel_attributes<double>();
-    if (o.precision == 1) init_kernel_attributes<float>();
+    if (o.precision >= 1) init_kernel_attributes<float>();
+    if (o.precision == 2) init_kernel_attributes_df();
     build_tables(ctx);
     const size_t ns = G.nspec();
     for (int f = 0; f < 3; ++f) {
@@ -933,7 +984,11 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->cvec = dalloc<C64>(ctx, ns);
     ctx->w = dalloc<C64>(ctx, ns);
     for (int i = 0; i < 4; ++i) ctx->tmp[i] = dalloc<C64>(ctx, ns);
-    if (o.precision == 1) {
+    if (o.precision == 2) {
+      ctx->crd = dalloc<dfl>(ctx, G.nphys());
+      ctx->ccd = dalloc<dfl>(ctx, G.nphys());
+    }
+    if (o.precision >= 1) {
       ctx->V32 = dalloc<C32>(ctx, ns * (size_t)(o.restart + 1));
       ctx->w32 = dalloc<C32>(ctx, ns);
       for (int i = 0; i < 4; ++i) ctx->tmp32[i] = dalloc<C32>(ctx, ns);
@@ -1082,10 +1137,10 @@ sgn_status sgn_elliptic_apply(sgn_t ctx, const double* h, const double* sigma, d
   API_BEGIN
   if (!h || !sigma || !out) return fail(ctx, SGN_EINVAL, "sgn_elliptic_apply: NULL pointer");
   reset_flags(ctx);
-  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
+  coef_phys(ctx, h);
   const double* fi[1] = {sigma};
   fwd2(ctx, fi, 1, &ctx->sig);
-  CK(launch_matvec<double>(ctx->G, ctx->tb, ctx->sig, ctx->cr, ctx->cc, ctx->w, ctx->tmp, false, EX(ctx)));
+  refine_matvec(ctx, false, EX(ctx));
   const C64* in[1] = {ctx->w};
   double* o[1] = {out};
   inv2(ctx, in, nullptr, nullptr, 1, o);
@@ -1101,7 +1156,7 @@ sgn_status sgn_gmres_solve(sgn_t ctx, const double* h, const double* b, double* 
   API_BEGIN
   if (!h || !b || !sigma) return fail(ctx, SGN_EINVAL, "sgn_gmres_solve: NULL pointer");
   reset_flags(ctx);
-  CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
+  coef_phys(ctx, h);
   const double* fb[1] = {b};
   fwd2(ctx, fb, 1, &ctx->bh);
   const double* fs[1] = {sigma};

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "fft_core.cuh"
 
 namespace sgn {
@@ -42,7 +43,7 @@ struct Tables {
   cpx<T>* twy = nullptr;  // W_Ny^k, k < Ny
   T* kx = nullptr;        // 2 pi m / Lx, m = 0..Nx/2, Nyquist 0   [Nxh]
   T* ky = nullptr;        // 2 pi m / Ly, m = 0..Ny/2-1, -Ny/2..-1, Nyquist 0 [Ny]
-  T* minv = nullptr;      // 1 / (3 + kx^2 + ky^2) per half-spectrum entry [Ny][ldS] (FP64 only)
+  T* minv = nullptr;      // 1 / (3 + kx^2 + ky^2) per half-spectrum entry [Ny][ldS] (FP64, double-float)
 };
 
 // GMRES scalars that live on the device (Hessenberg, rotations, residual).
@@ -228,6 +229,17 @@ template <typename T>
 cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
                           cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex,
                           const int* jsel = nullptr, size_t jstride = 0);
+
+// the same with sigma_hat and w stored in S and the passes in T (the
+// double-float refinement matvec: T = dfl, S = double)
+template <typename T, typename S>
+cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* sig, const T* cr, const T* cc,
+                             cpx<S>* w, cpx<T>* const* tmp, bool precond, const Exec& ex,
+                             const int* jsel = nullptr, size_t jstride = 0);
+// y-inverse of one FP64 half spectrum into the pass type T
+template <typename T>
+cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>* in, cpx<T>* out, const Exec& ex);
+void init_kernel_attributes_df();
 
 // RHS of one stage from state U (3 spectra), sigma_hat, h, cr; K goes through
 // the RK epilogue. tmp: 4 spectra. Writes b_hat of the next stage state.

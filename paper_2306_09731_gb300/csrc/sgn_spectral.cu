@@ -47,7 +47,7 @@ __device__ __forceinline__ void load_packed(cpx<T> (&v)[8], const cpx<T>* S0, co
     const int kk = (k <= half) ? k : N - k;
     cpx<T> A = ld(S0 + kk), B = ld(S1 + kk);
     if (deriv) {
-      const T kv = __ldg(kx + kk);
+      const T kv = ldr(kx + kk);
       A = mul_ik(A, kv);
       B = mul_ik(B, kv);
     }
@@ -213,6 +213,32 @@ __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, 
   }
 }
 
+// The same three coefficients in double-float (precision 2): 1/h by one Newton
+// step from the FP32 reciprocal (see recip), the factors 1/(2N) and 3/(2N) as
+// exact power-of-two scalings and one product by 1.5; h is the depth in FP32
+// range (1/h^3 must not overflow). The FP32 copies are the high parts. h may be
+// null (the refinement matvec reads only cr and cc).
+__device__ __forceinline__ void coef_point_df(dfl hv, float invN, dfl* h, dfl* cr, dfl* cc, size_t i, int* flags,
+                                              const CoefCopy& cp) {
+  if (!isfinite(hv.hi)) {
+    atomicOr(flags, FLAG_NONFINITE);
+  } else if (!(hv.hi > 0.0f)) {
+    atomicOr(flags, FLAG_CAVITATION);
+  }
+  const dfl r = recip(hv);
+  const dfl vr = scale_pow2(r, 0.5f * invN);
+  const dfl vc = scale_pow2(mul_f((r * r) * r, 1.5f), invN);
+  const dfl a = hv - dfl(1.0f);
+  if (h) h[i] = a;
+  cr[i] = vr;
+  cc[i] = vc;
+  if (cp.h) {
+    cp.h[i] = a.hi;
+    cp.cr[i] = vr.hi;
+    cp.cc[i] = vc.hi;
+  }
+}
+
 // Hy = y-inverse of h_hat; x-inverse gives N*h. Writes the anomaly h - 1,
 // cr = 0.5/(N h) and cc = 1.5/(N h^3): the coefficients of Eq. (sigmav) with
 // the factor 1/(2N) of the matvec's packed transforms folded in.
@@ -230,8 +256,15 @@ __global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restr
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
-    coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
+    if constexpr (std::is_same<T, dfl>::value) {
+      // N = Nx Ny is a power of two: the scaling by 1/N is exact
+      const float fN = (float)invN;
+      coef_point_df(scale_pow2(v[s].x, fN), fN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
+      coef_point_df(scale_pow2(v[s].y, fN), fN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
+    } else {
+      coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
+      coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
+    }
   }
 }
 
@@ -239,8 +272,12 @@ template <typename T>
 __global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, T* cc, int* flags, CoefCopy cp) {
   const double invN = 1.0 / (double)G.nphys();
   const size_t n = G.nphys();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    coef_point<T>(hp[i], invN, h, cr, cc, i, flags, cp);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<T, dfl>::value)
+      coef_point_df(dfl(hp[i]), (float)invN, h, cr, cc, i, flags, cp);
+    else
+      coef_point<T>(hp[i], invN, h, cr, cc, i, flags, cp);
+  }
 }
 
 // ---------------------------------------------------------- fused matvec x
@@ -291,7 +328,7 @@ __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const 
   for (int s = 0; s < 5; ++s) {
     if (!split_owns(s, L.t) || !L.valid) continue;
     const int k = L.t + s * T_;
-    const T kv = __ldg(kx + k);
+    const T kv = ldr(kx + k);
     Cout[o0 + k] = a0[s] - mul_ik(b0[s], kv);
     Cout[o1 + k] = a1[s] - mul_ik(b1[s], kv);
   }
@@ -392,7 +429,7 @@ __global__ void __launch_bounds__(256, rhs_min_blocks<T>()) k_rhs_x(Geom G, cons
   for (int s = 0; s < 5; ++s) {
     if (!split_owns(s, L.t) || !L.valid) continue;
     const int k = L.t + s * T_;
-    const T kv = __ldg(kx + k);
+    const T kv = ldr(kx + k);
     Cq[o0 + k] = mul_ik(f0[s], -kv);
     Cq[o1 + k] = mul_ik(f1[s], -kv);
   }
@@ -474,7 +511,7 @@ __global__ void __launch_bounds__(ypass_threads(NIN, sizeof(T))) k_ypass(Geom G,
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
       cpx<T> z = ld_as<T, S>(src + (size_t)row * G.ldS + col);
-      if (in.deriv[i]) z = mul_ik(z, __ldg(ky + row));
+      if (in.deriv[i]) z = mul_ik(z, ldr(ky + row));
       r[i][s] = z;
     }
     fft_regs<INV>(r[i], smb + c, tw, t, lN, lC);
@@ -496,26 +533,28 @@ struct EpiStore {
 };
 
 // w = [M^-1] (C - i ky By), M = 3 + kx^2 + ky^2 (Section 3 preconditioner)
-// minv (may be null): the FP64 path reads M^-1 from a table, because a division
-// costs about 25 FP64 instructions here; FP32 divides (cheap) on the fly.
-template <typename T>
+// minv (may be null): the FP64 and double-float passes read M^-1 from a table,
+// because a division costs about 25 FP64 instructions here; FP32 divides
+// (cheap) on the fly. SO: the storage type of w (the double-float refinement
+// matvec hands its result to the FP64 residual).
+template <typename T, typename SO = T>
 struct EpiMatvec {
-  cpx<T>* w;
+  cpx<SO>* w;
   const T* kx;
   int precond;
   const T* minv;
   __device__ __forceinline__ void operator()(cpx<T> (&r)[2][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
-    const T kxv = __ldg(kx + col);
+    const T kxv = ldr(kx + col);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
-      const T kyv = __ldg(ky + row);
+      const T kyv = ldr(ky + row);
       const size_t e = (size_t)row * G.ldS + col;
       cpx<T> z = r[0][s] - mul_ik(r[1][s], kyv);
-      if (precond) z = scl(z, minv ? __ldg(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
-      w[e] = z;
+      if (precond) z = scl(z, minv ? ldr(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+      w[e] = mk((SO)z.x, (SO)z.y);
     }
   }
 };
@@ -533,12 +572,12 @@ struct EpiK {
   __device__ __forceinline__ void operator()(cpx<T> (&r)[3][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
-    const T kxv = __ldg(kx + col);
+    const T kxv = ldr(kx + col);
     const bool keepx = !dealias || 3 * col <= G.Nx;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int row = t + s * T_;
-      const T kyv = __ldg(ky + row);
+      const T kyv = ldr(ky + row);
       const size_t e = (size_t)row * G.ldS + col;
       cpx<T> k0 = r[0][s] - mul_ik(r[1][s], kyv);
       cpx<T> k1 = mul_ik(r[2][s], -kxv);
@@ -806,17 +845,18 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
-                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
-                          size_t jstride) {
+// S: storage type of sigma_hat and w; T: arithmetic of the passes
+template <typename T, typename S>
+cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* sig, const T* cr, const T* cc,
+                             cpx<S>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
+                             size_t jstride) {
   dim3 grid, block;
   size_t smem;
   // y-inverse of sigma_hat and i ky sigma_hat
   y_config<T>(G, 2, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
-    YIn<T, 2> yi{};
+    YIn<T, 2, S> yi{};
     yi.src[0] = sig;
     yi.src[1] = sig;
     yi.deriv[0] = 0;
@@ -827,7 +867,7 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
     ep.dst[0] = tmp[0];
     ep.dst[1] = tmp[1];
     ex.begin(PK_MV_YINV);
-    k_ypass<T, true, 2, EpiStore<T, 2>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, true, 2, EpiStore<T, 2>, S, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   x_config<T>(G, grid, block, smem, 1);
@@ -843,12 +883,47 @@ cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig,
     YIn<T, 2> yi{};
     yi.src[0] = tmp[0];
     yi.src[1] = tmp[1];
-    EpiMatvec<T> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
+    EpiMatvec<T, S> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
     ex.begin(PK_MV_YFWD);
-    k_ypass<T, false, 2, EpiMatvec<T>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    k_ypass<T, false, 2, EpiMatvec<T, S>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
+                          cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
+                          size_t jstride) {
+  return launch_matvec_io<T, T>(G, tb, sig, cr, cc, w, tmp, precond, ex, jsel, jstride);
+}
+
+// y-inverse of one FP64 half spectrum into the pass type T (the coefficient
+// pass of the double-float path)
+template <typename T>
+cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>* in, cpx<T>* out, const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  y_config<T>(G, 1, grid, block, smem);
+  YIn<T, 1, double> yi{};
+  yi.src[0] = in;
+  EpiStore<T, 1> ep{};
+  ep.dst[0] = out;
+  ex.begin(PK_IO);
+  k_ypass<T, true, 1, EpiStore<T, 1>, double><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+  ex.end();
+  return cudaGetLastError();
+}
+
+// dynamic shared memory limits of the double-float kernels
+void init_kernel_attributes_df() {
+  typedef dfl T;
+  set_smem<T>((const void*)k_coef_x<T>);
+  set_smem<T>((const void*)k_mv_x<T>);
+  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>, double>);
+  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T, double>>);
+  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>, double>);
+  cudaGetLastError();
 }
 
 template <typename T, typename S>
@@ -989,6 +1064,15 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
 SGN_INST(double)
 
 template void init_kernel_attributes<float>();
+template cudaError_t launch_matvec_io<dfl, double>(const Geom&, const Tables<dfl>&, const cpx<double>*,
+                                                   const dfl*, const dfl*, cpx<double>*, cpx<dfl>* const*, bool,
+                                                   const Exec&, const int*, size_t);
+template cudaError_t launch_y_inv64<dfl>(const Geom&, const Tables<dfl>&, const cpx<double>*, cpx<dfl>*,
+                                         const Exec&);
+template cudaError_t launch_coef_x<dfl>(const Geom&, const Tables<dfl>&, const cpx<dfl>*, dfl*, dfl*, dfl*, int*,
+                                        const CoefCopy&, const Exec&);
+template cudaError_t launch_coef_phys<dfl>(const Geom&, const double*, dfl*, dfl*, dfl*, int*, const CoefCopy&,
+                                           const Exec&);
 template cudaError_t launch_matvec<float>(const Geom&, const Tables<float>&, const cpx<float>*, const float*,
                                           const float*, cpx<float>*, cpx<float>* const*, bool, const Exec&,
                                           const int*, size_t);

@@ -1,0 +1,159 @@
+"""Precision 2: the mixed path of precision 1 with the refinement residual's
+matvec and the coefficient pass in double-float arithmetic (value = sum of two
+FP32 numbers, 48-bit significand).
+
+Bars:
+  * L[sigma] (sgn_elliptic_apply of a precision-2 handle runs the double-float
+    matvec) within 1e-11 relative L2 of the FP64 oracle. The refinement only
+    needs the residual of c - A sigma resolved well below tol |c| = 1e-10 |c|;
+    the double-float unit roundoff 2^-48 ~ 3.6e-15, grown by the log2 N stages
+    of four transforms and the k^2 of the operator, stays near 1e-13 here.
+  * every GMRES solve meets the FP64 tolerance test, re-checked with the oracle;
+  * RK4 fields within 1e-5 of the oracle / the FP64 path (the FP32 bulk bar of
+    precision 1).
+"""
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2306_09731_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def solver(*a, **kw):
+    from paper_2306_09731_gb300.sgn import Solver
+    return Solver(*a, precision=2, **kw)
+
+
+GRIDS = [(8, 8, 3.0, 3.0), (64, 32, 8.0, 5.0), (256, 16, 80.0, 10.0), (32, 256, 4.0, 30.0),
+         (128, 128, 10.0, 10.0), (512, 1024, 40.0, 60.0), (2048, 64, 100.0, 5.0)]
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly", GRIDS)
+def test_df_elliptic_apply_parity(Nx, Ny, Lx, Ly):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + Ny)
+    s = solver(Nx, Ny, Lx, Ly)
+    out = host(s.elliptic_apply(dev(st.h), dev(st.sigma)))
+    ref = O.elliptic_apply(O.Grid(Nx, Ny, Lx, Ly), st.h, st.sigma)
+    assert rel(out, ref) < 1e-11
+    s.close()
+
+
+def test_df_elliptic_apply_soliton_and_gaussian():
+    """Smooth workloads of the paper: the line soliton (exact sigma) and the
+    Gaussian hump at 2048 x 2048, sampled against the oracle's operator."""
+    st = I.soliton_256x16()
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly)
+    out = host(s.elliptic_apply(dev(st.h), dev(st.sigma)))
+    ref = O.elliptic_apply(O.Grid(st.Nx, st.Ny, st.Lx, st.Ly), st.h, st.sigma)
+    assert rel(out, ref) < 1e-11
+    s.close()
+    g = I.gaussian_hump(2048, 100.0, 0.5)
+    X, Y = np.meshgrid(*I.coords(2048, 2048, 100.0, 100.0))
+    sig = 0.3 * np.exp(-0.5 * (X ** 2 + Y ** 2)) * np.cos(0.7 * X)
+    s = solver(2048, 2048, 100.0, 100.0)
+    out = host(s.elliptic_apply(dev(g.h), dev(sig)))
+    ref = O.elliptic_apply(O.Grid(2048, 2048, 100.0, 100.0), g.h, sig)
+    assert rel(out, ref) < 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly,tol", [(64, 32, 8.0, 5.0, 1e-10), (128, 128, 10.0, 10.0, 1e-10),
+                                            (256, 16, 80.0, 10.0, 1e-12), (32, 256, 4.0, 30.0, 1e-9),
+                                            (512, 1024, 40.0, 60.0, 1e-10)])
+def test_df_gmres_meets_fp64_tolerance(Nx, Ny, Lx, Ly, tol):
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + 7 * Ny)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    b = O.divergence_rhs(G, st.vx, st.vy)
+    s = solver(Nx, Ny, Lx, Ly, tol=tol)
+    sig, its, rr, conv = s.gmres_solve(dev(st.h), dev(b), dev(np.zeros_like(b)))
+    assert conv and rr <= tol
+    c = O.precond_solve(G, b)
+    r = c - O.precond_solve(G, O.elliptic_apply(G, st.h, host(sig)))
+    assert np.linalg.norm(r) / np.linalg.norm(c) <= 2 * tol
+    s.close()
+
+
+def test_df_rk4_soliton_against_oracle_and_exact():
+    st = I.soliton_256x16()
+    G = O.Grid(st.Nx, st.Ny, st.Lx, st.Ly)
+    s = solver(st.Nx, st.Ny, st.Lx, st.Ly, guess=2)
+    h, vx, vy, sg = dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)
+    s.rk4_step(h, vx, vy, sg, 5e-3, 10)
+    oh, ovx, _, _ = O.rk4_step(G, st.h, st.vx, st.vy, st.sigma, 5e-3, 10)
+    assert rel(host(h), oh) < 1e-5 and rel(host(vx), ovx) < 1e-5
+    s.rk4_step(h, vx, vy, sg, 5e-3, 90)
+    ex = I.soliton_256x16(t=0.5)
+    assert rel(host(h), ex.h) < 1e-5 and rel(host(vx), ex.vx) < 1e-5
+    s.close()
+
+
+def test_df_rk4_random_against_oracle():
+    Nx, Ny, L = 64, 64, 8.0
+    st = I.random_state(Nx, Ny, L, L, seed=31)
+    G = O.Grid(Nx, Ny, L, L)
+    phi = I.random_smooth(Nx, Ny, L, L, seed=32, kmax=4)
+    vx, vy = O.dx(G, phi), O.dy(G, phi)
+    z = np.zeros_like(vx)
+    s = solver(Nx, Ny, L, L, dealias=1)
+    a = [dev(st.h), dev(vx), dev(vy), dev(z)]
+    s.rk4_step(*a, 2e-3, 8)
+    ref = O.rk4_step(G, st.h, vx, vy, z, 2e-3, 8, tol=1e-13, dealias=True)
+    for x, r in zip(a[:3], ref[:3]):
+        assert rel(host(x), r) < 1e-5
+    s.close()
+
+
+def test_df_gaussian_2048_close_to_fp64_and_precision1():
+    """The benchmark workload: two steps of precision 2 stay within 1e-5 of
+    the FP64 path, as precision 1 does, and conserve mass."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.gaussian_hump(2048, 100.0, 0.5)
+    runs = {}
+    for prec in (2, 1, 0):
+        s = Solver(2048, 2048, 100.0, 100.0, precision=prec, guess=2)
+        f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+        m0 = s.invariants(*f)[0]
+        s.rk4_step(*f, 1e-3, 2)
+        m1 = s.invariants(*f)[0]
+        assert abs(m1 - m0) < 1e-14 * 100.0 * 100.0
+        runs[prec] = [host(x) for x in f[:3]]
+        s.close()
+    for a, b in zip(runs[2], runs[0]):
+        if np.linalg.norm(b) > 0:
+            assert rel(a, b) < 1e-5
+
+
+def test_df_cavitation_reported():
+    from paper_2306_09731_gb300.sgn import SGNError, SGN_ECAVITATION
+    st = I.random_state(32, 32, 6.0, 6.0, seed=1)
+    s = solver(32, 32, 6.0, 6.0)
+    bad = st.h.copy()
+    bad[3, 5] = -0.1
+    with pytest.raises(SGNError) as e:
+        s.elliptic_apply(dev(bad), dev(st.sigma))
+    assert e.value.status == SGN_ECAVITATION
+    out = host(s.elliptic_apply(dev(st.h), dev(st.sigma)))
+    assert rel(out, O.elliptic_apply(O.Grid(32, 32, 6.0, 6.0), st.h, st.sigma)) < 1e-11
+    s.close()
