@@ -293,6 +293,10 @@ constexpr int rhs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 // S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
 // Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
 // reads only its own row pair before writing it: Cout/Byout may alias S/Sy.
+// Three phases, each an inverse transform, a pointwise product and a forward
+// transform, so that one 8-slot signal is live at a time (plus the a^x half
+// spectra of phase 1 until phase 2 combines them): a = 3 sigma/h^3, then
+// bx = sigma_x/h, then by = sigma_y/h.
 template <typename T, int LN = 0>
 __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
@@ -302,28 +306,30 @@ __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const 
   const int lN = LN > 0 ? LN : G.lNx;
   const int N = 1 << lN, T_ = N >> 3;
   const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
-  cpx<T> X[8], Y[8], Z[8];
-  load_packed(X, S + o0, S + o1, true, kx, L.t, lN);
-  fft_regs<true>(X, sm, tw, L.t, lN);
-  load_packed(Y, Sy + o0, Sy + o1, false, kx, L.t, lN);
-  fft_regs<true>(Y, sm, tw, L.t, lN);
+  const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
+  cpx<T> Z[8];
+  cpx<T> a0[5], a1[5], b0[5], b1[5];
+  // a = 3 sigma / h^3
   load_packed(Z, S + o0, S + o1, false, kx, L.t, lN);
   fft_regs<true>(Z, sm, tw, L.t, lN);
-  const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    const T r0 = cr[p0 + x], r1 = cr[p1 + x], c0 = cc[p0 + x], c1 = cc[p1 + x];
-    Z[s] = mk(c0 * Z[s].x, c1 * Z[s].y);
-    X[s] = mk(r0 * X[s].x, r1 * X[s].y);
-    Y[s] = mk(r0 * Y[s].x, r1 * Y[s].y);
+    Z[s] = mk(cc[p0 + x] * Z[s].x, cc[p1 + x] * Z[s].y);
   }
-  cpx<T> a0[5], a1[5], b0[5], b1[5];
   fft_regs<false>(Z, sm, tw, L.t, lN);
   split_pair(Z, sm, L.t, lN, a0, a1);
   __syncthreads();
-  fft_regs<false>(X, sm, tw, L.t, lN);
-  split_pair(X, sm, L.t, lN, b0, b1);
+  // bx = sigma_x / h, combined with a
+  load_packed(Z, S + o0, S + o1, true, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    Z[s] = mk(cr[p0 + x] * Z[s].x, cr[p1 + x] * Z[s].y);
+  }
+  fft_regs<false>(Z, sm, tw, L.t, lN);
+  split_pair(Z, sm, L.t, lN, b0, b1);
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
     if (!split_owns(s, L.t) || !L.valid) continue;
@@ -333,8 +339,16 @@ __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const 
     Cout[o1 + k] = a1[s] - mul_ik(b1[s], kv);
   }
   __syncthreads();
-  fft_regs<false>(Y, sm, tw, L.t, lN);
-  split_pair(Y, sm, L.t, lN, b0, b1);
+  // by = sigma_y / h
+  load_packed(Z, Sy + o0, Sy + o1, false, kx, L.t, lN);
+  fft_regs<true>(Z, sm, tw, L.t, lN);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int x = L.t + s * T_;
+    Z[s] = mk(cr[p0 + x] * Z[s].x, cr[p1 + x] * Z[s].y);
+  }
+  fft_regs<false>(Z, sm, tw, L.t, lN);
+  split_pair(Z, sm, L.t, lN, b0, b1);
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
     if (!split_owns(s, L.t) || !L.valid) continue;
@@ -474,28 +488,34 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // Column tile: C = blockDim / (Ny/8) neighbouring kx columns, thread index
 // c + C*t. Each input column is transformed in registers; the epilogue gets
 // all NIN results of the thread's 8 rows.
-// Threads of a y-pass block: FP64 passes with 3 or 4 transforms per thread need
-// the registers of 256-thread blocks; FP32 ones fit 512 (two columns per block,
-// twice the bytes per row segment).
-constexpr int ypass_threads(int nin, int tbytes) { return (nin >= 3 && tbytes == 8) ? 256 : 512; }
+// Threads of a y-pass block. FP32: 512 (two columns per block at Ny = 2048,
+// twice the bytes per row segment). FP64: 256, the registers of one column per
+// block. Double-float: 256 for the inverse passes, 512 for the forward pass
+// with the matvec epilogue (measured at 2048^2: FP64 inverse 321 against 371 us
+// and forward 327 against 386 us; double-float inverse 158 against 182 us,
+// forward 140 against 172 us).
+template <typename T, bool INV>
+constexpr int ypass_threads() {
+  return sizeof(T) == 4 ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
+}
 
 // LN > 0: compile-time column length 2^LN; the interleave 2^LC of the block's
 // columns then follows from the block size the launcher uses.
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-template <int LN, int NIN, int TB>
+template <typename T, bool INV, int LN>
 constexpr int ypass_lc() {
-  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads(NIN, TB)) - (LN - 3), 0, 6);
+  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV>()) - (LN - 3), 0, 6);
 }
 
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads(NIN, sizeof(T))) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
+__global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
                                                 YIn<T, NIN, S> in, Epi epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
   const int lN = LN > 0 ? LN : G.lNy;
   const int T_ = 1 << (lN - 3);
-  constexpr int LCc = ypass_lc<LN, NIN, sizeof(T)>();
+  constexpr int LCc = ypass_lc<T, INV, LN>();
   const int lC = LCc >= 0 ? LCc : __ffs(blockDim.x >> (lN - 3)) - 1;
   const int c = threadIdx.x & ((1 << lC) - 1);
   const int t = threadIdx.x >> lC;
@@ -710,10 +730,10 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
   grid = dim3((G.Ny / 2 + P - 1) / P, nf);
   smem = (size_t)P * smem_elems(G.Nx) * sizeof(cpx<T>);
 }
-template <typename T>
-static inline void y_config(const Geom& G, int nin, dim3& grid, dim3& block, size_t& smem) {
+template <typename T, bool INV>
+static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem) {
   const int Tn = G.Ny >> 3;
-  const int tpb = ypass_threads(nin, sizeof(T));
+  const int tpb = ypass_threads<T, INV>();
   int C = tpb / Tn;
   if (C < 1) C = 1;
   if (C > 64) C = 64;
@@ -803,7 +823,10 @@ cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const
                          const int* deriv, int nf, cpx<T>* const* out, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  y_config<T>(G, 1, grid, block, smem);
+  if (inverse)
+    y_config<T, true>(G, grid, block, smem);
+  else
+    y_config<T, false>(G, grid, block, smem);
   for (int i = 0; i < nf; ++i) {
     YIn<T, 1> yi{};
     yi.src[0] = in[i];
@@ -853,7 +876,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
   dim3 grid, block;
   size_t smem;
   // y-inverse of sigma_hat and i ky sigma_hat
-  y_config<T>(G, 2, grid, block, smem);
+  y_config<T, true>(G, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2, S> yi{};
@@ -877,7 +900,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
     ex.end();
   });
-  y_config<T>(G, 2, grid, block, smem);
+  y_config<T, false>(G, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2> yi{};
@@ -904,7 +927,7 @@ template <typename T>
 cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>* in, cpx<T>* out, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  y_config<T>(G, 1, grid, block, smem);
+  y_config<T, true>(G, grid, block, smem);
   YIn<T, 1, double> yi{};
   yi.src[0] = in;
   EpiStore<T, 1> ep{};
@@ -932,7 +955,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                        cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  y_config<T>(G, 4, grid, block, smem);
+  y_config<T, true>(G, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 4, S> yi{};
@@ -957,7 +980,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                                                (T)rk.g, tmp[0], tmp[1], tmp[2]);
     ex.end();
   });
-  y_config<T>(G, 3, grid, block, smem);
+  y_config<T, false>(G, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 3> yi{};
