@@ -34,8 +34,51 @@ struct __align__(8) dfl {
   // nearest split of an FP64 value (folded at compile time for constants)
   __host__ __device__ constexpr dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  // (device passes that write FP64 use dfl_to_f64, which avoids the conversions)
   __host__ __device__ explicit operator float() const { return hi; }
 };
+
+// Split of an FP64 value into hi + lo without FP64 instructions (a conversion
+// through FP64 arithmetic keeps the slow FP64 pipe of this part busy in the
+// passes that read FP64 spectra). hi: the sign, the exponent and the top 23
+// stored mantissa bits (truncated); lo: the remaining 29 bits, turned into an
+// FP32 number with two exponent-bias tricks (2^23 + b - 2^23 is exact for
+// b < 2^23) and one FMA that rounds them to 24 bits, then scaled by
+// 2^(e - 1075) exactly. |lo| < ulp(hi), so hi + lo carries 47 bits. Branch
+// free (selects only): magnitudes below 2^-74 keep no low part and below
+// 2^-126 flush to a signed zero, beyond the FP32 range become infinite, NaN
+// stays NaN: the double-float passes work within the FP32 exponent range.
+__device__ __forceinline__ dfl dfl_from_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned top = (unsigned)(b >> 32);
+  const unsigned sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7ffu);
+  float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const float fb = __fsub_rn(__uint_as_float(0x4b000000u | (unsigned)(b & 0x7fffffu)), 8388608.0f);
+  const float fa = __fsub_rn(__uint_as_float(0x4b000000u | (unsigned)((b >> 23) & 0x3fu)), 8388608.0f);
+  float lo = __fmul_rn(__fmaf_rn(fa, 8388608.0f, fb), __uint_as_float((unsigned)(e - 948) << 23));
+  lo = sign ? -lo : lo;
+  if (e < 949) lo = 0.0f;
+  if (e < 897) hi = __uint_as_float(sign);
+  if (e > 1150) {
+    const bool nan = e == 2047 && (b & 0xfffffffffffffull) != 0ull;
+    hi = __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+    lo = 0.0f;
+  }
+  return dfl(hi, lo);
+}
+
+// hi + lo rounded to FP64 with one FP64 addition: each part is widened by
+// placing its bits instead of a conversion instruction (selects only: FP32
+// subnormals, below 2^-126, widen to zero; infinities and NaN keep their kind).
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long e64 = ex == 0u ? 0ull : (ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u));
+  const unsigned long long m64 = ex == 0u ? 0ull : (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (e64 << 52) | m64));
+}
+__device__ __forceinline__ double dfl_to_f64(dfl a) { return f32_to_f64_bits(a.hi) + f32_to_f64_bits(a.lo); }
 
 __device__ __forceinline__ dfl two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);

@@ -56,10 +56,11 @@ __device__ void givens_step(GmresDev* st, int j, GmresReadback* rb, const int* f
 }
 
 // True (in every thread) in the block that finishes last; it then sees every
-// other block's partials. Resets the counter for the next launch.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
+// other block's partials. Resets the counter for the next launch. wrote: this
+// thread stored a partial; only those stores need the fence before the ticket.
+__device__ __forceinline__ bool last_block(unsigned* counter, bool wrote = true) {
   __shared__ int s_last;
-  __threadfence();
+  if (wrote) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned total = gridDim.x * gridDim.y;
@@ -78,6 +79,53 @@ __device__ __forceinline__ double reduce_slot(const double* partials, int slot, 
   return block_reduce(v, red);
 }
 
+// out[s] = sum of the NBLK partials of slot s, s < nslots, one warp per slot:
+// each lane keeps 8 loads in flight over its lane-strided share, then a
+// shuffle tree. The order is fixed, so the sums are deterministic. Up to
+// blockDim/32 slots finish in one round (the slot-by-slot block reduction
+// took one dependent load chain and two barriers per slot).
+__device__ __forceinline__ void reduce_slots(const double* partials, int nslots, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int s = warp; s < nslots; s += nw) {
+    const double* p = partials + (size_t)s * NBLK;
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 0.0;
+    for (int b = lane; b < NBLK; b += 32 * 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int bb = b + 32 * u;
+        if (bb < NBLK) a[u] += __ldcg(p + bb);
+      }
+    }
+    double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[s] = v;
+  }
+}
+
+// Block sums of K values with one barrier: thread k (< K) returns the sum of
+// value k. Each warp sums in the accumulation type A (FP32 for the FP32
+// vectors: an FP64 shuffle tree costs more FP64-pipe time than the sweep
+// itself on this part), then the warp sums are added in FP64 in a fixed order.
+// red: K * 32 doubles of shared memory.
+template <int K, typename A>
+__device__ __forceinline__ double block_reduce_multi(A (&v)[K], double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k * 32 + wid] = (double)v[k];
+  }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < K)
+    for (int i = 0; i < nw; ++i) t += red[threadIdx.x * 32 + i];
+  return t;
+}
+
 // Per-thread accumulation type: FP64 vectors accumulate in FP64; FP32 vectors
 // (the inner solve of precision 1) form products and each thread's running
 // sum over its few entries (about 7 at 2048^2) in FP32 and hand the partial
@@ -92,12 +140,14 @@ struct Acc<float> {
   typedef float type;
 };
 
-constexpr int DOT_CHUNK = 4;  // dot products per block row of the grid (blockIdx.y)
+constexpr int DOT_CHUNK = 4;  // dot products per sweep of a block's entries
 
-// partials[i * NBLK + b] = block b's share of <V_i, w> for the chunk
-// i = 4*blockIdx.y .. +3 (i < nv); chunk 0 also writes |w|^2 to slot nv.
-// Four accumulators keep registers low enough for 4 blocks per SM: the
-// kernel is latency bound at lower occupancy.
+// partials[i * NBLK + b] = block b's share of <V_i, w> (i < nv) and
+// partials[nv * NBLK + b] its share of |w|^2. Each block runs over the basis in
+// chunks of four vectors (one sweep of its entries per chunk; at the usual
+// cycle lengths one chunk), so the grid does not depend on nv: graph mode reads
+// nv from the device. Four accumulators keep registers low enough for 4 blocks
+// per SM.
 // gate (may be null): the kernel does nothing unless *gate != 0.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
@@ -106,50 +156,47 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   if (jdev) nv = *jdev + 1;
-  __shared__ double red[32];
-  const int i0 = blockIdx.y * DOT_CHUNK;
-  const int nc = min(DOT_CHUNK, nv - i0);
-  const bool chunk0 = blockIdx.y == 0;
-  A acc[DOT_CHUNK];
+  __shared__ double red[(DOT_CHUNK + 1) * 32];
+  for (int i0 = 0; i0 < nv; i0 += DOT_CHUNK) {
+    const int nc = min(DOT_CHUNK, nv - i0);
+    const bool chunk0 = i0 == 0;
+    A acc[DOT_CHUNK];
 #pragma unroll
-  for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = (A)0;
-  A nrm = (A)0;
-  const cpx<T>* Vc = V + (size_t)i0 * vstride;
-  // chunks past nv (graph mode sizes the grid for the largest nv) only take part
-  // in the last-block ticket
-  if (nc > 0 || chunk0) {
-    for (Walk it(G); it.ok(); it.next()) {
-      const cpx<T> we = w[it.e];
-      const A wt = col_weight_k<A>(G, it.col);
-      const A wx = wt * (A)we.x, wy = wt * (A)we.y;
-      cpx<T> v[DOT_CHUNK];
+    for (int i = 0; i < DOT_CHUNK; ++i) acc[i] = (A)0;
+    A nrm = (A)0;
+    const cpx<T>* Vc = V + (size_t)i0 * vstride;
+    // two interleaved walkers: both entries' loads issue before any use
+    for (Walk a(G, 0, 2), b(G, 1, 2); a.ok(); a.next(), b.next()) {
+      const bool bok = b.ok();
+      const size_t eb = bok ? b.e : a.e;
+      const cpx<T> wa = w[a.e], wb = w[eb];
+      cpx<T> va[DOT_CHUNK], vb[DOT_CHUNK];
 #pragma unroll
       for (int i = 0; i < DOT_CHUNK; ++i)
-        if (i < nc) v[i] = Vc[i * vstride + it.e];
+        if (i < nc) {
+          va[i] = Vc[i * vstride + a.e];
+          vb[i] = Vc[i * vstride + eb];
+        }
+      const A ta = col_weight_k<A>(G, a.col), tb = bok ? col_weight_k<A>(G, b.col) : (A)0;
+      const A ax = ta * (A)wa.x, ay = ta * (A)wa.y, bx = tb * (A)wb.x, by = tb * (A)wb.y;
 #pragma unroll
       for (int i = 0; i < DOT_CHUNK; ++i)
-        if (i < nc) acc[i] += wx * (A)v[i].x + wy * (A)v[i].y;
-      if (chunk0) nrm += wx * (A)we.x + wy * (A)we.y;
+        if (i < nc) acc[i] += (ax * (A)va[i].x + ay * (A)va[i].y) + (bx * (A)vb[i].x + by * (A)vb[i].y);
+      if (chunk0) nrm += (ax * (A)wa.x + ay * (A)wa.y) + (bx * (A)wb.x + by * (A)wb.y);
     }
-  }
+    // thread i < DOT_CHUNK holds <V_{i0+i}, w>, thread DOT_CHUNK |w|^2
+    A vals[DOT_CHUNK + 1];
 #pragma unroll
-  for (int i = 0; i < DOT_CHUNK; ++i) {
-    if (i < nc) {
-      const double tot = block_reduce((double)acc[i], red);
-      if (threadIdx.x == 0) partials[(size_t)(i0 + i) * NBLK + blockIdx.x] = tot;
-    }
-  }
-  if (blockIdx.y == 0) {
-    const double tot = block_reduce((double)nrm, red);
-    if (threadIdx.x == 0) partials[(size_t)nv * NBLK + blockIdx.x] = tot;
+    for (int i = 0; i < DOT_CHUNK; ++i) vals[i] = acc[i];
+    vals[DOT_CHUNK] = nrm;
+    const double tot = block_reduce_multi<DOT_CHUNK + 1>(vals, red);
+    if (threadIdx.x < DOT_CHUNK && (int)threadIdx.x < nc)
+      partials[(size_t)(i0 + threadIdx.x) * NBLK + blockIdx.x] = tot;
+    if (threadIdx.x == DOT_CHUNK && chunk0) partials[(size_t)nv * NBLK + blockIdx.x] = tot;
+    __syncthreads();  // red is reused by the next chunk
   }
   // the last block combines all partials: out[i] = <V_i, w>, out[nv] = |w|^2
-  if (last_block(counter)) {
-    for (int i = 0; i <= nv; ++i) {
-      const double tot = reduce_slot(partials, i, red);
-      if (threadIdx.x == 0) out[i] = tot;
-    }
-  }
+  if (last_block(counter, threadIdx.x <= DOT_CHUNK)) reduce_slots(partials, nv + 1, out);
 }
 
 // w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
@@ -180,36 +227,46 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
     nv = j + 1;
   }
   __shared__ double red[32];
-  __shared__ A cf[MAXV];
-  if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
+  __shared__ A cf[MAXV + 4];
+  if (threadIdx.x < MAXV + 4) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
   __syncthreads();
   A nrm = (A)0;
-  for (Walk it(G); it.ok(); it.next()) {
-    const cpx<T> we = w[it.e];
-    A zx = (A)we.x, zy = (A)we.y;
-    int i = 0;
-    for (; i + 4 <= nv; i += 4) {
-      const cpx<T> v0 = V[(size_t)(i + 0) * vstride + it.e], v1 = V[(size_t)(i + 1) * vstride + it.e];
-      const cpx<T> v2 = V[(size_t)(i + 2) * vstride + it.e], v3 = V[(size_t)(i + 3) * vstride + it.e];
-      zx -= cf[i] * (A)v0.x + cf[i + 1] * (A)v1.x + cf[i + 2] * (A)v2.x + cf[i + 3] * (A)v3.x;
-      zy -= cf[i] * (A)v0.y + cf[i + 1] * (A)v1.y + cf[i + 2] * (A)v2.y + cf[i + 3] * (A)v3.y;
+  // two interleaved walkers; four basis vectors per round with predicated
+  // loads rather than a remainder loop, so that a round's loads (8 entries)
+  // are in flight together
+  for (Walk a(G, 0, 2), b(G, 1, 2); a.ok(); a.next(), b.next()) {
+    const bool bok = b.ok();
+    const size_t eb = bok ? b.e : a.e;
+    const cpx<T> wa = w[a.e], wb = w[eb];
+    A zax = (A)wa.x, zay = (A)wa.y, zbx = (A)wb.x, zby = (A)wb.y;
+    for (int i = 0; i < nv; i += 4) {
+      cpx<T> va[4], vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = i + u < nv;
+        va[u] = in ? V[(size_t)(i + u) * vstride + a.e] : mk((T)0, (T)0);
+        vb[u] = in ? V[(size_t)(i + u) * vstride + eb] : mk((T)0, (T)0);
+      }
+      zax -= (cf[i] * (A)va[0].x + cf[i + 1] * (A)va[1].x) + (cf[i + 2] * (A)va[2].x + cf[i + 3] * (A)va[3].x);
+      zay -= (cf[i] * (A)va[0].y + cf[i + 1] * (A)va[1].y) + (cf[i + 2] * (A)va[2].y + cf[i + 3] * (A)va[3].y);
+      zbx -= (cf[i] * (A)vb[0].x + cf[i + 1] * (A)vb[1].x) + (cf[i + 2] * (A)vb[2].x + cf[i + 3] * (A)vb[3].x);
+      zby -= (cf[i] * (A)vb[0].y + cf[i + 1] * (A)vb[1].y) + (cf[i + 2] * (A)vb[2].y + cf[i + 3] * (A)vb[3].y);
     }
-    for (; i < nv; ++i) {
-      const cpx<T> v0 = V[(size_t)i * vstride + it.e];
-      zx -= cf[i] * (A)v0.x;
-      zy -= cf[i] * (A)v0.y;
+    const cpx<T> za = mk((T)zax, (T)zay), zb = mk((T)zbx, (T)zby);
+    w[a.e] = za;
+    nrm += col_weight_k<A>(G, a.col) * ((A)za.x * (A)za.x + (A)za.y * (A)za.y);
+    if (bok) {
+      w[b.e] = zb;
+      nrm += col_weight_k<A>(G, b.col) * ((A)zb.x * (A)zb.x + (A)zb.y * (A)zb.y);
     }
-    const cpx<T> z = mk((T)zx, (T)zy);
-    w[it.e] = z;
-    const A wt = col_weight_k<A>(G, it.col);
-    nrm += wt * ((A)z.x * (A)z.x + (A)z.y * (A)z.y);
   }
-  const double tot = block_reduce((double)nrm, red);
+  A one[1] = {nrm};
+  const double tot = block_reduce_multi<1>(one, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   // the last block: |w'|^2, then (first pass) the DGKS test, and the Givens
   // step once the orthogonalisation is final. pass: 1 first pass with the DGKS
   // test, 2 second pass, 3 single pass (no reorthogonalisation)
-  if (last_block(counter)) {
+  if (last_block(counter, threadIdx.x == 0)) {
     const double n2 = reduce_slot(partials, 0, red);
     if (threadIdx.x == 0) {
       st->nrm2 = n2;
@@ -471,10 +528,8 @@ template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                         double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
                         const int* jdev) {
-  dim3 grid(NBLK, (nv + DOT_CHUNK - 1) / DOT_CHUNK);
-  if (grid.y == 0) grid.y = 1;
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<grid, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
+  k_dots<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
   ex.end();
   return cudaGetLastError();
 }

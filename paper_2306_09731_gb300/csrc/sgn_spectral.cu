@@ -274,7 +274,7 @@ __global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, 
   const size_t n = G.nphys();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if constexpr (std::is_same<T, dfl>::value)
-      coef_point_df(dfl(hp[i]), (float)invN, h, cr, cc, i, flags, cp);
+      coef_point_df(dfl_from_f64(hp[i]), (float)invN, h, cr, cc, i, flags, cp);
     else
       coef_point<T>(hp[i], invN, h, cr, cc, i, flags, cp);
   }
@@ -482,7 +482,10 @@ struct YIn {
 template <typename T, typename S>
 __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
   const cpx<S> v = *p;
-  return mk((T)v.x, (T)v.y);
+  if constexpr (std::is_same<T, dfl>::value && std::is_same<S, double>::value)
+    return mk(dfl_from_f64(v.x), dfl_from_f64(v.y));
+  else
+    return mk((T)v.x, (T)v.y);
 }
 
 // Column tile: C = blockDim / (Ny/8) neighbouring kx columns, thread index
@@ -574,7 +577,10 @@ struct EpiMatvec {
       const size_t e = (size_t)row * G.ldS + col;
       cpx<T> z = r[0][s] - mul_ik(r[1][s], kyv);
       if (precond) z = scl(z, minv ? ldr(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
-      w[e] = mk((SO)z.x, (SO)z.y);
+      if constexpr (std::is_same<T, dfl>::value && std::is_same<SO, double>::value)
+        w[e] = mk(dfl_to_f64(z.x), dfl_to_f64(z.y));
+      else
+        w[e] = mk((SO)z.x, (SO)z.y);
     }
   }
 };

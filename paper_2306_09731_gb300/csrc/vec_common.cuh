@@ -5,16 +5,19 @@
 namespace sgn {
 
 // Flat walk over the Ny*ldS entries of a half spectrum with the column (and
-// row) carried along, so that no per-entry division is needed. stride is the
-// total thread count; cstep = stride % ldS, rstep = stride / ldS.
+// row) carried along, so that no per-entry division is needed. With (k, K)
+// the thread takes every K-th of its grid-stride entries starting at the k-th
+// (K interleaved walkers keep K entries' loads in flight per iteration);
+// stride = K * thread count, cstep = stride % ldS, rstep = stride / ldS.
 struct Walk {
   size_t e, n, stride;
   int row, col, ldS, cstep, rstep;
-  __device__ __forceinline__ Walk(const Geom& G) {
+  __device__ __forceinline__ Walk(const Geom& G, int k = 0, int K = 1) {
     ldS = G.ldS;
     n = (size_t)G.Ny * ldS;
-    stride = (size_t)gridDim.x * blockDim.x;
-    e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+    stride = nthreads * (size_t)K;
+    e = (size_t)blockIdx.x * blockDim.x + threadIdx.x + (size_t)k * nthreads;
     row = (int)(e / ldS);
     col = (int)(e - (size_t)row * ldS);
     cstep = (int)(stride % ldS);
