@@ -11,13 +11,20 @@
 //   two_sum       Knuth's TwoSum: s + e == a + b exactly, any magnitudes
 //   fast_two_sum  Dekker's FastTwoSum: the same when |a| >= |b| (or a == 0)
 //   product       a*b - fl(a*b) is exact through one FMA (TwoProd)
-// Addition is Dekker's add2 (TwoSum of the high parts, the low parts added in
-// FP32, one renormalisation): its absolute error is a small multiple of
-// u^2 (|a| + |b|), u = 2^-24. That is the normwise bound the error analysis of
-// an FFT uses, and it holds under cancellation, where the relative error does
-// not. Multiplication is the FMA form of Dekker's mul2 (relative error a few
-// u^2). Every step uses explicit round-to-nearest intrinsics, so the compiler
-// can neither contract a product into an addition nor reorder an error term.
+// Addition is TwoSum of the high parts with the low parts and the TwoSum
+// error added in FP32, left unnormalised: the absolute error is a small
+// multiple of u^2 (|a| + |b|), u = 2^-24 (the two FP32 additions of terms of
+// size u |a| and u |b|). That is the normwise bound the error analysis of an
+// FFT uses; it holds under cancellation, where a relative bound does not, and
+// it does not need |lo| <= ulp(hi)/2 of its inputs. Dropping the final
+// FastTwoSum of Dekker's add2 saves 3 of 11 instructions; products and the
+// complex twiddle products end in a FastTwoSum and renormalise, so a low part
+// grows to at most a few u |hi| over the adds of one radix-8 butterfly chain.
+// renorm() restores |lo| <= ulp(hi)/2 where a consumer relies on it (the
+// Newton reciprocal). Multiplication is the FMA form of Dekker's mul2 (relative
+// error a few u^2). Every step uses explicit round-to-nearest intrinsics, so
+// the compiler can neither contract a product into an addition nor reorder an
+// error term.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -94,8 +101,10 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
 
 __device__ __forceinline__ dfl operator+(dfl a, dfl b) {
   const dfl s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  return dfl(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
+// |lo| <= ulp(hi)/2 again (TwoSum: exact also after a cancellation in hi)
+__device__ __forceinline__ dfl renorm(dfl a) { return two_sum(a.hi, a.lo); }
 __device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
 __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
 __device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
@@ -121,6 +130,7 @@ __device__ __forceinline__ dfl scale_pow2(dfl a, float s) { return dfl(__fmul_rn
 // residual 1 - b.hi r0 is exact through the FMA (it is below 2^-23 in size
 // and has no bits below 2^-48), so the step doubles the 24 correct bits.
 __device__ __forceinline__ dfl recip(dfl b) {
+  b = renorm(b);
   const float r0 = __frcp_rn(b.hi);
   const float e = __fmaf_rn(-b.lo, r0, __fmaf_rn(-b.hi, r0, 1.0f));
   return fast_two_sum(r0, __fmul_rn(r0, e));
@@ -128,7 +138,7 @@ __device__ __forceinline__ dfl recip(dfl b) {
 // a/b: quotient of the high parts, corrected by the df remainder a - b q1
 __device__ __forceinline__ dfl operator/(dfl a, dfl b) {
   const float q1 = __fdiv_rn(a.hi, b.hi);
-  const dfl r = a - mul_f(b, q1);
+  const dfl r = renorm(a - mul_f(b, q1));  // the remainder cancels in its high part
   return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
 }
 

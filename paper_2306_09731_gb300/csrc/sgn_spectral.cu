@@ -220,6 +220,10 @@ __device__ __forceinline__ void coef_point(double hv, double invN, T* h, T* cr, 
 // null (the refinement matvec reads only cr and cc).
 __device__ __forceinline__ void coef_point_df(dfl hv, float invN, dfl* h, dfl* cr, dfl* cc, size_t i, int* flags,
                                               const CoefCopy& cp) {
+  // the transforms leave their sums unnormalised: the FP32 copies, the sign
+  // and the finiteness test need hi to be the nearest FP32 value (near h = 1,
+  // an unnormalised hi is off by a few ulps of 1, all of it in h - 1)
+  hv = renorm(hv);
   if (!isfinite(hv.hi)) {
     atomicOr(flags, FLAG_NONFINITE);
   } else if (!(hv.hi > 0.0f)) {
@@ -228,7 +232,7 @@ __device__ __forceinline__ void coef_point_df(dfl hv, float invN, dfl* h, dfl* c
   const dfl r = recip(hv);
   const dfl vr = scale_pow2(r, 0.5f * invN);
   const dfl vc = scale_pow2(mul_f((r * r) * r, 1.5f), invN);
-  const dfl a = hv - dfl(1.0f);
+  const dfl a = renorm(hv - dfl(1.0f));
   if (h) h[i] = a;
   cr[i] = vr;
   cc[i] = vc;
