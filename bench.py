@@ -142,10 +142,10 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Double-float passes (precision 2) are bound by FP32 issue: 152 SMs x 128 FP32
 # lanes x 2.07 GHz instructions per second, divided by the FP32 instructions
-# one FP64-equivalent flop of a radix-8 FFT costs in this double-float
-# arithmetic: (52 adds x 11 + 4 products x 7 + 7 complex twiddle products x 38)
-# / (52 + 4 + 7 x 6) = 8.8.
-DF_INSTR_PER_FLOP = (52 * 11 + 4 * 7 + 7 * 38) / (52 + 4 + 7 * 6)
+# one FP64-equivalent flop of a radix-8 FFT butterfly costs in this
+# double-float arithmetic: (52 adds x 8 + 4 products x 7 + 7 complex twiddle
+# products x 38) / (52 + 4 + 7 x 6) = 7.2.
+DF_INSTR_PER_FLOP = (52 * 8 + 4 * 7 + 7 * 38) / (52 + 4 + 7 * 6)
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_INSTR_PER_FLOP / 1e12
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
@@ -204,9 +204,9 @@ KERNEL_NAMES = {"mv_yinv": "k_ypass<inv,2> (matvec y-inverse)", "mv_x": "k_mv_x 
                 "mv_yfwd": "k_ypass<fwd,EpiMatvec> (matvec y-forward + M^-1)",
                 "rhs_yinv": "k_ypass<inv,4> (RHS y-inverse)", "rhs_x": "k_rhs_x (fused RHS x-pass)",
                 "rhs_yfwd": "k_ypass<fwd,EpiK> (RHS y-forward)", "rk": "k_rk_update (RK4 stage update)",
-                "ref_yinv": "k_ypass<inv,2> FP64 (refinement matvec y-inverse)",
-                "ref_x": "k_mv_x FP64 (refinement matvec x-pass)",
-                "ref_yfwd": "k_ypass<fwd,EpiMatvec> FP64 (refinement matvec y-forward)"}
+                "ref_yinv": "k_ypass<inv,2> (refinement matvec y-inverse)",
+                "ref_x": "k_mv_x (refinement matvec x-pass)",
+                "ref_yfwd": "k_ypass<fwd,EpiMatvec> (refinement matvec y-forward)"}
 
 
 def class_roofline(cls, n, prec, prof, peaks):
