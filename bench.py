@@ -319,6 +319,7 @@ def run_ours(args, rank, world, local_rank):
     plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
             ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0))
     solvers = {}
+    devfields = {}
     for name, prec, guess, graph in plan:
         if args.path == "mixed" and not name.startswith("mixed"):
             continue
@@ -333,6 +334,7 @@ def run_ours(args, rank, world, local_rank):
         s, f, rec = time_path(prec, guess, args, st, n, world, graph)
         rec["precision"] = prec
         fields[name] = [x.cpu().numpy() for x in f[:3]]
+        devfields[name] = f
         solvers[name] = s
         paths[name] = rec
     # headline: the fastest arm of the headline path (all of them meet the same
@@ -370,6 +372,15 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
+    # the paper's monitoring quantities (row f4) on the final state: wall time of
+    # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
+    hf = devfields[head_name]
+    head_solver.diagnostics(hf[0], hf[1], hf[2])
+    torch.cuda.synchronize()
+    d0 = time.perf_counter()
+    for _ in range(5):
+        diag = head_solver.diagnostics(hf[0], hf[1], hf[2])
+    diag_ms = (time.perf_counter() - d0) / 5 * 1e3
     head_solver.close()
 
     fp32 = head_prec >= 1
@@ -415,6 +426,8 @@ def run_ours(args, rank, world, local_rank):
                                for c, r in rooflines.items() if r},
         "e2e": e2e,
         "clocks": clk,
+        "diagnostics": {"ms_per_call": diag_ms, "h_max": diag["h_max"], "c_fit": diag["c_fit"],
+                        "tail": diag["tail"]},
     }
     if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]

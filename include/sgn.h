@@ -202,6 +202,37 @@ sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly,
 /* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
 const char* sgn_last_error(sgn_t ctx);
 
+/* ------------------------------------------------------------------------
+ * Monitoring quantities of the paper's experiments (Sections 3 and 4):
+ *   h_max, i_max, x_s, y_s  L-infinity norm of h and the grid point where it is
+ *                           reached (lowest flat index y*Nx + x on ties; NaN
+ *                           counts as largest), x_j = -Lx/2 + j Lx/Nx as in
+ *                           sgn_create (Section 4.1 locates the crest this way)
+ *   c_fit                   sqrt(g h_max): the speed of the line solitary wave
+ *                           of Eq. (sol) whose crest is h_max (h_inf = 1;
+ *                           Section 4.2 fits c from the maximum this way)
+ *   dev_h, dev_vx           max |h - h_c|, max |vx - v_c| over the grid, h_c and
+ *                           v_c of Eq. (sol) with speed c_fit centred at x_s,
+ *                           nearest periodic image in x; NaN if h_max <= 1
+ *   max_vy                  max |vy| (zero for a line solitary wave)
+ *   tail[3]                 max |DFT coefficient| / (Nx Ny) of h, vx, vy over
+ *                           the outermost modes, 16 |m_x| >= 7 Nx or
+ *                           16 |m_y| >= 7 Ny (the decay of the DFT
+ *                           coefficients that Section 3 reads as resolution)
+ * h, vx, vy: device float64 [Ny][Nx], read only. Uses the handle's scratch
+ * spectra; synchronises the handle's stream. */
+typedef struct {
+  double h_max;
+  long long i_max;
+  double x_s, y_s;
+  double c_fit;
+  double dev_h, dev_vx;
+  double max_vy;
+  double tail[3];
+} sgn_diag;
+
+sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const double* vy, sgn_diag* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,9 +19,12 @@ Klein, "Numerical study of the Serre-Green-Naghdi equations in 2D" define:
   Section 3 (time integration paragraph);
 * the Krasny filter, Section 3;
 * mass, momentum and energy integrals, Section 2.3, Eqs. (total_mass),
-  (total_momentum), (total_energy).
+  (total_momentum), (total_energy);
+* the monitoring quantities of the transverse-stability runs, Sections 3,
+  4.1 and 4.2 (L-infinity norm and crest of h, the fitted solitary wave, the
+  decay of the DFT coefficients).
 
-Readings where the paper is silent or garbled (each is listed in the design doc):
+Readings where the paper is silent or garbled:
 * grid x_j = -Lx/2 + j Lx/Nx with the FULL period Lx (the paper's period is
   2 pi L_x; its collocation formula lost the "/N_x");
 * the Nyquist wavenumber is set to zero in i k, and the same zeroed k enter
@@ -257,6 +260,61 @@ def invariants(G: Grid, h, vx, vy, sigma, g=1.0):
                                    + 1.5 * sigma ** 2 / h ** 3
                                    + 0.5 * g * (h - H_INF) ** 2))
     return np.array([mass, px, py, energy])
+
+
+def line_soliton_profile(xi, a, g=1.0):
+    """h and v of the line solitary wave of Eq. (sol) with crest h_inf + a at xi = 0.
+
+    h = h_inf + a sech^2(kappa xi), kappa^2 = 3a / (4 h_inf^2 (h_inf + a)),
+    c^2 = g (h_inf + a), v = c - (c h_inf / h) (1 + (h^2)_xixi / 6).
+    """
+    c = np.sqrt(g * (H_INF + a))
+    kappa = np.sqrt(3.0 * a / (4.0 * H_INF ** 2 * (H_INF + a)))
+    sech2 = 1.0 / np.cosh(kappa * xi) ** 2
+    h = H_INF + a * sech2
+    # (h^2)'' = 2 (h'^2 + h h''), h' = a (sech^2)', (sech^2)'' = kappa^2 (4 sech^2 - 6 sech^4)
+    d1 = -2.0 * kappa * sech2 * np.tanh(kappa * xi)
+    d2 = kappa ** 2 * (4.0 * sech2 - 6.0 * sech2 ** 2)
+    h2xx = 2.0 * ((a * d1) ** 2 + h * a * d2)
+    v = c - (c * H_INF / h) * (1.0 + h2xx / 6.0)
+    return h, v
+
+
+def diagnostics(G: Grid, h, vx, vy, g=1.0):
+    """The monitoring quantities of Sections 3 and 4.
+
+    * the L-infinity norm of h and the grid point of the maximum (the crest
+      location x_s of Section 4.1; the first maximum in row-major order);
+    * the speed of the line solitary wave of Eq. (sol) whose maximum equals it,
+      c = sqrt(g h_max) (Section 4.2 fits c this way, h_inf = 1);
+    * the largest differences of h and vx from that solitary wave centred at
+      x_s (Sections 4.1, 4.2), the nearest periodic image in x, and max |vy|;
+    * the size of the DFT coefficients of h, vx, vy on the outermost modes,
+      16 |m_x| >= 7 Nx or 16 |m_y| >= 7 Ny, divided by Nx Ny (Section 3 reads
+      resolution from their decay).
+    """
+    i_max = int(np.argmax(h))
+    h_max = float(h.flat[i_max])
+    jy, jx = divmod(i_max, G.Nx)
+    x_s = float(G.x[jx])
+    y_s = float(G.y[jy])
+    c_fit = float(np.sqrt(g * h_max))
+    a = h_max - H_INF
+    if a > 0.0:
+        xi = G.x - x_s
+        xi = np.where(xi >= 0.5 * G.Lx, xi - G.Lx, xi)
+        xi = np.where(xi < -0.5 * G.Lx, xi + G.Lx, xi)
+        hc, vc = line_soliton_profile(xi, a, g)
+        dev_h = float(np.max(np.abs(h - hc[None, :])))
+        dev_vx = float(np.max(np.abs(vx - vc[None, :])))
+    else:
+        dev_h = dev_vx = float("nan")
+    mx = np.abs(np.fft.fftfreq(G.Nx, 1.0 / G.Nx))
+    my = np.abs(np.fft.fftfreq(G.Ny, 1.0 / G.Ny))
+    band = (16 * mx[None, :] >= 7 * G.Nx) | (16 * my[:, None] >= 7 * G.Ny)
+    tail = [float(np.max(np.abs(fft2(f))[band]) / (G.Nx * G.Ny)) for f in (h, vx, vy)]
+    return dict(h_max=h_max, i_max=i_max, x_s=x_s, y_s=y_s, c_fit=c_fit, dev_h=dev_h, dev_vx=dev_vx,
+                max_vy=float(np.max(np.abs(vy))), tail=tail)
 
 
 def dense_elliptic_matrix(G: Grid, h):

@@ -86,6 +86,8 @@ struct sgn_ctx {
   // kernels per step outside the loops, per restart cycle / sweep, per Arnoldi step
   long long graph_fixed = 0, graph_per_sweep = 0, graph_per_step = 0;
   GmresDev* gst_host = nullptr;  // pinned
+  DiagDev* diag = nullptr;       // sgn_diagnostics results (lazy)
+  DiagDev* diag_host = nullptr;  // pinned
   std::vector<cudaGraph_t> sweep_bodies, step_bodies;  // owned by their conditional nodes
   bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
   std::vector<void*> allocs;
@@ -179,6 +181,8 @@ void free_all(sgn_ctx* ctx) {
   if (ctx->rb_host) cudaFreeHost(ctx->rb_host);
   if (ctx->inv_host) cudaFreeHost(ctx->inv_host);
   if (ctx->gst_host) cudaFreeHost(ctx->gst_host);
+  if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
+  ctx->diag_host = nullptr;
   ctx->rb_host = nullptr;
   ctx->inv_host = nullptr;
   ctx->gst_host = nullptr;
@@ -1225,6 +1229,38 @@ sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, doubl
   for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const double* vy, sgn_diag* out) {
+  API_BEGIN
+  if (!h || !vx || !vy || !out) return fail(ctx, SGN_EINVAL, "sgn_diagnostics: NULL pointer");
+  if (!ctx->diag) {
+    ctx->diag = dalloc<DiagDev>(ctx, 1);
+    CK(cudaMallocHost((void**)&ctx->diag_host, sizeof(DiagDev)));
+  }
+  const Geom& G = ctx->G;
+  unsigned* cnt = ctx->counters + 7;  // the three passes run in order on one stream
+  CK(launch_diag_max(G, h, vy, ctx->partials, cnt, ctx->diag, EX(ctx)));
+  CK(launch_diag_soliton(G, h, vx, ctx->g, ctx->partials, cnt, ctx->diag, EX(ctx)));
+  const double* f3[3] = {h, vx, vy};
+  fwd2(ctx, f3, 3, ctx->tmp);
+  CK(launch_diag_tail(G, ctx->tmp[0], ctx->tmp[1], ctx->tmp[2], ctx->partials, cnt, ctx->diag, EX(ctx)));
+  CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag, sizeof(DiagDev), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->prof.on) ctx->prof.harvest();
+  const DiagDev& d = *ctx->diag_host;
+  out->h_max = d.h_max;
+  out->i_max = d.i_max;
+  const long long jx = d.i_max % G.Nx, jy = d.i_max / G.Nx;
+  out->x_s = -0.5 * G.Lx + G.Lx * (double)jx / (double)G.Nx;
+  out->y_s = -0.5 * G.Ly + G.Ly * (double)jy / (double)G.Ny;
+  out->c_fit = sqrt(ctx->g * d.h_max);
+  out->dev_h = d.dev_h;
+  out->dev_vx = d.dev_vx;
+  out->max_vy = d.max_vy;
+  for (int k = 0; k < 3; ++k) out->tail[k] = d.tail[k];
   return SGN_OK;
   API_END
 }

@@ -348,4 +348,23 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
                                   const double* sig, const double* sx, const double* sy, double g,
                                   double* partials, const Exec& ex);
 
+// ------------------------------------------------------------ diagnostics
+// Device results of the monitoring pass (sgn_diagnostics).
+struct DiagDev {
+  double h_max;
+  long long i_max;
+  double max_vy;
+  double dev_h, dev_vx;
+  double tail[3];
+};
+// max of h with its lowest index and max |vy|; partials: 3 * NBLK doubles
+cudaError_t launch_diag_max(const Geom& G, const double* h, const double* vy, double* partials, unsigned* counter,
+                            DiagDev* d, const Exec& ex);
+// deviation from the line solitary wave of speed sqrt(g h_max) at the crest
+cudaError_t launch_diag_soliton(const Geom& G, const double* h, const double* vx, double g, double* partials,
+                                unsigned* counter, DiagDev* d, const Exec& ex);
+// outer-band maximum of three FP64 half spectra, divided by Nx Ny
+cudaError_t launch_diag_tail(const Geom& G, const cpx<double>* s0, const cpx<double>* s1, const cpx<double>* s2,
+                             double* partials, unsigned* counter, DiagDev* d, const Exec& ex);
+
 }  // namespace sgn

@@ -55,23 +55,6 @@ __device__ void givens_step(GmresDev* st, int j, GmresReadback* rb, const int* f
   rb->flags = flags ? *flags : 0;
 }
 
-// True (in every thread) in the block that finishes last; it then sees every
-// other block's partials. Resets the counter for the next launch. wrote: this
-// thread stored a partial; only those stores need the fence before the ticket.
-__device__ __forceinline__ bool last_block(unsigned* counter, bool wrote = true) {
-  __shared__ int s_last;
-  if (wrote) __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned total = gridDim.x * gridDim.y;
-    const unsigned t = atomicAdd(counter, 1u);
-    s_last = (t == total - 1) ? 1 : 0;
-    if (s_last) *counter = 0u;
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
 // Fixed-order sum over the NBLK block partials of one slot (valid on thread 0).
 __device__ __forceinline__ double reduce_slot(const double* partials, int slot, double* red) {
   double v = 0.0;

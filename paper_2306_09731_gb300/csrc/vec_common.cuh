@@ -60,4 +60,21 @@ __device__ __forceinline__ double block_reduce(double v, double* red) {
   return tot;
 }
 
+// True (in every thread) in the block that finishes last; it then sees every
+// other block's partials. Resets the counter for the next launch. wrote: this
+// thread stored a partial; only those stores need the fence before the ticket.
+__device__ __forceinline__ bool last_block(unsigned* counter, bool wrote = true) {
+  __shared__ int s_last;
+  if (wrote) __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y;
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == total - 1) ? 1 : 0;
+    if (s_last) *counter = 0u;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
 }  // namespace sgn

@@ -24,7 +24,7 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_spectral_derivative", "sgn_fft2_r2c", "sgn_fft2_c2r", "sgn_elliptic_apply",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
-           "sgn_last_error"]
+           "sgn_diagnostics", "sgn_last_error"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
                    "ref_yinv", "ref_x", "ref_yfwd", "rk"]
@@ -40,6 +40,12 @@ class sgn_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("tol", ctypes.c_double), ("krasny", ctypes.c_int), ("krasny_thr", ctypes.c_double),
                 ("dealias", ctypes.c_int), ("guess", ctypes.c_int), ("graph", ctypes.c_int)]
+
+
+class sgn_diag(ctypes.Structure):
+    _fields_ = [("h_max", ctypes.c_double), ("i_max", ctypes.c_longlong), ("x_s", ctypes.c_double),
+                ("y_s", ctypes.c_double), ("c_fit", ctypes.c_double), ("dev_h", ctypes.c_double),
+                ("dev_vx", ctypes.c_double), ("max_vy", ctypes.c_double), ("tail", ctypes.c_double * 3)]
 
 
 class sgn_stats(ctypes.Structure):
@@ -85,6 +91,7 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         "sgn_get_profile": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I,
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "sgn_elliptic_apply_noalloc": (_I, [_I, _I, _D, _D, _P, _P, _P, _P]),
+        "sgn_diagnostics": (_I, [_P, _P, _P, _P, ctypes.POINTER(sgn_diag)]),
         "sgn_last_error": (ctypes.c_char_p, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -186,6 +193,14 @@ def sgn_invariants(handle, h, vx, vy, sigma):
     out = (_D * 4)()
     _check(handle, load_library().sgn_invariants(handle, _ptr(h), _ptr(vx), _ptr(vy), _ptr(sigma), out))
     return [out[i] for i in range(4)]
+
+
+def sgn_diagnostics(handle, h, vx, vy) -> dict:
+    """Monitoring quantities of the paper's experiments; see include/sgn.h."""
+    d = sgn_diag()
+    _check(handle, load_library().sgn_diagnostics(handle, _ptr(h), _ptr(vx), _ptr(vy), ctypes.byref(d)))
+    return dict(h_max=d.h_max, i_max=d.i_max, x_s=d.x_s, y_s=d.y_s, c_fit=d.c_fit, dev_h=d.dev_h,
+                dev_vx=d.dev_vx, max_vy=d.max_vy, tail=[d.tail[i] for i in range(3)])
 
 
 def sgn_get_stats(handle) -> dict:
@@ -294,6 +309,9 @@ class Solver:
 
     def stats(self):
         return sgn_get_stats(self.handle)
+
+    def diagnostics(self, h, vx, vy):
+        return sgn_diagnostics(self.handle, h, vx, vy)
 
     def set_profiling(self, on=True):
         sgn_set_profiling(self.handle, on)

@@ -394,3 +394,58 @@ def test_planted_mistakes_are_caught(name, monkeypatch):
             failed.append(fn.__name__)
             break
     assert failed, f"mutant {name} passed every pin"
+
+
+# ----------------------------------------------------------- diagnostics
+# Pins of oracle.diagnostics (Sections 3, 4.1, 4.2) against closed forms.
+
+def test_diagnostics_exact_soliton_closed_form():
+    """An exact line solitary wave centred on a grid point: crest at that point,
+    c from the crest equals the wave's speed, no deviation, vy = 0."""
+    G = O.Grid(256, 8, 80.0, 4.0)
+    j0 = 141
+    st = I.line_soliton(256, 8, 80.0, 4.0, a=0.5, x0=float(G.x[j0]))
+    d = O.diagnostics(G, st.h, st.vx, st.vy)
+    assert d["i_max"] == j0 and d["x_s"] == float(G.x[j0]) and d["y_s"] == float(G.y[0])
+    assert d["h_max"] == 1.5
+    assert abs(d["c_fit"] - I.Soliton1D(a=0.5).c) < 1e-15
+    assert d["dev_h"] < 1e-14 and d["dev_vx"] < 1e-13 and d["max_vy"] == 0.0
+
+
+def test_diagnostics_soliton_shifted_by_half_a_cell():
+    """A crest between grid points: the maximum sits on the nearer point and the
+    deviation is the closed-form difference between the two centres."""
+    G = O.Grid(512, 4, 80.0, 2.0)
+    j0 = 300
+    x0 = float(G.x[j0]) + 0.3 * G.Lx / G.Nx
+    st = I.line_soliton(512, 4, 80.0, 2.0, a=0.4, x0=x0)
+    d = O.diagnostics(G, st.h, st.vx, st.vy)
+    assert d["i_max"] == j0
+    sol = I.Soliton1D(a=d["h_max"] - 1.0)
+    xi = G.x - d["x_s"]
+    ref = np.max(np.abs(st.h[0] - sol.fields(xi)["h"]))
+    assert abs(d["dev_h"] - ref) < 1e-14 and d["dev_h"] > 1e-4
+
+
+def test_diagnostics_tail_of_single_modes():
+    """cos(m x): one DFT pair of size N/2 each, so the monitor reads 1/2 when m
+    lies in the outer band (16 m >= 7 N) and rounding level otherwise."""
+    G = O.Grid(64, 32, 2 * np.pi, 2 * np.pi)
+    X = np.broadcast_to(G.x[None, :], (32, 64))
+    Y = np.broadcast_to(G.y[:, None], (32, 64))
+    one = np.ones((32, 64))
+    d = O.diagnostics(G, one + 0.1 * np.cos(29 * X), np.cos(10 * X), np.sin(15 * Y))
+    assert abs(d["tail"][0] - 0.05) < 1e-15
+    assert d["tail"][1] < 1e-15
+    assert abs(d["tail"][2] - 0.5) < 1e-15
+
+
+def test_diagnostics_ties_and_no_crest():
+    G = O.Grid(16, 8, 4.0, 2.0)
+    h = np.ones((8, 16))
+    h[3, 5] = 1.2
+    h[2, 9] = 1.2
+    d = O.diagnostics(G, h, np.zeros_like(h), np.zeros_like(h))
+    assert d["i_max"] == 2 * 16 + 9 and d["h_max"] == 1.2
+    flat = O.diagnostics(G, np.ones((8, 16)), np.zeros((8, 16)), np.zeros((8, 16)))
+    assert flat["i_max"] == 0 and np.isnan(flat["dev_h"]) and np.isnan(flat["dev_vx"])
