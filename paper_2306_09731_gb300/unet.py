@@ -1,0 +1,119 @@
+"""ctypes binding of include/sgn_unet.h (the learned-guess U-Net).
+
+Argument marshalling only: every computation runs in the library's kernels.
+Tensors are CUDA float32 torch tensors (or raw device pointers as ints).
+"""
+import ctypes
+
+from . import sgn as S
+
+# every symbol include/sgn_unet.h declares
+UNET_EXPORTS = ["sgn_unet_create", "sgn_unet_destroy", "sgn_unet_set_stream", "sgn_unet_last_error",
+                "sgn_unet_num_params", "sgn_unet_set_params", "sgn_unet_get_params", "sgn_unet_get_grads",
+                "sgn_unet_forward", "sgn_unet_backward", "sgn_unet_adam_step"]
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_ready = False
+
+
+def load_library():
+    global _ready
+    lib = S.load_library()
+    if not _ready:
+        sig = {
+            "sgn_unet_create": (_I, [_I, _I, _I, ctypes.c_ulonglong, ctypes.POINTER(_P)]),
+            "sgn_unet_destroy": (_I, [_P]),
+            "sgn_unet_set_stream": (_I, [_P, _P]),
+            "sgn_unet_last_error": (ctypes.c_char_p, [_P]),
+            "sgn_unet_num_params": (ctypes.c_longlong, [_P]),
+            "sgn_unet_set_params": (_I, [_P, _P]),
+            "sgn_unet_get_params": (_I, [_P, _P]),
+            "sgn_unet_get_grads": (_I, [_P, _P]),
+            "sgn_unet_forward": (_I, [_P, _P, _P, _I]),
+            "sgn_unet_backward": (_I, [_P, _P, _P]),
+            "sgn_unet_adam_step": (_I, [_P, _F, _F, _F, _F, _I]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _ready = True
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _check(net, st):
+    if st != 0:
+        msg = load_library().sgn_unet_last_error(net) if net else b""
+        raise S.SGNError(st, (msg or b"").decode())
+
+
+class UNet:
+    """One network (coarse grid side n, up to max_batch samples per call)."""
+
+    def __init__(self, n, max_batch=8, bf16=True, seed=0):
+        import torch
+        self._torch = torch
+        lib = load_library()
+        h = _P()
+        _check(None, lib.sgn_unet_create(int(n), int(max_batch), 1 if bf16 else 0, int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.n = n
+        self.max_batch = max_batch
+        self.bf16 = bf16
+        lib.sgn_unet_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    def close(self):
+        if self.handle:
+            load_library().sgn_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(load_library().sgn_unet_num_params(self.handle))
+
+    def params(self):
+        p = self._torch.empty(self.num_params(), dtype=self._torch.float32, device="cuda")
+        _check(self.handle, load_library().sgn_unet_get_params(self.handle, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = p.to(device="cuda", dtype=self._torch.float32).contiguous()
+        _check(self.handle, load_library().sgn_unet_set_params(self.handle, _ptr(p)))
+        self._keep = p
+
+    def grads(self):
+        g = self._torch.empty(self.num_params(), dtype=self._torch.float32, device="cuda")
+        _check(self.handle, load_library().sgn_unet_get_grads(self.handle, _ptr(g)))
+        return g
+
+    def forward(self, x):
+        """x: [B][4][n][n] float32 CUDA tensor -> [B][1][n][n]."""
+        self._x = x.contiguous()
+        out = self._torch.empty((x.shape[0], 1, self.n, self.n), dtype=self._torch.float32, device="cuda")
+        _check(self.handle, load_library().sgn_unet_forward(self.handle, _ptr(self._x), _ptr(out), int(x.shape[0])))
+        return out
+
+    def backward(self, target):
+        """MSE against target [B][1][n][n] after forward; returns the loss (host float)."""
+        self._t = target.contiguous()
+        loss = self._torch.zeros(1, dtype=self._torch.float64, device="cuda")
+        _check(self.handle, load_library().sgn_unet_backward(self.handle, _ptr(self._t), _ptr(loss)))
+        return float(loss.item())
+
+    def adam_step(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(self.handle, load_library().sgn_unet_adam_step(self.handle, lr, beta1, beta2, eps, int(t)))

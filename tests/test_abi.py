@@ -12,11 +12,13 @@ import pytest
 from paper_2306_09731_gb300 import build as B
 from paper_2306_09731_gb300 import sgn as S
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sgn.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+HEADER = os.path.join(INCLUDE, "sgn.h")
+UNET_HEADER = os.path.join(INCLUDE, "sgn_unet.h")
 
 
-def declared_symbols():
-    text = open(HEADER).read()
+def declared_symbols(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(sgn_[a-z0-9_]+)\s*\(", text)))
 
@@ -28,12 +30,24 @@ def lib():
 
 
 def test_header_and_binding_agree():
+    from paper_2306_09731_gb300 import unet as UN
     assert declared_symbols() == sorted(S.EXPORTS)
+    assert declared_symbols(UNET_HEADER) == sorted(UN.UNET_EXPORTS)
+    assert sorted(os.listdir(INCLUDE)) == ["sgn.h", "sgn_unet.h"]
 
 
 def test_library_exports_every_declared_symbol(lib):
-    for name in declared_symbols():
+    for name in declared_symbols() + declared_symbols(UNET_HEADER):
         assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("n,batch", [(8, 1), (24, 1), (1024, 1), (64, 0), (64, 65)])
+def test_unet_create_rejects_bad_sizes(lib, n, batch):
+    from paper_2306_09731_gb300 import unet as UN
+    UN.load_library()
+    h = ctypes.c_void_p()
+    assert lib.sgn_unet_create(n, batch, 1, 0, ctypes.byref(h)) == 1  # SGN_EINVAL, before any device work
+    assert not h.value
 
 
 def test_default_options(lib):
