@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-mode arms")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-start arms (and their training)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
                                                  "mixed_df_graph, fp64, mixed_paper_start)")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
@@ -245,7 +246,7 @@ def class_roofline(cls, n, prec, prof, peaks):
     return out
 
 
-def time_path(precision, guess, args, st, n, world, graph=0):
+def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
     """W warm-up steps, then K timed RK4 steps of one path; returns its record.
 
     The host-driven loop (graph = 0) runs the timed steps with the per-launch
@@ -257,6 +258,9 @@ def time_path(precision, guess, args, st, n, world, graph=0):
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
     s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
+    if learned is not None:
+        net, in_scale, out_scale, tau_power = learned
+        s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
     stream = torch.cuda.current_stream()
     if args.warmup > 0:
         s.rk4_step(*f, DT, args.warmup)
@@ -337,15 +341,51 @@ def run_ours(args, rank, world, local_rank):
         devfields[name] = f
         solvers[name] = s
         paths[name] = rec
+    # learned start (row f2): networks trained here on solver snapshots of four
+    # other Gaussian humps (amplitudes 0.35-0.65, shifted centres), then run on
+    # the benchmark state: over the paper's start (tau = dt/2, coarse n/8) and
+    # over the extrapolated start (tau = (dt/2)^2, coarse n/16)
+    learned_info = {}
+    if not args.no_learned and args.path != "fp64" and (not args.arms or any("learned" in a for a in
+                                                                              args.arms.split(","))):
+        from paper_2306_09731_gb300 import learned as Lm
+        for name, prec, guess, graph, tau_power, coarse in (
+                ("mixed_df_paper_start", 2, 0, 0, 0, 0), ("mixed_df_paper_start_learned", 2, 0, 0, 1, n // 8),
+                ("mixed_df_learned_graph", 2, 2, 1, 2, n // 16)):
+            if args.arms and name not in args.arms.split(","):
+                continue
+            learned = None
+            if coarse:
+                t0 = time.perf_counter()
+                states = Lm.gaussian_states(n, L_DEFAULT, [0.35, 0.45, 0.55, 0.65], seed=1)
+                samples = Lm.generate(states, coarse, steps=8, dt=DT, precision=prec, guess=guess,
+                                      tau_power=tau_power)
+                t1 = time.perf_counter()
+                net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2,
+                                                            log_every=100)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                learned = (net, in_scale, out_scale, tau_power)
+                learned_info[name] = {"coarse_n": coarse, "samples": int(samples.shape[0]),
+                                      "data_s": t1 - t0, "train_s": t2 - t1, "losses": losses,
+                                      "params": net.num_params()}
+            s, f, rec = time_path(prec, guess, args, st, n, world, graph, learned)
+            rec["precision"] = prec
+            fields[name] = [x.cpu().numpy() for x in f[:3]]
+            devfields[name] = f
+            solvers[name] = s
+            paths[name] = rec
     # headline: the fastest arm of the headline path (all of them meet the same
     # FP64 tolerance test in every solve); its per-kernel figures come from the
     # host-driven arm of the same precision
     if args.path == "fp64":
         head_name = "fp64"
     else:
-        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph") if k in paths]
+        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph", "mixed_df_learned_graph")
+                 if k in paths]
         head_name = max(cands, key=lambda k: paths[k]["value"])
-    prof_name = head_name[:-len("_graph")] if head_name.endswith("_graph") else head_name
+    prof_name = {"mixed_graph": "mixed", "mixed_df_graph": "mixed_df",
+                 "mixed_df_learned_graph": "mixed_df"}.get(head_name, head_name)
     head_solver, head_rec = solvers[head_name], paths[head_name]
     head_prec = head_rec["precision"]
     for name, s in solvers.items():
@@ -447,6 +487,19 @@ def run_ours(args, rank, world, local_rank):
                 "graph": mg["value"], "host_loop": mh["value"], "unit": UNIT, "ratio": mg["value"] / mh["value"],
                 "fields_bitwise_equal": all(bool(np.array_equal(a, b))
                                             for a, b in zip(fields[base + "_graph"], fields[base]))}
+    if learned_info:
+        lr = {"training": learned_info}
+        for base, arm in (("mixed_df_paper_start", "mixed_df_paper_start_learned"),
+                          ("mixed_df_graph", "mixed_df_learned_graph")):
+            if base in paths and arm in paths:
+                b, a = paths[base], paths[arm]
+                lr[arm] = {"value": a["value"], "base": base, "base_value": b["value"],
+                           "speedup": a["value"] / b["value"],
+                           "inner_matvecs_per_step": a["gmres"]["inner_matvecs_per_step"],
+                           "base_inner_matvecs_per_step": b["gmres"]["inner_matvecs_per_step"],
+                           "refinements_per_stage": a["gmres"]["fp64_refinements_per_stage"],
+                           "base_refinements_per_stage": b["gmres"]["fp64_refinements_per_stage"]}
+        out["learned_start"] = lr
     if "mixed_paper_start" in paths:
         mp = paths["mixed_paper_start"]
         out["mixed_paper_start"] = {"value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms_per_step"],

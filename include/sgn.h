@@ -233,6 +233,43 @@ typedef struct {
 
 sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const double* vy, sgn_diag* out);
 
+/* ------------------------------------------------------------------------
+ * Learned GMRES start (row f2). Section 3 starts GMRES from the last computed
+ * sigma; a network (include/sgn_unet.h) can correct that start. At RK4 stages
+ * 2 and 4 (the stages whose state moved by O(dt) since the fallback's), after
+ * the start chosen by opt.guess, the library forms on an n x n coarse grid
+ *   in = (in_scale[0] (h - 1), in_scale[1] vx, in_scale[2] vy,
+ *         in_scale[3] sigma_start)
+ * as band-limited samples of the stage state (the Fourier modes |m_x|, |m_y|
+ * < n/2 evaluated at every (N/n)-th grid point), runs the network on it and
+ * adds out_scale * tau * net(in), tau = (dt/2)^tau_power, to the same modes of
+ * sigma's spectrum (with guess = 2, not at stage 2 of a call's first step,
+ * which has no extrapolation history). Every solve still meets opt.tol. n
+ * must be a power of two in [16, min(Nx, Ny)] and equal to the network's side;
+ * net = NULL detaches.
+ * The network runs on the handle's stream (it is re-pointed there). */
+sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_scale[4], float out_scale,
+                                 int tau_power);
+
+/* Records training samples for the learned start: during sgn_rk4_step and
+ * sgn_rk4_step_host with the host-driven loop (graph = 0; SGN_EINVAL
+ * otherwise), each stage 2 and 4 appends to buf (device float32, capacity
+ * samples of [5][n][n]) the four coarse inputs above without in_scale (channels
+ * 0-3, sigma_start taken before any learned correction) and the coarse target
+ * (sigma_solved - sigma_start) / tau (channel 4). Recording stops silently when
+ * buf is full; buf = NULL stops it. sgn_recorded_count returns the number of
+ * samples written since the last sgn_record_learned call. */
+sgn_status sgn_record_learned(sgn_t ctx, int n, float* buf, int capacity, int tau_power);
+sgn_status sgn_recorded_count(sgn_t ctx, int* count);
+
+/* The restriction and prolongation of the learned start, on physical fields:
+ * sgn_coarse_sample: out [n][n] (device float32) = the modes |m_x|, |m_y| < n/2
+ * of f (device float64 [Ny][Nx]) evaluated at the grid points (j Nx/n, i Ny/n);
+ * sgn_coarse_embed: f += the band-limited field whose samples at those points
+ * are scale * fc (fc device float32 [n][n]; its modes |m| < n/2 only). */
+sgn_status sgn_coarse_sample(sgn_t ctx, const double* f, int n, float* out);
+sgn_status sgn_coarse_embed(sgn_t ctx, const float* fc, int n, double scale, double* f);
+
 #ifdef __cplusplus
 }
 #endif

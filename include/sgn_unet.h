@@ -49,6 +49,8 @@ const char* sgn_unet_last_error(sgn_unet_t net);
 
 /* number of FP32 parameters */
 long long sgn_unet_num_params(sgn_unet_t net);
+/* the coarse grid side n the network was created for (-1 for NULL) */
+int sgn_unet_side(sgn_unet_t net);
 /* copy all parameters from / to a device FP32 array of sgn_unet_num_params entries */
 sgn_status sgn_unet_set_params(sgn_unet_t net, const float* params);
 sgn_status sgn_unet_get_params(sgn_unet_t net, float* params);

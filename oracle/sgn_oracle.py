@@ -317,6 +317,29 @@ def diagnostics(G: Grid, h, vx, vy, g=1.0):
                 max_vy=float(np.max(np.abs(vy))), tail=tail)
 
 
+def _band(N, n):
+    m = np.fft.fftfreq(N, 1.0 / N)
+    return np.abs(m) < n / 2
+
+
+def coarse_sample(G: Grid, f, n):
+    """The Fourier modes |m_x|, |m_y| < n/2 of f, evaluated at the grid points
+    (j Nx/n, i Ny/n): the coarse inputs of the learned GMRES start."""
+    F = fft2(f) * (_band(G.Ny, n)[:, None] & _band(G.Nx, n)[None, :])
+    return ifft2_real(F)[::G.Ny // n, ::G.Nx // n]
+
+
+def coarse_embed(G: Grid, fc, n, scale=1.0):
+    """The field on the fine grid with Fourier modes |m| < n/2 only whose
+    samples at the points of coarse_sample are scale * fc (modes of fc with
+    |m| >= n/2 dropped)."""
+    D = np.fft.fft2(scale * np.asarray(fc, dtype=np.float64)) * (_band(n, n)[:, None] & _band(n, n)[None, :])
+    F = np.zeros((G.Ny, G.Nx), dtype=complex)
+    m = np.fft.fftfreq(n, 1.0 / n).astype(int)
+    F[np.ix_(m % G.Ny, m % G.Nx)] = D * (G.Nx * G.Ny / (n * n))
+    return ifft2_real(F)
+
+
 def dense_elliptic_matrix(G: Grid, h):
     """Columns L e_j of the discrete operator, for tiny grids (N <= a few hundred)."""
     N = G.Nx * G.Ny

@@ -23,6 +23,7 @@
 
 #include "sgn.h"
 #include "sgn_internal.h"
+#include "sgn_unet.h"
 
 using namespace sgn;
 
@@ -87,6 +88,27 @@ struct sgn_ctx {
   long long graph_fixed = 0, graph_per_sweep = 0, graph_per_step = 0;
   GmresDev* gst_host = nullptr;  // pinned
   DiagDev* diag = nullptr;       // sgn_diagnostics results (lazy)
+  // learned start (sgn_set_learned_guess)
+  sgn_unet_t net = nullptr;
+  int ln = 0;
+  float in_scale[4] = {1.f, 1.f, 1.f, 1.f};
+  float out_scale = 1.f;
+  int tau_pow = 1;
+  float2* ltw = nullptr;  // e^{2 pi i t / ln}
+  float2* lY = nullptr;   // restriction / prolongation scratch
+  float* lin = nullptr;   // network input [4][ln][ln]
+  float* lout = nullptr;  // network output [ln][ln]
+  // recording of training samples (sgn_record_learned)
+  float* rec_buf = nullptr;
+  int rec_n = 0, rec_cap = 0, rec_count = 0, rec_tau_pow = 1;
+  bool rec_stage = false;  // the current stage is being recorded
+  float2* rtw = nullptr;
+  float2* rY = nullptr;
+  C64* sig_fb = nullptr;  // sigma_start of the recorded stage
+  // sgn_coarse_sample / sgn_coarse_embed scratch
+  int cn = 0;
+  float2* ctw = nullptr;
+  float2* cY = nullptr;
   DiagDev* diag_host = nullptr;  // pinned
   std::vector<cudaGraph_t> sweep_bodies, step_bodies;  // owned by their conditional nodes
   bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
@@ -536,6 +558,87 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
   return ctx->opt.precision >= 1 ? gmres_mixed(ctx, iters_out, relres_out) : gmres_fp64(ctx, iters_out, relres_out);
 }
 
+// ------------------------------------------------------- learned start
+// Kernels one network forward pass launches (13) for the launch count.
+constexpr int kUnetLaunches = 13;
+
+double learned_tau(int pw, double dt) { return pw == 0 ? 1.0 : (pw == 1 ? 0.5 * dt : 0.25 * dt * dt); }
+
+// Stages 2 and 4, after the start of opt.guess: record the coarse inputs (and
+// keep sigma_start) and/or add the network's correction to sigma_hat.
+void learned_pre(sgn_ctx* ctx, C64* const* U, int mode, double dt, bool graph = false) {
+  ctx->rec_stage = false;
+  if (mode != RK_STAGE2 && mode != RK_FINAL) return;
+  // with the extrapolated start, stage 2 of a call's first step has no
+  // stage-3 history and starts from sigma_1 instead: a start of another kind,
+  // left alone (graph mode tests the device flag)
+  const bool s2_plain = ctx->opt.guess == 2 && mode == RK_STAGE2;
+  if (s2_plain && !graph && !ctx->have_s3) return;
+  const Geom& G = ctx->G;
+  if (ctx->rec_buf && ctx->rec_count < ctx->rec_cap) {
+    const int n = ctx->rec_n;
+    const size_t nn = (size_t)n * n;
+    float* slot = ctx->rec_buf + (size_t)ctx->rec_count * 5 * nn;
+    CoarseIn ci{};
+    for (int f = 0; f < 4; ++f) {
+      ci.spec[f] = f < 3 ? U[f] : ctx->sig;
+      ci.out[f] = slot + f * nn;
+      ci.scale[f] = 1.f;
+      ci.shift[f] = f == 0 ? -1.f : 0.f;
+    }
+    CK(launch_restrict(G, ci, 4, n, ctx->rtw, ctx->rY, EX(ctx)));
+    CK(cudaMemcpyAsync(ctx->sig_fb, ctx->sig, G.nspec() * sizeof(C64), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->rec_stage = true;
+  }
+  if (ctx->net) {
+    const int n = ctx->ln;
+    const size_t nn = (size_t)n * n;
+    CoarseIn ci{};
+    for (int f = 0; f < 4; ++f) {
+      ci.spec[f] = f < 3 ? U[f] : ctx->sig;
+      ci.out[f] = ctx->lin + f * nn;
+      ci.scale[f] = ctx->in_scale[f];
+      ci.shift[f] = f == 0 ? -1.f : 0.f;
+    }
+    CK(launch_restrict(G, ci, 4, n, ctx->ltw, ctx->lY, EX(ctx)));
+    sgn_unet_set_stream(ctx->net, ctx->stream);
+    const sgn_status st = sgn_unet_forward(ctx->net, ctx->lin, ctx->lout, 1);
+    if (st != SGN_OK) {
+      ctx->err = std::string("learned start: ") + sgn_unet_last_error(ctx->net);
+      throw Fail{st};
+    }
+    ctx->prof.launches += kUnetLaunches;
+    CK(launch_prolong_add(G, ctx->lout, n, ctx->ltw, ctx->lY, nullptr,
+                          (double)ctx->out_scale * learned_tau(ctx->tau_pow, dt), ctx->sig, EX(ctx),
+                          s2_plain && graph ? &ctx->gst->have_s3 : nullptr));
+  }
+}
+
+// after the solve of a recorded stage: target (sigma_solved - sigma_start) / tau
+void learned_post(sgn_ctx* ctx, double dt) {
+  if (!ctx->rec_stage) return;
+  const Geom& G = ctx->G;
+  const int n = ctx->rec_n;
+  const size_t nn = (size_t)n * n;
+  float* slot = ctx->rec_buf + (size_t)ctx->rec_count * 5 * nn;
+  CK(cudaMemcpyAsync(ctx->tmp[0], ctx->sig, G.nspec() * sizeof(C64), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_axpby<double>(G, -1.0, ctx->sig_fb, 1.0, ctx->tmp[0], EX(ctx)));
+  CoarseIn ci{};
+  ci.spec[0] = ctx->tmp[0];
+  ci.out[0] = slot + 4 * nn;
+  ci.scale[0] = (float)(1.0 / learned_tau(ctx->rec_tau_pow, dt));
+  CK(launch_restrict(G, ci, 1, n, ctx->rtw, ctx->rY, EX(ctx)));
+  ctx->rec_count += 1;
+  ctx->rec_stage = false;
+}
+
+// coarse scratch for side n: twiddles and 5 * n * n/2 complex values
+void coarse_alloc(sgn_ctx* ctx, int n, float2** tw, float2** Y) {
+  *tw = dalloc<float2>(ctx, n);
+  *Y = dalloc<float2>(ctx, (size_t)5 * n * (n / 2));
+  CK(launch_coarse_twiddles(n, *tw, EX(ctx)));
+}
+
 // one RK4 stage (s = 1..4) or a plain RHS evaluation (mode RK_STORE_K)
 bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
@@ -548,7 +651,9 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
     if (mode == RK_STAGE2 && ctx->have_s3) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx)));
     if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
   }
+  learned_pre(ctx, U, mode, dt);
   const bool conv = gmres(ctx, nullptr, nullptr);
+  learned_post(ctx, dt);
   if (ctx->opt.guess == 2) {
     const size_t bytes = ctx->G.nspec() * sizeof(C64);
     if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -770,6 +875,7 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
         CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx), &ctx->gst->have_s3));
       if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
     }
+    learned_pre(ctx, U, mode, dt, true);  // no recording in graph mode (sgn_record_learned refuses it)
   });
   graph_gmres(ctx, top);
   ctx->graph_fixed += count_launches(ctx, [&] {
@@ -872,11 +978,13 @@ void build_step_graph(sgn_ctx* ctx, double dt) {
     cudaGetLastError();
     ctx->stream = saved;
     ctx->prof.on = prof_on;
+    if (ctx->net) sgn_unet_set_stream(ctx->net, ctx->stream);
     free_graph(ctx);
     throw;
   }
   ctx->stream = saved;
   ctx->prof.on = prof_on;
+  if (ctx->net) sgn_unet_set_stream(ctx->net, ctx->stream);
   ctx->graph_dt = dt;
 }
 
@@ -1229,6 +1337,110 @@ sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, doubl
   for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+  return SGN_OK;
+  API_END
+}
+
+static bool coarse_side_ok(const sgn_ctx* ctx, int n) {
+  return n >= 16 && (n & (n - 1)) == 0 && n <= ctx->G.Nx && n <= ctx->G.Ny;
+}
+
+sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_scale[4], float out_scale,
+                                 int tau_power) {
+  API_BEGIN
+  // the captured step graph contains the network (or not): rebuild it
+  free_graph(ctx);
+  if (!net) {
+    ctx->net = nullptr;
+    return SGN_OK;
+  }
+  sgn_unet_t u = static_cast<sgn_unet_t>(net);
+  if (!coarse_side_ok(ctx, n) || sgn_unet_side(u) != n)
+    return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: n must be a power of two in [16, min(Nx, Ny)] and the "
+                                 "network's side");
+  if (!in_scale || !isfinite(out_scale) || tau_power < 0 || tau_power > 2)
+    return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: bad in_scale, out_scale or tau_power");
+  if (ctx->ln != n) {
+    coarse_alloc(ctx, n, &ctx->ltw, &ctx->lY);
+    ctx->lin = dalloc<float>(ctx, (size_t)4 * n * n);
+    ctx->lout = dalloc<float>(ctx, (size_t)n * n);
+    ctx->ln = n;
+  }
+  for (int f = 0; f < 4; ++f) ctx->in_scale[f] = in_scale[f];
+  ctx->out_scale = out_scale;
+  ctx->tau_pow = tau_power;
+  ctx->net = u;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_record_learned(sgn_t ctx, int n, float* buf, int capacity, int tau_power) {
+  API_BEGIN
+  if (!buf) {
+    ctx->rec_buf = nullptr;
+    return SGN_OK;
+  }
+  if (ctx->opt.graph) return fail(ctx, SGN_EINVAL, "sgn_record_learned: needs the host-driven loop (graph = 0)");
+  if (!coarse_side_ok(ctx, n) || capacity < 1 || tau_power < 0 || tau_power > 2)
+    return fail(ctx, SGN_EINVAL, "sgn_record_learned: bad n, capacity or tau_power");
+  if (ctx->rec_n != n) {
+    coarse_alloc(ctx, n, &ctx->rtw, &ctx->rY);
+    ctx->rec_n = n;
+  }
+  if (!ctx->sig_fb) ctx->sig_fb = dalloc<C64>(ctx, ctx->G.nspec());
+  ctx->rec_buf = buf;
+  ctx->rec_cap = capacity;
+  ctx->rec_count = 0;
+  ctx->rec_tau_pow = tau_power;
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_recorded_count(sgn_t ctx, int* count) {
+  if (!ctx || !count) return SGN_EINVAL;
+  *count = ctx->rec_count;
+  return SGN_OK;
+}
+
+sgn_status sgn_coarse_sample(sgn_t ctx, const double* f, int n, float* out) {
+  API_BEGIN
+  if (!f || !out || !coarse_side_ok(ctx, n)) return fail(ctx, SGN_EINVAL, "sgn_coarse_sample: bad argument");
+  if (ctx->cn != n) {
+    coarse_alloc(ctx, n, &ctx->ctw, &ctx->cY);
+    ctx->cn = n;
+  }
+  const float2* tw = ctx->ctw;
+  float2* Y = ctx->cY;
+  const double* fi[1] = {f};
+  fwd2(ctx, fi, 1, &ctx->w);
+  CoarseIn ci{};
+  ci.spec[0] = ctx->w;
+  ci.out[0] = out;
+  ci.scale[0] = 1.f;
+  CK(launch_restrict(ctx->G, ci, 1, n, tw, Y, EX(ctx)));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_coarse_embed(sgn_t ctx, const float* fc, int n, double scale, double* f) {
+  API_BEGIN
+  if (!f || !fc || !coarse_side_ok(ctx, n) || !isfinite(scale))
+    return fail(ctx, SGN_EINVAL, "sgn_coarse_embed: bad argument");
+  if (ctx->cn != n) {
+    coarse_alloc(ctx, n, &ctx->ctw, &ctx->cY);
+    ctx->cn = n;
+  }
+  const float2* tw = ctx->ctw;
+  float2* Y = ctx->cY;
+  const double* fi[1] = {f};
+  fwd2(ctx, fi, 1, &ctx->w);
+  CK(launch_prolong_add(ctx->G, fc, n, tw, Y, nullptr, scale, ctx->w, EX(ctx)));
+  const C64* in[1] = {ctx->w};
+  double* o[1] = {f};
+  inv2(ctx, in, nullptr, nullptr, 1, o);
+  CK(cudaStreamSynchronize(ctx->stream));
   return SGN_OK;
   API_END
 }

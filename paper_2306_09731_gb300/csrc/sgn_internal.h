@@ -367,4 +367,24 @@ cudaError_t launch_diag_soliton(const Geom& G, const double* h, const double* vx
 cudaError_t launch_diag_tail(const Geom& G, const cpx<double>* s0, const cpx<double>* s1, const cpx<double>* s2,
                              double* partials, unsigned* counter, DiagDev* d, const Exec& ex);
 
+// ------------------------------------------------------- learned start
+// Restriction of up to 5 FP64 half spectra to n x n coarse samples:
+// out[f] = scale[f] * (band-limited sample + shift[f]).
+struct CoarseIn {
+  const cpx<double>* spec[5];
+  float* out[5];
+  float scale[5];
+  float shift[5];
+};
+// tw[t] = e^{2 pi i t / n}, t < n (FP32)
+cudaError_t launch_coarse_twiddles(int n, float2* tw, const Exec& ex);
+// Y: scratch of nf * n * n/2 float2
+cudaError_t launch_restrict(const Geom& G, const CoarseIn& in, int nf, int n, const float2* tw, float2* Y,
+                            const Exec& ex);
+// X += (*scale if scale else 1) * sconst * prolongation(fc); Z: scratch n * n/2 float2;
+// nothing is added when gate is set and *gate == 0
+cudaError_t launch_prolong_add(const Geom& G, const float* fc, int n, const float2* tw, float2* Z,
+                               const double* scale, double sconst, cpx<double>* X, const Exec& ex,
+                               const int* gate = nullptr);
+
 }  // namespace sgn

@@ -620,6 +620,8 @@ const char* sgn_unet_last_error(sgn_unet_t net) { return net ? net->err.c_str() 
 
 long long sgn_unet_num_params(sgn_unet_t net) { return net ? net->P : -1; }
 
+int sgn_unet_side(sgn_unet_t net) { return net ? net->n : -1; }
+
 sgn_status sgn_unet_set_params(sgn_unet_t net, const float* p) {
   UAPI_BEGIN
   if (!p) return ufail(net, SGN_EINVAL, "sgn_unet_set_params: NULL");

@@ -24,7 +24,8 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_spectral_derivative", "sgn_fft2_r2c", "sgn_fft2_c2r", "sgn_elliptic_apply",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
-           "sgn_diagnostics", "sgn_last_error"]
+           "sgn_diagnostics", "sgn_set_learned_guess", "sgn_record_learned", "sgn_recorded_count",
+           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_last_error"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
                    "ref_yinv", "ref_x", "ref_yfwd", "rk"]
@@ -92,6 +93,11 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "sgn_elliptic_apply_noalloc": (_I, [_I, _I, _D, _D, _P, _P, _P, _P]),
         "sgn_diagnostics": (_I, [_P, _P, _P, _P, ctypes.POINTER(sgn_diag)]),
+        "sgn_set_learned_guess": (_I, [_P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.c_float, _I]),
+        "sgn_record_learned": (_I, [_P, _I, _P, _I, _I]),
+        "sgn_recorded_count": (_I, [_P, ctypes.POINTER(_I)]),
+        "sgn_coarse_sample": (_I, [_P, _P, _I, _P]),
+        "sgn_coarse_embed": (_I, [_P, _P, _I, _D, _P]),
         "sgn_last_error": (ctypes.c_char_p, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +209,38 @@ def sgn_diagnostics(handle, h, vx, vy) -> dict:
                 dev_vx=d.dev_vx, max_vy=d.max_vy, tail=[d.tail[i] for i in range(3)])
 
 
+def _ptr32(x):
+    if x is None or isinstance(x, int):
+        return x
+    if not x.is_cuda or x.dtype.itemsize != 4 or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    return x.data_ptr()
+
+
+def sgn_set_learned_guess(handle, net, n, in_scale, out_scale, tau_power):
+    """Attach (net = a UNet handle) or detach (net = None) the learned start; see include/sgn.h."""
+    sc = (ctypes.c_float * 4)(*[float(v) for v in in_scale])
+    _check(handle, load_library().sgn_set_learned_guess(handle, net, int(n), sc, float(out_scale), int(tau_power)))
+
+
+def sgn_record_learned(handle, n, buf, capacity, tau_power):
+    _check(handle, load_library().sgn_record_learned(handle, int(n), _ptr32(buf), int(capacity), int(tau_power)))
+
+
+def sgn_recorded_count(handle) -> int:
+    c = _I(0)
+    _check(handle, load_library().sgn_recorded_count(handle, ctypes.byref(c)))
+    return c.value
+
+
+def sgn_coarse_sample(handle, f, n, out):
+    _check(handle, load_library().sgn_coarse_sample(handle, _ptr(f), int(n), _ptr32(out)))
+
+
+def sgn_coarse_embed(handle, fc, n, scale, f):
+    _check(handle, load_library().sgn_coarse_embed(handle, _ptr32(fc), int(n), float(scale), _ptr(f)))
+
+
 def sgn_get_stats(handle) -> dict:
     s = sgn_stats()
     _check(handle, load_library().sgn_get_stats(handle, ctypes.byref(s)))
@@ -312,6 +350,32 @@ class Solver:
 
     def diagnostics(self, h, vx, vy):
         return sgn_diagnostics(self.handle, h, vx, vy)
+
+    def coarse_sample(self, f, n):
+        out = self._torch.empty((n, n), dtype=self._torch.float32, device="cuda")
+        sgn_coarse_sample(self.handle, f, n, out)
+        return out
+
+    def coarse_embed(self, fc, n, scale, f):
+        sgn_coarse_embed(self.handle, fc.contiguous(), n, scale, f)
+
+    def set_learned_guess(self, net, n=None, in_scale=(1.0, 1.0, 1.0, 1.0), out_scale=1.0, tau_power=1):
+        """net: a unet.UNet (kept alive by the solver) or None."""
+        self._net = net
+        sgn_set_learned_guess(self.handle, net.handle if net is not None else None,
+                              n if n is not None else (net.n if net is not None else 0), in_scale, out_scale,
+                              tau_power)
+
+    def record_learned(self, n, capacity, tau_power=1):
+        """Start recording; returns the device buffer [capacity][5][n][n] that fills as stages run."""
+        buf = self._torch.zeros((capacity, 5, n, n), dtype=self._torch.float32, device="cuda")
+        sgn_record_learned(self.handle, n, buf, capacity, tau_power)
+        self._rec = buf
+        return buf
+
+    def stop_recording(self):
+        sgn_record_learned(self.handle, 0, None, 0, 1)
+        return sgn_recorded_count(self.handle)
 
     def set_profiling(self, on=True):
         sgn_set_profiling(self.handle, on)

@@ -9,8 +9,8 @@ from . import sgn as S
 
 # every symbol include/sgn_unet.h declares
 UNET_EXPORTS = ["sgn_unet_create", "sgn_unet_destroy", "sgn_unet_set_stream", "sgn_unet_last_error",
-                "sgn_unet_num_params", "sgn_unet_set_params", "sgn_unet_get_params", "sgn_unet_get_grads",
-                "sgn_unet_forward", "sgn_unet_backward", "sgn_unet_adam_step"]
+                "sgn_unet_num_params", "sgn_unet_side", "sgn_unet_set_params", "sgn_unet_get_params",
+                "sgn_unet_get_grads", "sgn_unet_forward", "sgn_unet_backward", "sgn_unet_adam_step"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -28,6 +28,7 @@ def load_library():
             "sgn_unet_set_stream": (_I, [_P, _P]),
             "sgn_unet_last_error": (ctypes.c_char_p, [_P]),
             "sgn_unet_num_params": (ctypes.c_longlong, [_P]),
+            "sgn_unet_side": (_I, [_P]),
             "sgn_unet_set_params": (_I, [_P, _P]),
             "sgn_unet_get_params": (_I, [_P, _P]),
             "sgn_unet_get_grads": (_I, [_P, _P]),
@@ -49,6 +50,13 @@ def _ptr(t):
     if isinstance(t, int):
         return t
     return t.data_ptr()
+
+
+def _on_current_stream(net):
+    """The solver re-points an attached network to its own stream: every call
+    from Python puts it back on torch's current stream first."""
+    import torch
+    load_library().sgn_unet_set_stream(net, torch.cuda.current_stream().cuda_stream)
 
 
 def _check(net, st):
@@ -88,16 +96,19 @@ class UNet:
 
     def params(self):
         p = self._torch.empty(self.num_params(), dtype=self._torch.float32, device="cuda")
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_get_params(self.handle, _ptr(p)))
         return p
 
     def set_params(self, p):
         p = p.to(device="cuda", dtype=self._torch.float32).contiguous()
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_set_params(self.handle, _ptr(p)))
         self._keep = p
 
     def grads(self):
         g = self._torch.empty(self.num_params(), dtype=self._torch.float32, device="cuda")
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_get_grads(self.handle, _ptr(g)))
         return g
 
@@ -105,6 +116,7 @@ class UNet:
         """x: [B][4][n][n] float32 CUDA tensor -> [B][1][n][n]."""
         self._x = x.contiguous()
         out = self._torch.empty((x.shape[0], 1, self.n, self.n), dtype=self._torch.float32, device="cuda")
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_forward(self.handle, _ptr(self._x), _ptr(out), int(x.shape[0])))
         return out
 
@@ -112,8 +124,10 @@ class UNet:
         """MSE against target [B][1][n][n] after forward; returns the loss (host float)."""
         self._t = target.contiguous()
         loss = self._torch.zeros(1, dtype=self._torch.float64, device="cuda")
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_backward(self.handle, _ptr(self._t), _ptr(loss)))
         return float(loss.item())
 
     def adam_step(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        _on_current_stream(self.handle)
         _check(self.handle, load_library().sgn_unet_adam_step(self.handle, lr, beta1, beta2, eps, int(t)))

@@ -1,0 +1,142 @@
+"""The learned GMRES start (row f2): coarse transfer parity, tolerance kept,
+graph mode, recording, and what a trained network gains.
+
+Bars. Coarse transfer: FP32 sums of at most n terms with FP32 twiddles
+(|error| ~ n x 6e-8 of the field's scale): 1e-5 of the largest value. With a
+network attached every solve still meets the tolerance, so the fields agree
+with the run without it within the path's bar (FP64 path 1e-9, mixed 1e-5).
+Graph mode replays the same kernels: bitwise equal to the host loop.
+"""
+import numpy as np
+import pytest
+
+from oracle import sgn_oracle as O
+from paper_2306_09731_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("Nx,Ny,Lx,Ly,n", [(64, 32, 8.0, 5.0, 16), (256, 256, 20.0, 20.0, 32),
+                                           (512, 128, 40.0, 10.0, 64), (2048, 2048, 100.0, 100.0, 128)])
+def test_coarse_transfer_matches_oracle(Nx, Ny, Lx, Ly, n):
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.random_state(Nx, Ny, Lx, Ly, seed=Nx + n)
+    G = O.Grid(Nx, Ny, Lx, Ly)
+    s = Solver(Nx, Ny, Lx, Ly)
+    c = host(s.coarse_sample(dev(st.h), n))
+    ref = O.coarse_sample(G, st.h, n)
+    assert np.max(np.abs(c - ref)) <= 1e-5 * np.max(np.abs(ref))
+    fc = np.random.default_rng(n).standard_normal((n, n)).astype(np.float32)
+    f = dev(st.vx)
+    s.coarse_embed(torch.tensor(fc, device="cuda"), n, 0.5, f)
+    ref = st.vx + O.coarse_embed(G, fc.astype(np.float64), n, 0.5)
+    assert np.max(np.abs(host(f) - ref)) <= 1e-5 * np.max(np.abs(ref))
+    s.close()
+
+
+def run(st, steps, dt, net=None, tau_power=1, **opts):
+    from paper_2306_09731_gb300.sgn import Solver
+    s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, **opts)
+    if net is not None:
+        s.set_learned_guess(net, net.n, (2.0, 1.0, 1.0, 3.0), 0.01, tau_power)
+    f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+    s.rk4_step(*f, dt, steps)
+    out = [host(x) for x in f]
+    stats = s.stats()
+    s.close()
+    return out, stats
+
+
+@pytest.mark.parametrize("precision,bar", [(0, 1e-9), (2, 1e-5)])
+def test_untrained_network_keeps_the_tolerance(precision, bar):
+    """A random network makes a poor start; every solve still meets tol."""
+    from paper_2306_09731_gb300.unet import UNet
+    st = I.perturbed_soliton(256, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=3)
+    net = UNet(32, max_batch=1, bf16=True, seed=5)
+    a, sa = run(st, 6, 2e-3, net=net, precision=precision, guess=0)
+    b, sb = run(st, 6, 2e-3, precision=precision, guess=0)
+    for x, y in zip(a[:3], b[:3]):
+        assert rel(x, y) < bar
+    assert sa["solves"] == sb["solves"] == 24
+    net.close()
+
+
+def test_learned_start_graph_mode_bitwise():
+    from paper_2306_09731_gb300.unet import UNet
+    st = I.perturbed_soliton(256, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=4)
+    net = UNet(32, max_batch=1, bf16=True, seed=6)
+    a, sa = run(st, 5, 2e-3, net=net, tau_power=2, precision=2, guess=2, graph=1)
+    b, sb = run(st, 5, 2e-3, net=net, tau_power=2, precision=2, guess=2, graph=0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert sa["matvecs"] == sb["matvecs"]
+    net.close()
+
+
+def test_recording_samples_stages_two_and_four():
+    """Two samples per step; channel 0 (h - 1) keeps the mean of h - 1, which
+    every RK stage conserves (mass, Section 2.3); the target is finite."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.gaussian_hump(256, 25.0, 0.5)
+    s = Solver(256, 256, 25.0, 25.0, precision=2)
+    f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+    buf = s.record_learned(32, 20, 1)
+    s.rk4_step(*f, 1e-3, 6)
+    n = s.stop_recording()
+    assert n == 12
+    b = host(buf[:n])
+    assert np.all(np.isfinite(b))
+    m0 = float(np.mean(st.h - 1.0))
+    assert np.max(np.abs(b[:, 0].mean(axis=(1, 2)) - m0)) < 1e-6 * max(1.0, abs(m0)) + 1e-7
+    assert np.max(np.abs(b[:, 4])) > 0
+    s.close()
+
+
+def test_trained_network_reduces_iterations_over_the_paper_start():
+    """Trained on solver snapshots of four Gaussian humps and run on a fifth,
+    the learned correction of the paper's start (the last sigma) cuts GMRES
+    iterations; the fields stay within the mixed-precision bar of the run
+    without it."""
+    from paper_2306_09731_gb300 import learned as Lm
+    N, L, dt, n = 256, 25.0, 2e-3, 32
+    train_states = Lm.gaussian_states(N, L, [0.3, 0.4, 0.6, 0.7], seed=1)
+    samples = Lm.generate(train_states, n, steps=10, dt=dt, precision=2, guess=0, tau_power=1)
+    net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2, log_every=100)
+    assert losses[-1] < 0.5 * losses[0]
+    st = Lm.gaussian_states(N, L, [0.5], seed=7)[0]
+    from paper_2306_09731_gb300.sgn import Solver
+    res = {}
+    for use in (False, True):
+        s = Solver(N, N, L, L, precision=2, guess=0)
+        if use:
+            Lm.attach(s, net, in_scale, out_scale, 1)
+        f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+        s.rk4_step(*f, dt, 12)
+        res[use] = ([host(x) for x in f], s.stats())
+        s.close()
+    base, learned = res[False][1]["matvecs"], res[True][1]["matvecs"]
+    print(f"matvecs over 12 steps: paper start {base}, learned start {learned}; losses {losses}")
+    assert learned < base
+    for x, y in zip(res[True][0][:3], res[False][0][:3]):
+        assert rel(x, y) < 1e-5
+    net.close()

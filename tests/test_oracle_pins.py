@@ -449,3 +449,30 @@ def test_diagnostics_ties_and_no_crest():
     assert d["i_max"] == 2 * 16 + 9 and d["h_max"] == 1.2
     flat = O.diagnostics(G, np.ones((8, 16)), np.zeros((8, 16)), np.zeros((8, 16)))
     assert flat["i_max"] == 0 and np.isnan(flat["dev_h"]) and np.isnan(flat["dev_vx"])
+
+
+# ------------------------------------------- coarse transfer of the learned start
+
+def test_coarse_sample_of_band_limited_field_is_point_sampling():
+    G = O.Grid(64, 32, 6.0, 3.0)
+    X = np.broadcast_to(G.x[None, :], (32, 64))
+    Y = np.broadcast_to(G.y[:, None], (32, 64))
+    kx, ky = 2 * np.pi / 6.0, 2 * np.pi / 3.0
+    f = 1.0 + 0.5 * np.cos(3 * kx * X) * np.sin(2 * ky * Y) + 0.2 * np.sin(7 * kx * X)
+    c = O.coarse_sample(G, f, 16)
+    assert np.max(np.abs(c - f[::2, ::4])) < 1e-13
+    # modes at or above n/2 = 8 vanish from the samples
+    g = np.cos(8 * kx * X) + np.sin(9 * ky * Y)
+    assert np.max(np.abs(O.coarse_sample(G, g, 16))) < 1e-13
+
+
+def test_coarse_embed_is_band_limited_interpolation():
+    G = O.Grid(64, 64, 2 * np.pi, 2 * np.pi)
+    i = np.arange(16)
+    fc = np.cos(2 * np.pi * 3 * i[None, :] / 16) * np.ones((16, 1)) + 0.5 * np.sin(2 * np.pi * 5 * i[:, None] / 16)
+    f = O.coarse_embed(G, fc, 16, scale=2.0)
+    X = np.broadcast_to(G.x[None, :] - G.x[0], (64, 64))
+    Y = np.broadcast_to(G.y[:, None] - G.y[0], (64, 64))
+    ref = 2.0 * (np.cos(3 * X) + 0.5 * np.sin(5 * Y))
+    assert np.max(np.abs(f - ref)) < 1e-13
+    assert np.max(np.abs(O.coarse_sample(G, f, 16) - 2.0 * fc)) < 1e-13
