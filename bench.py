@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-mode arms")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start arms (and their training)")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
                                                  "mixed_df_graph, fp64, mixed_paper_start)")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
@@ -412,6 +413,29 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
+    # ensembles (row f3): 64 perturbed line solitons, a ~ U[0.1, 1], eps ~ U[1e-3, 5e-2], on
+    # 256^2, 512x256 and 1024x512 grids, dt = 2e-3, each member with its own handle and
+    # stream: sgn_rk4_step_batch against the members stepped one by one (wall time of
+    # K steps of all members after W warm-up steps; host timers around calls that
+    # synchronise)
+    ensemble = None
+    if not args.no_ensemble and world == 1 and args.path != "fp64" and not args.arms:
+        from paper_2306_09731_gb300.ensemble import GRIDS, Ensemble, perturbed_members
+        members = perturbed_members(64, seed=11)
+        E = Ensemble(members, precision=2, guess=2, graph=1)
+        E.step(2e-3, max(1, args.warmup))
+        torch.cuda.synchronize()
+        b0 = time.perf_counter()
+        E.step(2e-3, args.steps)
+        b1 = time.perf_counter()
+        E.step_one_by_one(2e-3, args.steps)
+        b2 = time.perf_counter()
+        E.close()
+        ensemble = {"members": len(members), "grids": [list(g[:2]) for g in GRIDS], "dt": 2e-3,
+                    "steps": args.steps, "unit": "member-steps/s",
+                    "batch": len(members) * args.steps / (b1 - b0),
+                    "one_by_one": len(members) * args.steps / (b2 - b1),
+                    "speedup": (b2 - b1) / (b1 - b0)}
     # the paper's monitoring quantities (row f4) on the final state: wall time of
     # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
     hf = devfields[head_name]
@@ -468,6 +492,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "diagnostics": {"ms_per_call": diag_ms, "h_max": diag["h_max"], "c_fit": diag["c_fit"],
                         "tail": diag["tail"]},
+        "ensemble": ensemble,
     }
     if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]

@@ -202,6 +202,18 @@ sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly,
 /* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
 const char* sgn_last_error(sgn_t ctx);
 
+/* Ensembles (row f3): count independent problems, each with its own handle
+ * (its own grid size, options and stream, set with sgn_set_stream), advanced
+ * by nsteps RK4 steps each, like sgn_rk4_step on h[i], vx[i], vy[i],
+ * sigma[i]. Members created with graph = 1 are all enqueued on their streams
+ * before any is waited for, so members on distinct streams run concurrently on
+ * the GPU; members with graph = 0 run one after another (their GMRES loop
+ * synchronises). status (may be NULL) receives each member's status; the
+ * return value is SGN_OK or the first failing member's status. Results are
+ * those of sgn_rk4_step on each member. */
+sgn_status sgn_rk4_step_batch(sgn_t* ctxs, int count, double* const* h, double* const* vx, double* const* vy,
+                              double* const* sigma, double dt, int nsteps, sgn_status* status);
+
 /* ------------------------------------------------------------------------
  * Monitoring quantities of the paper's experiments (Sections 3 and 4):
  *   h_max, i_max, x_s, y_s  L-infinity norm of h and the grid point where it is

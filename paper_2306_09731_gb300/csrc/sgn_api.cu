@@ -990,8 +990,11 @@ void build_step_graph(sgn_ctx* ctx, double dt) {
 
 // rk4_device with each step replayed from the step graph. The GMRES
 // statistics and the depth flags are read once, after the last step.
-void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
-                      bool* conv_all) {
+// Graph-mode steps in two halves: everything up to the asynchronous readback
+// of the device statistics, then (after a synchronisation) their harvest. A
+// batch of handles enqueues all members first and harvests after, so that the
+// members' work overlaps on their streams.
+void rk4_graph_enqueue(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps) {
   if (!ctx->step_exec || ctx->graph_dt != dt) build_step_graph(ctx, dt);
   const double* f3[3] = {h, vx, vy};
   reset_flags(ctx);
@@ -1007,7 +1010,12 @@ void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* s
   inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
   CK(cudaMemcpyAsync(ctx->gst_host, ctx->gst, sizeof(GmresDev), cudaMemcpyDeviceToHost, ctx->stream));
   CK(launch_readback_scalar(ctx->scal, ctx->flags, ctx->rb_dev, EX(ctx)));
-  sync_read(ctx);
+  CK(cudaMemcpyAsync(ctx->rb_host, ctx->rb_dev, sizeof(GmresReadback), cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+void rk4_graph_finish(sgn_ctx* ctx, int nsteps, bool* conv_all) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->prof.on) ctx->prof.harvest();
   const GmresDev& st = *ctx->gst_host;
   ctx->stats.solves += (int)st.tot_solves;
   ctx->stats.matvecs += st.tot_its;
@@ -1019,6 +1027,12 @@ void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* s
                         st.tot_its * ctx->graph_per_step;
   check_flags(ctx, ctx->rb_host->flags);
   *conv_all = st.notconv == 0;
+}
+
+void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
+                      bool* conv_all) {
+  rk4_graph_enqueue(ctx, h, vx, vy, sigma, dt, nsteps);
+  rk4_graph_finish(ctx, nsteps, conv_all);
 }
 
 }  // namespace
@@ -1318,6 +1332,55 @@ sgn_status sgn_rk4_step(sgn_t ctx, double* h, double* vx, double* vy, double* si
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
   return SGN_OK;
   API_END
+}
+
+sgn_status sgn_rk4_step_batch(sgn_t* ctxs, int count, double* const* h, double* const* vx, double* const* vy,
+                              double* const* sigma, double dt, int nsteps, sgn_status* status) {
+  if (!ctxs || count < 1 || !h || !vx || !vy || !sigma || nsteps < 0 || !isfinite(dt)) return SGN_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !h[i] || !vx[i] || !vy[i] || !sigma[i]) return SGN_EINVAL;
+    if (status) status[i] = SGN_OK;
+  }
+  if (nsteps == 0) return SGN_OK;
+  // phase 1: enqueue every member (graph-mode members without a host wait;
+  // host-loop members run to completion here)
+  std::vector<sgn_status> st(count, SGN_OK);
+  std::vector<char> pending(count, 0);
+  for (int i = 0; i < count; ++i) {
+    sgn_t ctx = ctxs[i];
+    ctx->err.clear();
+    try {
+      if (ctx->opt.graph && !ctx->prof.on) {
+        rk4_graph_enqueue(ctx, h[i], vx[i], vy[i], sigma[i], dt, nsteps);
+        pending[i] = 1;
+      } else {
+        bool conv = true;
+        rk4_device(ctx, h[i], vx[i], vy[i], sigma[i], dt, nsteps, &conv);
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!conv) st[i] = fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+      }
+    } catch (Fail& f) {
+      st[i] = f.st;
+    }
+  }
+  // phase 2: wait for and harvest the graph-mode members
+  for (int i = 0; i < count; ++i) {
+    if (!pending[i]) continue;
+    sgn_t ctx = ctxs[i];
+    try {
+      bool conv = true;
+      rk4_graph_finish(ctx, nsteps, &conv);
+      if (!conv) st[i] = fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
+    } catch (Fail& f) {
+      st[i] = f.st;
+    }
+  }
+  sgn_status first = SGN_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = st[i];
+    if (first == SGN_OK && st[i] != SGN_OK) first = st[i];
+  }
+  return first;
 }
 
 sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, double* sigma, double dt,

@@ -25,7 +25,7 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
            "sgn_diagnostics", "sgn_set_learned_guess", "sgn_record_learned", "sgn_recorded_count",
-           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_last_error"]
+           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_rk4_step_batch", "sgn_last_error"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
                    "ref_yinv", "ref_x", "ref_yfwd", "rk"]
@@ -98,6 +98,8 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         "sgn_recorded_count": (_I, [_P, ctypes.POINTER(_I)]),
         "sgn_coarse_sample": (_I, [_P, _P, _I, _P]),
         "sgn_coarse_embed": (_I, [_P, _P, _I, _D, _P]),
+        "sgn_rk4_step_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_I)]),
         "sgn_last_error": (ctypes.c_char_p, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -239,6 +241,22 @@ def sgn_coarse_sample(handle, f, n, out):
 
 def sgn_coarse_embed(handle, fc, n, scale, f):
     _check(handle, load_library().sgn_coarse_embed(handle, _ptr32(fc), int(n), float(scale), _ptr(f)))
+
+
+def sgn_rk4_step_batch(handles, fields, dt, nsteps):
+    """fields: per member [h, vx, vy, sigma] (CUDA float64 tensors); returns the member statuses.
+    Raises SGNError with the first failing member's status."""
+    n = len(handles)
+    arr = lambda vals: (_P * n)(*vals)
+    hs = arr([h.value if hasattr(h, "value") else h for h in handles])
+    ps = [arr([_ptr(f[k]) for f in fields]) for k in range(4)]
+    st = (_I * n)()
+    rc = load_library().sgn_rk4_step_batch(hs, n, ps[0], ps[1], ps[2], ps[3], float(dt), int(nsteps), st)
+    statuses = [st[i] for i in range(n)]
+    if rc != 0:
+        bad = next(i for i in range(n) if statuses[i] != 0)
+        raise SGNError(rc, f"member {bad}: {sgn_last_error(handles[bad])}")
+    return statuses
 
 
 def sgn_get_stats(handle) -> dict:
