@@ -87,6 +87,24 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
 }
 __device__ __forceinline__ double dfl_to_f64(dfl a) { return f32_to_f64_bits(a.hi) + f32_to_f64_bits(a.lo); }
 
+// FP64 -> FP32 rounded to nearest (the split's two parts added in FP32; the
+// range rules of dfl_from_f64) without an FP64-pipe conversion
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const dfl d = dfl_from_f64(x);
+  return __fadd_rn(d.hi, d.lo);
+}
+
+// conversions between the storage types of the passes, off the FP64 pipe
+template <typename TO, typename TI>
+__device__ __forceinline__ TO cvt(TI v) {
+  if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8)
+    return f64_to_f32_bits(v);
+  else if constexpr (sizeof(TO) == 8 && sizeof(TI) == 4)
+    return f32_to_f64_bits(v);
+  else
+    return (TO)v;
+}
+
 __device__ __forceinline__ dfl two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);

@@ -291,13 +291,13 @@ template <typename TI, typename TO>
 __global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int invert, cpx<TO>* y, const int* ysel,
                         size_t ystride) {
   if (ysel) y += (size_t)(*ysel) * ystride;
-  // arithmetic in the wider of the two types (FP32 when both are FP32)
-  typedef typename Acc<decltype(TI() * TO())>::type A;
+  // arithmetic in the output type: an FP32 result (the inner basis) is
+  // scaled in FP32 after the conversion, which stays off the FP64 pipe
   const double f0 = *factor;
-  const A f = (A)(invert ? 1.0 / f0 : f0);
+  const TO f = (TO)(invert ? 1.0 / f0 : f0);
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<TI> v = x[it.e];
-    y[it.e] = mk((TO)((A)v.x * f), (TO)((A)v.y * f));
+    y[it.e] = mk(cvt<TO>(v.x) * f, cvt<TO>(v.y) * f);
   }
 }
 
@@ -321,7 +321,7 @@ __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, c
       dy += cf[i] * (A)v.y;
     }
     const cpx<TX> xv = x[it.e];
-    x[it.e] = mk((TX)(xv.x + (TX)dx), (TX)(xv.y + (TX)dy));
+    x[it.e] = mk(xv.x + cvt<TX>(dx), xv.y + cvt<TX>(dy));
   }
 }
 

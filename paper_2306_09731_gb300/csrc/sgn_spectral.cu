@@ -486,6 +486,9 @@ struct YIn {
 template <typename T, typename S>
 __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
   const cpx<S> v = *p;
+  // double-float from FP64 without FP64 instructions; FP32 from FP64 with the
+  // native conversion (measured: the bit-level one costs more issue slots in
+  // the issue-bound RHS y-inverse than the FP64-pipe conversion saves)
   if constexpr (std::is_same<T, dfl>::value && std::is_same<S, double>::value)
     return mk(dfl_from_f64(v.x), dfl_from_f64(v.y));
   else
@@ -515,9 +518,9 @@ constexpr int ypass_lc() {
   return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV>()) - (LN - 3), 0, 6);
 }
 
-template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
-                                                YIn<T, NIN, S> in, Epi epi) {
+template <typename T, bool INV, int NIN, class Epi, typename S, int LN>
+__device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
+                                           const YIn<T, NIN, S>& in, const Epi& epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
   const int lN = LN > 0 ? LN : G.lNy;
@@ -544,6 +547,29 @@ __global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const
     fft_regs<INV>(r[i], smb + c, tw, t, lN, lC);
   }
   epi(r, col, t, T_, valid, G, ky);
+}
+
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
+__global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw,
+                                                                   const T* __restrict__ ky, YIn<T, NIN, S> in,
+                                                                   Epi epi) {
+  ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
+}
+// FP32 passes with at most two transforms per thread: two 512-thread blocks
+// per SM (64 registers; measured: matvec y-forward 34 against 39 us at
+// 2048^2). The other passes keep the compiler's register choice.
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
+__global__ void __launch_bounds__(ypass_threads<T, INV>(), 2) k_ypass_o2(Geom G, const cpx<T>* __restrict__ tw,
+                                                                        const T* __restrict__ ky,
+                                                                        YIn<T, NIN, S> in, Epi epi) {
+  ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
+}
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
+constexpr auto ypass_fn() {
+  if constexpr (sizeof(T) == 4 && NIN <= 2)
+    return &k_ypass_o2<T, INV, NIN, Epi, S, LN>;
+  else
+    return &k_ypass<T, INV, NIN, Epi, S, LN>;
 }
 
 template <typename T, int NIN>
@@ -642,7 +668,7 @@ __global__ void k_rk_update(Geom G, RkK<T, S> a) {
     const size_t e = it.e;
     cpx<S> kk[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) kk[f] = mk((S)a.K[f][e].x, (S)a.K[f][e].y);
+    for (int f = 0; f < 3; ++f) kk[f] = mk(cvt<S>(a.K[f][e].x), cvt<S>(a.K[f][e].y));
     if (rk.mode == RK_STORE_K) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) a.acc[f][e] = kk[f];
@@ -763,10 +789,10 @@ template <typename T, int L>
 static void set_attrs_ln() {
   set_smem<T>((const void*)k_mv_x<T, L>);
   set_smem<T>((const void*)k_rhs_x<T, L>);
-  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>, T, L>);
-  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>, T, L>);
-  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>, double, L>);
-  set_smem<T>((const void*)k_ypass<T, false, 3, EpiK<T>, T, L>);
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, L>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L>());
 }
 
 template <typename T>
@@ -782,14 +808,14 @@ void init_kernel_attributes() {
   set_smem<T>((const void*)k_coef_x<T>);
   set_smem<T>((const void*)k_mv_x<T>);
   set_smem<T>((const void*)k_rhs_x<T>);
-  set_smem<T>((const void*)k_ypass<T, false, 1, EpiStore<T, 1>>);
-  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>>);
-  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>>);
-  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>>);
-  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T>>);
-  set_smem<T>((const void*)k_ypass<T, false, 3, EpiK<T>>);
-  set_smem<T>((const void*)k_ypass<T, true, 4, EpiStore<T, 4>, double>);
-  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>, double>);
+  set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStore<T, 1>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double>());
+  set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double>());
   cudaGetLastError();
 }
 
@@ -845,12 +871,12 @@ cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const
     ep.dst[0] = out[i];
     if (inverse) {
       ex.begin(PK_IO);
-      k_ypass<T, true, 1, EpiStore<T, 1>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      ypass_fn<T, true, 1, EpiStore<T, 1>>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
       ex.end();
     }
     else {
       ex.begin(PK_IO);
-      k_ypass<T, false, 1, EpiStore<T, 1>><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      ypass_fn<T, false, 1, EpiStore<T, 1>>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
       ex.end();
     }
   }
@@ -900,7 +926,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     ep.dst[0] = tmp[0];
     ep.dst[1] = tmp[1];
     ex.begin(PK_MV_YINV);
-    k_ypass<T, true, 2, EpiStore<T, 2>, S, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, true, 2, EpiStore<T, 2>, S, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   x_config<T>(G, grid, block, smem, 1);
@@ -918,7 +944,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     yi.src[1] = tmp[1];
     EpiMatvec<T, S> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
     ex.begin(PK_MV_YFWD);
-    k_ypass<T, false, 2, EpiMatvec<T, S>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, false, 2, EpiMatvec<T, S>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   return cudaGetLastError();
@@ -943,7 +969,7 @@ cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>
   EpiStore<T, 1> ep{};
   ep.dst[0] = out;
   ex.begin(PK_IO);
-  k_ypass<T, true, 1, EpiStore<T, 1>, double><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+  ypass_fn<T, true, 1, EpiStore<T, 1>, double>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
   ex.end();
   return cudaGetLastError();
 }
@@ -953,9 +979,9 @@ void init_kernel_attributes_df() {
   typedef dfl T;
   set_smem<T>((const void*)k_coef_x<T>);
   set_smem<T>((const void*)k_mv_x<T>);
-  set_smem<T>((const void*)k_ypass<T, true, 2, EpiStore<T, 2>, double>);
-  set_smem<T>((const void*)k_ypass<T, false, 2, EpiMatvec<T, double>>);
-  set_smem<T>((const void*)k_ypass<T, true, 1, EpiStore<T, 1>, double>);
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double>());
   cudaGetLastError();
 }
 
@@ -977,7 +1003,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     EpiStore<T, 4> ep{};
     for (int i = 0; i < 4; ++i) ep.dst[i] = tmp[i];
     ex.begin(PK_RHS_YINV);
-    k_ypass<T, true, 4, EpiStore<T, 4>, S, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, true, 4, EpiStore<T, 4>, S, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   // each block reads only its own row pair before writing it, so the outputs
@@ -1004,7 +1030,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     ep.kx = tb.kx;
     ep.dealias = rk.dealias;
     ex.begin(PK_RHS_YFWD);
-    k_ypass<T, false, 3, EpiK<T>, T, L><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, false, 3, EpiK<T>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   {
