@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start arms (and their training)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
+    ap.add_argument("--no-crossing", action="store_true",
+                    help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
                                                  "mixed_df_graph, fp64, mixed_paper_start)")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
@@ -301,6 +303,38 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
     return s, f, rec
 
 
+def time_crossing(st, precision, guess, graph, learned, steps, warmup):
+    """Wall time of `steps` graph-mode RK4 steps (after `warmup`) of one GMRES
+    start on a crossing-soliton state; CUDA events on the launching stream."""
+    import torch
+
+    from paper_2306_09731_gb300.sgn import Solver
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+    s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
+    if learned is not None:
+        net, in_scale, out_scale, tau_power = learned
+        s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
+    s.rk4_step(*f, DT, warmup)
+    torch.cuda.synchronize()
+    st0 = s.stats()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.rk4_step(*f, DT, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = s.stats()
+    solves = st1["solves"] - st0["solves"]
+    s.close()
+    return {"value": steps / (ms / 1000.0), "ms_per_step": ms / steps,
+            "iters_per_stage": (st1["matvecs"] - st0["matvecs"]) / max(solves, 1),
+            "fp64_refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1),
+            "max_iters": st1["max_iters"]}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -350,6 +384,7 @@ def run_ours(args, rank, world, local_rank):
     # the benchmark state: over the paper's start (tau = dt/2, coarse n/8) and
     # over the extrapolated start (tau = (dt/2)^2, coarse n/16)
     learned_info = {}
+    nets = {}
     if not args.no_learned and args.path != "fp64" and (not args.arms or any("learned" in a for a in
                                                                               args.arms.split(","))):
         from paper_2306_09731_gb300 import learned as Lm
@@ -370,6 +405,7 @@ def run_ours(args, rank, world, local_rank):
                 torch.cuda.synchronize()
                 t2 = time.perf_counter()
                 learned = (net, in_scale, out_scale, tau_power)
+                nets[name] = learned
                 learned_info[name] = {"coarse_n": coarse, "samples": int(samples.shape[0]),
                                       "data_s": t1 - t0, "train_s": t2 - t1, "losses": losses,
                                       "params": net.num_params()}
@@ -450,6 +486,34 @@ def run_ours(args, rank, world, local_rank):
     diag_ms = (time.perf_counter() - d0) / 5 * 1e3
     head_solver.close()
 
+    # crossing line solitons at 4096^2 (the learned start's workload): two a = 0.6
+    # solitons rotated by +-theta, precision 2, graph mode, every solve to the
+    # FP64 tolerance 1e-10; the paper's start (last sigma), the extrapolated
+    # start, and each with the network trained above on the 2048^2 Gaussian
+    # snapshots (coarse grids 256 and 128)
+    crossing = None
+    if not args.no_crossing and world == 1 and args.path != "fp64" and not args.arms and n == N_DEFAULT:
+        del devfields, hf
+        torch.cuda.empty_cache()
+        ksteps, kwarm = max(3, args.steps // 4), 2
+        crossing = {"workload": "crossing_solitons_4096x4096", "grid": [4096, 4096], "box": [-100.0, 100.0],
+                    "a": 0.6, "dt": DT, "precision": 2, "graph": True, "steps": ksteps, "warmup": kwarm,
+                    "unit": UNIT, "tol": 1e-10, "theta": {}}
+        for theta in (15.0, 30.0):
+            cst = I.crossing_solitons(4096, 200.0, 0.6, theta)
+            arms = {}
+            for name, guess, lname in (("paper_start", 0, None),
+                                       ("paper_start_learned", 0, "mixed_df_paper_start_learned"),
+                                       ("extrapolated", 2, None),
+                                       ("extrapolated_learned", 2, "mixed_df_learned_graph")):
+                if lname is not None and lname not in nets:
+                    continue
+                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, kwarm)
+            crossing["theta"][f"{theta:g}"] = arms
+            del cst
+        for ln, (net, *_rest) in nets.items():
+            crossing.setdefault("networks", {})[ln] = {"coarse_n": net.n}
+
     fp32 = head_prec >= 1
     # a run restricted to graph arms (--arms) has no per-launch timers
     prof = paths[prof_name]["prof"] if prof_name in paths else {"ms": {}, "counts": {}, "launches": 0}
@@ -496,6 +560,7 @@ def run_ours(args, rank, world, local_rank):
         "diagnostics": {"ms_per_call": diag_ms, "h_max": diag["h_max"], "c_fit": diag["c_fit"],
                         "tail": diag["tail"]},
         "ensemble": ensemble,
+        "crossing_4096": crossing,
     }
     if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]

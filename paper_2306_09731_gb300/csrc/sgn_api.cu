@@ -1057,8 +1057,8 @@ void sgn_default_options(sgn_options* o) {
 sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_options* opt, sgn_t* out) {
   if (!out) return fail(nullptr, SGN_EINVAL, "sgn_create: out is NULL");
   *out = nullptr;
-  if (!pow2(Nx) || !pow2(Ny) || Nx < 8 || Ny < 8 || Nx > 2048 || Ny > 2048)
-    return fail(nullptr, SGN_EINVAL, "sgn_create: Nx, Ny must be powers of two in [8, 2048]");
+  if (!pow2(Nx) || !pow2(Ny) || Nx < 8 || Ny < 8 || Nx > 4096 || Ny > 4096)
+    return fail(nullptr, SGN_EINVAL, "sgn_create: Nx, Ny must be powers of two in [8, 4096]");
   if (!(Lx > 0.0) || !(Ly > 0.0) || !isfinite(Lx) || !isfinite(Ly) || !isfinite(g))
     return fail(nullptr, SGN_EINVAL, "sgn_create: Lx, Ly must be positive and finite, g finite");
   sgn_options o;

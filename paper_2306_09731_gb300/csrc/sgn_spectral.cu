@@ -289,10 +289,13 @@ __global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, 
 // Resident 256-thread blocks per SM the x-passes ask the compiler for: the
 // FP32 passes are latency bound and need the warps; the FP64 ones are
 // FP64-issue bound and keep their registers.
-template <typename T>
-constexpr int mv_min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
-template <typename T>
-constexpr int rhs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
+// At 4096 points (LN = 12) a row pair takes 512 threads: one block per SM.
+template <int LN>
+constexpr int xpass_threads() { return LN == 12 ? 512 : 256; }
+template <typename T, int LN>
+constexpr int mv_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 3 : 2); }
+template <typename T, int LN>
+constexpr int rhs_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 2 : 1); }
 
 // S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
 // Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
@@ -302,7 +305,7 @@ constexpr int rhs_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 // spectra of phase 1 until phase 2 combines them): a = 3 sigma/h^3, then
 // bx = sigma_x/h, then by = sigma_y/h.
 template <typename T, int LN = 0>
-__global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+__global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
                                                const T* __restrict__ cc, cpx<T>* Cout, cpx<T>* Byout) {
   const XLayout L = x_layout<LN>(G);
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(256, mv_min_blocks<T>()) k_mv_x(Geom G, const 
 // depth anomaly hh = h - 1. Writes Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and
 // Fh = F^x with F = |v|^2/2 - |grad sigma|^2/(2h^2) + g (h - 1) - 9 sigma^2/(2h^4).
 template <typename T, int LN = 0>
-__global__ void __launch_bounds__(256, rhs_min_blocks<T>()) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
+__global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                 const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
                                                 const cpx<T>* Sy, const T* __restrict__ hh,
                                                 const T* __restrict__ cr, T g, cpx<T>* Cq, cpx<T>* Qy,
@@ -504,9 +507,10 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // with the matvec epilogue (measured at 2048^2: FP64 inverse 321 against 371 us
 // and forward 327 against 386 us; double-float inverse 158 against 182 us,
 // forward 140 against 172 us).
-template <typename T, bool INV>
+// At 4096 points (LN = 12) one column takes 512 threads in every type.
+template <typename T, bool INV, int LN = 0>
 constexpr int ypass_threads() {
-  return sizeof(T) == 4 ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
+  return (sizeof(T) == 4 || LN == 12) ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
 }
 
 // LN > 0: compile-time column length 2^LN; the interleave 2^LC of the block's
@@ -515,7 +519,7 @@ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 template <typename T, bool INV, int LN>
 constexpr int ypass_lc() {
-  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV>()) - (LN - 3), 0, 6);
+  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV, LN>()) - (LN - 3), 0, 6);
 }
 
 template <typename T, bool INV, int NIN, class Epi, typename S, int LN>
@@ -550,7 +554,7 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
 }
 
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw,
+__global__ void __launch_bounds__(ypass_threads<T, INV, LN>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw,
                                                                    const T* __restrict__ ky, YIn<T, NIN, S> in,
                                                                    Epi epi) {
   ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(ypass_threads<T, INV>()) k_ypass(Geom G, const
 // per SM (64 registers; measured: matvec y-forward 34 against 39 us at
 // 2048^2). The other passes keep the compiler's register choice.
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads<T, INV>(), 2) k_ypass_o2(Geom G, const cpx<T>* __restrict__ tw,
+__global__ void __launch_bounds__(ypass_threads<T, INV, LN>(), 2) k_ypass_o2(Geom G, const cpx<T>* __restrict__ tw,
                                                                         const T* __restrict__ ky,
                                                                         YIn<T, NIN, S> in, Epi epi) {
   ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
@@ -736,9 +740,14 @@ cudaError_t launch_hermitian_fix(const Geom& G, cpx<T>* x, const Exec& ex) {
 // ------------------------------------------------------------ launchers
 
 // Calls f(std::integral_constant<int, LN>) with LN = lN for the sizes that have
-// compile-time FP32 kernels (256..2048 points), LN = 0 (runtime size) otherwise.
+// compile-time kernels (FP32: 256..4096 points; every type: 4096, whose
+// transforms take 512 threads), LN = 0 (runtime size) otherwise.
 template <typename T, class F>
 static inline void dispatch_ln(int lN, F&& f) {
+  if (lN == 12) {
+    f(std::integral_constant<int, 12>());
+    return;
+  }
   if constexpr (sizeof(T) == 4) {
     switch (lN) {
       case 8: f(std::integral_constant<int, 8>()); return;
@@ -749,6 +758,16 @@ static inline void dispatch_ln(int lN, F&& f) {
     }
   }
   f(std::integral_constant<int, 0>());
+}
+
+// LN = 12 at 4096 points, else LN = 0: the passes that have no other
+// compile-time sizes.
+template <class F>
+static inline void dispatch_l12(int lN, F&& f) {
+  if (lN == 12)
+    f(std::integral_constant<int, 12>());
+  else
+    f(std::integral_constant<int, 0>());
 }
 
 template <typename T>
@@ -769,7 +788,7 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
 template <typename T, bool INV>
 static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem) {
   const int Tn = G.Ny >> 3;
-  const int tpb = ypass_threads<T, INV>();
+  const int tpb = G.lNy == 12 ? ypass_threads<T, INV, 12>() : ypass_threads<T, INV>();
   int C = tpb / Tn;
   if (C < 1) C = 1;
   if (C > 64) C = 64;
@@ -793,6 +812,11 @@ static void set_attrs_ln() {
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L>());
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L>());
   set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L>());
+  if constexpr (L == 12) {
+    set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, T, L>());
+    set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStore<T, 1>, T, L>());
+    set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double, L>());
+  }
 }
 
 template <typename T>
@@ -803,6 +827,7 @@ void init_kernel_attributes() {
     set_attrs_ln<T, 10>();
     set_attrs_ln<T, 11>();
   }
+  set_attrs_ln<T, 12>();
   set_smem<T>((const void*)k_x_r2c<T>);
   set_smem<T>((const void*)k_x_c2r<T>);
   set_smem<T>((const void*)k_coef_x<T>);
@@ -869,16 +894,15 @@ cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const
     yi.deriv[0] = deriv ? deriv[i] : 0;
     EpiStore<T, 1> ep{};
     ep.dst[0] = out[i];
-    if (inverse) {
+    dispatch_l12(G.lNy, [&](auto ln) {
+      constexpr int L = decltype(ln)::value;
       ex.begin(PK_IO);
-      ypass_fn<T, true, 1, EpiStore<T, 1>>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      if (inverse)
+        ypass_fn<T, true, 1, EpiStore<T, 1>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+      else
+        ypass_fn<T, false, 1, EpiStore<T, 1>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
       ex.end();
-    }
-    else {
-      ex.begin(PK_IO);
-      ypass_fn<T, false, 1, EpiStore<T, 1>>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
-      ex.end();
-    }
+    });
   }
   return cudaGetLastError();
 }
@@ -968,9 +992,12 @@ cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>
   yi.src[0] = in;
   EpiStore<T, 1> ep{};
   ep.dst[0] = out;
-  ex.begin(PK_IO);
-  ypass_fn<T, true, 1, EpiStore<T, 1>, double>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
-  ex.end();
+  dispatch_l12(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
+    ex.begin(PK_IO);
+    ypass_fn<T, true, 1, EpiStore<T, 1>, double, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  });
   return cudaGetLastError();
 }
 
@@ -982,6 +1009,10 @@ void init_kernel_attributes_df() {
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double>());
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double>());
+  set_smem<T>((const void*)k_mv_x<T, 12>);
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12>());
+  set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double, 12>());
   cudaGetLastError();
 }
 

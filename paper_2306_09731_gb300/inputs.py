@@ -190,3 +190,74 @@ def random_state(Nx, Ny, Lx, Ly, seed=0, kmax=6, h_amp=0.15, v_amp=0.1) -> State
     sig = random_smooth(Nx, Ny, Lx, Ly, seed=seed + 3, kmax=kmax, amp=v_amp)
     return State(Nx, Ny, Lx, Ly, h=h, vx=vx, vy=vy, sigma=sig,
                  meta=dict(kind="random_state", seed=seed))
+
+
+def _smooth_step(t: np.ndarray) -> np.ndarray:
+    """C-infinity step: 0 for t <= 0, 1 for t >= 1, e^{-1/t} / (e^{-1/t} + e^{-1/(1-t)}) between."""
+    t = np.clip(t, 0.0, 1.0)
+    with np.errstate(divide="ignore", over="ignore"):
+        a = np.where(t > 0.0, np.exp(-1.0 / np.where(t > 0.0, t, 1.0)), 0.0)
+        b = np.where(t < 1.0, np.exp(-1.0 / np.where(t < 1.0, 1.0 - t, 1.0)), 0.0)
+    return a / (a + b)
+
+
+def crossing_solitons(N=4096, L=200.0, a=0.6, theta_deg=30.0, window=(0.35, 0.45)) -> State:
+    """Two line solitary waves of amplitude a whose crests cross at the origin,
+    rotated by +theta and -theta from the y axis (Section 5 crosses them at 90
+    degrees; this is the rotated variant), on [-L/2, L/2)^2 with N^2 points.
+
+    Soliton i has unit normal n_i = (cos theta_i, sin theta_i) and travelling
+    coordinate xi_i = n_i . (x, y); it contributes its depth anomaly a sech^2
+    (kappa xi_i) and its velocity profile v(xi_i) n_i of Eq. (sol). A line
+    with an irrational slope is not periodic on the box, so both are tapered
+    to zero in y by a C-infinity window w(y) (1 for |y| <= window[0] L, 0 for
+    |y| >= window[1] L): the data are smooth and periodic.
+        h = 1 + w(y) sum_i a sech^2(kappa xi_i),   v = w(y) sum_i v(xi_i) n_i.
+    sigma starts at zero (no closed form).
+    """
+    sol = Soliton1D(a=a)
+    x, y = coords(N, N, L, L)
+    X, Y = x[None, :], y[:, None]
+    y0, y1 = window[0] * L, window[1] * L
+    w = 1.0 - _smooth_step((np.abs(Y) - y0) / (y1 - y0))
+    h = np.ones((N, N))
+    vx = np.zeros((N, N))
+    vy = np.zeros((N, N))
+    th = math.radians(theta_deg)
+    for t in (th, -th):
+        nx, ny = math.cos(t), math.sin(t)
+        f = sol.fields(nx * X + ny * Y)
+        h += w * (f["h"] - 1.0)
+        vx += w * f["v"] * nx
+        vy += w * f["v"] * ny
+    return State(N, N, L, L, h=h, vx=vx, vy=vy, sigma=np.zeros((N, N)),
+                 meta=dict(kind="crossing_solitons", a=a, theta_deg=theta_deg, window=window))
+
+
+def random_band(Nx, Ny, Lx, Ly, seed=0, kx_max=60, ky_max=6, amp=0.2, mean=0.0) -> np.ndarray:
+    """Seeded band-limited real field with separate mode limits per axis:
+    mean + Re sum_{0 <= mx <= kx_max, |my| <= ky_max} c_m e^{i(mx X + my Y)},
+    c_m = amp (p + i q) / (1 + mx^2 + my^2), p, q ~ N(0, 1), X, Y the
+    coordinates scaled to [0, 2 pi). The sum is formed as the matrix product
+    E_y C E_x^T of the coefficient matrix with the two exponential factors,
+    so wide bands stay cheap on long axes."""
+    rng = np.random.default_rng(seed)
+    x, y = coords(Nx, Ny, Lx, Ly)
+    X = 2 * math.pi * (x + 0.5 * Lx) / Lx
+    Y = 2 * math.pi * (y + 0.5 * Ly) / Ly
+    mxs = np.arange(0, min(kx_max, Nx // 2 - 1) + 1)
+    kyl = min(ky_max, Ny // 2 - 1)
+    mys = np.arange(-kyl, kyl + 1)
+    MY, MX = np.meshgrid(mys, mxs, indexing="ij")
+    C = amp * (rng.standard_normal(MX.shape) + 1j * rng.standard_normal(MX.shape)) / (1.0 + MX ** 2 + MY ** 2)
+    C[(MX == 0) & (MY <= 0)] = 0.0
+    Ey = np.exp(1j * np.outer(Y, mys))
+    Ex = np.exp(1j * np.outer(X, mxs))
+    return float(mean) + np.real(Ey @ C @ Ex.T)
+
+
+def random_band_state(Nx, Ny, Lx, Ly, seed=0, kx_max=60, ky_max=6, h_amp=0.15, v_amp=0.1) -> State:
+    """Seeded smooth positive depth and velocity from random_band fields."""
+    f = lambda s, a, m=0.0: random_band(Nx, Ny, Lx, Ly, seed=seed + s, kx_max=kx_max, ky_max=ky_max, amp=a, mean=m)
+    return State(Nx, Ny, Lx, Ly, h=f(0, h_amp, 1.0), vx=f(1, v_amp), vy=f(2, v_amp), sigma=f(3, v_amp),
+                 meta=dict(kind="random_band_state", seed=seed))

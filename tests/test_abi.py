@@ -56,7 +56,7 @@ def test_default_options(lib):
         (0, 20, 1000, 1e-10, 0, 1e-12, 0, 0)
 
 
-@pytest.mark.parametrize("Nx,Ny", [(12, 16), (16, 4), (4096, 16), (0, 8), (16, -8)])
+@pytest.mark.parametrize("Nx,Ny", [(12, 16), (16, 4), (8192, 16), (16, 8192), (0, 8), (16, -8)])
 def test_create_rejects_bad_sizes(lib, Nx, Ny):
     h = ctypes.c_void_p()
     st = lib.sgn_create(Nx, Ny, 1.0, 1.0, 1.0, None, ctypes.byref(h))
