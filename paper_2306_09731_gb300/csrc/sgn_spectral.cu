@@ -508,8 +508,13 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // and forward 327 against 386 us; double-float inverse 158 against 182 us,
 // forward 140 against 172 us).
 // At 4096 points (LN = 12) one column takes 512 threads in every type.
-template <typename T, bool INV, int LN = 0>
+// FP32 passes with at most two inputs (NIN <= 2): 1024 threads, four columns
+// per block at Ny = 2048, so that a warp's access covers 8 rows x 32 bytes (8
+// cache lines) instead of 16 rows x 16 bytes (16 lines): the strided column
+// accesses cost L1 wavefronts per line touched.
+template <typename T, bool INV, int LN = 0, int NIN = 0>
 constexpr int ypass_threads() {
+  if (sizeof(T) == 4 && NIN >= 1 && NIN <= 2) return 1024;
   return (sizeof(T) == 4 || LN == 12) ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
 }
 
@@ -517,19 +522,91 @@ constexpr int ypass_threads() {
 // columns then follows from the block size the launcher uses.
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-template <typename T, bool INV, int LN>
+template <typename T, bool INV, int LN, int NIN>
 constexpr int ypass_lc() {
-  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV, LN>()) - (LN - 3), 0, 6);
+  return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV, LN, NIN>()) - (LN - 3), 0, 6);
 }
 
-template <typename T, bool INV, int NIN, class Epi, typename S, int LN>
+// Input staging of a y-pass (compile-time mask FL). The inputs are column
+// segments read at a stride of one row, so a thread's loads wait out the full
+// memory latency and, with one transform per input, the next input's loads
+// only start after the previous transform:
+//   yf_pf(i), i >= 1: input i is copied to shared memory by cp.async when the
+//     block starts, so its loads overlap the loads and transforms of the
+//     inputs before it;
+//   yf_dup(i), i >= 1: input i is i ky times input i-1 (same source, deriv 0
+//     there): the raw values of input i-1 are kept in shared memory and input
+//     i is formed from them instead of being read again.
+// Each thread stages only the elements it reads back itself (slot s of thread
+// tid at s * blockDim + tid), so no barrier orders the copies.
+__host__ __device__ constexpr int yf_pf(int i) { return 1 << i; }
+__host__ __device__ constexpr int yf_dup(int i) { return 1 << (8 + i); }
+
+// staging bytes per thread of the inputs before input `upto`
+template <typename T, typename S, int FL>
+__host__ __device__ constexpr int ystage_bytes(int upto) {
+  int b = 0;
+  for (int j = 1; j < upto; ++j) {
+    if (FL & yf_pf(j)) b += 8 * (int)sizeof(cpx<S>);
+    else if (FL & yf_dup(j)) b += 8 * (int)sizeof(cpx<T>);
+  }
+  return b;
+}
+
+// byte offset of the staging area: the transform buffers, rounded up to 16
+__host__ __device__ constexpr size_t ystage_offset(int lN, int lC, int esize) {
+  return ((((size_t)smem_elems(1 << lN) << lC) * (size_t)esize) + 15) & ~(size_t)15;
+}
+
+// staging masks of the fused passes (see ypass_body): the matvec y-inverse
+// prefetches its second input (sigma_hat again, for i ky sigma_hat: keeping the
+// first input's raw values in shared memory instead spilled 244 bytes at the
+// 64 registers of the FP32 pass); the y-forward passes stage every input after
+// the first; the RHS y-inverse forms i ky sigma_hat from a staged copy of
+// sigma_hat and, in FP64 and double-float below 4096 points, also stages v_y
+// and sigma_hat (the FP32 one measured 117 against 107 us with them staged:
+// 196 KB of shared memory leave little L1; FP64 at 4096 has no room for them)
+constexpr int FL_MV_INV = yf_pf(1);
+constexpr int FL_MV_FWD = yf_pf(1);
+constexpr int FL_RHS_FWD = yf_pf(1) | yf_pf(2);
+template <typename T, int LN>
+constexpr int fl_rhs_inv() {
+  return (sizeof(T) == 4 || LN == 12) ? yf_dup(3) : (yf_pf(1) | yf_pf(2) | yf_dup(3));
+}
+
+template <typename E>
+__device__ __forceinline__ void cp_async_elem(E* dst, const E* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(E) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+// shared-memory read that stays where it is written (FP32 pairs by an asm
+// load, so that the compiler does not schedule it early and hold the value
+// across the transform before it)
+template <typename T>
+__device__ __forceinline__ cpx<T> lds_fenced(const cpx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    float a, b;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(a), "=f"(b) : "r"(d) : "memory");
+    return mk((T)a, (T)b);
+  } else {
+    return *p;
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T, bool INV, int NIN, class Epi, typename S, int LN, int FL>
 __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
                                            const YIn<T, NIN, S>& in, const Epi& epi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
   const int lN = LN > 0 ? LN : G.lNy;
   const int T_ = 1 << (lN - 3);
-  constexpr int LCc = ypass_lc<T, INV, LN>();
+  constexpr int LCc = ypass_lc<T, INV, LN, NIN>();
   const int lC = LCc >= 0 ? LCc : __ffs(blockDim.x >> (lN - 3)) - 1;
   const int c = threadIdx.x & ((1 << lC) - 1);
   const int t = threadIdx.x >> lC;
@@ -538,42 +615,85 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
   if (!valid) col = G.Nxh - 1;
   cpx<T> r[NIN][8];
   const size_t soff = in.sel ? (size_t)(*in.sel) * in.sel_stride : 0;
+  // staging area: after the C transform buffers of the exchanges
+  unsigned char* stage = smraw + ystage_offset(lN, lC, (int)sizeof(cpx<T>));
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  if constexpr (FL != 0) {
+#pragma unroll
+    for (int i = 1; i < NIN; ++i) {
+      if (FL & yf_pf(i)) {
+        cpx<S>* st = reinterpret_cast<cpx<S>*>(stage + (size_t)nthr * ystage_bytes<T, S, FL>(i));
+        const cpx<S>* src = in.src[i] + soff;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) cp_async_elem(st + s * nthr + tid, src + (size_t)(t + s * T_) * G.ldS + col);
+      }
+    }
+    cp_async_commit();
+  }
+  bool waited = false;
 #pragma unroll
   for (int i = 0; i < NIN; ++i) {
-    const cpx<S>* src = in.src[i] + soff;
+    if (i > 0 && (FL & yf_pf(i))) {
+      if (!waited) cp_async_wait_all();
+      waited = true;
+      const cpx<S>* st = reinterpret_cast<const cpx<S>*>(stage + (size_t)nthr * ystage_bytes<T, S, FL>(i));
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int row = t + s * T_;
-      cpx<T> z = ld_as<T, S>(src + (size_t)row * G.ldS + col);
-      if (in.deriv[i]) z = mul_ik(z, ldr(ky + row));
-      r[i][s] = z;
+      for (int s = 0; s < 8; ++s) {
+        cpx<T> z = ld_as<T, S>(st + s * nthr + tid);
+        if (in.deriv[i]) z = mul_ik(z, ldr(ky + t + s * T_));
+        r[i][s] = z;
+      }
+    } else if (i > 0 && (FL & yf_dup(i))) {
+      const cpx<T>* st = reinterpret_cast<const cpx<T>*>(stage + (size_t)nthr * ystage_bytes<T, S, FL>(i));
+#pragma unroll
+      for (int s = 0; s < 8; ++s) r[i][s] = mul_ik(lds_fenced(st + s * nthr + tid), ldr(ky + t + s * T_));
+    } else {
+      const cpx<S>* src = in.src[i] + soff;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int row = t + s * T_;
+        cpx<T> z = ld_as<T, S>(src + (size_t)row * G.ldS + col);
+        if (in.deriv[i]) z = mul_ik(z, ldr(ky + row));
+        r[i][s] = z;
+      }
+    }
+    if (i + 1 < NIN && (FL & yf_dup(i + 1))) {
+      cpx<T>* st = reinterpret_cast<cpx<T>*>(stage + (size_t)nthr * ystage_bytes<T, S, FL>(i + 1));
+#pragma unroll
+      for (int s = 0; s < 8; ++s) st[s * nthr + tid] = r[i][s];
+      // the copy is read back after the transform: keep the compiler from
+      // carrying the raw values in registers across it instead
+      asm volatile("" ::: "memory");
     }
     fft_regs<INV>(r[i], smb + c, tw, t, lN, lC);
   }
   epi(r, col, t, T_, valid, G, ky);
 }
 
-template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads<T, INV, LN>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw,
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0>
+__global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>()) k_ypass(Geom G, const cpx<T>* __restrict__ tw,
                                                                    const T* __restrict__ ky, YIn<T, NIN, S> in,
                                                                    Epi epi) {
-  ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
+  ypass_body<T, INV, NIN, Epi, S, LN, FL>(G, tw, ky, in, epi);
 }
-// FP32 passes with at most two transforms per thread: two 512-thread blocks
-// per SM (64 registers; measured: matvec y-forward 34 against 39 us at
-// 2048^2). The other passes keep the compiler's register choice.
-template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
-__global__ void __launch_bounds__(ypass_threads<T, INV, LN>(), 2) k_ypass_o2(Geom G, const cpx<T>* __restrict__ tw,
+// FP32 passes with at most two transforms per thread: 64 registers, 32 warps
+// per SM (measured with two 512-thread blocks: matvec y-forward 34 against
+// 39 us at 2048^2 with the compiler's choice). The other passes keep the
+// compiler's register choice.
+template <typename T, bool INV, int NIN>
+constexpr int ypass_o2_blocks() { return ypass_threads<T, INV, 0, NIN>() >= 1024 ? 1 : 2; }
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0>
+__global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>(), ypass_o2_blocks<T, INV, NIN>()) k_ypass_o2(Geom G, const cpx<T>* __restrict__ tw,
                                                                         const T* __restrict__ ky,
                                                                         YIn<T, NIN, S> in, Epi epi) {
-  ypass_body<T, INV, NIN, Epi, S, LN>(G, tw, ky, in, epi);
+  ypass_body<T, INV, NIN, Epi, S, LN, FL>(G, tw, ky, in, epi);
 }
-template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0>
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0>
 constexpr auto ypass_fn() {
   if constexpr (sizeof(T) == 4 && NIN <= 2)
-    return &k_ypass_o2<T, INV, NIN, Epi, S, LN>;
+    return &k_ypass_o2<T, INV, NIN, Epi, S, LN, FL>;
   else
-    return &k_ypass<T, INV, NIN, Epi, S, LN>;
+    return &k_ypass<T, INV, NIN, Epi, S, LN, FL>;
 }
 
 template <typename T, int NIN>
@@ -785,19 +905,21 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
   grid = dim3((G.Ny / 2 + P - 1) / P, nf);
   smem = (size_t)P * smem_elems(G.Nx) * sizeof(cpx<T>);
 }
-template <typename T, bool INV>
-static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem) {
+template <typename T, bool INV, int NIN>
+static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int stage_per_thread = 0) {
   const int Tn = G.Ny >> 3;
-  const int tpb = G.lNy == 12 ? ypass_threads<T, INV, 12>() : ypass_threads<T, INV>();
+  const int tpb = G.lNy == 12 ? ypass_threads<T, INV, 12, NIN>() : ypass_threads<T, INV, 0, NIN>();
   int C = tpb / Tn;
   if (C < 1) C = 1;
   if (C > 64) C = 64;
   block = dim3(Tn * C);
   grid = dim3((G.Nxh + C - 1) / C);
-  smem = (size_t)C * smem_elems(G.Ny) * sizeof(cpx<T>);
+  int lC = 0;
+  while ((1 << lC) < C) ++lC;
+  smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + (size_t)block.x * stage_per_thread;
 }
 
-static constexpr int kMaxDynSmem = 160 * 1024;
+static constexpr int kMaxDynSmem = 227 * 1024;
 
 template <typename T>
 static void set_smem(const void* fn) {
@@ -808,10 +930,10 @@ template <typename T, int L>
 static void set_attrs_ln() {
   set_smem<T>((const void*)k_mv_x<T, L>);
   set_smem<T>((const void*)k_rhs_x<T, L>);
-  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, L>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L>());
-  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L>());
-  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L>());
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, L, FL_MV_INV>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L, FL_MV_FWD>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L, fl_rhs_inv<T, L>()>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L, FL_RHS_FWD>());
   if constexpr (L == 12) {
     set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, T, L>());
     set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStore<T, 1>, T, L>());
@@ -835,11 +957,11 @@ void init_kernel_attributes() {
   set_smem<T>((const void*)k_rhs_x<T>);
   set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStore<T, 1>>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>>());
-  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>>());
-  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>>());
-  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>>());
-  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double>());
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, 0, FL_MV_INV>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, T, 0, fl_rhs_inv<T, 0>()>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, 0, FL_MV_FWD>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, FL_RHS_FWD>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 0, fl_rhs_inv<T, 0>()>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double>());
   cudaGetLastError();
 }
@@ -885,9 +1007,9 @@ cudaError_t launch_y_fft(const Geom& G, const Tables<T>& tb, bool inverse, const
   dim3 grid, block;
   size_t smem;
   if (inverse)
-    y_config<T, true>(G, grid, block, smem);
+    y_config<T, true, 1>(G, grid, block, smem);
   else
-    y_config<T, false>(G, grid, block, smem);
+    y_config<T, false, 1>(G, grid, block, smem);
   for (int i = 0; i < nf; ++i) {
     YIn<T, 1> yi{};
     yi.src[0] = in[i];
@@ -935,8 +1057,9 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
                              size_t jstride) {
   dim3 grid, block;
   size_t smem;
-  // y-inverse of sigma_hat and i ky sigma_hat
-  y_config<T, true>(G, grid, block, smem);
+  // y-inverse of sigma_hat and i ky sigma_hat (read once, the second formed
+  // from the staged copy)
+  y_config<T, true, 2>(G, grid, block, smem, ystage_bytes<T, S, FL_MV_INV>(2));
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2, S> yi{};
@@ -950,7 +1073,8 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     ep.dst[0] = tmp[0];
     ep.dst[1] = tmp[1];
     ex.begin(PK_MV_YINV);
-    ypass_fn<T, true, 2, EpiStore<T, 2>, S, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, true, 2, EpiStore<T, 2>, S, L, FL_MV_INV>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi,
+                                                                                        ep);
     ex.end();
   });
   x_config<T>(G, grid, block, smem, 1);
@@ -960,7 +1084,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
     ex.end();
   });
-  y_config<T, false>(G, grid, block, smem);
+  y_config<T, false, 2>(G, grid, block, smem, ystage_bytes<T, T, FL_MV_FWD>(2));
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2> yi{};
@@ -968,7 +1092,8 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     yi.src[1] = tmp[1];
     EpiMatvec<T, S> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
     ex.begin(PK_MV_YFWD);
-    ypass_fn<T, false, 2, EpiMatvec<T, S>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, false, 2, EpiMatvec<T, S>, T, L, FL_MV_FWD>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi,
+                                                                                          ep);
     ex.end();
   });
   return cudaGetLastError();
@@ -987,7 +1112,7 @@ template <typename T>
 cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>* in, cpx<T>* out, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  y_config<T, true>(G, grid, block, smem);
+  y_config<T, true, 1>(G, grid, block, smem);
   YIn<T, 1, double> yi{};
   yi.src[0] = in;
   EpiStore<T, 1> ep{};
@@ -1006,12 +1131,12 @@ void init_kernel_attributes_df() {
   typedef dfl T;
   set_smem<T>((const void*)k_coef_x<T>);
   set_smem<T>((const void*)k_mv_x<T>);
-  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>>());
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 0, FL_MV_INV>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 0, FL_MV_FWD>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double>());
   set_smem<T>((const void*)k_mv_x<T, 12>);
-  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12>());
+  set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12, FL_MV_INV>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12, FL_MV_FWD>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double, 12>());
   cudaGetLastError();
 }
@@ -1022,9 +1147,10 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                        cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  y_config<T, true>(G, grid, block, smem);
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
+    constexpr int FL = fl_rhs_inv<T, L>();
+    y_config<T, true, 4>(G, grid, block, smem, ystage_bytes<T, S, FL>(4));
     YIn<T, 4, S> yi{};
     yi.src[0] = U[1];
     yi.src[1] = U[2];
@@ -1034,7 +1160,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     EpiStore<T, 4> ep{};
     for (int i = 0; i < 4; ++i) ep.dst[i] = tmp[i];
     ex.begin(PK_RHS_YINV);
-    ypass_fn<T, true, 4, EpiStore<T, 4>, S, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, true, 4, EpiStore<T, 4>, S, L, FL>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   // each block reads only its own row pair before writing it, so the outputs
@@ -1047,7 +1173,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                                                (T)rk.g, tmp[0], tmp[1], tmp[2]);
     ex.end();
   });
-  y_config<T, false>(G, grid, block, smem);
+  y_config<T, false, 3>(G, grid, block, smem, ystage_bytes<T, T, FL_RHS_FWD>(3));
   dispatch_ln<T>(G.lNy, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 3> yi{};
@@ -1061,7 +1187,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     ep.kx = tb.kx;
     ep.dealias = rk.dealias;
     ex.begin(PK_RHS_YFWD);
-    ypass_fn<T, false, 3, EpiK<T>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ypass_fn<T, false, 3, EpiK<T>, T, L, FL_RHS_FWD>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
     ex.end();
   });
   {
