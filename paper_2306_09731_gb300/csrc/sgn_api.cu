@@ -112,6 +112,9 @@ struct sgn_ctx {
   DiagDev* diag_host = nullptr;  // pinned
   std::vector<cudaGraph_t> sweep_bodies, step_bodies;  // owned by their conditional nodes
   bool trace = false;  // SGN_TRACE=1: one stderr line per mixed-precision sweep
+  // tensor maps of the FP32 matvec y-passes (precisions 1, 2); SGN_TMA=0
+  // loads their inputs with plain and cp.async loads instead
+  MvTma mvt{};
   std::vector<void*> allocs;
   std::string err;
   sgn_stats stats{};
@@ -172,6 +175,8 @@ void cos_sin_2pi(long k, long n, double* c, double* s) {
   }
 }
 
+// Every device buffer starts zeroed, so the padding column of the spectra is
+// zero in every buffer that no pass writes there.
 template <typename P>
 P* dalloc(sgn_ctx* ctx, size_t count) {
   void* p = nullptr;
@@ -182,6 +187,12 @@ P* dalloc(sgn_ctx* ctx, size_t count) {
     throw Fail{SGN_ENOMEM};
   }
   ctx->allocs.push_back(p);
+  e = cudaMemset(p, 0, count * sizeof(P));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = std::string("cudaMemset: ") + cudaGetErrorString(e);
+    throw Fail{SGN_ECUDA};
+  }
   return static_cast<P*>(p);
 }
 
@@ -351,6 +362,10 @@ void check_flags(sgn_ctx* ctx, int flags) {
     ctx->err = "cavitation: h <= 0 somewhere";
     throw Fail{SGN_ECAVITATION};
   }
+  if (flags & FLAG_WAIT) {
+    ctx->err = "a y-pass stopped waiting for its tensor copies (bounded wait ran out)";
+    throw Fail{SGN_ECUDA};
+  }
 }
 
 // coefficient fields from the spectral depth h_hat
@@ -375,7 +390,7 @@ void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, c
   const Geom& G = ctx->G;
   const size_t vs = G.nspec();
   const int nv = j + 1;
-  CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx)));
+  CK(launch_matvec<T>(G, tb, V + (size_t)j * vs, cr, cc, w, tmp, true, EX(ctx), nullptr, 0, &ctx->mvt));
   const int* gate = &ctx->gst->reorth;
   unsigned* cnt = ctx->counters;
   // FP64 Arnoldi (the plain path and nothing else) reorthogonalises by the DGKS
@@ -523,6 +538,7 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
     int k = 0;
     for (int j = 0; j < m; ++j) {
       arnoldi_step<float>(ctx, ctx->tb32, ctx->cr32, ctx->cc32, V, ctx->w32, ctx->tmp32, j);
+      check_flags(ctx, ctx->rb_host->flags);
       ++its;
       res_in = ctx->rb_host->res;
       const double hnext = ctx->rb_host->hnext;
@@ -783,7 +799,7 @@ void graph_arnoldi(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, 
   const int* gate = &ctx->gst->reorth;
   unsigned* cnt = ctx->counters;
   const bool dgks = sizeof(T) == 8;
-  CK(launch_matvec<T>(G, tb, V, cr, cc, w, tmp, true, EX(ctx), jd, vs));
+  CK(launch_matvec<T>(G, tb, V, cr, cc, w, tmp, true, EX(ctx), jd, vs, &ctx->mvt));
   CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx), jd));
   CK(launch_cgs_update<T>(G, V, vs, m, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, 0, dgks ? 1 : 3, cnt + 1,
                           ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl));
@@ -1086,7 +1102,10 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   G.lNx = ilog2(Nx);
   G.lNy = ilog2(Ny);
   G.Nxh = Nx / 2 + 1;
-  G.ldS = G.Nxh;
+  // rows padded to an even count of entries: 16-byte row strides for the
+  // FP32 spectra, as the tensor copies of the y-passes require (the padding
+  // column is zero in every spectrum and has Parseval weight 0)
+  G.ldS = G.Nxh + (G.Nxh & 1);
   G.Lx = Lx;
   G.Ly = Ly;
   try {
@@ -1135,6 +1154,11 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->flags = dalloc<int>(ctx, 1);
     ctx->counters = dalloc<unsigned>(ctx, 8);
     CK(cudaMemset(ctx->counters, 0, 8 * sizeof(unsigned)));
+    if (o.precision >= 1) {
+      const char* tv = getenv("SGN_TMA");
+      if (!(tv && tv[0] == '0'))
+        make_mv_tma(G, ctx->V32, o.restart + 1, ctx->tmp32[0], ctx->tmp32[1], ctx->flags, &ctx->mvt);
+    }
     CK(cudaMallocHost((void**)&ctx->rb_host, sizeof(GmresReadback)));
     CK(cudaMallocHost((void**)&ctx->inv_host, 4 * sizeof(double)));
     CK(cudaMemset(ctx->flags, 0, sizeof(int)));

@@ -1,5 +1,6 @@
 // sgn_internal.h - host-side interface between the C-ABI layer and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -24,8 +25,28 @@ struct Geom {
   __host__ __device__ size_t nspec() const { return (size_t)Ny * ldS; }
 };
 
-// Device flags raised by the coefficient pass (OR-ed bits).
-enum : int { FLAG_CAVITATION = 1, FLAG_NONFINITE = 2 };
+// Device flags raised by the coefficient pass (OR-ed bits); FLAG_WAIT: a
+// y-pass gave up waiting for its tensor copies (a bounded wait ran out).
+enum : int { FLAG_CAVITATION = 1, FLAG_NONFINITE = 2, FLAG_WAIT = 4 };
+
+// Tensor maps of the FP32 matvec y-passes (built when a handle is made):
+// v: the Krylov basis as a [nvec][Ny][2 ldS] FP32 tensor, t0, t1: the two
+// y-forward inputs as [1][Ny][2 ldS]; the boxes are [1][rows][2 C], C the
+// columns of one block. ok = 0: the passes load their inputs with plain and
+// cp.async loads instead.
+struct MvTma {
+  CUtensorMap v, t0, t1;
+  const void* vbase;
+  const void* t0base;
+  const void* t1base;
+  size_t vs;
+  int nvec;
+  int ok;
+  int* flags;
+};
+// Builds the maps for the basis V (nvec vectors) and tmp[0], tmp[1]; returns
+// false (ok = 0) if the driver's encoder is unavailable or refuses them.
+bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags, MvTma* out);
 
 // Epilogue modes of the RHS y-forward pass (the RK4 stage update, Section 3).
 enum RkMode : int {
@@ -225,10 +246,12 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
 // tmp: 4 spectra of scratch (S, Sy, C, By).
 // jsel (may be null): the input is sig + (*jsel) * jstride (graph mode: the
 // Arnoldi step index lives on the device)
+// tma (may be null; FP32): tensor maps of V and tmp[0..1]; used when sig lies
+// in V (sig = V + j vs, or V with jsel) and tmp is the maps' pair.
 template <typename T>
 cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
                           cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex,
-                          const int* jsel = nullptr, size_t jstride = 0);
+                          const int* jsel = nullptr, size_t jstride = 0, const MvTma* tma = nullptr);
 
 // the same with sigma_hat and w stored in S and the passes in T (the
 // double-float refinement matvec: T = dfl, S = double)

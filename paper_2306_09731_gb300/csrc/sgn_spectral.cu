@@ -597,11 +597,62 @@ __device__ __forceinline__ cpx<T> lds_fenced(const cpx<T>* p) {
   }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Tensor copies (TMA) of column tiles. yf_tma(i): input i arrives as one tile
+// of [Ny rows][C columns] copied by the tensor engine (boxes of up to 256 rows,
+// issued by one thread); its mbarrier completes on the tile's bytes. The FP32
+// matvec passes take their inputs this way: one thread's few bulk copies
+// replace 8 strided loads per thread and input, whose queue (LSU throttle) was
+// the first stall of those passes.
+__host__ __device__ constexpr int yf_tma(int i) { return 1 << (16 + i); }
+constexpr int kTmaMaxMaps = 2;
+struct YTma {
+  CUtensorMap map[kTmaMaxMaps];
+  int z[kTmaMaxMaps];  // coordinate along the vector dimension of each map
+  const int* zsel;     // may be null: map 0's z read from the device instead
+  int* flags;          // FLAG_WAIT when a wait runs out
+};
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait on phase 0 of bar: about a second at most (try_wait suspends
+// between polls). The block-wide vote keeps every thread on the same path.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
+  bool ok = false;
+  for (int it = 0; it < (1 << 20) && !ok; ++it) ok = mbar_try_wait(bar, 0);
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T, bool INV, int NIN, class Epi, typename S, int LN, int FL>
 __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
-                                           const YIn<T, NIN, S>& in, const Epi& epi) {
+                                           const YIn<T, NIN, S>& in, const Epi& epi,
+                                           const YTma* tm = nullptr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* smb = reinterpret_cast<cpx<T>*>(smraw);
   const int lN = LN > 0 ? LN : G.lNy;
@@ -618,6 +669,30 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
   // staging area: after the C transform buffers of the exchanges
   unsigned char* stage = smraw + ystage_offset(lN, lC, (int)sizeof(cpx<T>));
   const int nthr = blockDim.x, tid = threadIdx.x;
+  // tensor-copied tiles: [Ny][C] per map, 128-byte aligned in the shared window
+  constexpr int NMAP = ((FL & yf_tma(0)) ? 1 : 0) + ((NIN > 1 && (FL & yf_tma(1))) ? 1 : 0);
+  cpx<T>* tstage = nullptr;
+  __shared__ uint64_t tbar[NMAP > 0 ? NMAP : 1];
+  if constexpr (NMAP > 0) {
+    const unsigned sb = smem_u32(stage);
+    tstage = reinterpret_cast<cpx<T>*>(stage + (((sb + 127u) & ~127u) - sb));
+    if (tid == 0) {
+#pragma unroll
+      for (int m = 0; m < NMAP; ++m) mbar_init(&tbar[m], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int Ny = 1 << lN, C = 1 << lC, BR = Ny < 256 ? Ny : 256;
+#pragma unroll
+      for (int m = 0; m < NMAP; ++m) {
+        const int z = (m == 0 && tm->zsel) ? *tm->zsel : tm->z[m];
+        mbar_expect_tx(&tbar[m], (unsigned)(Ny * C * (int)sizeof(cpx<T>)));
+        for (int b = 0; b < Ny; b += BR)
+          tma_load_3d(tstage + ((size_t)m * Ny + b) * C, &tm->map[m], 2 * (int)(blockIdx.x << lC), b, z, &tbar[m]);
+      }
+    }
+  }
   if constexpr (FL != 0) {
 #pragma unroll
     for (int i = 1; i < NIN; ++i) {
@@ -633,6 +708,28 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
   bool waited = false;
 #pragma unroll
   for (int i = 0; i < NIN; ++i) {
+    if constexpr (NMAP > 0) {
+      if ((FL & yf_tma(i)) || (i > 0 && (FL & yf_dup(i)) && (FL & yf_tma(i - 1)))) {
+        const int m = (i > 0 && (FL & yf_tma(0)) && (FL & yf_tma(i))) ? 1 : 0;
+        const bool dup = !(FL & yf_tma(i));
+        if (!dup) {
+          if (!mbar_wait_bounded(&tbar[m])) {
+            if (tid == 0) atomicOr(tm->flags, FLAG_WAIT);
+            return;
+          }
+        }
+        const cpx<T>* st = tstage + (size_t)m * (1 << lN) * (1 << lC);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int row = t + s * T_;
+          cpx<T> z = st[(row << lC) + c];
+          if (in.deriv[i]) z = mul_ik(z, ldr(ky + row));
+          r[i][s] = z;
+        }
+        fft_regs<INV>(r[i], smb + c, tw, t, lN, lC);
+        continue;
+      }
+    }
     if (i > 0 && (FL & yf_pf(i))) {
       if (!waited) cp_async_wait_all();
       waited = true;
@@ -688,6 +785,16 @@ __global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>(), ypass_o2_blo
                                                                         YIn<T, NIN, S> in, Epi epi) {
   ypass_body<T, INV, NIN, Epi, S, LN, FL>(G, tw, ky, in, epi);
 }
+// FP32 passes whose inputs arrive by tensor copies (see yf_tma)
+template <typename T, bool INV, int NIN, class Epi, int LN, int FL>
+__global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>(), ypass_o2_blocks<T, INV, NIN>())
+    k_ypass_tma(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky, YIn<T, NIN, T> in,
+                const __grid_constant__ YTma tm, Epi epi) {
+  ypass_body<T, INV, NIN, Epi, T, LN, FL>(G, tw, ky, in, epi, &tm);
+}
+constexpr int FL_MV_INV_TMA = yf_tma(0) | yf_dup(1);
+constexpr int FL_MV_FWD_TMA = yf_tma(0) | yf_tma(1);
+
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0>
 constexpr auto ypass_fn() {
   if constexpr (sizeof(T) == 4 && NIN <= 2)
@@ -921,9 +1028,19 @@ static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
 
 static constexpr int kMaxDynSmem = 227 * 1024;
 
+// Dynamic shared memory limit of a kernel: the device's opt-in maximum less
+// the kernel's static shared memory (the mbarriers of the tensor-copy passes),
+// capped at 227 KB.
 template <typename T>
 static void set_smem(const void* fn) {
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  int dev = 0, optin = kMaxDynSmem;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, fn);
+  int lim = optin - (int)fa.sharedSizeBytes;
+  if (lim > kMaxDynSmem) lim = kMaxDynSmem;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <typename T, int L>
@@ -932,6 +1049,10 @@ static void set_attrs_ln() {
   set_smem<T>((const void*)k_rhs_x<T, L>);
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, L, FL_MV_INV>());
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L, FL_MV_FWD>());
+  if constexpr (sizeof(T) == 4) {
+    set_smem<T>((const void*)k_ypass_tma<T, true, 2, EpiStore<T, 2>, L, FL_MV_INV_TMA>);
+    set_smem<T>((const void*)k_ypass_tma<T, false, 2, EpiMatvec<T, T>, L, FL_MV_FWD_TMA>);
+  }
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L, fl_rhs_inv<T, L>()>());
   set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L, FL_RHS_FWD>());
   if constexpr (L == 12) {
@@ -958,6 +1079,10 @@ void init_kernel_attributes() {
   set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStore<T, 1>>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>>());
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, 0, FL_MV_INV>());
+  if constexpr (sizeof(T) == 4) {
+    set_smem<T>((const void*)k_ypass_tma<T, true, 2, EpiStore<T, 2>, 0, FL_MV_INV_TMA>);
+    set_smem<T>((const void*)k_ypass_tma<T, false, 2, EpiMatvec<T, T>, 0, FL_MV_FWD_TMA>);
+  }
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, T, 0, fl_rhs_inv<T, 0>()>());
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, 0, FL_MV_FWD>());
   set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, FL_RHS_FWD>());
@@ -1051,6 +1176,128 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
 }
 
 // S: storage type of sigma_hat and w; T: arithmetic of the passes
+// Columns per block of the FP32 two-input y-passes (both directions).
+static inline int mv_y_columns(const Geom& G) {
+  dim3 grid, block;
+  size_t smem;
+  y_config<float, false, 2>(G, grid, block, smem);
+  return (int)block.x / (G.Ny >> 3);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// [nvec][Ny][2 ldS] FP32 tensor at base, box [1][min(Ny, 256)][2 C]
+static bool encode_spectra(EncodeTiledFn enc, const Geom& G, const void* base, int nvec, int C, CUtensorMap* m) {
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * G.ldS, (cuuint64_t)G.Ny, (cuuint64_t)nvec};
+  const cuuint64_t strides[2] = {(cuuint64_t)G.ldS * 8, (cuuint64_t)G.ldS * 8 * G.Ny};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * C), (cuuint32_t)(G.Ny < 256 ? G.Ny : 256), 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags, MvTma* out) {
+  *out = MvTma{};
+  // row strides must be multiples of 16 bytes, and a box at most 256 wide
+  const int C = mv_y_columns(G);
+  if ((G.ldS * 8) % 16 != 0 || 2 * C > 256) return false;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
+  if (!encode_spectra(enc, G, V, nvec, C, &out->v) || !encode_spectra(enc, G, t0, 1, C, &out->t0) ||
+      !encode_spectra(enc, G, t1, 1, C, &out->t1))
+    return false;
+  out->vbase = V;
+  out->t0base = t0;
+  out->t1base = t1;
+  out->vs = G.nspec();
+  out->nvec = nvec;
+  out->flags = flags;
+  out->ok = 1;
+  return true;
+}
+
+// The FP32 matvec with tensor-copied y-pass inputs; false if it does not apply.
+template <typename T>
+static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc, cpx<T>* w,
+                       cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel, const MvTma* tma) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    if (!tma || !tma->ok || tmp[0] != tma->t0base || tmp[1] != tma->t1base) return false;
+    long long zj = 0;
+    if (!jsel) {
+      const long long off = (const char*)sig - (const char*)tma->vbase;
+      const long long vb = (long long)(tma->vs * sizeof(cpx<T>));
+      if (off < 0 || off % vb != 0 || off / vb >= tma->nvec) return false;
+      zj = off / vb;
+    } else if (sig != tma->vbase) {
+      return false;
+    }
+    dim3 grid, block;
+    size_t smem;
+    y_config<T, true, 2>(G, grid, block, smem);
+    const int C = (int)block.x / (G.Ny >> 3);
+    int lC = 0;
+    while ((1 << lC) < C) ++lC;
+    const size_t tile = (size_t)G.Ny * C * sizeof(cpx<T>);
+    YTma ti{};
+    ti.map[0] = tma->v;
+    ti.z[0] = (int)zj;
+    ti.zsel = jsel;
+    ti.flags = tma->flags;
+    smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + 128 + tile;
+    dispatch_ln<T>(G.lNy, [&](auto ln) {
+      constexpr int L = decltype(ln)::value;
+      YIn<T, 2> yi{};
+      yi.src[0] = sig;
+      yi.src[1] = sig;
+      yi.deriv[1] = 1;
+      EpiStore<T, 2> ep{};
+      ep.dst[0] = tmp[0];
+      ep.dst[1] = tmp[1];
+      ex.begin(PK_MV_YINV);
+      k_ypass_tma<T, true, 2, EpiStore<T, 2>, L, FL_MV_INV_TMA><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi,
+                                                                                           ti, ep);
+      ex.end();
+    });
+    x_config<T>(G, grid, block, smem, 1);
+    dispatch_ln<T>(G.lNx, [&](auto ln) {
+      constexpr int L = decltype(ln)::value;
+      ex.begin(PK_MV_X);
+      k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
+      ex.end();
+    });
+    y_config<T, false, 2>(G, grid, block, smem);
+    YTma tf{};
+    tf.map[0] = tma->t0;
+    tf.map[1] = tma->t1;
+    tf.flags = tma->flags;
+    smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + 128 + 2 * tile;
+    dispatch_ln<T>(G.lNy, [&](auto ln) {
+      constexpr int L = decltype(ln)::value;
+      YIn<T, 2> yi{};
+      yi.src[0] = tmp[0];
+      yi.src[1] = tmp[1];
+      EpiMatvec<T, T> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
+      ex.begin(PK_MV_YFWD);
+      k_ypass_tma<T, false, 2, EpiMatvec<T, T>, L, FL_MV_FWD_TMA><<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi,
+                                                                                              tf, ep);
+      ex.end();
+    });
+    return true;
+  }
+}
+
 template <typename T, typename S>
 cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* sig, const T* cr, const T* cc,
                              cpx<S>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
@@ -1102,7 +1349,8 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
 template <typename T>
 cudaError_t launch_matvec(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, const T* cr, const T* cc,
                           cpx<T>* w, cpx<T>* const* tmp, bool precond, const Exec& ex, const int* jsel,
-                          size_t jstride) {
+                          size_t jstride, const MvTma* tma) {
+  if (matvec_tma<T>(G, tb, sig, cr, cc, w, tmp, precond, ex, jsel, tma)) return cudaGetLastError();
   return launch_matvec_io<T, T>(G, tb, sig, cr, cc, w, tmp, precond, ex, jsel, jstride);
 }
 
@@ -1270,7 +1518,8 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
   template cudaError_t launch_coef_phys<T>(const Geom&, const double*, T*, T*, T*, int*, const CoefCopy&,   \
                                            const Exec&);                                                    \
   template cudaError_t launch_matvec<T>(const Geom&, const Tables<T>&, const cpx<T>*, const T*, const T*,    \
-                                        cpx<T>*, cpx<T>* const*, bool, const Exec&, const int*, size_t);    \
+                                        cpx<T>*, cpx<T>* const*, bool, const Exec&, const int*, size_t,     \
+                                        const MvTma*);                                                      \
   template cudaError_t launch_spec_div<T>(const Geom&, const Tables<T>&, const cpx<T>*, const cpx<T>*,      \
                                           cpx<T>*, const Exec&);                                            \
   template cudaError_t launch_precond<T>(const Geom&, const Tables<T>&, const cpx<T>*, cpx<T>*, double*,    \
@@ -1291,7 +1540,7 @@ template cudaError_t launch_coef_phys<dfl>(const Geom&, const double*, dfl*, dfl
                                            const Exec&);
 template cudaError_t launch_matvec<float>(const Geom&, const Tables<float>&, const cpx<float>*, const float*,
                                           const float*, cpx<float>*, cpx<float>* const*, bool, const Exec&,
-                                          const int*, size_t);
+                                          const int*, size_t, const MvTma*);
 template cudaError_t launch_rhs<double, double>(const Geom&, const Tables<double>&, const Tables<double>&,
                                                 cpx<double>* const*, const cpx<double>*, const double*,
                                                 const double*, cpx<double>* const*, cpx<double>* const*,
