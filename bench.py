@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start arms (and their training)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the built-in launch shapes (no sgn_autotune before the warm-up)")
     ap.add_argument("--no-crossing", action="store_true",
                     help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
@@ -256,6 +258,7 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
     s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
+    tuning = None if args.no_tune else s.autotune(5)
     if learned is not None:
         net, in_scale, out_scale, tau_power = learned
         s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
@@ -291,11 +294,12 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
                      "iters_per_stage": (st1["matvecs"] - st0["matvecs"]) / max(solves, 1),
                      "fp64_refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1)},
            "launches": prof["launches"] - l0,
-           "prof": None if graph else prof}
+           "prof": None if graph else prof,
+           "tuning": tuning}
     return s, f, rec
 
 
-def time_crossing(st, precision, guess, graph, learned, steps, warmup):
+def time_crossing(st, precision, guess, graph, learned, steps, warmup, tune=True):
     """Wall time of `steps` graph-mode RK4 steps (after `warmup`) of one GMRES
     start on a crossing-soliton state; CUDA events on the launching stream."""
     import torch
@@ -304,6 +308,8 @@ def time_crossing(st, precision, guess, graph, learned, steps, warmup):
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
     s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
+    if tune:
+        s.autotune(5)
     if learned is not None:
         net, in_scale, out_scale, tau_power = learned
         s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
@@ -453,20 +459,27 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_ensemble and world == 1 and args.path != "fp64" and not args.arms:
         from paper_2306_09731_gb300.ensemble import GRIDS, Ensemble, perturbed_members
         members = perturbed_members(64, seed=11)
-        E = Ensemble(members, precision=2, guess=2, graph=1)
-        E.step(2e-3, max(1, args.warmup))
-        torch.cuda.synchronize()
-        b0 = time.perf_counter()
-        E.step(2e-3, args.steps)
-        b1 = time.perf_counter()
-        E.step_one_by_one(2e-3, args.steps)
-        b2 = time.perf_counter()
-        E.close()
+        ens = {}
+        for tuned in ((False, True) if not args.no_tune else (False,)):
+            E = Ensemble(members, tune=tuned, precision=2, guess=2, graph=1)
+            E.step(2e-3, max(1, args.warmup))
+            torch.cuda.synchronize()
+            b0 = time.perf_counter()
+            E.step(2e-3, args.steps)
+            b1 = time.perf_counter()
+            E.step_one_by_one(2e-3, args.steps)
+            b2 = time.perf_counter()
+            ens[tuned] = (b1 - b0, b2 - b1, E.tuning[:3] if tuned else None)
+            E.close()
+        tb, to, tuning = ens[max(ens)]
         ensemble = {"members": len(members), "grids": [list(g[:2]) for g in GRIDS], "dt": 2e-3,
                     "steps": args.steps, "unit": "member-steps/s",
-                    "batch": len(members) * args.steps / (b1 - b0),
-                    "one_by_one": len(members) * args.steps / (b2 - b1),
-                    "speedup": (b2 - b1) / (b1 - b0)}
+                    "batch": len(members) * args.steps / tb,
+                    "one_by_one": len(members) * args.steps / to,
+                    "speedup": to / tb, "tuned": max(ens)}
+        if True in ens and False in ens:
+            ensemble["batch_builtin_shapes"] = len(members) * args.steps / ens[False][0]
+            ensemble["tuning_first_members"] = tuning
     # the paper's monitoring quantities (row f4) on the final state: wall time of
     # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
     hf = devfields[head_name]
@@ -500,7 +513,7 @@ def run_ours(args, rank, world, local_rank):
                                        ("extrapolated_learned", 2, "mixed_df_learned_graph")):
                 if lname is not None and lname not in nets:
                     continue
-                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, kwarm)
+                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, kwarm, not args.no_tune)
             crossing["theta"][f"{theta:g}"] = arms
             del cst
         for ln, (net, *_rest) in nets.items():
@@ -527,12 +540,17 @@ def run_ours(args, rank, world, local_rank):
                 + (", each RK4 step one CUDA graph with device-side GMRES control"
                    if head_name.endswith("_graph") else ", host-driven GMRES loop"),
         "arms": {k: dict({"value": v["value"], "ms_per_step": v["ms_per_step"], "precision": v["precision"],
-                          "graph": k.endswith("_graph"), "iters_per_stage": v["gmres"]["iters_per_stage"]},
+                          "graph": k.endswith("_graph"), "iters_per_stage": v["gmres"]["iters_per_stage"],
+                          "tuned_threads": ({ty: {ps: r["threads"] for ps, r in d.items()}
+                                             for ty, d in v["tuning"].items()} if v.get("tuning") else None)},
                          **({"avg_launch_ms": {c: v["prof"]["ms"][c] / v["prof"]["counts"][c]
                                                for c in v["prof"]["ms"] if v["prof"]["counts"][c]}}
                             if v["prof"] else {}))
                  for k, v in paths.items()},
         "gmres": head_rec["gmres"],
+        # launch shapes sgn_autotune picked for the headline handle, with the
+        # timed launch (us) of each pass in the built-in and the picked shape
+        "tuning": head_rec.get("tuning"),
         "time_share": {k: v / total_prof for k, v in prof["ms"].items() if v > 0},
         "gmres_share": gmres_ms / total_prof if total_prof else None,
         # kernel time summed from the event timers of the host-driven run: the

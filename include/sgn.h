@@ -246,6 +246,40 @@ typedef struct {
 sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const double* vy, sgn_diag* out);
 
 /* ------------------------------------------------------------------------
+ * Launch shapes of the transform passes. Every 2D transform of Section 3's
+ * spectral derivatives runs as an x-pass over row pairs and a y-pass over
+ * column tiles. How many columns one y-pass block transforms (row pairs for
+ * an x-pass) trades the width of its memory accesses against the number of
+ * blocks, and the best choice depends on the grid and the arithmetic: a 256^2
+ * grid has 129 columns, which the built-in 4096-point-sized tiles spread over
+ * a handful of blocks. sgn_autotune times every candidate shape of every pass
+ * the handle runs (threads per block: powers of two, whole columns or row
+ * pairs, up to each kernel's launch bound), `reps` launches each after one
+ * untimed launch, on the handle's own buffers, and keeps the fastest; later
+ * calls of the handle use those shapes. Shapes change no formula: FP64 and
+ * double-float results are bitwise identical to those of the built-in shapes;
+ * an FP32 pass whose picked shape differs from the built-in one runs the
+ * kernel compiled for runtime lengths, whose FP32 rounding may differ in the
+ * last bit (multiply-adds fused differently), and every solve still meets
+ * opt.tol.
+ * out (may be NULL): per arithmetic [type] (0 FP32, 1 FP64, 2 double-float)
+ * and pass [pass] (0 matvec y-inverse, 1 matvec y-forward, 2 RHS y-inverse,
+ * 3 RHS y-forward, 4 matvec x-pass, 5 RHS x-pass): threads per block chosen
+ * and built in, and the average launch time of each in microseconds; 0
+ * threads for the passes the handle's precision does not run.
+ * Overwrites the handle's scratch spectra (not the warm start of sigma);
+ * synchronises the handle's stream; call it between steps. reps in [1, 100],
+ * else SGN_EINVAL. */
+typedef struct {
+  int threads[3][6];
+  int default_threads[3][6];
+  float us_tuned[3][6];
+  float us_default[3][6];
+} sgn_tuning;
+
+sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out);
+
+/* ------------------------------------------------------------------------
  * Learned GMRES start (row f2). Section 3 starts GMRES from the last computed
  * sigma; a network (include/sgn_unet.h) can correct that start. At RK4 stages
  * 2 and 4 (the stages whose state moved by O(dt) since the fallback's), after

@@ -115,6 +115,7 @@ struct sgn_ctx {
   // tensor maps of the FP32 matvec y-passes (precisions 1, 2); SGN_TMA=0
   // loads their inputs with plain and cp.async loads instead
   MvTma mvt{};
+  Tune tune{};  // launch shapes picked by sgn_autotune (0: built-in)
   std::vector<void*> allocs;
   std::string err;
   sgn_stats stats{};
@@ -303,6 +304,7 @@ CoefCopy coef_copy(sgn_ctx* ctx) {
 Exec EX(sgn_ctx* ctx, int kind_override = -1) {
   Exec e{ctx->stream, &ctx->prof};
   e.kind_override = kind_override;
+  e.tune = &ctx->tune;
   return e;
 }
 
@@ -1157,7 +1159,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     if (o.precision >= 1) {
       const char* tv = getenv("SGN_TMA");
       if (!(tv && tv[0] == '0'))
-        make_mv_tma(G, ctx->V32, o.restart + 1, ctx->tmp32[0], ctx->tmp32[1], ctx->flags, &ctx->mvt);
+        make_mv_tma(G, ctx->V32, o.restart + 1, ctx->tmp32[0], ctx->tmp32[1], ctx->flags, &ctx->tune, &ctx->mvt);
     }
     CK(cudaMallocHost((void**)&ctx->rb_host, sizeof(GmresReadback)));
     CK(cudaMallocHost((void**)&ctx->inv_host, 4 * sizeof(double)));
@@ -1560,6 +1562,125 @@ sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const d
   out->dev_vx = d.dev_vx;
   out->max_vy = d.max_vy;
   for (int k = 0; k < 3; ++k) out->tail[k] = d.tail[k];
+  return SGN_OK;
+  API_END
+}
+
+// ------------------------------------------------------------- autotuning
+namespace {
+
+// One timed operation of the autotuner: the FP32, FP64 or double-float matvec
+// or the RHS, on the handle's scratch.
+void tune_run(sgn_ctx* ctx, int op) {
+  const Geom& G = ctx->G;
+  switch (op) {
+    case 0:  // FP32 matvec (inner solve of precisions 1, 2)
+      CK(launch_matvec<float>(G, ctx->tb32, ctx->V32, ctx->cr32, ctx->cc32, ctx->w32, ctx->tmp32, true, EX(ctx),
+                              nullptr, 0, &ctx->mvt));
+      break;
+    case 1:  // FP64 matvec of precision 0 (Arnoldi and residual)
+      CK(launch_matvec<double>(G, ctx->tb, ctx->V, ctx->cr, ctx->cc, ctx->w, ctx->tmp, true, EX(ctx)));
+      break;
+    case 2:  // refinement matvec of precisions 1 (FP64) and 2 (double-float)
+      refine_matvec(ctx, true, EX_REFINE(ctx));
+      break;
+    default: {  // one RHS evaluation (K into the RK accumulator, scratch between steps)
+      RkArgs rk{};
+      rk.mode = RK_STORE_K;
+      rk.g = ctx->g;
+      if (ctx->opt.precision >= 1)
+        CK((launch_rhs<float, double>(G, ctx->tb32, ctx->tb, ctx->Un, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32,
+                                      ctx->Un, ctx->Us, ctx->acc, nullptr, rk, EX(ctx))));
+      else
+        CK((launch_rhs<double, double>(G, ctx->tb, ctx->tb, ctx->Un, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
+                                       ctx->Us, ctx->acc, nullptr, rk, EX(ctx))));
+    }
+  }
+}
+
+// Average launch time (us) of profiling class cls over reps runs of op, after
+// one untimed run.
+double tune_time(sgn_ctx* ctx, int op, int cls, int reps) {
+  ctx->prof.on = false;
+  tune_run(ctx, op);
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.reset();
+  ctx->prof.on = true;
+  for (int r = 0; r < reps; ++r) tune_run(ctx, op);
+  ctx->prof.harvest();
+  ctx->prof.on = false;
+  const long long c = ctx->prof.cnt[cls];
+  return c > 0 ? 1e3 * ctx->prof.ms[cls] / (double)c : 1e30;
+}
+
+}  // namespace
+
+sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
+  API_BEGIN
+  if (reps < 1 || reps > 100) return fail(ctx, SGN_EINVAL, "sgn_autotune: reps must be in [1, 100]");
+  const Geom& G = ctx->G;
+  const int prec = ctx->opt.precision;
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_graph(ctx);  // a captured step keeps the shapes it was captured with
+  ctx->prof.init();
+  const bool was_on = ctx->prof.on;
+  const long long launches0 = ctx->prof.launches;
+  ctx->prof.harvest();
+  sgn_tuning res{};
+  // (op, arithmetic, the passes it times with their profiling classes)
+  struct Job {
+    int op, type;
+    int pass[3], cls[3];
+  };
+  std::vector<Job> jobs;
+  if (prec >= 1) {
+    jobs.push_back({0, TT_F32, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD}, {PK_MV_YINV, PK_MV_X, PK_MV_YFWD}});
+    jobs.push_back({2, prec == 2 ? TT_DFL : TT_F64, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD},
+                    {PK_REF_YINV, PK_REF_X, PK_REF_YFWD}});
+    jobs.push_back({3, TT_F32, {TP_RHS_YINV, TP_RHS_X, TP_RHS_YFWD}, {PK_RHS_YINV, PK_RHS_X, PK_RHS_YFWD}});
+  } else {
+    jobs.push_back({1, TT_F64, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD}, {PK_MV_YINV, PK_MV_X, PK_MV_YFWD}});
+    jobs.push_back({3, TT_F64, {TP_RHS_YINV, TP_RHS_X, TP_RHS_YFWD}, {PK_RHS_YINV, PK_RHS_X, PK_RHS_YFWD}});
+  }
+  auto remap = [&]() {
+    if (prec >= 1 && ctx->mvt.ok)
+      make_mv_tma(G, ctx->V32, ctx->opt.restart + 1, ctx->tmp32[0], ctx->tmp32[1], ctx->flags, &ctx->tune,
+                  &ctx->mvt);
+  };
+  for (const Job& jb : jobs) {
+    for (int k = 0; k < 3; ++k) {
+      const int ps = jb.pass[k], ty = jb.type;
+      const int def = pass_default_threads(G, ty, ps);
+      int cand[16];
+      const int nc = pass_candidates(G, ty, ps, cand, 16);
+      ctx->tune.tpb[ty][ps] = def;
+      remap();
+      const double t_def = tune_time(ctx, jb.op, jb.cls[k], reps);
+      int best = def;
+      double t_best = t_def;
+      for (int c = 0; c < nc; ++c) {
+        if (cand[c] == def) continue;
+        ctx->tune.tpb[ty][ps] = cand[c];
+        remap();
+        const double t = tune_time(ctx, jb.op, jb.cls[k], reps);
+        if (t < t_best) {
+          t_best = t;
+          best = cand[c];
+        }
+      }
+      ctx->tune.tpb[ty][ps] = best;
+      remap();
+      res.threads[ty][ps] = best;
+      res.default_threads[ty][ps] = def;
+      res.us_default[ty][ps] = (float)t_def;
+      res.us_tuned[ty][ps] = (float)t_best;
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.reset();
+  ctx->prof.launches = launches0;
+  ctx->prof.on = was_on;
+  if (out) *out = res;
   return SGN_OK;
   API_END
 }

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "fft_core.cuh"
 
@@ -29,6 +31,20 @@ struct Geom {
 // y-pass gave up waiting for its tensor copies (a bounded wait ran out).
 enum : int { FLAG_CAVITATION = 1, FLAG_NONFINITE = 2, FLAG_WAIT = 4 };
 
+// Launch shapes of the transform passes picked by sgn_autotune: threads per
+// block of each pass, per arithmetic (0 = the built-in choice). A y-pass block
+// of t threads transforms t / (Ny/8) columns, an x-pass block t / (Nx/8) row
+// pairs; the shape changes no arithmetic, only how the work is tiled.
+enum TunePass : int { TP_MV_YINV = 0, TP_MV_YFWD, TP_RHS_YINV, TP_RHS_YFWD, TP_MV_X, TP_RHS_X, TP_COUNT };
+enum TuneType : int { TT_F32 = 0, TT_F64, TT_DFL, TT_COUNT };
+struct Tune {
+  int tpb[TT_COUNT][TP_COUNT];
+};
+template <typename T>
+constexpr int tune_type() {
+  return sizeof(T) == 4 ? TT_F32 : (std::is_same<T, double>::value ? TT_F64 : TT_DFL);
+}
+
 // Tensor maps of the FP32 matvec y-passes (built when a handle is made):
 // v: the Krylov basis as a [nvec][Ny][2 ldS] FP32 tensor, t0, t1: the two
 // y-forward inputs as [1][Ny][2 ldS]; the boxes are [1][rows][2 C], C the
@@ -41,12 +57,20 @@ struct MvTma {
   const void* t1base;
   size_t vs;
   int nvec;
+  int cinv, cfwd;  // columns per block the boxes were made for
   int ok;
   int* flags;
 };
-// Builds the maps for the basis V (nvec vectors) and tmp[0], tmp[1]; returns
-// false (ok = 0) if the driver's encoder is unavailable or refuses them.
-bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags, MvTma* out);
+// Builds the maps for the basis V (nvec vectors) and tmp[0], tmp[1], for the
+// y-pass shapes of tune (may be null: built-in shapes); returns false (ok = 0)
+// if the driver's encoder is unavailable or refuses them.
+bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags,
+                 const Tune* tune, MvTma* out);
+// Threads per block of a pass: the built-in choice and the candidates the
+// autotuner tries (powers of two, whole columns or row pairs, within the
+// kernel's launch bound), for arithmetic `type` (TuneType).
+int pass_default_threads(const Geom& G, int type, int pass);
+int pass_candidates(const Geom& G, int type, int pass, int* out, int max_out);
 
 // Epilogue modes of the RHS y-forward pass (the RK4 stage update, Section 3).
 enum RkMode : int {
@@ -190,6 +214,8 @@ struct Exec {
   Prof* p;
   int kind_override = -1;  // time every launch of this call under one class
   bool refine = false;     // matvec passes count as the FP64 refinement classes
+  const Tune* tune = nullptr;
+  int tpb(int type, int pass) const { return tune ? tune->tpb[type][pass] : 0; }
   void begin(int k, int nlaunch = 1) const {
     if (!p) return;
     if (kind_override >= 0) k = kind_override;

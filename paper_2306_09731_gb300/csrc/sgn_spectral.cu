@@ -518,10 +518,11 @@ constexpr int ypass_threads() {
   return (sizeof(T) == 4 || LN == 12) ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
 }
 
-// LN > 0: compile-time column length 2^LN; the interleave 2^LC of the block's
-// columns then follows from the block size the launcher uses.
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+// LN > 0: compile-time column length 2^LN, and the built-in shape's column
+// interleave 2^LC (folds the index arithmetic of the stages; a tuned shape
+// other than the built-in one runs the runtime-length kernel, LN = 0)
 template <typename T, bool INV, int LN, int NIN>
 constexpr int ypass_lc() {
   return LN == 0 ? -1 : clampi(ilog2c(ypass_threads<T, INV, LN, NIN>()) - (LN - 3), 0, 6);
@@ -1006,19 +1007,33 @@ static inline int x_pairs_per_block(const Geom& G) {
   return P;
 }
 template <typename T>
-static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int nf) {
-  const int P = x_pairs_per_block<T>(G);
+static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int nf, int tpb = 0) {
+  int P = x_pairs_per_block<T>(G);
+  // tuned shape: whole row pairs, a power of two, within the launch bound
+  const int Tn = G.Nx >> 3;
+  if (tpb > 0 && tpb % Tn == 0) {
+    const int q = tpb / Tn;
+    if ((q & (q - 1)) == 0 && tpb <= (G.lNx == 12 ? 512 : 256) && q <= (G.Ny >> 1)) P = q;
+  }
   block = dim3((G.Nx >> 3) * P);
   grid = dim3((G.Ny / 2 + P - 1) / P, nf);
   smem = (size_t)P * smem_elems(G.Nx) * sizeof(cpx<T>);
 }
 template <typename T, bool INV, int NIN>
-static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int stage_per_thread = 0) {
+static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int stage_per_thread = 0,
+                            int tpb_tuned = 0, bool* builtin = nullptr) {
   const int Tn = G.Ny >> 3;
-  const int tpb = G.lNy == 12 ? ypass_threads<T, INV, 12, NIN>() : ypass_threads<T, INV, 0, NIN>();
-  int C = tpb / Tn;
+  const int bound = G.lNy == 12 ? ypass_threads<T, INV, 12, NIN>() : ypass_threads<T, INV, 0, NIN>();
+  int C = bound / Tn;
   if (C < 1) C = 1;
   if (C > 64) C = 64;
+  const int C0 = C;
+  // tuned shape: whole columns, a power of two, within the launch bound
+  if (tpb_tuned > 0 && tpb_tuned % Tn == 0) {
+    const int q = tpb_tuned / Tn;
+    if ((q & (q - 1)) == 0 && q <= 64 && tpb_tuned <= bound && tpb_tuned >= 32) C = q;
+  }
+  if (builtin) *builtin = C == C0;
   block = dim3(Tn * C);
   grid = dim3((G.Nxh + C - 1) / C);
   int lC = 0;
@@ -1176,12 +1191,59 @@ cudaError_t launch_coef_phys(const Geom& G, const double* hphys, T* h, T* cr, T*
 }
 
 // S: storage type of sigma_hat and w; T: arithmetic of the passes
-// Columns per block of the FP32 two-input y-passes (both directions).
-static inline int mv_y_columns(const Geom& G) {
+// Columns per block of the FP32 two-input y-passes (tpb: tuned threads or 0).
+static inline int mv_y_columns(const Geom& G, int tpb) {
   dim3 grid, block;
   size_t smem;
-  y_config<float, false, 2>(G, grid, block, smem);
+  y_config<float, false, 2>(G, grid, block, smem, 0, tpb);
   return (int)block.x / (G.Ny >> 3);
+}
+
+// Launch bound of a y-pass in threads, per arithmetic and pass (mirrors
+// ypass_threads), and of an x-pass.
+static int y_bound(const Geom& G, int type, int pass) {
+  const bool inv = pass == TP_MV_YINV || pass == TP_RHS_YINV;
+  const int nin = (pass == TP_MV_YINV || pass == TP_MV_YFWD) ? 2 : (pass == TP_RHS_YINV ? 4 : 3);
+  const bool l12 = G.lNy == 12;
+  if (type == TT_F32) return nin <= 2 ? 1024 : 512;
+  if (type == TT_F64) return l12 ? 512 : 256;
+  return (l12 || !inv) ? 512 : 256;
+}
+static bool is_y_pass(int pass) { return pass <= TP_RHS_YFWD; }
+
+int pass_default_threads(const Geom& G, int type, int pass) {
+  if (is_y_pass(pass)) {
+    const int Tn = G.Ny >> 3;
+    int C = y_bound(G, type, pass) / Tn;
+    if (C < 1) C = 1;
+    if (C > 64) C = 64;
+    return Tn * C;
+  }
+  const int Tn = G.Nx >> 3;
+  int P = Tn >= 256 ? 1 : 256 / Tn;
+  if (P > (G.Ny >> 1)) P = G.Ny >> 1;
+  return Tn * P;
+}
+
+int pass_candidates(const Geom& G, int type, int pass, int* out, int max_out) {
+  int n = 0;
+  if (is_y_pass(pass)) {
+    const int Tn = G.Ny >> 3, bound = y_bound(G, type, pass);
+    for (int C = 1; C <= 64 && n < max_out; C *= 2) {
+      const int t = Tn * C;
+      if (t > bound) break;
+      if (t >= 32) out[n++] = t;
+    }
+  } else {
+    const int Tn = G.Nx >> 3, bound = G.lNx == 12 ? 512 : 256;
+    for (int P = 1; P <= (G.Ny >> 1) && n < max_out; P *= 2) {
+      const int t = Tn * P;
+      if (t > bound) break;
+      if (t >= 32 || P == (G.Ny >> 1) || t * 2 > bound) out[n++] = t;
+    }
+  }
+  if (n == 0 && max_out > 0) out[n++] = pass_default_threads(G, type, pass);
+  return n;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1199,11 +1261,13 @@ static bool encode_spectra(EncodeTiledFn enc, const Geom& G, const void* base, i
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags, MvTma* out) {
+bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const void* t1, int* flags,
+                 const Tune* tune, MvTma* out) {
   *out = MvTma{};
   // row strides must be multiples of 16 bytes, and a box at most 256 wide
-  const int C = mv_y_columns(G);
-  if ((G.ldS * 8) % 16 != 0 || 2 * C > 256) return false;
+  const int Ci = mv_y_columns(G, tune ? tune->tpb[TT_F32][TP_MV_YINV] : 0);
+  const int Cf = mv_y_columns(G, tune ? tune->tpb[TT_F32][TP_MV_YFWD] : 0);
+  if ((G.ldS * 8) % 16 != 0 || 2 * Ci > 256 || 2 * Cf > 256) return false;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
@@ -1213,9 +1277,11 @@ bool make_mv_tma(const Geom& G, const void* V, int nvec, const void* t0, const v
     return false;
   }
   EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
-  if (!encode_spectra(enc, G, V, nvec, C, &out->v) || !encode_spectra(enc, G, t0, 1, C, &out->t0) ||
-      !encode_spectra(enc, G, t1, 1, C, &out->t1))
+  if (!encode_spectra(enc, G, V, nvec, Ci, &out->v) || !encode_spectra(enc, G, t0, 1, Cf, &out->t0) ||
+      !encode_spectra(enc, G, t1, 1, Cf, &out->t1))
     return false;
+  out->cinv = Ci;
+  out->cfwd = Cf;
   out->vbase = V;
   out->t0base = t0;
   out->t1base = t1;
@@ -1245,8 +1311,16 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
     }
     dim3 grid, block;
     size_t smem;
-    y_config<T, true, 2>(G, grid, block, smem);
+    // the boxes of the maps fix the columns per block
+    bool bi = true, bf = true;
+    y_config<T, true, 2>(G, grid, block, smem, 0, ex.tpb(TT_F32, TP_MV_YINV), &bi);
     const int C = (int)block.x / (G.Ny >> 3);
+    {
+      dim3 g2, b2;
+      size_t s2;
+      y_config<T, false, 2>(G, g2, b2, s2, 0, ex.tpb(TT_F32, TP_MV_YFWD), &bf);
+      if (C != tma->cinv || (int)b2.x / (G.Ny >> 3) != tma->cfwd) return false;
+    }
     int lC = 0;
     while ((1 << lC) < C) ++lC;
     const size_t tile = (size_t)G.Ny * C * sizeof(cpx<T>);
@@ -1256,7 +1330,7 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
     ti.zsel = jsel;
     ti.flags = tma->flags;
     smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + 128 + tile;
-    dispatch_ln<T>(G.lNy, [&](auto ln) {
+    dispatch_ln<T>(bi ? G.lNy : 0, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       YIn<T, 2> yi{};
       yi.src[0] = sig;
@@ -1270,20 +1344,24 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
                                                                                            ti, ep);
       ex.end();
     });
-    x_config<T>(G, grid, block, smem, 1);
+    x_config<T>(G, grid, block, smem, 1, ex.tpb(TT_F32, TP_MV_X));
     dispatch_ln<T>(G.lNx, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       ex.begin(PK_MV_X);
       k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
       ex.end();
     });
-    y_config<T, false, 2>(G, grid, block, smem);
+    y_config<T, false, 2>(G, grid, block, smem, 0, ex.tpb(TT_F32, TP_MV_YFWD));
+    const int Cf = (int)block.x / (G.Ny >> 3);
+    int lCf = 0;
+    while ((1 << lCf) < Cf) ++lCf;
+    const size_t tilef = (size_t)G.Ny * Cf * sizeof(cpx<T>);
     YTma tf{};
     tf.map[0] = tma->t0;
     tf.map[1] = tma->t1;
     tf.flags = tma->flags;
-    smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + 128 + 2 * tile;
-    dispatch_ln<T>(G.lNy, [&](auto ln) {
+    smem = ystage_offset(G.lNy, lCf, (int)sizeof(cpx<T>)) + 128 + 2 * tilef;
+    dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       YIn<T, 2> yi{};
       yi.src[0] = tmp[0];
@@ -1306,8 +1384,10 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
   size_t smem;
   // y-inverse of sigma_hat and i ky sigma_hat (read once, the second formed
   // from the staged copy)
-  y_config<T, true, 2>(G, grid, block, smem, ystage_bytes<T, S, FL_MV_INV>(2));
-  dispatch_ln<T>(G.lNy, [&](auto ln) {
+  bool bi = true;
+  y_config<T, true, 2>(G, grid, block, smem, ystage_bytes<T, S, FL_MV_INV>(2), ex.tpb(tune_type<T>(), TP_MV_YINV),
+                       &bi);
+  dispatch_ln<T>(bi ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2, S> yi{};
     yi.src[0] = sig;
@@ -1324,15 +1404,17 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
                                                                                         ep);
     ex.end();
   });
-  x_config<T>(G, grid, block, smem, 1);
+  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_MV_X));
   dispatch_ln<T>(G.lNx, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     ex.begin(PK_MV_X);
     k_mv_x<T, L><<<grid, block, smem, ex.s>>>(G, tb.twx, tb.kx, tmp[0], tmp[1], cr, cc, tmp[0], tmp[1]);
     ex.end();
   });
-  y_config<T, false, 2>(G, grid, block, smem, ystage_bytes<T, T, FL_MV_FWD>(2));
-  dispatch_ln<T>(G.lNy, [&](auto ln) {
+  bool bf = true;
+  y_config<T, false, 2>(G, grid, block, smem, ystage_bytes<T, T, FL_MV_FWD>(2), ex.tpb(tune_type<T>(), TP_MV_YFWD),
+                        &bf);
+  dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 2> yi{};
     yi.src[0] = tmp[0];
@@ -1395,10 +1477,12 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                        cpx<S>* const* Unext, cpx<S>* const* acc, cpx<S>* bhat, const RkArgs& rk, const Exec& ex) {
   dim3 grid, block;
   size_t smem;
-  dispatch_ln<T>(G.lNy, [&](auto ln) {
+  bool bi = true;
+  y_config<T, true, 4>(G, grid, block, smem, 0, ex.tpb(tune_type<T>(), TP_RHS_YINV), &bi);
+  dispatch_ln<T>(bi ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     constexpr int FL = fl_rhs_inv<T, L>();
-    y_config<T, true, 4>(G, grid, block, smem, ystage_bytes<T, S, FL>(4));
+    y_config<T, true, 4>(G, grid, block, smem, ystage_bytes<T, S, FL>(4), ex.tpb(tune_type<T>(), TP_RHS_YINV));
     YIn<T, 4, S> yi{};
     yi.src[0] = U[1];
     yi.src[1] = U[2];
@@ -1413,7 +1497,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
   });
   // each block reads only its own row pair before writing it, so the outputs
   // may overwrite the inputs
-  x_config<T>(G, grid, block, smem, 1);
+  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_RHS_X));
   dispatch_ln<T>(G.lNx, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     ex.begin(PK_RHS_X);
@@ -1421,8 +1505,10 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
                                                (T)rk.g, tmp[0], tmp[1], tmp[2]);
     ex.end();
   });
-  y_config<T, false, 3>(G, grid, block, smem, ystage_bytes<T, T, FL_RHS_FWD>(3));
-  dispatch_ln<T>(G.lNy, [&](auto ln) {
+  bool bf = true;
+  y_config<T, false, 3>(G, grid, block, smem, ystage_bytes<T, T, FL_RHS_FWD>(3), ex.tpb(tune_type<T>(), TP_RHS_YFWD),
+                        &bf);
+  dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     YIn<T, 3> yi{};
     yi.src[0] = tmp[0];

@@ -30,16 +30,21 @@ def perturbed_members(count, seed=0, grids=GRIDS):
 class Ensemble:
     """Handles, streams and device fields of a list of initial states."""
 
-    def __init__(self, states, **opts):
+    def __init__(self, states, tune=False, **opts):
+        """tune: run sgn_autotune on each member's handle (launch shapes for
+        its grid; members of the ensemble's small grids gain the most)."""
         import torch
         self._torch = torch
         self.states = states
         self.streams = [torch.cuda.Stream() for _ in states]
         self.solvers = []
         self.fields = []
+        self.tuning = []
         for st, s in zip(states, self.streams):
             sol = Solver(st.Nx, st.Ny, st.Lx, st.Ly, **opts)
             sol.set_stream(s)
+            if tune:
+                self.tuning.append(sol.autotune(3))
             self.solvers.append(sol)
             self.fields.append([torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
                                 for a in (st.h, st.vx, st.vy, st.sigma)])

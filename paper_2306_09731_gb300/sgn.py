@@ -25,7 +25,11 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
            "sgn_diagnostics", "sgn_set_learned_guess", "sgn_record_learned", "sgn_recorded_count",
-           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_rk4_step_batch", "sgn_last_error"]
+           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_rk4_step_batch", "sgn_autotune", "sgn_last_error"]
+
+# index names of sgn_tuning's [type][pass] arrays
+TUNE_TYPES = ["fp32", "fp64", "dfl"]
+TUNE_PASSES = ["mv_yinv", "mv_yfwd", "rhs_yinv", "rhs_yfwd", "mv_x", "rhs_x"]
 
 PROFILE_CLASSES = ["coef", "mv_yinv", "mv_x", "mv_yfwd", "rhs_yinv", "rhs_x", "rhs_yfwd", "krylov", "io",
                    "ref_yinv", "ref_x", "ref_yfwd", "rk"]
@@ -47,6 +51,11 @@ class sgn_diag(ctypes.Structure):
     _fields_ = [("h_max", ctypes.c_double), ("i_max", ctypes.c_longlong), ("x_s", ctypes.c_double),
                 ("y_s", ctypes.c_double), ("c_fit", ctypes.c_double), ("dev_h", ctypes.c_double),
                 ("dev_vx", ctypes.c_double), ("max_vy", ctypes.c_double), ("tail", ctypes.c_double * 3)]
+
+
+class sgn_tuning(ctypes.Structure):
+    _fields_ = [("threads", (ctypes.c_int * 6) * 3), ("default_threads", (ctypes.c_int * 6) * 3),
+                ("us_tuned", (ctypes.c_float * 6) * 3), ("us_default", (ctypes.c_float * 6) * 3)]
 
 
 class sgn_stats(ctypes.Structure):
@@ -93,6 +102,7 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "sgn_elliptic_apply_noalloc": (_I, [_I, _I, _D, _D, _P, _P, _P, _P]),
         "sgn_diagnostics": (_I, [_P, _P, _P, _P, ctypes.POINTER(sgn_diag)]),
+        "sgn_autotune": (_I, [_P, _I, ctypes.POINTER(sgn_tuning)]),
         "sgn_set_learned_guess": (_I, [_P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.c_float, _I]),
         "sgn_record_learned": (_I, [_P, _I, _P, _I, _I]),
         "sgn_recorded_count": (_I, [_P, ctypes.POINTER(_I)]),
@@ -209,6 +219,21 @@ def sgn_diagnostics(handle, h, vx, vy) -> dict:
     _check(handle, load_library().sgn_diagnostics(handle, _ptr(h), _ptr(vx), _ptr(vy), ctypes.byref(d)))
     return dict(h_max=d.h_max, i_max=d.i_max, x_s=d.x_s, y_s=d.y_s, c_fit=d.c_fit, dev_h=d.dev_h,
                 dev_vx=d.dev_vx, max_vy=d.max_vy, tail=[d.tail[i] for i in range(3)])
+
+
+def sgn_autotune(handle, reps=5) -> dict:
+    """Times the launch shapes of the handle's transform passes and keeps the
+    fastest; see include/sgn.h. Returns {type: {pass: {...}}} for the passes
+    the handle runs."""
+    t = sgn_tuning()
+    _check(handle, load_library().sgn_autotune(handle, int(reps), ctypes.byref(t)))
+    out = {}
+    for i, ty in enumerate(TUNE_TYPES):
+        for j, ps in enumerate(TUNE_PASSES):
+            if t.threads[i][j] > 0:
+                out.setdefault(ty, {})[ps] = dict(threads=t.threads[i][j], default_threads=t.default_threads[i][j],
+                                                  us=t.us_tuned[i][j], us_default=t.us_default[i][j])
+    return out
 
 
 def _ptr32(x):
@@ -368,6 +393,9 @@ class Solver:
 
     def diagnostics(self, h, vx, vy):
         return sgn_diagnostics(self.handle, h, vx, vy)
+
+    def autotune(self, reps=5):
+        return sgn_autotune(self.handle, reps)
 
     def coarse_sample(self, f, n):
         out = self._torch.empty((n, n), dtype=self._torch.float32, device="cuda")
