@@ -377,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
         devfields[name] = f
         solvers[name] = s
         paths[name] = rec
-    # learned start (row f2): networks trained here on solver snapshots of four
+    # learned start: networks trained here on solver snapshots of four
     # other Gaussian humps (amplitudes 0.35-0.65, shifted centres), then run on
     # the benchmark state: over the paper's start (tau = dt/2, coarse n/8) and
     # over the extrapolated start (tau = (dt/2)^2, coarse n/16)
@@ -450,7 +450,7 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
                "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
-    # ensembles (row f3): 64 perturbed line solitons, a ~ U[0.1, 1], eps ~ U[1e-3, 5e-2], on
+    # ensembles: 64 perturbed line solitons, a ~ U[0.1, 1], eps ~ U[1e-3, 5e-2], on
     # 256^2, 512x256 and 1024x512 grids, dt = 2e-3, each member with its own handle and
     # stream: sgn_rk4_step_batch against the members stepped one by one (wall time of
     # K steps of all members after W warm-up steps; host timers around calls that
@@ -480,7 +480,7 @@ def run_ours(args, rank, world, local_rank):
         if True in ens and False in ens:
             ensemble["batch_builtin_shapes"] = len(members) * args.steps / ens[False][0]
             ensemble["tuning_first_members"] = tuning
-    # the paper's monitoring quantities (row f4) on the final state: wall time of
+    # the paper's monitoring quantities on the final state: wall time of
     # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
     hf = devfields[head_name]
     head_solver.diagnostics(hf[0], hf[1], hf[2])

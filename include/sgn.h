@@ -202,7 +202,7 @@ sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly,
 /* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
 const char* sgn_last_error(sgn_t ctx);
 
-/* Ensembles (row f3): count independent problems, each with its own handle
+/* Ensembles: count independent problems, each with its own handle
  * (its own grid size, options and stream, set with sgn_set_stream), advanced
  * by nsteps RK4 steps each, like sgn_rk4_step on h[i], vx[i], vy[i],
  * sigma[i]. Members created with graph = 1 are all enqueued on their streams
@@ -280,7 +280,7 @@ typedef struct {
 sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out);
 
 /* ------------------------------------------------------------------------
- * Learned GMRES start (row f2). Section 3 starts GMRES from the last computed
+ * Learned GMRES start. Section 3 starts GMRES from the last computed
  * sigma; a network (include/sgn_unet.h) can correct that start. At RK4 stages
  * 2 and 4 (the stages whose state moved by O(dt) since the fallback's), after
  * the start chosen by opt.guess, the library forms on an n x n coarse grid

@@ -1,4 +1,4 @@
-"""Ensembles (row f3): sgn_rk4_step_batch over uneven grids.
+"""Ensembles: sgn_rk4_step_batch over uneven grids.
 
 Each member is exactly the single-member computation on its own handle and
 stream, so the bar is bitwise equality with sgn_rk4_step member by member, and

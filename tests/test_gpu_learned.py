@@ -1,4 +1,4 @@
-"""The learned GMRES start (row f2): coarse transfer parity, tolerance kept,
+"""The learned GMRES start: coarse transfer parity, tolerance kept,
 graph mode, recording, and what a trained network gains.
 
 Bars. Coarse transfer: FP32 sums of at most n terms with FP32 twiddles
