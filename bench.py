@@ -160,6 +160,12 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_INSTR_PER_FLOP / 1e12
 MEASURED_TRAFFIC = {
     ("ref_x", "df", 2048): {"bytes": 134.603264e6 + 22.911744e6, "source": "profiles/k_mv_x_df_gaussian2048.md"},
     ("mv_x", "fp32", 2048): {"bytes": 67.196928e6 + 0.668928e6, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
+    ("mv_yinv", "fp32", 2048): {"bytes": 16.893696e6 + 0.13824e6, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
+    ("mv_yfwd", "fp32", 2048): {"bytes": 33.669888e6 + 0.076288e6, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
+    ("rhs_yinv", "fp32", 2048): {"bytes": 102.639616e6 + 31.659264e6,
+                                 "source": "profiles/k_ypass_fp32_gaussian2048.md"},
+    ("rhs_yfwd", "fp32", 2048): {"bytes": 50.482688e6 + 3.486976e6,
+                                 "source": "profiles/k_ypass_fp32_gaussian2048.md"},
     ("rhs_x", "fp32", 2048): {"bytes": 100.807424e6 + 6.458624e6, "source": "profiles/k_rhs_x_fp32_gaussian2048.md"},
     ("rk", "fp32", 2048): {"bytes": 151.211264e6 + 182.635776e6, "source": "profiles/k_rk_update_gaussian2048.md"},
     ("mv_x", "fp64", 2048): {"bytes": 134.8608e6 + 29.78304e6, "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
