@@ -115,6 +115,9 @@ struct sgn_ctx {
   // tensor maps of the FP32 matvec y-passes (precisions 1, 2); SGN_TMA=0
   // loads their inputs with plain and cp.async loads instead
   MvTma mvt{};
+  // sgn_rk4_step_host: copy stream and its events (made on first use)
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev[9] = {};
   Tune tune{};  // launch shapes picked by sgn_autotune (0: built-in)
   std::vector<void*> allocs;
   std::string err;
@@ -210,6 +213,13 @@ void free_all(sgn_ctx* ctx) {
   free_graph(ctx);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   ctx->cap = nullptr;
+  if (ctx->io_stream) {
+    cudaStreamSynchronize(ctx->io_stream);
+    cudaStreamDestroy(ctx->io_stream);
+    for (int i = 0; i < 9; ++i)
+      if (ctx->io_ev[i]) cudaEventDestroy(ctx->io_ev[i]);
+  }
+  ctx->io_stream = nullptr;
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   if (ctx->rb_host) cudaFreeHost(ctx->rb_host);
@@ -347,6 +357,48 @@ void inv2(sgn_ctx* ctx, const C64* const* in, const int* dx, const int* dy, int 
   CK(launch_y_fft<double>(ctx->G, ctx->tb, true, in, dy, nf, ctx->tmp, EX(ctx)));
   CK(launch_x_c2r<double>(ctx->G, ctx->tb, (const C64* const*)ctx->tmp, dx, nf, out,
                           1.0 / (double)ctx->G.nphys(), EX(ctx)));
+}
+
+// Host-buffer calls: per-field copies on a copy stream, overlapped with the
+// per-field transforms on the handle's stream (field i's transform waits only
+// for its own host-to-device copy; field i's device-to-host copy starts as
+// soon as its inverse transform is done).
+struct HostIO {
+  cudaStream_t cs;
+  cudaEvent_t in[4], out[4];
+  double* host[4];
+  size_t bytes;
+};
+
+// (h, vx, vy) -> Un, sigma -> sig (spectral); io may be null
+void fwd_state(sgn_ctx* ctx, const double* const* f, const HostIO* io) {
+  if (!io) {
+    fwd2(ctx, f, 3, ctx->Un);
+    fwd2(ctx, f + 3, 1, &ctx->sig);
+    return;
+  }
+  C64* dst[4] = {ctx->Un[0], ctx->Un[1], ctx->Un[2], ctx->sig};
+  for (int i = 0; i < 4; ++i) {
+    CK(cudaStreamWaitEvent(ctx->stream, io->in[i], 0));
+    fwd2(ctx, f + i, 1, dst + i);
+  }
+}
+
+// Un -> (h, vx, vy), sig -> sigma (physical); with io, each field is copied to
+// io->host[i] on the copy stream once it is ready
+void inv_state(sgn_ctx* ctx, double* const* o, const HostIO* io) {
+  if (!io) {
+    inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o);
+    inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, o + 3);
+    return;
+  }
+  const C64* src[4] = {ctx->Un[0], ctx->Un[1], ctx->Un[2], ctx->sig};
+  for (int i = 0; i < 4; ++i) {
+    inv2(ctx, src + i, nullptr, nullptr, 1, o + i);
+    CK(cudaEventRecord(io->out[i], ctx->stream));
+    CK(cudaStreamWaitEvent(io->cs, io->out[i], 0));
+    CK(cudaMemcpyAsync(io->host[i], o[i], io->bytes, cudaMemcpyDeviceToHost, io->cs));
+  }
 }
 
 void sync_read(sgn_ctx* ctx) {
@@ -705,12 +757,10 @@ void ensure_phys(sgn_ctx* ctx) {
 }
 
 void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
-                bool* conv_all) {
-  const double* f3[3] = {h, vx, vy};
+                bool* conv_all, const HostIO* io = nullptr) {
+  const double* f4[4] = {h, vx, vy, sigma};
   reset_flags(ctx);
-  fwd2(ctx, f3, 3, ctx->Un);
-  const double* fs[1] = {sigma};
-  fwd2(ctx, fs, 1, &ctx->sig);
+  fwd_state(ctx, f4, io);
   CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
   ctx->have_s3 = false;  // the extrapolation history lives within one call
   bool conv = true;
@@ -720,10 +770,8 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
     conv &= stage(ctx, RK_STAGE3, dt);
     conv &= stage(ctx, RK_FINAL, dt);
   }
-  double* o3[3] = {h, vx, vy};
-  inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o3);
-  double* os[1] = {sigma};
-  inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
+  double* o4[4] = {h, vx, vy, sigma};
+  inv_state(ctx, o4, io);
   *conv_all = conv;
 }
 
@@ -1012,20 +1060,17 @@ void build_step_graph(sgn_ctx* ctx, double dt) {
 // of the device statistics, then (after a synchronisation) their harvest. A
 // batch of handles enqueues all members first and harvests after, so that the
 // members' work overlaps on their streams.
-void rk4_graph_enqueue(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps) {
+void rk4_graph_enqueue(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
+                       const HostIO* io = nullptr) {
   if (!ctx->step_exec || ctx->graph_dt != dt) build_step_graph(ctx, dt);
-  const double* f3[3] = {h, vx, vy};
+  const double* f4[4] = {h, vx, vy, sigma};
   reset_flags(ctx);
   CK(cudaMemsetAsync(ctx->gst, 0, sizeof(GmresDev), ctx->stream));
-  fwd2(ctx, f3, 3, ctx->Un);
-  const double* fs[1] = {sigma};
-  fwd2(ctx, fs, 1, &ctx->sig);
+  fwd_state(ctx, f4, io);
   CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
   for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
-  double* o3[3] = {h, vx, vy};
-  inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o3);
-  double* os[1] = {sigma};
-  inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, os);
+  double* o4[4] = {h, vx, vy, sigma};
+  inv_state(ctx, o4, io);
   CK(cudaMemcpyAsync(ctx->gst_host, ctx->gst, sizeof(GmresDev), cudaMemcpyDeviceToHost, ctx->stream));
   CK(launch_readback_scalar(ctx->scal, ctx->flags, ctx->rb_dev, EX(ctx)));
   CK(cudaMemcpyAsync(ctx->rb_host, ctx->rb_dev, sizeof(GmresReadback), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1048,8 +1093,8 @@ void rk4_graph_finish(sgn_ctx* ctx, int nsteps, bool* conv_all) {
 }
 
 void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
-                      bool* conv_all) {
-  rk4_graph_enqueue(ctx, h, vx, vy, sigma, dt, nsteps);
+                      bool* conv_all, const HostIO* io = nullptr) {
+  rk4_graph_enqueue(ctx, h, vx, vy, sigma, dt, nsteps, io);
   rk4_graph_finish(ctx, nsteps, conv_all);
 }
 
@@ -1417,13 +1462,42 @@ sgn_status sgn_rk4_step_host(sgn_t ctx, double* h, double* vx, double* vy, doubl
   ensure_phys(ctx);
   const size_t bytes = ctx->G.nphys() * sizeof(double);
   double* hv[4] = {h, vx, vy, sigma};
-  for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->phys[i], hv[i], bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if (nsteps == 0) {
+    for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(ctx->phys[i], hv[i], bytes, cudaMemcpyHostToDevice, ctx->stream));
+    for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SGN_OK;
+  }
+  if (!ctx->io_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 9; ++i) CK(cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming));
+  }
+  HostIO io{};
+  io.cs = ctx->io_stream;
+  io.bytes = bytes;
+  for (int i = 0; i < 4; ++i) {
+    io.in[i] = ctx->io_ev[i];
+    io.out[i] = ctx->io_ev[4 + i];
+    io.host[i] = hv[i];
+  }
+  // the copies follow whatever the handle's stream holds already; whatever
+  // happens below, no copy into the caller's buffers outlives the call
+  struct IoSync {
+    cudaStream_t s;
+    ~IoSync() { cudaStreamSynchronize(s); }
+  } io_sync{io.cs};
+  CK(cudaEventRecord(ctx->io_ev[8], ctx->stream));
+  CK(cudaStreamWaitEvent(io.cs, ctx->io_ev[8], 0));
+  for (int i = 0; i < 4; ++i) {
+    CK(cudaMemcpyAsync(ctx->phys[i], hv[i], bytes, cudaMemcpyHostToDevice, io.cs));
+    CK(cudaEventRecord(io.in[i], io.cs));
+  }
   bool conv = true;
-  if (nsteps > 0 && ctx->opt.graph && !ctx->prof.on)
-    rk4_device_graph(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
-  else if (nsteps > 0)
-    rk4_device(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv);
-  for (int i = 0; i < 4; ++i) CK(cudaMemcpyAsync(hv[i], ctx->phys[i], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->opt.graph && !ctx->prof.on)
+    rk4_device_graph(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv, &io);
+  else
+    rk4_device(ctx, ctx->phys[0], ctx->phys[1], ctx->phys[2], ctx->phys[3], dt, nsteps, &conv, &io);
+  CK(cudaStreamSynchronize(io.cs));
   CK(cudaStreamSynchronize(ctx->stream));
   if (!conv) return fail(ctx, SGN_ENOTCONV, "GMRES reached maxit in at least one stage");
   return SGN_OK;
