@@ -288,6 +288,9 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
 // y-inverse of one FP64 half spectrum into the pass type T
 template <typename T>
 cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>* in, cpx<T>* out, const Exec& ex);
+// y-forward of one half spectrum of type T, stored as FP64
+template <typename T>
+cudaError_t launch_y_fwd64(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<double>* out, const Exec& ex);
 void init_kernel_attributes_df();
 
 // RHS of one stage from state U (3 spectra), sigma_hat, h, cr; K goes through

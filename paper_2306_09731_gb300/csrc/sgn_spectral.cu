@@ -117,6 +117,23 @@ __device__ __forceinline__ cpx<T>* x_smem(const Geom& G, int grp) {
 
 // ------------------------------------------------------------ plain x-passes
 
+// FP64 values into and out of a pass's type (double-float: exact split and
+// bit placement, no FP64-pipe arithmetic)
+template <typename T>
+__device__ __forceinline__ T from_f64(double x) {
+  if constexpr (std::is_same<T, dfl>::value)
+    return dfl_from_f64(x);
+  else
+    return (T)x;
+}
+template <typename T>
+__device__ __forceinline__ double to_f64(T x) {
+  if constexpr (std::is_same<T, dfl>::value)
+    return dfl_to_f64(x);
+  else
+    return (double)x;
+}
+
 template <typename T>
 struct XR2CArgs {
   const double* f[4];
@@ -133,7 +150,7 @@ __global__ void k_x_r2c(Geom G, const cpx<T>* __restrict__ tw, XR2CArgs<T> a) {
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    v[s] = mk((T)f[(size_t)L.y0 * N + x], (T)f[(size_t)L.y1 * N + x]);
+    v[s] = mk(from_f64<T>(f[(size_t)L.y0 * N + x]), from_f64<T>(f[(size_t)L.y1 * N + x]));
   }
   fft_regs<false>(v, sm, tw, L.t, G.lNx);
   cpx<T> f0[5], f1[5];
@@ -144,8 +161,8 @@ __global__ void k_x_r2c(Geom G, const cpx<T>* __restrict__ tw, XR2CArgs<T> a) {
   for (int s = 0; s < 5; ++s) {
     if (!split_owns(s, L.t)) continue;
     const int k = L.t + s * T_;
-    o[(size_t)L.y0 * G.ldS + k] = scl(f0[s], (T)0.5);
-    o[(size_t)L.y1 * G.ldS + k] = scl(f1[s], (T)0.5);
+    o[(size_t)L.y0 * G.ldS + k] = scl(f0[s], (T)0.5f);
+    o[(size_t)L.y1 * G.ldS + k] = scl(f1[s], (T)0.5f);
   }
 }
 
@@ -172,8 +189,8 @@ __global__ void k_x_c2r(Geom G, const cpx<T>* __restrict__ tw, const T* __restri
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int x = L.t + s * T_;
-    o[(size_t)L.y0 * N + x] = (double)v[s].x * scale;
-    o[(size_t)L.y1 * N + x] = (double)v[s].y * scale;
+    o[(size_t)L.y0 * N + x] = to_f64<T>(v[s].x) * scale;
+    o[(size_t)L.y1 * N + x] = to_f64<T>(v[s].y) * scale;
   }
 }
 
@@ -817,6 +834,19 @@ struct EpiStore {
   }
 };
 
+// one transform stored as FP64 (the double-float conversion passes of the
+// state of precision 2)
+template <typename T>
+struct EpiStoreF64 {
+  cpx<double>* dst;
+  __device__ __forceinline__ void operator()(cpx<T> (&r)[1][8], int col, int t, int T_, bool valid, const Geom& G,
+                                             const T* ky) const {
+    if (!valid) return;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) dst[(size_t)(t + s * T_) * G.ldS + col] = mk(to_f64<T>(r[0][s].x), to_f64<T>(r[0][s].y));
+  }
+};
+
 // w = [M^-1] (C - i ky By), M = 3 + kx^2 + ky^2 (Section 3 preconditioner)
 // minv (may be null): the FP64 and double-float passes read M^-1 from a table,
 // because a division costs about 25 FP64 instructions here; FP32 divides
@@ -1456,6 +1486,23 @@ cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_y_fwd64(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<double>* out, const Exec& ex) {
+  dim3 grid, block;
+  size_t smem;
+  y_config<T, false, 1>(G, grid, block, smem);
+  YIn<T, 1> yi{};
+  yi.src[0] = in;
+  EpiStoreF64<T> ep{out};
+  dispatch_l12(G.lNy, [&](auto ln) {
+    constexpr int L = decltype(ln)::value;
+    ex.begin(PK_IO);
+    ypass_fn<T, false, 1, EpiStoreF64<T>, T, L>()<<<grid, block, smem, ex.s>>>(G, tb.twy, tb.ky, yi, ep);
+    ex.end();
+  });
+  return cudaGetLastError();
+}
+
 // dynamic shared memory limits of the double-float kernels
 void init_kernel_attributes_df() {
   typedef dfl T;
@@ -1468,6 +1515,10 @@ void init_kernel_attributes_df() {
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12, FL_MV_INV>());
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12, FL_MV_FWD>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double, 12>());
+  set_smem<T>((const void*)k_x_r2c<T>);
+  set_smem<T>((const void*)k_x_c2r<T>);
+  set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStoreF64<T>, T, 0>());
+  set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStoreF64<T>, T, 12>());
   cudaGetLastError();
 }
 
@@ -1620,6 +1671,12 @@ template cudaError_t launch_matvec_io<dfl, double>(const Geom&, const Tables<dfl
                                                    const Exec&, const int*, size_t);
 template cudaError_t launch_y_inv64<dfl>(const Geom&, const Tables<dfl>&, const cpx<double>*, cpx<dfl>*,
                                          const Exec&);
+template cudaError_t launch_y_fwd64<dfl>(const Geom&, const Tables<dfl>&, const cpx<dfl>*, cpx<double>*,
+                                         const Exec&);
+template cudaError_t launch_x_r2c<dfl>(const Geom&, const Tables<dfl>&, const double* const*, int,
+                                       cpx<dfl>* const*, const Exec&);
+template cudaError_t launch_x_c2r<dfl>(const Geom&, const Tables<dfl>&, const cpx<dfl>* const*, const int*, int,
+                                       double* const*, double, const Exec&);
 template cudaError_t launch_coef_x<dfl>(const Geom&, const Tables<dfl>&, const cpx<dfl>*, dfl*, dfl*, dfl*, int*,
                                         const CoefCopy&, const Exec&);
 template cudaError_t launch_coef_phys<dfl>(const Geom&, const double*, dfl*, dfl*, dfl*, int*, const CoefCopy&,
