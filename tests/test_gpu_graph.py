@@ -171,15 +171,18 @@ def test_graph_host_buffers_and_profiling_fallback():
     s.close()
 
 
-@pytest.mark.parametrize("precision,graph", [(2, 1), (2, 0), (0, 1)])
-def test_host_buffer_calls_match_device_calls(precision, graph):
-    """sgn_rk4_step_host copies each field on its own stream while the others
-    are transformed: the fields equal those of the device-buffer call bitwise,
-    over two calls in a row, and nsteps = 0 returns the inputs unchanged."""
+@pytest.mark.parametrize("precision,graph,pinned", [(2, 1, True), (2, 0, True), (0, 1, True), (2, 1, False),
+                                                    (0, 0, False)])
+def test_host_buffer_calls_match_device_calls(precision, graph, pinned):
+    """sgn_rk4_step_host copies each field on a copy stream while the others
+    are transformed, from pinned or pageable arrays: the fields equal those of
+    the device-buffer call bitwise, over two calls in a row, and nsteps = 0
+    returns the inputs unchanged."""
     from paper_2306_09731_gb300.sgn import Solver, sgn_rk4_step_host
     st = I.perturbed_soliton(512, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=8)
     s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, graph=graph, precision=precision, guess=2)
-    hh = [torch.tensor(np.ascontiguousarray(a)).pin_memory().numpy() for a in (st.h, st.vx, st.vy, st.sigma)]
+    arrs = [np.ascontiguousarray(a).copy() for a in (st.h, st.vx, st.vy, st.sigma)]
+    hh = [torch.tensor(a).pin_memory().numpy() for a in arrs] if pinned else arrs
     ref = [h.copy() for h in hh]
     sgn_rk4_step_host(s.handle, *hh, 2e-3, 0)
     for x, y in zip(hh, ref):
