@@ -393,6 +393,9 @@ cudaError_t launch_ctl_begin(GmresDev* st, const double* cnorm, GraphCtl ctl, co
 cudaError_t launch_ctl_sweep(GmresDev* st, const double* beta, GraphCtl ctl, const Exec& ex);
 cudaError_t launch_ctl_after(GmresDev* st, GraphCtl ctl, const Exec& ex);
 cudaError_t launch_set_int(int* p, int v, const Exec& ex);
+// *flag = 1 if the three spectra b equal a within rel * max|a| (see sgn_krylov.cu)
+cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const cpx<double>* const* b, double rel,
+                              double* partials, unsigned* counter, int* flag, const Exec& ex);
 cudaError_t launch_readback_scalar(const double* x, const int* flags, GmresReadback* rb_dev, const Exec& ex);
 
 // invariants: physical pointwise sums (mass, px, py, energy) -> partials[4][NBLK]

@@ -474,6 +474,55 @@ __global__ void k_set_int(int* p, int v) {
   if (threadIdx.x == 0) *p = v;
 }
 
+// *flag = 1 when every component of the three spectra b is within rel * max|a|
+// of a's (a: the state the handle returned last, b: a call's input state),
+// else 0 (NaN counts as a difference). Block maxima in partials, combined by
+// the last block.
+__global__ void __launch_bounds__(256) k_same_state(Geom G, const cpx<double>* a0, const cpx<double>* a1,
+                                                    const cpx<double>* a2, const cpx<double>* b0,
+                                                    const cpx<double>* b1, const cpx<double>* b2, double rel,
+                                                    double* partials, unsigned* counter, int* flag) {
+  __shared__ double red[2][32];
+  const cpx<double>* A[3] = {a0, a1, a2};
+  const cpx<double>* B[3] = {b0, b1, b2};
+  double md = 0.0, ma = 0.0;
+  for (Walk it(G); it.ok(); it.next()) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const cpx<double> a = A[f][it.e], b = B[f][it.e];
+      const double dx = fabs(b.x - a.x), dy = fabs(b.y - a.y);
+      md = fmax(md, (dx != dx || dy != dy) ? INFINITY : fmax(dx, dy));
+      ma = fmax(ma, fmax(fabs(a.x), fabs(a.y)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = md;
+    red[1][wid] = ma;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      md = fmax(md, red[0][i]);
+      ma = fmax(ma, red[1][i]);
+    }
+    partials[blockIdx.x] = md;
+    partials[NBLK + blockIdx.x] = ma;
+  }
+  if (last_block(counter, threadIdx.x == 0) && threadIdx.x == 0) {
+    double D = 0.0, M = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      D = fmax(D, __ldcg(partials + b));
+      M = fmax(M, __ldcg(partials + NBLK + b));
+    }
+    *flag = (M > 0.0 && D <= rel * M) ? 1 : 0;
+  }
+}
+
 __global__ void k_readback_scalar(const double* x, const int* flags, GmresReadback* rb) {
   if (threadIdx.x != 0) return;
   rb->scalar = *x;
@@ -619,6 +668,14 @@ cudaError_t launch_ctl_after(GmresDev* st, GraphCtl ctl, const Exec& ex) {
   ex.end();
   return cudaGetLastError();
 }
+cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const cpx<double>* const* b, double rel,
+                              double* partials, unsigned* counter, int* flag, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_same_state<<<NBLK, 256, 0, ex.s>>>(G, a[0], a[1], a[2], b[0], b[1], b[2], rel, partials, counter, flag);
+  ex.end();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_int(int* p, int v, const Exec& ex) {
   ex.begin(PK_KRYLOV);
   k_set_int<<<1, 32, 0, ex.s>>>(p, v);
