@@ -63,7 +63,10 @@ typedef struct {
   int guess;          /* GMRES start: 0 = the last computed sigma (Section 3), 1 = zero,
                          2 = linear extrapolation in time inside sgn_rk4_step (stage 2 from
                          sigma(t) and the previous step's sigma(t - dt/2), stage 4 from
-                         sigma(t + dt/2) and sigma(t)); every solve still meets tol */
+                         sigma(t + dt/2) and sigma(t)); the previous step's sigma is kept
+                         from the handle's last RK4 call when the new call has the same dt
+                         and its input state is that call's output (within 1e-8 of the
+                         largest Fourier coefficient); every solve still meets tol */
   int graph;          /* 1: sgn_rk4_step and sgn_rk4_step_host run each RK4 step as one
                          CUDA graph whose GMRES loops are conditional WHILE nodes driven
                          by device-side tests (no host synchronisation inside the call;
