@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the built-in launch shapes (no sgn_autotune before the warm-up)")
+    ap.add_argument("--transverse", action="store_true",
+                    help="also run the transverse-stability workload to t = 10 (1024x256, FP64 and precision 1)")
     ap.add_argument("--no-crossing", action="store_true",
                     help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
@@ -339,6 +341,54 @@ def time_crossing(st, precision, guess, graph, learned, steps, warmup, tune=True
             "max_iters": st1["max_iters"]}
 
 
+def transverse_stability(tend=10.0, dt=2e-3, marks=5):
+    """The line solitary wave of amplitude a in {0.2, 0.5, 1.0} on 1024 x 256
+    over [-60, 60) x [-15, 15) with h += 1e-2 exp(-x^2) cos(2 pi y/Ly + phi),
+    to t = tend with dt, in FP64 (the paper's method) and precision 1, graph
+    mode, extrapolated start: the L-infinity deviation from the fitted line
+    soliton (Section 4.1) and the relative mass and energy drift (Section 2.3,
+    from the state after the first step) at `marks` times, and the final
+    difference between the precisions."""
+    import numpy as np
+    import torch
+
+    from paper_2306_09731_gb300 import inputs as I
+    from paper_2306_09731_gb300.sgn import Solver
+    nsteps = int(round(tend / dt)) - 1
+    per = nsteps // marks
+    out = {}
+    for a in (0.2, 0.5, 1.0):
+        st = I.perturbed_soliton(1024, 256, 120.0, 30.0, a=a, eps=1e-2, seed=0)
+        fin = {}
+        for prec in (0, 1):
+            s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, precision=prec, guess=2, graph=1)
+            f = [torch.tensor(x, dtype=torch.float64, device="cuda").contiguous()
+                 for x in (st.h, st.vx, st.vy, st.sigma)]
+            # the input sigma is 0: drifts are measured from the first step on,
+            # once sigma solves its equation for the state (the energy contains it)
+            s.rk4_step(*f, dt, 1)
+            inv0 = s.invariants(*f)
+            rows = []
+            t0 = time.perf_counter()
+            for k in range(1, marks + 1):
+                s.rk4_step(*f, dt, per)
+                inv = s.invariants(*f)
+                d = s.diagnostics(f[0], f[1], f[2])
+                rows.append({"t": round((1 + k * per) * dt, 6), "dev_h": d["dev_h"], "x_s": d["x_s"],
+                             "mass_drift": (inv[0] - inv0[0]) / abs(inv0[0]),
+                             "energy_drift": (inv[3] - inv0[3]) / abs(inv0[3])})
+            torch.cuda.synchronize()
+            fin[prec] = [x.cpu().numpy() for x in f[:3]]
+            out.setdefault(f"a={a}", {})["fp64" if prec == 0 else "mixed"] = {
+                "marks": rows, "wall_s": time.perf_counter() - t0}
+            s.close()
+        out[f"a={a}"]["mixed_vs_fp64_rel_l2"] = {
+            nm: float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+            for nm, x, y in zip(("h", "vx", "vy"), fin[1], fin[0])}
+    return {"grid": [1024, 256], "box": [[-60.0, 60.0], [-15.0, 15.0]], "eps": 1e-2, "dt": dt, "t_end": tend,
+            "runs": out}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -577,6 +627,7 @@ def run_ours(args, rank, world, local_rank):
                         "tail": diag["tail"]},
         "ensemble": ensemble,
         "crossing_4096": crossing,
+        "transverse": transverse_stability() if (args.transverse and world == 1) else None,
     }
     if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]
