@@ -344,7 +344,7 @@ def time_crossing(st, precision, guess, graph, learned, steps, warmup, tune=True
 def transverse_stability(tend=10.0, dt=2e-3, marks=5):
     """The line solitary wave of amplitude a in {0.2, 0.5, 1.0} on 1024 x 256
     over [-60, 60) x [-15, 15) with h += 1e-2 exp(-x^2) cos(2 pi y/Ly + phi),
-    to t = tend with dt, in FP64 (the paper's method) and precision 1, graph
+    to t = tend with dt, in FP64 (the paper's method), precision 1 and 3, graph
     mode, extrapolated start: the L-infinity deviation from the fitted line
     soliton (Section 4.1) and the relative mass and energy drift (Section 2.3,
     from the state after the first step) at `marks` times, and the final
@@ -360,7 +360,7 @@ def transverse_stability(tend=10.0, dt=2e-3, marks=5):
     for a in (0.2, 0.5, 1.0):
         st = I.perturbed_soliton(1024, 256, 120.0, 30.0, a=a, eps=1e-2, seed=0)
         fin = {}
-        for prec in (0, 1):
+        for prec in (0, 1, 3):
             s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, precision=prec, guess=2, graph=1)
             f = [torch.tensor(x, dtype=torch.float64, device="cuda").contiguous()
                  for x in (st.h, st.vx, st.vy, st.sigma)]
@@ -379,12 +379,12 @@ def transverse_stability(tend=10.0, dt=2e-3, marks=5):
                              "energy_drift": (inv[3] - inv0[3]) / abs(inv0[3])})
             torch.cuda.synchronize()
             fin[prec] = [x.cpu().numpy() for x in f[:3]]
-            out.setdefault(f"a={a}", {})["fp64" if prec == 0 else "mixed"] = {
+            out.setdefault(f"a={a}", {})[{0: "fp64", 1: "mixed", 3: "precision3"}[prec]] = {
                 "marks": rows, "wall_s": time.perf_counter() - t0}
             s.close()
-        out[f"a={a}"]["mixed_vs_fp64_rel_l2"] = {
-            nm: float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
-            for nm, x, y in zip(("h", "vx", "vy"), fin[1], fin[0])}
+        for p, key in ((1, "mixed_vs_fp64_rel_l2"), (3, "precision3_vs_fp64_rel_l2")):
+            out[f"a={a}"][key] = {nm: float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+                                  for nm, x, y in zip(("h", "vx", "vy"), fin[p], fin[0])}
     return {"grid": [1024, 256], "box": [[-60.0, 60.0], [-15.0, 15.0]], "eps": 1e-2, "dt": dt, "t_end": tend,
             "runs": out}
 
@@ -413,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
     # from the last sigma); mixed_paper_start: precision 1 with the paper's
     # start, for attribution
     plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
-            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0))
+            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0), ("mixed_df3_graph", 3, 2, 1))
     solvers = {}
     devfields = {}
     for name, prec, guess, graph in plan:

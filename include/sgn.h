@@ -53,7 +53,13 @@ typedef struct {
                          coefficient pass run in double-float arithmetic (a value is
                          the sum of two FP32 numbers: 48-bit significand, FP32
                          exponent range, so 1/h^3 must stay below ~3e38); the
-                         tolerance test is unchanged */
+                         tolerance test is unchanged;
+                         3 = as 2, with the right-hand side of the RK4 stages (its
+                         transforms, products and the K spectra) in double-float as
+                         well: only the inner GMRES runs in FP32, so the trajectory
+                         follows the FP64 one to its own rounding (for long runs
+                         whose small modes grow, where FP32 right-hand-side rounding
+                         would seed them); also converts the state in double-float */
   int restart;        /* GMRES restart length m, 1..32 (default 20) */
   int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
   double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */

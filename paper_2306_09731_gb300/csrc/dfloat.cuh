@@ -26,6 +26,7 @@
 // the compiler can neither contract a product into an addition nor reorder an
 // error term.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "fft_core.cuh"
@@ -97,7 +98,9 @@ __device__ __forceinline__ float f64_to_f32_bits(double x) {
 // conversions between the storage types of the passes, off the FP64 pipe
 template <typename TO, typename TI>
 __device__ __forceinline__ TO cvt(TI v) {
-  if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8)
+  if constexpr (std::is_same<TI, dfl>::value && std::is_same<TO, double>::value)
+    return dfl_to_f64(v);
+  else if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8)
     return f64_to_f32_bits(v);
   else if constexpr (sizeof(TO) == 8 && sizeof(TI) == 4)
     return f32_to_f64_bits(v);

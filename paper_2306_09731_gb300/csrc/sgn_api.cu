@@ -64,6 +64,7 @@ struct sgn_ctx {
   Tables<dfl> tbd{};
   dfl* crd = nullptr;
   dfl* ccd = nullptr;
+  dfl* hd = nullptr;  // precision 3: h - 1 in double-float for the RHS
   // extrapolated GMRES start (guess = 2): sigma of stage 1 of this step and
   // of stage 3 of the previous step, as half spectra
   C64* sig_s1 = nullptr;
@@ -273,7 +274,7 @@ void build_tables(sgn_ctx* ctx) {
   CK(cudaMemcpy(ctx->tb.twy, ty.data(), G.Ny * sizeof(C64), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.kx, kx.data(), G.Nxh * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.ky, ky.data(), G.Ny * sizeof(double), cudaMemcpyHostToDevice));
-  if (ctx->opt.precision == 2) {
+  if (ctx->opt.precision >= 2) {
     // double-float copies: nearest FP32 pair of each FP64 entry
     std::vector<CDF> dx(G.Nx), dy(G.Ny);
     for (int k = 0; k < G.Nx; ++k) dx[k] = CDF{dfl(tx[k].x), dfl(tx[k].y)};
@@ -335,7 +336,7 @@ CDF* const* tmp_df(sgn_ctx* ctx) { return reinterpret_cast<CDF* const*>(ctx->tmp
 // w = [M^-1] L sigma_hat in the handle's refinement arithmetic: double-float
 // for precision 2, FP64 otherwise
 void refine_matvec(sgn_ctx* ctx, bool precond, const Exec& ex) {
-  if (ctx->opt.precision == 2)
+  if (ctx->opt.precision >= 2)
     CK((launch_matvec_io<dfl, double>(ctx->G, ctx->tbd, ctx->sig, ctx->crd, ctx->ccd, ctx->w, tmp_df(ctx), precond,
                                       ex)));
   else
@@ -344,8 +345,8 @@ void refine_matvec(sgn_ctx* ctx, bool precond, const Exec& ex) {
 
 // coefficient fields from a physical depth h
 void coef_phys(sgn_ctx* ctx, const double* h) {
-  if (ctx->opt.precision == 2)
-    CK(launch_coef_phys<dfl>(ctx->G, h, nullptr, ctx->crd, ctx->ccd, ctx->flags, coef_copy(ctx), EX(ctx)));
+  if (ctx->opt.precision >= 2)
+    CK(launch_coef_phys<dfl>(ctx->G, h, ctx->hd, ctx->crd, ctx->ccd, ctx->flags, coef_copy(ctx), EX(ctx)));
   else
     CK(launch_coef_phys<double>(ctx->G, h, ctx->h, ctx->cr, ctx->cc, ctx->flags, coef_copy(ctx), EX(ctx)));
 }
@@ -392,7 +393,7 @@ void inv1_df(sgn_ctx* ctx, const C64* in, double* out) {
 
 // (h, vx, vy) -> Un, sigma -> sig (spectral); io may be null
 void fwd_state(sgn_ctx* ctx, const double* const* f, const HostIO* io) {
-  const bool df = ctx->opt.precision == 2;
+  const bool df = ctx->opt.precision >= 2;
   if (!io && !df) {
     fwd2(ctx, f, 3, ctx->Un);
     fwd2(ctx, f + 3, 1, &ctx->sig);
@@ -411,7 +412,7 @@ void fwd_state(sgn_ctx* ctx, const double* const* f, const HostIO* io) {
 // Un -> (h, vx, vy), sig -> sigma (physical); with io, each field is copied to
 // io->host[i] on the copy stream once it is ready
 void inv_state(sgn_ctx* ctx, double* const* o, const HostIO* io) {
-  const bool df = ctx->opt.precision == 2;
+  const bool df = ctx->opt.precision >= 2;
   if (!io && !df) {
     inv2(ctx, (const C64* const*)ctx->Un, nullptr, nullptr, 3, o);
     inv2(ctx, (const C64* const*)&ctx->sig, nullptr, nullptr, 1, o + 3);
@@ -453,9 +454,9 @@ void check_flags(sgn_ctx* ctx, int flags) {
 
 // coefficient fields from the spectral depth h_hat
 void coef_from_spectral(sgn_ctx* ctx, const C64* hh) {
-  if (ctx->opt.precision == 2) {
+  if (ctx->opt.precision >= 2) {
     CK(launch_y_inv64<dfl>(ctx->G, ctx->tbd, hh, tmp_df(ctx)[0], EX(ctx, PK_COEF)));
-    CK(launch_coef_x<dfl>(ctx->G, ctx->tbd, tmp_df(ctx)[0], nullptr, ctx->crd, ctx->ccd, ctx->flags,
+    CK(launch_coef_x<dfl>(ctx->G, ctx->tbd, tmp_df(ctx)[0], ctx->hd, ctx->crd, ctx->ccd, ctx->flags,
                           coef_copy(ctx), EX(ctx)));
     return;
   }
@@ -738,6 +739,20 @@ void coarse_alloc(sgn_ctx* ctx, int n, float2** tw, float2** Y) {
   CK(launch_coarse_twiddles(n, *tw, EX(ctx)));
 }
 
+// RHS of state U (K into the RK epilogue) in the handle's arithmetic: FP64
+// (precision 0), FP32 (1, 2) or double-float (3)
+void launch_rhs_ctx(sgn_ctx* ctx, C64* const* U, C64* bnext, const RkArgs& rk) {
+  if (ctx->opt.precision == 3)
+    CK((launch_rhs<dfl, double>(ctx->G, ctx->tbd, ctx->tb, U, ctx->sig, ctx->hd, ctx->crd, tmp_df(ctx), ctx->Un,
+                                ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
+  else if (ctx->opt.precision >= 1)
+    CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32, ctx->Un,
+                                  ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
+  else
+    CK((launch_rhs<double, double>(ctx->G, ctx->tb, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
+                                   ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
+}
+
 // one RK4 stage (s = 1..4) or a plain RHS evaluation (mode RK_STORE_K)
 bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
@@ -769,12 +784,7 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   rk.krasny_thr = ctx->opt.krasny_thr;
   rk.g = ctx->g;
   C64* bnext = mode == RK_STORE_K ? nullptr : ctx->bh;
-  if (ctx->opt.precision >= 1)
-    CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32, ctx->Un,
-                                  ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
-  else
-    CK((launch_rhs<double, double>(ctx->G, ctx->tb, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
-                                   ctx->Us, ctx->acc, bnext, rk, EX(ctx))));
+  launch_rhs_ctx(ctx, U, bnext, rk);
   return conv;
 }
 
@@ -1021,12 +1031,7 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
     rk.krasny = ctx->opt.krasny;
     rk.krasny_thr = ctx->opt.krasny_thr;
     rk.g = ctx->g;
-    if (ctx->opt.precision >= 1)
-      CK((launch_rhs<float, double>(ctx->G, ctx->tb32, ctx->tb, U, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32,
-                                    ctx->Un, ctx->Us, ctx->acc, ctx->bh, rk, EX(ctx))));
-    else
-      CK((launch_rhs<double, double>(ctx->G, ctx->tb, ctx->tb, U, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
-                                     ctx->Us, ctx->acc, ctx->bh, rk, EX(ctx))));
+    launch_rhs_ctx(ctx, U, ctx->bh, rk);
   });
 }
 
@@ -1193,10 +1198,10 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
   sgn_options o;
   sgn_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision < 0 || o.precision > 2)
+  if (o.precision < 0 || o.precision > 3)
     return fail(nullptr, SGN_EINVAL,
-                "sgn_create: precision must be 0 (FP64), 1 (FP32 + FP64 refinement) or 2 (FP32 + double-float "
-                "refinement)");
+                "sgn_create: precision must be 0 (FP64), 1 (FP32 + FP64 refinement), 2 (FP32 + double-float "
+                "refinement) or 3 (precision 2 with a double-float right-hand side)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
   if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2 ||
       (o.graph != 0 && o.graph != 1))
@@ -1225,7 +1230,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     CK(cudaGetDevice(&ctx->device));
     init_kernel_attributes<double>();
     if (o.precision >= 1) init_kernel_attributes<float>();
-    if (o.precision == 2) init_kernel_attributes_df();
+    if (o.precision >= 2) init_kernel_attributes_df();
     build_tables(ctx);
     const size_t ns = G.nspec();
     for (int f = 0; f < 3; ++f) {
@@ -1242,10 +1247,11 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     ctx->cvec = dalloc<C64>(ctx, ns);
     ctx->w = dalloc<C64>(ctx, ns);
     for (int i = 0; i < 4; ++i) ctx->tmp[i] = dalloc<C64>(ctx, ns);
-    if (o.precision == 2) {
+    if (o.precision >= 2) {
       ctx->crd = dalloc<dfl>(ctx, G.nphys());
       ctx->ccd = dalloc<dfl>(ctx, G.nphys());
     }
+    if (o.precision == 3) ctx->hd = dalloc<dfl>(ctx, G.nphys());
     if (o.precision >= 1) {
       ctx->V32 = dalloc<C32>(ctx, ns * (size_t)(o.restart + 1));
       ctx->w32 = dalloc<C32>(ctx, ns);
@@ -1732,12 +1738,7 @@ void tune_run(sgn_ctx* ctx, int op) {
       RkArgs rk{};
       rk.mode = RK_STORE_K;
       rk.g = ctx->g;
-      if (ctx->opt.precision >= 1)
-        CK((launch_rhs<float, double>(G, ctx->tb32, ctx->tb, ctx->Un, ctx->sig, ctx->h32, ctx->cr32, ctx->tmp32,
-                                      ctx->Un, ctx->Us, ctx->acc, nullptr, rk, EX(ctx))));
-      else
-        CK((launch_rhs<double, double>(G, ctx->tb, ctx->tb, ctx->Un, ctx->sig, ctx->h, ctx->cr, ctx->tmp, ctx->Un,
-                                       ctx->Us, ctx->acc, nullptr, rk, EX(ctx))));
+      launch_rhs_ctx(ctx, ctx->Un, nullptr, rk);
     }
   }
 }
@@ -1779,9 +1780,10 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
   std::vector<Job> jobs;
   if (prec >= 1) {
     jobs.push_back({0, TT_F32, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD}, {PK_MV_YINV, PK_MV_X, PK_MV_YFWD}});
-    jobs.push_back({2, prec == 2 ? TT_DFL : TT_F64, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD},
+    jobs.push_back({2, prec >= 2 ? TT_DFL : TT_F64, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD},
                     {PK_REF_YINV, PK_REF_X, PK_REF_YFWD}});
-    jobs.push_back({3, TT_F32, {TP_RHS_YINV, TP_RHS_X, TP_RHS_YFWD}, {PK_RHS_YINV, PK_RHS_X, PK_RHS_YFWD}});
+    jobs.push_back({3, prec == 3 ? TT_DFL : TT_F32, {TP_RHS_YINV, TP_RHS_X, TP_RHS_YFWD},
+                    {PK_RHS_YINV, PK_RHS_X, PK_RHS_YFWD}});
   } else {
     jobs.push_back({1, TT_F64, {TP_MV_YINV, TP_MV_X, TP_MV_YFWD}, {PK_MV_YINV, PK_MV_X, PK_MV_YFWD}});
     jobs.push_back({3, TT_F64, {TP_RHS_YINV, TP_RHS_X, TP_RHS_YFWD}, {PK_RHS_YINV, PK_RHS_X, PK_RHS_YFWD}});

@@ -532,6 +532,9 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 template <typename T, bool INV, int LN = 0, int NIN = 0>
 constexpr int ypass_threads() {
   if (sizeof(T) == 4 && NIN >= 1 && NIN <= 2) return 1024;
+  // double-float RHS passes (three or four transforms): the registers of
+  // 256 threads, as in FP64
+  if (std::is_same<T, dfl>::value && NIN >= 3) return LN == 12 ? 512 : 256;
   return (sizeof(T) == 4 || LN == 12) ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
 }
 
@@ -1237,6 +1240,7 @@ static int y_bound(const Geom& G, int type, int pass) {
   const bool l12 = G.lNy == 12;
   if (type == TT_F32) return nin <= 2 ? 1024 : 512;
   if (type == TT_F64) return l12 ? 512 : 256;
+  if (nin >= 3) return l12 ? 512 : 256;
   return (l12 || !inv) ? 512 : 256;
 }
 static bool is_y_pass(int pass) { return pass <= TP_RHS_YFWD; }
@@ -1515,6 +1519,13 @@ void init_kernel_attributes_df() {
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12, FL_MV_INV>());
   set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12, FL_MV_FWD>());
   set_smem<T>((const void*)ypass_fn<T, true, 1, EpiStore<T, 1>, double, 12>());
+  // precision 3: the double-float RHS
+  set_smem<T>((const void*)k_rhs_x<T, 0>);
+  set_smem<T>((const void*)k_rhs_x<T, 12>);
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 0, fl_rhs_inv<T, 0>()>());
+  set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 12, fl_rhs_inv<T, 12>()>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, FL_RHS_FWD>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 12, FL_RHS_FWD>());
   set_smem<T>((const void*)k_x_r2c<T>);
   set_smem<T>((const void*)k_x_c2r<T>);
   set_smem<T>((const void*)ypass_fn<T, false, 1, EpiStoreF64<T>, T, 0>());
@@ -1694,5 +1705,10 @@ template cudaError_t launch_rhs<float, double>(const Geom&, const Tables<float>&
                                                const float*, cpx<float>* const*, cpx<double>* const*,
                                                cpx<double>* const*, cpx<double>* const*, cpx<double>*,
                                                const RkArgs&, const Exec&);
+template cudaError_t launch_rhs<dfl, double>(const Geom&, const Tables<dfl>&, const Tables<double>&,
+                                             cpx<double>* const*, const cpx<double>*, const dfl*,
+                                             const dfl*, cpx<dfl>* const*, cpx<double>* const*,
+                                             cpx<double>* const*, cpx<double>* const*, cpx<double>*,
+                                             const RkArgs&, const Exec&);
 
 }  // namespace sgn

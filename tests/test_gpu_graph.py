@@ -50,7 +50,7 @@ def run(st, graph, steps, dt, **opts):
 STAT_KEYS = ("matvecs", "solves", "max_iters", "last_iters", "last_relres", "refinements")
 
 
-@pytest.mark.parametrize("precision,guess", [(0, 0), (0, 2), (1, 0), (1, 2), (2, 2)])
+@pytest.mark.parametrize("precision,guess", [(0, 0), (0, 2), (1, 0), (1, 2), (2, 2), (3, 2)])
 def test_graph_matches_host_loop_bitwise(precision, guess):
     st = I.perturbed_soliton(256, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=3)
     a, sa = run(st, 1, 6, 2e-3, precision=precision, guess=guess)
