@@ -55,30 +55,38 @@ __device__ void givens_step(GmresDev* st, int j, GmresReadback* rb, const int* f
   rb->flags = flags ? *flags : 0;
 }
 
-// Fixed-order sum over the NBLK block partials of one slot (valid on thread 0).
-__device__ __forceinline__ double reduce_slot(const double* partials, int slot, double* red) {
+// Fixed-order sum over the first nblk block partials of one slot (slot
+// stride NBLK; valid on thread 0).
+__device__ __forceinline__ double reduce_slot(const double* partials, int slot, double* red, int nblk = NBLK) {
   double v = 0.0;
-  for (int b = threadIdx.x; b < NBLK; b += blockDim.x) v += __ldcg(partials + (size_t)slot * NBLK + b);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += __ldcg(partials + (size_t)slot * NBLK + b);
   return block_reduce(v, red);
 }
 
-// out[s] = sum of the NBLK partials of slot s, s < nslots, one warp per slot:
+// Blocks of the Gram-Schmidt sweeps: one wave at four 256-thread blocks per
+// SM (a sweep is ~7 entries a thread at 2048^2 with NBLK blocks, and the
+// block reductions and the last block's sum over the partials are a fixed
+// cost per block)
+constexpr int KBLK = 608;
+
+// out[s] = sum of the first nblk partials of slot s (slot stride NBLK),
+// s < nslots, one warp per slot:
 // each lane keeps 8 loads in flight over its lane-strided share, then a
 // shuffle tree. The order is fixed, so the sums are deterministic. Up to
 // blockDim/32 slots finish in one round (the slot-by-slot block reduction
 // took one dependent load chain and two barriers per slot).
-__device__ __forceinline__ void reduce_slots(const double* partials, int nslots, double* out) {
+__device__ __forceinline__ void reduce_slots(const double* partials, int nslots, double* out, int nblk = NBLK) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int s = warp; s < nslots; s += nw) {
     const double* p = partials + (size_t)s * NBLK;
     double a[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) a[u] = 0.0;
-    for (int b = lane; b < NBLK; b += 32 * 8) {
+    for (int b = lane; b < nblk; b += 32 * 8) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int bb = b + 32 * u;
-        if (bb < NBLK) a[u] += __ldcg(p + bb);
+        if (bb < nblk) a[u] += __ldcg(p + bb);
       }
     }
     double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
     __syncthreads();  // red is reused by the next chunk
   }
   // the last block combines all partials: out[i] = <V_i, w>, out[nv] = |w|^2
-  if (last_block(counter, threadIdx.x <= DOT_CHUNK)) reduce_slots(partials, nv + 1, out);
+  if (last_block(counter, threadIdx.x <= DOT_CHUNK)) reduce_slots(partials, nv + 1, out, gridDim.x);
 }
 
 // w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
   // step once the orthogonalisation is final. pass: 1 first pass with the DGKS
   // test, 2 second pass, 3 single pass (no reorthogonalisation)
   if (last_block(counter, threadIdx.x == 0)) {
-    const double n2 = reduce_slot(partials, 0, red);
+    const double n2 = reduce_slot(partials, 0, red, gridDim.x);
     if (threadIdx.x == 0) {
       st->nrm2 = n2;
       bool final_pass = (pass == 2);
@@ -561,7 +569,7 @@ cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, 
                         double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
                         const int* jdev) {
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
+  k_dots<T><<<KBLK, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
   ex.end();
   return cudaGetLastError();
 }
@@ -573,7 +581,7 @@ cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, in
   GraphCtl c{};
   if (ctl) c = *ctl;
   ex.begin(PK_KRYLOV);
-  k_cgs_update<T><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate, st, j, pass, counter, rb,
+  k_cgs_update<T><<<KBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate, st, j, pass, counter, rb,
                                          flags, jdev, c);
   ex.end();
   return cudaGetLastError();
