@@ -482,9 +482,12 @@ void arnoldi_step(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, c
   // pass: it only has to reduce its residual by 1e-6 and the FP64 refinement
   // checks the result (measured: same iteration and refinement counts, 4% faster)
   const bool dgks = sizeof(T) == 8;
-  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx)));
+  // the FP32 basis is stored unnormalised (GmresDev::vscl): the update writes
+  // the next basis vector itself, with no scaling pass
+  const double* vscl = dgks ? nullptr : ctx->gst->vscl;
+  CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx), nullptr, vscl));
   CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, j, dgks ? 1 : 3,
-                          cnt + 1, ctx->rb_dev, ctx->flags, EX(ctx)));
+                          cnt + 1, ctx->rb_dev, ctx->flags, EX(ctx), nullptr, nullptr, !dgks));
   if (dgks) {
     CK(launch_dots<T>(G, V, vs, nv, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx)));
     CK(launch_cgs_update<T>(G, V, vs, nv, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, j, 2, cnt + 3,
@@ -628,10 +631,9 @@ bool gmres_mixed(sgn_ctx* ctx, int* iters_out, double* relres_out) {
       const double hnext = ctx->rb_host->hnext;
       k = j + 1;
       if (res_in <= inner_target || its >= ctx->opt.maxit || !(hnext > 0.0) || res_in != res_in) break;
-      if (j + 1 < m) CK(launch_scale<float, float>(G, ctx->w32, &ctx->gst->hnext, true, V + (size_t)(j + 1) * vs, EX(ctx)));
     }
     CK(launch_backsolve(ctx->gst, k, EX(ctx)));
-    CK(launch_axpy_multi<float, double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx)));
+    CK(launch_axpy_multi<float, double>(G, V, vs, k, ctx->gst->y, ctx->sig, EX(ctx), nullptr, ctx->gst->vscl));
     if (ctx->trace)
       fprintf(stderr, "[sgn] mixed sweep: beta/|c| %.3e, inner its %d, inner estimate/|c| %.3e, total its %d\n",
               beta / cnorm, k, res_in / cnorm, its);
@@ -921,17 +923,19 @@ void graph_arnoldi(sgn_ctx* ctx, const Tables<T>& tb, const T* cr, const T* cc, 
   const int* gate = &ctx->gst->reorth;
   unsigned* cnt = ctx->counters;
   const bool dgks = sizeof(T) == 8;
+  const double* vscl = dgks ? nullptr : ctx->gst->vscl;
   CK(launch_matvec<T>(G, tb, V, cr, cc, w, tmp, true, EX(ctx), jd, vs, &ctx->mvt));
-  CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx), jd));
+  CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, nullptr, ctx->gst->h1, cnt + 0, EX(ctx), jd, vscl));
   CK(launch_cgs_update<T>(G, V, vs, m, ctx->gst->h1, w, ctx->partials, nullptr, ctx->gst, 0, dgks ? 1 : 3, cnt + 1,
-                          ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl));
+                          ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl, !dgks));
   if (dgks) {
     CK(launch_dots<T>(G, V, vs, m, w, ctx->partials, gate, ctx->gst->h2, cnt + 2, EX(ctx), jd));
     CK(launch_cgs_update<T>(G, V, vs, m, ctx->gst->h2, w, ctx->partials, gate, ctx->gst, 0, 2, cnt + 3,
                             ctx->rb_dev, ctx->flags, EX(ctx), jd, &ctl));
   }
-  // V_{j+1} = w / H[j+1][j]; j has already advanced (index m is the spare slot)
-  CK(launch_scale<T, T>(G, w, &ctx->gst->hnext, true, V, EX(ctx), jd, vs));
+  // FP64: V_{j+1} = w / H[j+1][j]; j has already advanced (index m is the
+  // spare slot). FP32: the update stored the unnormalised V_{j+1} itself.
+  if (dgks) CK(launch_scale<T, T>(G, w, &ctx->gst->hnext, true, V, EX(ctx), jd, vs));
 }
 
 // One GMRES solve (FP64 or mixed) appended to the top-level segment.
@@ -989,7 +993,8 @@ void graph_gmres(sgn_ctx* ctx, GraphSeg& top) {
   per_sweep += count_launches(ctx, [&] {
     CK(launch_backsolve(ctx->gst, 0, EX(ctx), &ctx->gst->k));
     if (mixed)
-      CK((launch_axpy_multi<float, double>(G, ctx->V32, vs, 0, ctx->gst->y, ctx->sig, EX(ctx), &ctx->gst->k)));
+      CK((launch_axpy_multi<float, double>(G, ctx->V32, vs, 0, ctx->gst->y, ctx->sig, EX(ctx), &ctx->gst->k,
+                                           ctx->gst->vscl)));
     else
       CK((launch_axpy_multi<double, double>(G, ctx->V, vs, 0, ctx->gst->y, ctx->sig, EX(ctx), &ctx->gst->k)));
     CK(launch_ctl_after(ctx->gst, ctl, EX(ctx)));

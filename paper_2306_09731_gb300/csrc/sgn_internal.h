@@ -96,6 +96,9 @@ struct GmresDev {
   double H[(MAXM + 1) * MAXM];  // column-major, H[i + j*(MAXM+1)]
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
   double h1[MAXV + 1], h2[MAXV + 1];  // Gram-Schmidt passes; slot nv holds |w|^2
+  // FP32 inner solve: basis vector i is stored unnormalised, V_i = vscl[i] X_i
+  // (the orthogonalised vector of step i-1, written straight into its slot)
+  double vscl[MAXV + 1];
   double nrm2;                // squared norm of the orthogonalised vector
   int reorth;                 // second pass needed (DGKS test)
   int pad_;
@@ -345,7 +348,7 @@ cudaError_t launch_precond(const Geom& G, const Tables<T>& tb, const cpx<T>* in,
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                         double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
-                        const int* jdev = nullptr);
+                        const int* jdev = nullptr, const double* vscl = nullptr);
 // Gram-Schmidt update w -= sum_i coef[i] V_i of Arnoldi step j; the last block
 // stores |w'|^2, takes the DGKS decision (pass 1) and runs the Givens step once
 // the orthogonalisation is final (pass 1 without reorthogonalisation, pass 2,
@@ -357,7 +360,7 @@ template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
                               unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex,
-                              const int* jdev = nullptr, const GraphCtl* ctl = nullptr);
+                              const int* jdev = nullptr, const GraphCtl* ctl = nullptr, bool scaled = false);
 // r = c - w, and partial squared norm of r
 template <typename T>
 cudaError_t launch_residual(const Geom& G, const cpx<T>* c, const cpx<T>* w, cpx<T>* r, double* partials,
@@ -370,7 +373,7 @@ cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, 
 // x += sum_i coef[i] V_i (V in TV, x in TX); ndev (may be null): nv = *ndev
 template <typename TV, typename TX>
 cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
-                              cpx<TX>* x, const Exec& ex, const int* ndev = nullptr);
+                              cpx<TX>* x, const Exec& ex, const int* ndev = nullptr, const double* vscl = nullptr);
 // x = 0; gate (may be null): only if *gate != 0
 template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex, const int* gate = nullptr);

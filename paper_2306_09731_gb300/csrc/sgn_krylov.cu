@@ -143,7 +143,7 @@ constexpr int DOT_CHUNK = 4;  // dot products per sweep of a block's entries
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                                                  double* partials, const int* gate, double* out,
-                                                 unsigned* counter, const int* jdev) {
+                                                 unsigned* counter, const int* jdev, const double* vscl) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   if (jdev) nv = *jdev + 1;
@@ -187,7 +187,18 @@ __global__ void __launch_bounds__(256, 4) k_dots(Geom G, const cpx<T>* V, size_t
     __syncthreads();  // red is reused by the next chunk
   }
   // the last block combines all partials: out[i] = <V_i, w>, out[nv] = |w|^2
-  if (last_block(counter, threadIdx.x <= DOT_CHUNK)) reduce_slots(partials, nv + 1, out, gridDim.x);
+  if (last_block(counter, threadIdx.x <= DOT_CHUNK)) {
+    reduce_slots(partials, nv + 1, out, gridDim.x);
+    // scaled basis (vscl): V_i = s_i X_i and w = s_j w~ for the stored X_i and
+    // the matvec of X_j: <V_i, w> = s_i s_j <X_i, w~>, |w|^2 = s_j^2 |w~|^2
+    if (vscl) {
+      __syncthreads();
+      if ((int)threadIdx.x <= nv) {
+        const double sj = vscl[nv - 1];
+        out[threadIdx.x] *= ((int)threadIdx.x < nv ? vscl[threadIdx.x] : sj) * sj;
+      }
+    }
+  }
 }
 
 // w -= sum_i coef[i] V_i (i < nv) and |w_new|^2 into slot 0. Gated like k_dots.
@@ -205,12 +216,16 @@ __device__ __forceinline__ void ctl_step(GmresDev* st, int j, const GraphCtl& ct
   cudaGraphSetConditional(ctl.h_step, stop ? 0u : 1u);
 }
 
+// scaled (FP32 inner solve): the basis is stored unnormalised, V_i = s_i X_i
+// (s = st->vscl) and w holds w~ = A X_j; the kernel writes X_{j+1} = w~ -
+// sum_i (h_i s_i / s_j) X_i = w' / s_j straight into slot j+1 of V (no scaling
+// pass), |w'|^2 = s_j^2 |X_{j+1}|^2, and s_{j+1} = s_j / |w'|.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, size_t vstride, int nv,
                                                     const double* __restrict__ coef, cpx<T>* w, double* partials,
                                                     const int* gate, GmresDev* st, int j, int pass,
                                                     unsigned* counter, GmresReadback* rb, const int* flags,
-                                                    const int* jdev, GraphCtl ctl) {
+                                                    const int* jdev, GraphCtl ctl, int scaled) {
   typedef typename Acc<T>::type A;
   if (gate && *gate == 0) return;
   if (jdev) {
@@ -219,8 +234,13 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
   }
   __shared__ double red[32];
   __shared__ A cf[MAXV + 4];
-  if (threadIdx.x < MAXV + 4) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
+  if (threadIdx.x < MAXV + 4) {
+    double c = threadIdx.x < nv ? coef[threadIdx.x] : 0.0;
+    if (scaled && threadIdx.x < nv) c *= st->vscl[threadIdx.x] / st->vscl[j];
+    cf[threadIdx.x] = (A)c;
+  }
   __syncthreads();
+  cpx<T>* wout = scaled ? const_cast<cpx<T>*>(V) + (size_t)(j + 1) * vstride : w;
   A nrm = (A)0;
   // two interleaved walkers; four basis vectors per round with predicated
   // loads rather than a remainder loop, so that a round's loads (8 entries)
@@ -244,10 +264,10 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
       zby -= (cf[i] * (A)vb[0].y + cf[i + 1] * (A)vb[1].y) + (cf[i + 2] * (A)vb[2].y + cf[i + 3] * (A)vb[3].y);
     }
     const cpx<T> za = mk((T)zax, (T)zay), zb = mk((T)zbx, (T)zby);
-    w[a.e] = za;
+    wout[a.e] = za;
     nrm += col_weight_k<A>(G, a.col) * ((A)za.x * (A)za.x + (A)za.y * (A)za.y);
     if (bok) {
-      w[b.e] = zb;
+      wout[b.e] = zb;
       nrm += col_weight_k<A>(G, b.col) * ((A)zb.x * (A)zb.x + (A)zb.y * (A)zb.y);
     }
   }
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
   if (last_block(counter, threadIdx.x == 0)) {
     const double n2 = reduce_slot(partials, 0, red, gridDim.x);
     if (threadIdx.x == 0) {
-      st->nrm2 = n2;
+      st->nrm2 = scaled ? n2 * st->vscl[j] * st->vscl[j] : n2;
       bool final_pass = (pass == 2);
       if (pass == 1 || pass == 3) {
         // pass 3: first pass of an Arnoldi step that never reorthogonalises
@@ -275,6 +295,7 @@ __global__ void __launch_bounds__(256) k_cgs_update(Geom G, const cpx<T>* V, siz
       if (ctl.enabled) cudaGraphSetConditional(ctl.h_step, 0u);
       if (final_pass) {
         givens_step(st, j, rb, flags);
+        if (scaled) st->vscl[j + 1] = st->hnext > 0.0 ? st->vscl[j] / st->hnext : 0.0;
         if (ctl.enabled) ctl_step(st, j, ctl);
       }
     }
@@ -314,12 +335,14 @@ __global__ void k_scale(Geom G, const cpx<TI>* x, const double* factor, int inve
 // to match the FP32 basis) and added to x in x's type.
 template <typename TV, typename TX>
 __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, const double* __restrict__ coef,
-                             cpx<TX>* x, const int* ndev) {
+                             cpx<TX>* x, const int* ndev, const double* vscl) {
   typedef typename Acc<TV>::type A;
   if (ndev) nv = *ndev;
   if (nv <= 0) return;
   __shared__ A cf[MAXV];
-  if (threadIdx.x < MAXV) cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] : 0.0);
+  // scaled basis (vscl): V_i = s_i X_i
+  if (threadIdx.x < MAXV)
+    cf[threadIdx.x] = (A)(threadIdx.x < nv ? coef[threadIdx.x] * (vscl ? vscl[threadIdx.x] : 1.0) : 0.0);
   __syncthreads();
   for (Walk it(G); it.ok(); it.next()) {
     A dx = (A)0, dy = (A)0;
@@ -381,6 +404,7 @@ __global__ void k_gmres_start(GmresDev* st, const double* beta) {
   for (int i = 0; i <= MAXM; ++i) st->g[i] = 0.0;
   st->g[0] = *beta;
   st->res = *beta;
+  st->vscl[0] = 1.0;
 }
 
 // Column j of the Hessenberg matrix from the two CGS passes and the norm,
@@ -440,6 +464,7 @@ __global__ void k_ctl_sweep(GmresDev* st, const double* beta_d, GraphCtl ctl) {
   st->beta = beta;
   st->k = 0;
   st->j = 0;
+  st->vscl[0] = 1.0;
   st->sweeps += 1;
   st->tot_sweeps += 1;
   const bool done = !(beta > st->target);
@@ -567,9 +592,9 @@ __global__ void __launch_bounds__(256) k_invariant_sums(Geom G, const double* h,
 template <typename T>
 cudaError_t launch_dots(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const cpx<T>* w,
                         double* partials, const int* gate, double* out, unsigned* counter, const Exec& ex,
-                        const int* jdev) {
+                        const int* jdev, const double* vscl) {
   ex.begin(PK_KRYLOV);
-  k_dots<T><<<KBLK, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev);
+  k_dots<T><<<KBLK, 256, 0, ex.s>>>(G, V, vstride, nv, w, partials, gate, out, counter, jdev, vscl);
   ex.end();
   return cudaGetLastError();
 }
@@ -577,12 +602,12 @@ template <typename T>
 cudaError_t launch_cgs_update(const Geom& G, const cpx<T>* V, size_t vstride, int nv, const double* coef,
                               cpx<T>* w, double* partials, const int* gate, GmresDev* st, int j, int pass,
                               unsigned* counter, GmresReadback* rb, const int* flags, const Exec& ex,
-                              const int* jdev, const GraphCtl* ctl) {
+                              const int* jdev, const GraphCtl* ctl, bool scaled) {
   GraphCtl c{};
   if (ctl) c = *ctl;
   ex.begin(PK_KRYLOV);
   k_cgs_update<T><<<KBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, w, partials, gate, st, j, pass, counter, rb,
-                                         flags, jdev, c);
+                                         flags, jdev, c, scaled ? 1 : 0);
   ex.end();
   return cudaGetLastError();
 }
@@ -604,9 +629,9 @@ cudaError_t launch_scale(const Geom& G, const cpx<TI>* x, const double* factor, 
 }
 template <typename TV, typename TX>
 cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, int nv, const double* coef,
-                              cpx<TX>* x, const Exec& ex, const int* ndev) {
+                              cpx<TX>* x, const Exec& ex, const int* ndev, const double* vscl) {
   ex.begin(PK_KRYLOV);
-  k_axpy_multi<TV, TX><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x, ndev);
+  k_axpy_multi<TV, TX><<<NBLK, 256, 0, ex.s>>>(G, V, vstride, nv, coef, x, ndev, vscl);
   ex.end();
   return cudaGetLastError();
 }
@@ -708,11 +733,12 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
 
 #define SGN_KRYLOV_INST(T)                                                                                   \
   template cudaError_t launch_dots<T>(const Geom&, const cpx<T>*, size_t, int, const cpx<T>*, double*,       \
-                                      const int*, double*, unsigned*, const Exec&, const int*);             \
+                                      const int*, double*, unsigned*, const Exec&, const int*,              \
+                                      const double*);                                                      \
   template cudaError_t launch_cgs_update<T>(const Geom&, const cpx<T>*, size_t, int, const double*, cpx<T>*, \
                                             double*, const int*, GmresDev*, int, int, unsigned*,            \
                                             GmresReadback*, const int*, const Exec&, const int*,            \
-                                            const GraphCtl*);                                               \
+                                            const GraphCtl*, bool);                                         \
   template cudaError_t launch_residual<T>(const Geom&, const cpx<T>*, const cpx<T>*, cpx<T>*, double*,       \
                                           const Exec&);                                                     \
   template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&, const int*);                       \
@@ -728,8 +754,10 @@ template cudaError_t launch_scale<double, float>(const Geom&, const cpx<double>*
 template cudaError_t launch_scale<float, float>(const Geom&, const cpx<float>*, const double*, bool,
                                                 cpx<float>*, const Exec&, const int*, size_t);
 template cudaError_t launch_axpy_multi<double, double>(const Geom&, const cpx<double>*, size_t, int,
-                                                       const double*, cpx<double>*, const Exec&, const int*);
+                                                       const double*, cpx<double>*, const Exec&, const int*,
+                                                       const double*);
 template cudaError_t launch_axpy_multi<float, double>(const Geom&, const cpx<float>*, size_t, int,
-                                                      const double*, cpx<double>*, const Exec&, const int*);
+                                                      const double*, cpx<double>*, const Exec&, const int*,
+                                                      const double*);
 
 }  // namespace sgn
