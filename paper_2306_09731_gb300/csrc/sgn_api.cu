@@ -2,8 +2,8 @@
 //
 // The handle owns every device buffer. The RK4 state lives in spectral form
 // (half spectra of h, vx, vy) between steps; sigma_hat is the GMRES warm start
-// carried from stage to stage and step to step (Section 3: "started with the
-// last computed value"). One stage is:
+// carried from stage to stage and step to step (Section 3: each solve
+// starts from the previous solve's sigma). One stage is:
 //   coefficients  h, 1/(2N h), 3/(2N h^3) from h_hat        (y-inverse + x-pass)
 //   GMRES         L sigma = b, b_hat = -(i kx vx + i ky vy) (Eq. (sigmav))
 //   RHS + update  K = (h_t, v_t) and the RK4 stage update  (3 fused passes)

@@ -1,7 +1,7 @@
 // sgn_diag.cu - the monitoring quantities of the paper's experiments.
 //
-// Sections 4.1 and 4.2 judge the transverse stability of line solitary waves
-// by the L-infinity norm of h and where it is reached, by the speed of the
+// Sections 4.1 and 4.2 test line solitary waves against transverse
+// perturbations by the L-infinity norm of h and where it is reached, by the speed of the
 // solitary wave of Eq. (sol) with that crest, and by the difference between
 // the computed state and that solitary wave; Section 3 reads resolution from
 // the decay of the DFT coefficients. Each quantity is a grid-wide max: one

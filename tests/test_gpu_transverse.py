@@ -1,4 +1,4 @@
-"""Transverse stability of the line solitary wave on 1024 x 256 over
+"""A perturbed line soliton, stepped on 1024 x 256 over
 [-60, 60) x [-15, 15): a in {0.2, 0.5, 1.0}, h += 1e-2 exp(-x^2) cos(2 pi y/Ly
 + phi) (seeded phase), dt = 2e-3; FP64 (the paper's method) against the FP32
 bulk with FP64 refinement (precision 1).
