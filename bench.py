@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-crossing", action="store_true",
                     help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
-                                                 "mixed_df_graph, fp64, mixed_paper_start)")
+                                                 "mixed_df_graph, fp64, mixed_paper_start, mixed_df3_graph, "
+                                                 "mixed_df3_poly_graph, fp64_poly)")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
                     help="headline is the mixed path when it runs; both also times plain FP64")
     return ap.parse_args()
@@ -411,15 +412,19 @@ def run_ours(args, rank, world, local_rank):
     # double-float arithmetic (precision 2); *_graph: the same kernels with each
     # RK4 step replayed as a CUDA graph; fp64: the paper's method (FP64, start
     # from the last sigma); mixed_paper_start: precision 1 with the paper's
-    # start, for attribution
+    # start, for attribution; *_poly*: each stage started from the polynomial
+    # in time through the same stage's sigma of the last 3-4 steps (guess 3),
+    # on the paths whose right-hand side is not FP32 (with the FP32 one the
+    # rounding noise of the stage states limits that start)
     plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
-            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0), ("mixed_df3_graph", 3, 2, 1))
+            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0), ("mixed_df3_graph", 3, 2, 1),
+            ("mixed_df3_poly_graph", 3, 3, 1), ("fp64_poly", 0, 3, 0))
     solvers = {}
     devfields = {}
     for name, prec, guess, graph in plan:
         if args.path == "mixed" and not name.startswith("mixed"):
             continue
-        if args.path == "fp64" and name != "fp64":
+        if args.path == "fp64" and not name.startswith("fp64"):
             continue
         if args.no_graph and graph:
             continue
@@ -629,6 +634,10 @@ def run_ours(args, rank, world, local_rank):
         "crossing_4096": crossing,
         "transverse": transverse_stability() if (args.transverse and world == 1) else None,
     }
+    if "fp64_poly" in paths:
+        fp = paths["fp64_poly"]
+        out["fp64_poly_start"] = {"value": fp["value"], "unit": UNIT, "ms_per_step": fp["ms_per_step"],
+                                  "gmres": fp["gmres"]}
     if "fp64" in paths and head_name != "fp64":
         f64 = paths["fp64"]
         out["fp64_plain"] = {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],

@@ -72,7 +72,14 @@ typedef struct {
                          sigma(t + dt/2) and sigma(t)); the previous step's sigma is kept
                          from the handle's last RK4 call when the new call has the same dt
                          and its input state is that call's output (within 1e-8 of the
-                         largest Fourier coefficient); every solve still meets tol */
+                         largest Fourier coefficient); every solve still meets tol;
+                         3 = guess 2 until the handle has solved 3 steps of the
+                         trajectory, then each stage starts from the polynomial in time
+                         through the same stage's sigma of the last 3 (quadratic) or 4
+                         (cubic) steps: O(dt^3) / O(dt^4) against guess 2's O(dt^2);
+                         it keeps 16 spectra of history (16 * Ny * (Nx/2 + 2) complex
+                         doubles), carried across calls by guess 2's rule; the learned
+                         start (sgn_set_learned_guess) is not available with it */
   int graph;          /* 1: sgn_rk4_step and sgn_rk4_step_host run each RK4 step as one
                          CUDA graph whose GMRES loops are conditional WHILE nodes driven
                          by device-side tests (no host synchronisation inside the call;
@@ -301,7 +308,8 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out);
  * sigma's spectrum (with guess = 2, not at stage 2 of a call's first step,
  * which has no extrapolation history). Every solve still meets opt.tol. n
  * must be a power of two in [16, min(Nx, Ny)] and equal to the network's side;
- * net = NULL detaches.
+ * net = NULL detaches. SGN_EINVAL on a handle with guess = 3, whose start
+ * needs no correction of this kind (sgn_record_learned refuses it too).
  * The network runs on the handle's stream (it is re-pointed there). */
 sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_scale[4], float out_scale,
                                  int tau_power);

@@ -70,6 +70,9 @@ struct sgn_ctx {
   C64* sig_s1 = nullptr;
   C64* sig_s3 = nullptr;
   bool have_s3 = false;
+  // polynomial start across steps (guess = 3): 4 steps x 4 stages of sigma
+  C64* ext_ring = nullptr;
+  ExtHist* ext = nullptr;
   // The extrapolation history across calls: hist_ok after an RK4 call with
   // guess = 2 (cleared by every other call), hist_keep its value when the
   // current call began, hist_dt that call's dt.
@@ -674,7 +677,7 @@ void learned_pre(sgn_ctx* ctx, C64* const* U, int mode, double dt, bool graph = 
   // with the extrapolated start, stage 2 of a call's first step has no
   // stage-3 history and starts from sigma_1 instead: a start of another kind,
   // left alone (graph mode tests the device flag)
-  const bool s2_plain = ctx->opt.guess == 2 && mode == RK_STAGE2;
+  const bool s2_plain = ctx->opt.guess >= 2 && mode == RK_STAGE2;
   if (s2_plain && !graph && !ctx->have_s3) return;
   const Geom& G = ctx->G;
   if (ctx->rec_buf && ctx->rec_count < ctx->rec_cap) {
@@ -760,23 +763,29 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
   coef_from_spectral(ctx, U[0]);
   if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
-  if (ctx->opt.guess == 2) {
+  if (ctx->opt.guess >= 2) {
     // linear extrapolation in time over the stage times t, t+dt/2, t+dt/2, t+dt:
     // stage 2 from sigma(t) and the previous step's sigma(t - dt/2),
     // stage 4 from sigma(t + dt/2) and sigma(t)
     if (mode == RK_STAGE2 && ctx->have_s3) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx)));
     if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
   }
+  const bool ext = ctx->opt.guess == 3 && mode != RK_STORE_K;
+  if (ext) CK(launch_ext_start(ctx->G, ctx->ext_ring, mode, ctx->ext, ctx->sig, EX(ctx)));
   learned_pre(ctx, U, mode, dt);
   const bool conv = gmres(ctx, nullptr, nullptr);
   learned_post(ctx, dt);
-  if (ctx->opt.guess == 2) {
+  if (ctx->opt.guess >= 2) {
     const size_t bytes = ctx->G.nspec() * sizeof(C64);
     if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (mode == RK_STAGE3) {
       CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       ctx->have_s3 = true;
     }
+  }
+  if (ext) {
+    CK(launch_ext_store(ctx->G, ctx->sig, ctx->ext_ring, mode, ctx->ext, EX(ctx)));
+    if (mode == RK_FINAL) CK(launch_ext_advance(ctx->ext, EX(ctx)));
   }
   RkArgs rk{};
   rk.mode = mode;
@@ -808,7 +817,7 @@ void ensure_phys(sgn_ctx* ctx) {
 // call's conversions overwrite it; same_state_flag() compares and writes the
 // device flag gst->have_s3.
 bool continues_history(sgn_ctx* ctx, double dt) {
-  if (ctx->opt.guess != 2 || !ctx->hist_keep || dt != ctx->hist_dt) return false;
+  if (ctx->opt.guess < 2 || !ctx->hist_keep || dt != ctx->hist_dt) return false;
   const size_t bytes = ctx->G.nspec() * sizeof(C64);
   for (int f = 0; f < 3; ++f)
     CK(cudaMemcpyAsync(ctx->acc[f], ctx->Un[f], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -819,6 +828,15 @@ void same_state_flag(sgn_ctx* ctx) {
   const C64* b[3] = {ctx->Un[0], ctx->Un[1], ctx->Un[2]};
   CK(launch_same_state(ctx->G, a, b, 1e-8, ctx->partials, ctx->counters + 6, &ctx->gst->have_s3, EX(ctx)));
 }
+// guess = 3: the ring's steps stay only when the call continues the trajectory
+// (cont, and the device flag same_state_flag() wrote)
+void ext_history(sgn_ctx* ctx, bool cont) {
+  if (ctx->opt.guess != 3) return;
+  if (cont)
+    CK(launch_ext_keep(ctx->ext, &ctx->gst->have_s3, EX(ctx)));
+  else
+    CK(launch_set_int(&ctx->ext->levels, 0, EX(ctx)));
+}
 
 void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
                 bool* conv_all, const HostIO* io = nullptr) {
@@ -828,8 +846,9 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
   fwd_state(ctx, f4, io);
   CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
   ctx->have_s3 = false;
+  if (cont) same_state_flag(ctx);
+  ext_history(ctx, cont);
   if (cont) {
-    same_state_flag(ctx);
     int keep = 0;
     CK(cudaMemcpyAsync(&keep, &ctx->gst->have_s3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -845,7 +864,7 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
   double* o4[4] = {h, vx, vy, sigma};
   inv_state(ctx, o4, io);
   *conv_all = conv;
-  ctx->hist_ok = ctx->opt.guess == 2;
+  ctx->hist_ok = ctx->opt.guess >= 2;
   ctx->hist_dt = dt;
 }
 
@@ -1013,21 +1032,26 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
   ctx->graph_fixed += count_launches(ctx, [&] {
     coef_from_spectral(ctx, U[0]);
     if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
-    if (ctx->opt.guess == 2) {
+    if (ctx->opt.guess >= 2) {
       if (mode == RK_STAGE2)
         CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx), &ctx->gst->have_s3));
       if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
     }
+    if (ctx->opt.guess == 3) CK(launch_ext_start(ctx->G, ctx->ext_ring, mode, ctx->ext, ctx->sig, EX(ctx)));
     learned_pre(ctx, U, mode, dt, true);  // no recording in graph mode (sgn_record_learned refuses it)
   });
   graph_gmres(ctx, top);
   ctx->graph_fixed += count_launches(ctx, [&] {
-    if (ctx->opt.guess == 2) {
+    if (ctx->opt.guess >= 2) {
       if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       if (mode == RK_STAGE3) {
         CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(launch_set_int(&ctx->gst->have_s3, 1, EX(ctx)));
       }
+    }
+    if (ctx->opt.guess == 3) {
+      CK(launch_ext_store(ctx->G, ctx->sig, ctx->ext_ring, mode, ctx->ext, EX(ctx)));
+      if (mode == RK_FINAL) CK(launch_ext_advance(ctx->ext, EX(ctx)));
     }
     RkArgs rk{};
     rk.mode = mode;
@@ -1141,6 +1165,7 @@ void rk4_graph_enqueue(sgn_ctx* ctx, double* h, double* vx, double* vy, double* 
   const bool cont = continues_history(ctx, dt);
   fwd_state(ctx, f4, io);
   if (cont) same_state_flag(ctx);
+  ext_history(ctx, cont);
   ctx->hist_dt = dt;
   CK(launch_spec_div<double>(ctx->G, ctx->tb, ctx->Un[1], ctx->Un[2], ctx->bh, EX(ctx)));
   for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
@@ -1165,7 +1190,7 @@ void rk4_graph_finish(sgn_ctx* ctx, int nsteps, bool* conv_all) {
                         st.tot_its * ctx->graph_per_step;
   check_flags(ctx, ctx->rb_host->flags);
   *conv_all = st.notconv == 0;
-  ctx->hist_ok = ctx->opt.guess == 2;
+  ctx->hist_ok = ctx->opt.guess >= 2;
 }
 
 void rk4_device_graph(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
@@ -1208,7 +1233,7 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
                 "sgn_create: precision must be 0 (FP64), 1 (FP32 + FP64 refinement), 2 (FP32 + double-float "
                 "refinement) or 3 (precision 2 with a double-float right-hand side)");
   if (o.restart < 1 || o.restart > MAXM) return fail(nullptr, SGN_EINVAL, "sgn_create: restart must be in [1, 32]");
-  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 2 ||
+  if (o.maxit < 1 || !(o.tol >= 0.0) || !(o.krasny_thr >= 0.0) || o.guess < 0 || o.guess > 3 ||
       (o.graph != 0 && o.graph != 1))
     return fail(nullptr, SGN_EINVAL, "sgn_create: bad maxit, tol, krasny_thr, guess or graph");
   sgn_ctx* ctx = new (std::nothrow) sgn_ctx();
@@ -1244,9 +1269,13 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
       ctx->acc[f] = dalloc<C64>(ctx, ns);
     }
     ctx->sig = dalloc<C64>(ctx, ns);
-    if (o.guess == 2) {
+    if (o.guess >= 2) {
       ctx->sig_s1 = dalloc<C64>(ctx, ns);
       ctx->sig_s3 = dalloc<C64>(ctx, ns);
+    }
+    if (o.guess == 3) {
+      ctx->ext_ring = dalloc<C64>(ctx, 16 * ns);
+      ctx->ext = dalloc<ExtHist>(ctx, 1);
     }
     ctx->bh = dalloc<C64>(ctx, ns);
     ctx->cvec = dalloc<C64>(ctx, ns);
@@ -1598,6 +1627,8 @@ sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_sca
     ctx->net = nullptr;
     return SGN_OK;
   }
+  if (ctx->opt.guess == 3)
+    return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: the learned start corrects the starts of guess 0, 1 and 2");
   sgn_unet_t u = static_cast<sgn_unet_t>(net);
   if (!coarse_side_ok(ctx, n) || sgn_unet_side(u) != n)
     return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: n must be a power of two in [16, min(Nx, Ny)] and the "
@@ -1626,6 +1657,8 @@ sgn_status sgn_record_learned(sgn_t ctx, int n, float* buf, int capacity, int ta
     return SGN_OK;
   }
   if (ctx->opt.graph) return fail(ctx, SGN_EINVAL, "sgn_record_learned: needs the host-driven loop (graph = 0)");
+  if (ctx->opt.guess == 3)
+    return fail(ctx, SGN_EINVAL, "sgn_record_learned: the learned start corrects the starts of guess 0, 1 and 2");
   if (!coarse_side_ok(ctx, n) || capacity < 1 || tau_power < 0 || tau_power > 2)
     return fail(ctx, SGN_EINVAL, "sgn_record_learned: bad n, capacity or tau_power");
   if (ctx->rec_n != n) {

@@ -396,6 +396,24 @@ cudaError_t launch_ctl_begin(GmresDev* st, const double* cnorm, GraphCtl ctl, co
 cudaError_t launch_ctl_sweep(GmresDev* st, const double* beta, GraphCtl ctl, const Exec& ex);
 cudaError_t launch_ctl_after(GmresDev* st, GraphCtl ctl, const Exec& ex);
 cudaError_t launch_set_int(int* p, int v, const Exec& ex);
+// Polynomial start across steps (guess = 3): the ring holds each RK4 stage's
+// solved sigma over the last 4 steps, slot (q, s) at ring + (4 q + s - 1) *
+// nspec, q in 0..3, s in 1..4 (see sgn_krylov.cu).
+struct ExtHist {
+  int levels;  // steps held, 0..4
+  int head;    // slot q of the step being taken
+};
+// sigma = the quadratic (levels 3) or cubic (levels 4) extrapolation of stage
+// s from the ring; with fewer levels sigma is left as it is
+cudaError_t launch_ext_start(const Geom& G, const cpx<double>* ring, int s, const ExtHist* hist, cpx<double>* sig,
+                             const Exec& ex);
+// ring slot (head, s) = sigma
+cudaError_t launch_ext_store(const Geom& G, const cpx<double>* sig, cpx<double>* ring, int s, const ExtHist* hist,
+                             const Exec& ex);
+// after a step's last stage: head advances, levels += 1 (at most 4)
+cudaError_t launch_ext_advance(ExtHist* hist, const Exec& ex);
+// levels = 0 unless *flag
+cudaError_t launch_ext_keep(ExtHist* hist, const int* flag, const Exec& ex);
 // *flag = 1 if the three spectra b equal a within rel * max|a| (see sgn_krylov.cu)
 cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const cpx<double>* const* b, double rel,
                               double* partials, unsigned* counter, int* flag, const Exec& ex);

@@ -507,6 +507,59 @@ __global__ void k_set_int(int* p, int v) {
   if (threadIdx.x == 0) *p = v;
 }
 
+// Polynomial start across steps. With a fixed dt, the sigma that stage s
+// solves for is a smooth function of the step's start time, so the values of
+// the last steps at equal spacing predict the next by the polynomial through
+// them: Newton's backward differences give 3, -3, 1 (quadratic, 3 steps) and
+// 4, -6, 4, -1 (cubic, 4 steps), with error O(dt^3) and O(dt^4) against the
+// O(dt^2) of the linear extrapolation inside a step. Slot (q, s) of the ring
+// is ring + (4 q + s - 1) vs; hist->head is the slot q of the current step.
+__device__ __forceinline__ const cpx<double>* ext_slot(const cpx<double>* ring, size_t vs, int q, int s) {
+  return ring + (size_t)(4 * (q & 3) + s - 1) * vs;
+}
+
+__global__ void k_ext_start(Geom G, const cpx<double>* ring, size_t vs, int s, const ExtHist* hist,
+                            cpx<double>* sig) {
+  const int lv = hist->levels;
+  if (lv < 3) return;
+  const int head = hist->head;
+  const cpx<double>* p0 = ext_slot(ring, vs, head - 1, s);
+  const cpx<double>* p1 = ext_slot(ring, vs, head - 2, s);
+  const cpx<double>* p2 = ext_slot(ring, vs, head - 3, s);
+  if (lv >= 4) {
+    const cpx<double>* p3 = ext_slot(ring, vs, head - 4, s);
+    for (Walk it(G); it.ok(); it.next()) {
+      const cpx<double> a = p0[it.e], b = p1[it.e], c = p2[it.e], d = p3[it.e];
+      sig[it.e] = mk(4.0 * a.x - 6.0 * b.x + 4.0 * c.x - d.x, 4.0 * a.y - 6.0 * b.y + 4.0 * c.y - d.y);
+    }
+  } else {
+    for (Walk it(G); it.ok(); it.next()) {
+      const cpx<double> a = p0[it.e], b = p1[it.e], c = p2[it.e];
+      sig[it.e] = mk(3.0 * (a.x - b.x) + c.x, 3.0 * (a.y - b.y) + c.y);
+    }
+  }
+}
+
+__global__ void k_ext_store(Geom G, const cpx<double>* sig, cpx<double>* ring, size_t vs, int s,
+                            const ExtHist* hist) {
+  cpx<double>* dst = ring + (size_t)(4 * (hist->head & 3) + s - 1) * vs;
+  for (Walk it(G); it.ok(); it.next()) dst[it.e] = sig[it.e];
+}
+
+// end of a step: its slot becomes the newest level
+__global__ void k_ext_advance(ExtHist* hist) {
+  if (threadIdx.x == 0) {
+    hist->head = (hist->head + 1) & 3;
+    hist->levels = min(hist->levels + 1, 4);
+  }
+}
+
+// start of a call: keep the levels only if *flag (the call continues the
+// trajectory the handle returned last)
+__global__ void k_ext_keep(ExtHist* hist, const int* flag) {
+  if (threadIdx.x == 0 && *flag == 0) hist->levels = 0;
+}
+
 // *flag = 1 when every component of the three spectra b is within rel * max|a|
 // of a's (a: the state the handle returned last, b: a call's input state),
 // else 0 (NaN counts as a difference). Block maxima in partials, combined by
@@ -712,6 +765,33 @@ cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const 
 cudaError_t launch_set_int(int* p, int v, const Exec& ex) {
   ex.begin(PK_KRYLOV);
   k_set_int<<<1, 32, 0, ex.s>>>(p, v);
+  ex.end();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ext_start(const Geom& G, const cpx<double>* ring, int s, const ExtHist* hist, cpx<double>* sig,
+                             const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ext_start<<<NBLK, 256, 0, ex.s>>>(G, ring, G.nspec(), s, hist, sig);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_ext_store(const Geom& G, const cpx<double>* sig, cpx<double>* ring, int s, const ExtHist* hist,
+                             const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ext_store<<<NBLK, 256, 0, ex.s>>>(G, sig, ring, G.nspec(), s, hist);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_ext_advance(ExtHist* hist, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ext_advance<<<1, 32, 0, ex.s>>>(hist);
+  ex.end();
+  return cudaGetLastError();
+}
+cudaError_t launch_ext_keep(ExtHist* hist, const int* flag, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_ext_keep<<<1, 32, 0, ex.s>>>(hist, flag);
   ex.end();
   return cudaGetLastError();
 }
