@@ -76,7 +76,10 @@ typedef struct {
                          3 = guess 2 until the handle has solved 3 steps of the
                          trajectory, then each stage starts from the polynomial in time
                          through the same stage's sigma of the last 3 (quadratic) or 4
-                         (cubic) steps: O(dt^3) / O(dt^4) against guess 2's O(dt^2);
+                         (cubic) steps: O(dt^3) / O(dt^4) against guess 2's O(dt^2)
+                         (with the FP32 right-hand side of precisions 1 and 2 the
+                         rounding noise of the stage states bounds that gain, and near
+                         rest it is gone);
                          it keeps 16 spectra of history (16 * Ny * (Nx/2 + 2) complex
                          doubles), carried across calls by guess 2's rule; the learned
                          start (sgn_set_learned_guess) is not available with it */
