@@ -53,7 +53,8 @@ def parse():
                     help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
     ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
                                                  "mixed_df_graph, fp64, mixed_paper_start, mixed_df3_graph, "
-                                                 "mixed_df3_poly_graph, fp64_poly)")
+                                                 "mixed_df_poly, mixed_df_poly_graph, mixed_df3_poly_graph, "
+                                                 "fp64_poly)")
     ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
                     help="headline is the mixed path when it runs; both also times plain FP64")
     return ap.parse_args()
@@ -413,12 +414,11 @@ def run_ours(args, rank, world, local_rank):
     # RK4 step replayed as a CUDA graph; fp64: the paper's method (FP64, start
     # from the last sigma); mixed_paper_start: precision 1 with the paper's
     # start, for attribution; *_poly*: each stage started from the polynomial
-    # in time through the same stage's sigma of the last 3-4 steps (guess 3),
-    # on the paths whose right-hand side is not FP32 (with the FP32 one the
-    # rounding noise of the stage states limits that start)
+    # in time through the same stage's sigma of the last 3-4 steps (guess 3)
     plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
             ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0), ("mixed_df3_graph", 3, 2, 1),
-            ("mixed_df3_poly_graph", 3, 3, 1), ("fp64_poly", 0, 3, 0))
+            ("mixed_df_poly", 2, 3, 0), ("mixed_df_poly_graph", 2, 3, 1), ("mixed_df3_poly_graph", 3, 3, 1),
+            ("fp64_poly", 0, 3, 0))
     solvers = {}
     devfields = {}
     for name, prec, guess, graph in plan:
@@ -480,11 +480,11 @@ def run_ours(args, rank, world, local_rank):
     if args.path == "fp64":
         head_name = "fp64"
     else:
-        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph", "mixed_df_learned_graph")
-                 if k in paths]
+        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph", "mixed_df_learned_graph",
+                             "mixed_df_poly", "mixed_df_poly_graph") if k in paths]
         head_name = max(cands, key=lambda k: paths[k]["value"])
-    prof_name = {"mixed_graph": "mixed", "mixed_df_graph": "mixed_df",
-                 "mixed_df_learned_graph": "mixed_df"}.get(head_name, head_name)
+    prof_name = {"mixed_graph": "mixed", "mixed_df_graph": "mixed_df", "mixed_df_learned_graph": "mixed_df",
+                 "mixed_df_poly_graph": "mixed_df_poly"}.get(head_name, head_name)
     head_solver, head_rec = solvers[head_name], paths[head_name]
     head_prec = head_rec["precision"]
     for name, s in solvers.items():
@@ -595,9 +595,11 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
         "config": dict(config(n, fp32), parallelism=f"replicas{world}" if world > 1 else "single"),
         "path": ({0: "plain FP64",
-                  1: "mixed: FP32 bulk + FP64 refinement to the FP64 tolerance, GMRES start extrapolated in time",
-                  2: "mixed: FP32 bulk + double-float refinement matvec and coefficients to the FP64 tolerance, "
-                     "GMRES start extrapolated in time"}[head_prec])
+                  1: "mixed: FP32 bulk + FP64 refinement to the FP64 tolerance",
+                  2: "mixed: FP32 bulk + double-float refinement matvec and coefficients to the FP64 tolerance"}
+                 [head_prec])
+                + (", GMRES start: each stage's sigma extrapolated by the cubic in time through the same stage "
+                   "of the last 4 steps" if "_poly" in head_name else ", GMRES start extrapolated in time")
                 + (", each RK4 step one CUDA graph with device-side GMRES control"
                    if head_name.endswith("_graph") else ", host-driven GMRES loop"),
         "arms": {k: dict({"value": v["value"], "ms_per_step": v["ms_per_step"], "precision": v["precision"],
@@ -649,7 +651,7 @@ def run_ours(args, rank, world, local_rank):
             errs[nm] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
         out["headline_vs_fp64_rel_l2"] = errs
         out["headline_vs_fp64_after_steps"] = args.warmup + args.steps
-    for base in ("mixed", "mixed_df"):
+    for base in ("mixed", "mixed_df", "mixed_df_poly"):
         if base + "_graph" in paths and base in paths:
             mg, mh = paths[base + "_graph"], paths[base]
             out.setdefault("graph_vs_host_loop", {})[base] = {

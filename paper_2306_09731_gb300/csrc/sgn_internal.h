@@ -316,6 +316,10 @@ struct RkK {
   cpx<S>* b;
   const S* kxs;
   const S* kys;
+  // stage state and sigma_hat of the right-hand side (its linear part, added
+  // by the update when the passes run in FP32)
+  const cpx<S>* Y[3];
+  const cpx<S>* sig;
   RkArgs rk;
 };
 

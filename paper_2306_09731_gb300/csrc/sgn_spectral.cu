@@ -387,6 +387,15 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
 // Inputs (y-inverse outputs): Vx, Vy, S = sigma, Sy = i ky sigma, and the
 // depth anomaly hh = h - 1. Writes Cq = -i kx (h u_x)^x, Qy = (h u_y)^x and
 // Fh = F^x with F = |v|^2/2 - |grad sigma|^2/(2h^2) + g (h - 1) - 9 sigma^2/(2h^4).
+//
+// In FP32 (rhs_lin_split) the pass leaves out the terms linear in the state:
+// h u = v + (h - 1) v - grad sigma keeps only (h - 1) v, and F drops g (h - 1).
+// k_rk_update adds them back in the state's arithmetic from its spectra
+// (-i k.v_hat - |k|^2 sigma_hat and -i k g h_hat), so the FP32 rounding of
+// the right-hand side scales with its nonlinear part, not with the whole.
+template <typename T>
+constexpr bool rhs_lin_split() { return std::is_same<T, float>::value; }
+
 template <typename T, int LN = 0>
 __global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) k_rhs_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                 const cpx<T>* Vx, const cpx<T>* Vy, const cpx<T>* S,
@@ -412,8 +421,8 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) 
     const int x = L.t + s * T_;
     const T r0 = cr[p0 + x] * twoN, r1 = cr[p1 + x] * twoN;
     const T sx0 = QX[s].x * n, sx1 = QX[s].y * n, sy0 = QY[s].x * n, sy1 = QY[s].y * n;
-    QX[s] = mk(-sx0, -sx1);
-    QY[s] = mk(-sy0, -sy1);
+    QX[s] = rhs_lin_split<T>() ? mk((T)0, (T)0) : mk(-sx0, -sx1);
+    QY[s] = rhs_lin_split<T>() ? mk((T)0, (T)0) : mk(-sy0, -sy1);
     F[s] = mk((T)-0.5 * r0 * r0 * (sx0 * sx0 + sy0 * sy0), (T)-0.5 * r1 * r1 * (sx1 * sx1 + sy1 * sy1));
   }
   // sigma: -9 sigma^2 / (2 h^4)
@@ -436,8 +445,8 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) 
     const int x = L.t + s * T_;
     const T a0 = hh[p0 + x], a1 = hh[p1 + x];  // h - 1
     const T v0 = Z[s].x * n, v1 = Z[s].y * n;
-    QX[s].x += v0 + a0 * v0;
-    QX[s].y += v1 + a1 * v1;
+    QX[s].x += rhs_lin_split<T>() ? a0 * v0 : v0 + a0 * v0;
+    QX[s].y += rhs_lin_split<T>() ? a1 * v1 : v1 + a1 * v1;
     F[s].x += (T)0.5 * v0 * v0;
     F[s].y += (T)0.5 * v1 * v1;
   }
@@ -449,12 +458,13 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) 
     const int x = L.t + s * T_;
     const T a0 = hh[p0 + x], a1 = hh[p1 + x];  // h - 1
     const T v0 = Z[s].x * n, v1 = Z[s].y * n;
-    QY[s].x += v0 + a0 * v0;
-    QY[s].y += v1 + a1 * v1;
+    QY[s].x += rhs_lin_split<T>() ? a0 * v0 : v0 + a0 * v0;
+    QY[s].y += rhs_lin_split<T>() ? a1 * v1 : v1 + a1 * v1;
     // g (h - h_inf): the constant g h_inf of the Bernoulli equation (2) has no
     // gradient; leaving it out keeps F's rounding relative to its variation
-    F[s].x += (T)0.5 * v0 * v0 + g * a0;
-    F[s].y += (T)0.5 * v1 * v1 + g * a1;
+    const T gh0 = rhs_lin_split<T>() ? (T)0 : g * a0, gh1 = rhs_lin_split<T>() ? (T)0 : g * a1;
+    F[s].x += (T)0.5 * v0 * v0 + gh0;
+    F[s].y += (T)0.5 * v1 * v1 + gh1;
     // the split returns twice the half spectra: pre-scale by 1/2
     QX[s] = scl(QX[s], (T)0.5);
     QY[s] = scl(QY[s], (T)0.5);
@@ -923,17 +933,34 @@ struct EpiK {
 //   stage 1: acc = K,    U_s = U_n + dt/2 K;   stage 2: acc += 2K, U_s = U_n + dt/2 K
 //   stage 3: acc += 2K,  U_s = U_n + dt K;     final:   U_n += dt/6 (acc + K), Krasny
 //   RK_STORE_K: acc = K (one RHS evaluation)
+// With an FP32 right-hand side (rhs_lin_split), K holds only its nonlinear
+// part; the linear part comes from the stage state Y and sigma_hat here:
+//   h_t += -i kx vx - i ky vy - (kx^2 + ky^2) sigma,  v_t += -i k g h,
+// with the zeroed-Nyquist wavenumbers and the 2/3 mask of the FP32 pass.
 template <typename T, typename S>
 __global__ void k_rk_update(Geom G, RkK<T, S> a) {
   const RkArgs rk = a.rk;
   const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
   const S c6 = (S)(rk.dt / 6.0);
   const S cdt = (S)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
+  const S g = (S)rk.g;
   for (Walk it(G); it.ok(); it.next()) {
     const size_t e = it.e;
     cpx<S> kk[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) kk[f] = mk(cvt<S>(a.K[f][e].x), cvt<S>(a.K[f][e].y));
+    if (rhs_lin_split<T>()) {
+      const int my = it.row <= (G.Ny >> 1) ? it.row : G.Ny - it.row;
+      const bool keep = it.col < G.Nxh && (!rk.dealias || (3 * it.col <= G.Nx && 3 * my <= G.Ny));
+      if (keep) {
+        const S kxv = __ldg(a.kxs + it.col);
+        const S kyv = __ldg(a.kys + it.row);
+        const cpx<S> yh = a.Y[0][e], yx = a.Y[1][e], yy = a.Y[2][e], sg = a.sig[e];
+        kk[0] = kk[0] - mul_ik(yx, kxv) - mul_ik(yy, kyv) - scl(sg, kxv * kxv + kyv * kyv);
+        kk[1] = kk[1] - mul_ik(yh, g * kxv);
+        kk[2] = kk[2] - mul_ik(yh, g * kyv);
+      }
+    }
     if (rk.mode == RK_STORE_K) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) a.acc[f][e] = kk[f];
@@ -1597,6 +1624,8 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     a.b = bhat;
     a.kxs = tbs.kx;
     a.kys = tbs.ky;
+    for (int f = 0; f < 3; ++f) a.Y[f] = U[f];
+    a.sig = sig;
     a.rk = rk;
     ex.begin(PK_RK);
     k_rk_update<T, S><<<NBLK, 256, 0, ex.s>>>(G, a);

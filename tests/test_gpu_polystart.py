@@ -5,12 +5,10 @@ stage's sigma at the last 3 (quadratic) or 4 (cubic) steps; until the handle
 has 3 steps of the trajectory it starts as guess 2 does. Only GMRES's starting
 value changes, so the bars are those of every other start: the FP64 oracle
 within 1e-10 (FP64 path) and 1e-5 (the FP32 bulk), graph mode bitwise equal to
-the host loop, and, once the history is built, fewer matvecs than guess 2 on
-the paths whose right-hand side is FP64 or double-float (precisions 0 and 3).
-With the FP32 right-hand side (precisions 1 and 2) the rounding of each stage
-state enters sigma as step-to-step noise that the cubic amplifies; near rest,
-where sigma is small, that noise is as large as guess 2's O(dt^2) error, and
-there the start saves nothing.
+the host loop, and, once the history is built, fewer matvecs than guess 2.
+With the FP32 right-hand side the start relies on the update adding the
+right-hand side's linear part in FP64: FP32 rounding of the whole would enter
+sigma as step-to-step noise that the cubic amplifies.
 """
 import numpy as np
 import pytest
@@ -92,7 +90,7 @@ def test_poly_start_parity_with_oracle(precision, graph, bar):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [0, 3])
+@pytest.mark.parametrize("precision", [0, 2, 3])
 def test_poly_start_fewer_matvecs_than_linear(precision):
     """Once 4 steps are held the cubic start leaves far less for GMRES to do
     than guess 2's linear extrapolation inside a step; the trajectories agree
@@ -112,7 +110,7 @@ def test_poly_start_fewer_matvecs_than_linear(precision):
         fields[guess] = [host(x) for x in f[:3]]
         s.close()
     assert per[3] <= 0.6 * per[2], per
-    bar = 1e-9
+    bar = 1e-9 if precision != 2 else 1e-6
     for x, y in zip(fields[3], fields[2]):
         assert rel(x, y) < bar
 

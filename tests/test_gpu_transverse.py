@@ -13,7 +13,7 @@ sigma is 0 and the energy contains sigma) to 1e-9 relative in FP64 (RK4 at dt =
 to 1e-6 with the FP32 bulk (each step's FP32 right-hand side carries ~1e-7
 relative rounding into dt K, ~250 x 2e-3 x 1e-7 at worst), and the
 L-infinity deviation from the line soliton (Section 4.1) equal in both
-precisions to 1e-5 of its size.
+precisions to 1e-5 of max |h| (the mixed bar, pointwise).
 """
 import numpy as np
 import pytest
@@ -89,6 +89,9 @@ def test_transverse_fp64_against_mixed(a):
         _, inv0, inv1, _ = out[prec]
         assert abs(inv1[0] - inv0[0]) <= 1e-12 * abs(inv0[0])
         assert abs(inv1[3] - inv0[3]) <= ebar * abs(inv0[3])
+    # the two deviations differ by at most the pointwise difference of h, which
+    # the mixed bar holds to 1e-5 of h itself (h ~ 2 at a = 1, the deviation
+    # ~ 0.02)
     d0, d1 = out[0][3], out[1][3]
-    assert abs(d1["dev_h"] - d0["dev_h"]) <= 1e-5 * d0["dev_h"] + 1e-12
+    assert abs(d1["dev_h"] - d0["dev_h"]) <= 1e-5 * float(np.max(np.abs(hd)))
     assert 0.0 < d0["dev_h"] < 0.1
