@@ -566,18 +566,23 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         ksteps, kwarm = max(3, args.steps // 4), 2
         crossing = {"workload": "crossing_solitons_4096x4096", "grid": [4096, 4096], "box": [-100.0, 100.0],
-                    "a": 0.6, "dt": DT, "precision": 2, "graph": True, "steps": ksteps, "warmup": kwarm,
+                    "a": 0.6, "dt": DT, "precision": 2, "graph": True, "steps": ksteps,
+                    "warmup": kwarm, "warmup_polynomial": max(kwarm, 4),
                     "unit": UNIT, "tol": 1e-10, "theta": {}}
         for theta in (15.0, 30.0):
             cst = I.crossing_solitons(4096, 200.0, 0.6, theta)
             arms = {}
+            # the polynomial start needs 4 steps of history before the cubic:
+            # its arm warms up for 4 steps
             for name, guess, lname in (("paper_start", 0, None),
                                        ("paper_start_learned", 0, "mixed_df_paper_start_learned"),
                                        ("extrapolated", 2, None),
-                                       ("extrapolated_learned", 2, "mixed_df_learned_graph")):
+                                       ("extrapolated_learned", 2, "mixed_df_learned_graph"),
+                                       ("polynomial", 3, None)):
                 if lname is not None and lname not in nets:
                     continue
-                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, kwarm, not args.no_tune)
+                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps,
+                                           max(kwarm, 4) if guess == 3 else kwarm, not args.no_tune)
             crossing["theta"][f"{theta:g}"] = arms
             del cst
         for ln, (net, *_rest) in nets.items():
