@@ -544,6 +544,14 @@ def run_ours(args, rank, world, local_rank):
         if True in ens and False in ens:
             ensemble["batch_builtin_shapes"] = len(members) * args.steps / ens[False][0]
             ensemble["tuning_first_members"] = tuning
+        # the same batch with the polynomial start (4 warm-up steps of history)
+        E = Ensemble(members, tune=max(ens), precision=2, guess=3, graph=1)
+        E.step(2e-3, max(4, args.warmup))
+        torch.cuda.synchronize()
+        b0 = time.perf_counter()
+        E.step(2e-3, args.steps)
+        ensemble["batch_polynomial"] = len(members) * args.steps / (time.perf_counter() - b0)
+        E.close()
     # the paper's monitoring quantities on the final state: wall time of
     # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
     hf = devfields[head_name]
