@@ -74,7 +74,7 @@ struct sgn_ctx {
   C64* ext_ring = nullptr;
   ExtHist* ext = nullptr;
   // The extrapolation history across calls: hist_ok after an RK4 call with
-  // guess = 2 (cleared by every other call), hist_keep its value when the
+  // guess 2 or 3 (cleared by every other call), hist_keep its value when the
   // current call began, hist_dt that call's dt.
   bool hist_ok = false, hist_keep = false;
   double hist_dt = 0.0;
@@ -806,14 +806,15 @@ void ensure_phys(sgn_ctx* ctx) {
   for (int i = 0; i < 4; ++i) ctx->phys[i] = dalloc<double>(ctx, ctx->G.nphys());
 }
 
-// The extrapolated start (guess = 2) carries stage-3 sigma from one step to
-// the next. A call that continues the trajectory the handle's last RK4 call
+// The extrapolated starts (guess 2 and 3) carry sigma from one step to the
+// next: stage 3's (guess 2) and every stage's of the last 4 steps (guess 3). A call that continues the trajectory the handle's last RK4 call
 // returned (same dt, and an input state equal to that output within 1e-8 of
 // the largest coefficient: the conversions' round trip, and the
 // anti-Hermitian remainder that FP32 increments leave in the kx = 0 and Nyquist
 // columns and the real output drops, ~1e-10) keeps that history, so its first
-// step extrapolates too; any other input starts without it. The history only chooses GMRES's starting value: every solve still meets
-// opt.tol. continues_history() saves the last output state (Un) before the
+// step extrapolates too; any other input starts without it. The history only
+// chooses GMRES's starting value: every solve still meets opt.tol.
+// continues_history() saves the last output state (Un) before the
 // call's conversions overwrite it; same_state_flag() compares and writes the
 // device flag gst->have_s3.
 bool continues_history(sgn_ctx* ctx, double dt) {
