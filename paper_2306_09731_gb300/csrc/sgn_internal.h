@@ -389,11 +389,8 @@ cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx
 // reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
 cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
                           const Exec& ex);
-// second Gram-Schmidt pass needed? (sets st->reorth, zeroes h2 if not)
-cudaError_t launch_reorth_decide(GmresDev* st, int nv, const Exec& ex);
 // GMRES scalar kernels (one thread)
 cudaError_t launch_gmres_start(GmresDev* st, const double* beta, const Exec& ex);
-cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int* flags, const Exec& ex);
 cudaError_t launch_backsolve(GmresDev* st, int k, const Exec& ex, const int* kdev = nullptr);
 // graph-mode control kernels (one thread); see csrc/sgn_krylov.cu
 cudaError_t launch_ctl_begin(GmresDev* st, const double* cnorm, GraphCtl ctl, const Exec& ex);

@@ -384,18 +384,6 @@ __global__ void k_reduce(const double* partials, int n, double* out, int sqrt_ou
   }
 }
 
-// DGKS test after the first Gram-Schmidt pass: reorthogonalise when the
-// update removed more than half of |w|^2 (|w'| < |w|/sqrt 2); otherwise the
-// second-pass coefficients are zero.
-__global__ void k_reorth_decide(GmresDev* st, int nv) {
-  if (threadIdx.x != 0) return;
-  const double nw = st->h1[nv];
-  const int need = (st->nrm2 < 0.5 * nw) ? 1 : 0;
-  st->reorth = need;
-  if (!need)
-    for (int i = 0; i < MAXV; ++i) st->h2[i] = 0.0;
-}
-
 // ---------------------------------------------------------- scalar kernels
 
 // g = (beta, 0, ...), the start of a GMRES cycle
@@ -405,14 +393,6 @@ __global__ void k_gmres_start(GmresDev* st, const double* beta) {
   st->g[0] = *beta;
   st->res = *beta;
   st->vscl[0] = 1.0;
-}
-
-// Column j of the Hessenberg matrix from the two CGS passes and the norm,
-// previous rotations applied, new rotation zeroing H[j+1][j], residual
-// estimate |g_{j+1}|.
-__global__ void k_givens(GmresDev* st, int j, GmresReadback* rb, const int* flags) {
-  if (threadIdx.x != 0) return;
-  givens_step(st, j, rb, flags);
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution
@@ -712,21 +692,9 @@ cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_
   ex.end();
   return cudaGetLastError();
 }
-cudaError_t launch_reorth_decide(GmresDev* st, int nv, const Exec& ex) {
-  ex.begin(PK_KRYLOV);
-  k_reorth_decide<<<1, 32, 0, ex.s>>>(st, nv);
-  ex.end();
-  return cudaGetLastError();
-}
 cudaError_t launch_gmres_start(GmresDev* st, const double* beta, const Exec& ex) {
   ex.begin(PK_KRYLOV);
   k_gmres_start<<<1, 32, 0, ex.s>>>(st, beta);
-  ex.end();
-  return cudaGetLastError();
-}
-cudaError_t launch_givens(GmresDev* st, int j, GmresReadback* rb_dev, const int* flags, const Exec& ex) {
-  ex.begin(PK_KRYLOV);
-  k_givens<<<1, 32, 0, ex.s>>>(st, j, rb_dev, flags);
   ex.end();
   return cudaGetLastError();
 }
