@@ -3,10 +3,12 @@
 // The handle owns every device buffer. The RK4 state lives in spectral form
 // (half spectra of h, vx, vy) between steps; sigma_hat is the GMRES warm start
 // carried from stage to stage and step to step (Section 3: each solve
-// starts from the previous solve's sigma). One stage is:
+// starts from the previous solve's sigma; opt.guess 2 and 3 extrapolate it in
+// time instead). One stage is:
 //   coefficients  h, 1/(2N h), 3/(2N h^3) from h_hat        (y-inverse + x-pass)
 //   GMRES         L sigma = b, b_hat = -(i kx vx + i ky vy) (Eq. (sigmav))
-//   RHS + update  K = (h_t, v_t) and the RK4 stage update  (3 fused passes)
+//   RHS + update  K = (h_t, v_t) and the RK4 stage update  (3 fused passes and
+//                 the update, which adds K's linear part when the passes are FP32)
 // By default the GMRES loop runs on the host: each Arnoldi step enqueues its
 // kernels and reads back one residual estimate (one stream synchronisation per
 // step). With opt.graph = 1 one RK4 step is a CUDA graph instead: the restart
