@@ -16,7 +16,10 @@
 // partials in a fixed order (deterministic). On a GB300 these BLAS-1 kernels
 // are FP64-issue bound, not HBM bound (4 DFMA per 16-byte entry against an
 // FP64:HBM balance below 1 DFMA per byte), so each entry's Parseval weight is
-// folded into w once rather than into every dot product.
+// folded into w once rather than into every dot product. The Gram-Schmidt
+// pair runs one wave of KBLK blocks (4 per SM). The FP32 basis of the inner
+// solve is kept unnormalised, V_i = s_i X_i with the scales s_i on the device,
+// so no pass rescales a vector (k_cgs_update writes X_{j+1} itself).
 #include <math.h>
 
 #include "sgn_internal.h"

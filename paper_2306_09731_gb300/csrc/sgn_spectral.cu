@@ -16,7 +16,9 @@
 //  * RHS (Eq. (1) and the v-form of Eq. (2)): y-inverse of vx, vy, sigma,
 //    i ky sigma; x-pass forms q = h v - grad sigma (= h u) and
 //    F = |v|^2/2 - |grad sigma|^2/(2h^2) + g h - 9 sigma^2/(2 h^4), forward x;
-//    y-forward with -i k combinations and the RK4 stage update.
+//    y-forward with -i k combinations and the RK4 stage update. In FP32 the
+//    passes form only the part of q and F that is nonlinear in the state, and
+//    the update adds the linear part from the FP64 spectra (rhs_lin_split).
 #include <math.h>
 
 #include <type_traits>
