@@ -48,7 +48,10 @@ typedef enum {
 typedef struct {
   int precision;      /* 0 = FP64 throughout; 1 = FP32 transforms, pointwise work and
                          inner GMRES, with FP64 state, dot products, Givens and an
-                         FP64 refinement residual (same FP64 tolerance test);
+                         FP64 refinement residual (same FP64 tolerance test); the
+                         FP32 passes form only the right-hand side's part nonlinear
+                         in the state, and the RK update adds the linear part
+                         (-i k.v - |k|^2 sigma in h_t, -i k g h in v_t) in FP64;
                          2 = as 1, but the refinement residual's matvec and the
                          coefficient pass run in double-float arithmetic (a value is
                          the sum of two FP32 numbers: 48-bit significand, FP32
@@ -58,8 +61,9 @@ typedef struct {
                          transforms, products and the K spectra) in double-float as
                          well: only the inner GMRES runs in FP32, so the trajectory
                          follows the FP64 one to its own rounding (for long runs
-                         whose small modes grow, where FP32 right-hand-side rounding
-                         would seed them); also converts the state in double-float */
+                         whose small modes grow, where the FP32 rounding of the
+                         nonlinear part would seed them); also converts the state in
+                         double-float */
   int restart;        /* GMRES restart length m, 1..32 (default 20) */
   int maxit;          /* cap on GMRES matvecs per solve, all cycles (default 1000) */
   double tol;         /* stop when ||M^-1(b - L sigma)||_2 <= tol ||M^-1 b||_2 (default 1e-10) */
