@@ -2,22 +2,35 @@
 """Benchmark: 2D SGN RK4 steps/s on the 2048^2 Gaussian-hump workload.
 
 Workload: h = 1 + 0.5 exp(-(x^2+y^2)), v = 0 on [-50,50)^2, 2048 x 2048 points,
-dt = 1e-3, GMRES restart 20 and tolerance 1e-10 (FP64 path). One step is one
-classic RK4 step (4 RHS evaluations, each with its GMRES solve), the whole hot
-path. Inputs are resident in HBM when the timed region starts; the state and
-the Krylov basis (about 1.3 GB) are far larger than L2, so no flush is needed.
+dt = 1e-3, GMRES restart 20 and tolerance 1e-10 on the FP64 residual of every
+solve. One step is one classic RK4 step (4 right-hand sides, each with its
+GMRES solve): the whole hot path. Inputs are resident in HBM when the timed
+region starts; the state and the Krylov basis (about 1.3 GB) are far larger
+than L2, so no flush is needed.
 
-Prints ONE JSON line on rank 0. Under torchrun every rank steps its own
-replica (weak scaling, no collective on the data path); value = total steps of
-all ranks / max time over ranks.
+The headline is ONE configuration, timed on its own: precision 2 (FP32
+transforms, pointwise work and inner GMRES; double-float refinement residual
+and coefficients; FP64 state), the polynomial GMRES start (guess 3), each RK4
+step replayed as one CUDA graph. Beside it, the paper's method (plain FP64,
+GMRES started from the last sigma) is timed the same way (`fp64_plain`), and
+the host-driven loop of the headline's kernels is timed with per-launch
+CUDA events for the roofline of its dominant kernel.
 
---impl reference times the FP64 CPU oracle on the host cores instead (each
-step is a bounded sample: one RK4 stage, scaled x4).
+The LAST stdout line is one compact JSON object (a few KB). Everything else
+(per-kernel tables, extra arms, ensembles, 4096^2 runs) goes to the detail
+file (--detail, default gpurun_out/bench_detail.json). Under torchrun every
+rank steps its own replica (weak scaling, no collective on the data path);
+value = total steps of all ranks / max time over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead: each
+step is one whole oracle RK4 step of the same workload at 512^2, scaled to
+2048^2 by the measured cost ratio of one oracle matvec at the two sizes.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -30,42 +43,49 @@ sys.path.insert(0, ROOT)
 METRIC = "SGN RK4 steps/s at 2048² to fixed GMRES tol: plain FP64 vs mixed+learned"
 UNIT = "steps/s"
 N_DEFAULT, L_DEFAULT, ALPHA, DT = 2048, 100.0, 0.5, 1e-3
+# the CPU oracle's bounded sample: whole RK4 steps of the same workload on a
+# coarser grid of the same box (well resolved: the hump's spectrum is below
+# 1e-25 at the 512-point Nyquist wavenumber)
+ORACLE_SAMPLE_N = 512
+
+# the headline configuration: (precision, guess, graph)
+HEADLINE = (2, 3, 1)
+HEADLINE_PATH = ("precision 2: FP32 transforms, pointwise work and inner GMRES, FP64 state, dots and Givens, "
+                 "double-float refinement residual and coefficients, every solve to the FP64 tolerance; "
+                 "GMRES start: each stage's sigma from the cubic in time through the same stage of the last "
+                 "4 steps; each RK4 step one CUDA graph with device-side GMRES control")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="grid points per side (default 2048)")
+    ap.add_argument("--sample-n", type=int, default=ORACLE_SAMPLE_N,
+                    help="grid side of the CPU oracle's sample (default 512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--no-graph", action="store_true", help="skip the graph-mode arms")
-    ap.add_argument("--no-df", action="store_true", help="skip the double-float refinement arms")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-start arms (and their training)")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the end-to-end leg (default: --steps)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 arm")
+    ap.add_argument("--no-prof", action="store_true", help="skip the host-loop arm with per-launch timers")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the built-in launch shapes (no sgn_autotune before the warm-up)")
+    ap.add_argument("--full", action="store_true",
+                    help="also run the other arms, the learned start, the 64-member ensemble and the 4096^2 "
+                         "crossing solitons (detail file only)")
     ap.add_argument("--transverse", action="store_true",
-                    help="also run the transverse-stability workload to t = 10 (1024x256, FP64 and precision 1)")
-    ap.add_argument("--no-crossing", action="store_true",
-                    help="skip the 4096^2 crossing-soliton measurement (GMRES starts compared)")
-    ap.add_argument("--arms", default=None, help="comma list: run only these arms (mixed, mixed_graph, mixed_df, "
-                                                 "mixed_df_graph, fp64, mixed_paper_start, mixed_df3_graph, "
-                                                 "mixed_df_poly, mixed_df_poly_graph, mixed_df3_poly_graph, "
-                                                 "fp64_poly)")
-    ap.add_argument("--path", choices=["both", "mixed", "fp64"], default="both",
-                    help="headline is the mixed path when it runs; both also times plain FP64")
-    return ap.parse_args()
+                    help="also run the transverse-stability workload to t = 10 (detail file only)")
+    ap.add_argument("--detail", default=os.path.join("gpurun_out", "bench_detail.json"),
+                    help="where the detailed record goes")
+    return ap.parse_args(argv)
 
 
-def config(n, fp32=False):
+def config(n, precision_desc):
     return {"workload": f"gaussian_hump_{n}x{n}", "grid": [n, n], "box": [-L_DEFAULT / 2, L_DEFAULT / 2],
             "h0": f"1+{ALPHA}*exp(-(x^2+y^2))", "v0": "0", "dt": DT, "gmres_restart": 20, "gmres_tol": 1e-10,
-            "precision": ("fp32 transforms/pointwise/inner GMRES, fp64 state, dots, Givens and refinement "
-                          "residual" if fp32 else "fp64"),
-            "l2": "inputs larger than L2 (state + Krylov basis, 0.9-1.3 GB), no flush"}
+            "precision": precision_desc,
+            "l2": "inputs larger than L2 (state + Krylov basis, 0.9-1.3 GB resident), no flush"}
 
 
 class ClockSampler:
@@ -103,23 +123,29 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        sm.sort()
-        med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock under load, the maximum clock and the throttle reasons
+    seen in nvidia-smi csv lines (index, sm, max sm, power, reasons...)."""
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    sm.sort()
+    med = sm[len(sm) // 2] if sm else None
+    return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -148,19 +174,9 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 rate of a GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz max clock
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Double-float passes (precision 2) are bound by FP32 issue: 152 SMs x 128 FP32
-# lanes x 2.07 GHz instructions per second, divided by the FP32 instructions
-# one FP64-equivalent flop of a radix-8 FFT butterfly costs in this
-# double-float arithmetic: (52 adds x 8 + 4 products x 7 + 7 complex twiddle
-# products x 38) / (52 + 4 + 7 x 6) = 7.2.
-DF_INSTR_PER_FLOP = (52 * 8 + 4 * 7 + 7 * 38) / (52 + 4 + 7 * 6)
-DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_INSTR_PER_FLOP / 1e12
-
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# is now, with the summary that holds the command; set to None when the kernel
-# changes.
+# is now, with the summary that holds the command. An entry is removed when its
+# kernel changes, so that the line reports null until the next capture.
 MEASURED_TRAFFIC = {
     ("ref_x", "df", 2048): {"bytes": 134.603264e6 + 22.911744e6, "source": "profiles/k_mv_x_df_gaussian2048.md"},
     ("mv_x", "fp32", 2048): {"bytes": 67.196928e6 + 0.668928e6, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
@@ -181,11 +197,10 @@ SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs
 def kernel_work(cls, n, tbytes):
     """Algorithmic (flops, DRAM bytes) of one launch of a kernel class at n x n.
 
-    tbytes: bytes per real of the pass (8 FP64, 4 FP32); the RK4 state, sigma
-    and b stay FP64 (8) in both modes. FFT flops: 5 m log2 m per complex
-    transform of length m, 2.5 m log2 m per real one.
+    tbytes: bytes per real of the pass (8 FP64 and double-float, 4 FP32); the
+    RK4 state, sigma and b stay FP64 (8) in every precision. FFT flops: 5 m
+    log2 m per complex transform of length m, 2.5 m log2 m per real one.
     """
-    import math
     nxh = n // 2 + 1
     spec = n * nxh * 2 * tbytes       # one half spectrum of the pass's type
     spec_s = n * nxh * 2 * 8          # one FP64 half spectrum (state)
@@ -223,63 +238,70 @@ KERNEL_NAMES = {"mv_yinv": "k_ypass<inv,2> (matvec y-inverse)", "mv_x": "k_mv_x 
                 "ref_yfwd": "k_ypass<fwd,EpiMatvec> (refinement matvec y-forward)"}
 
 
-def class_roofline(cls, n, prec, prof, peaks):
-    """Live roofline of one kernel class from the library's event timers."""
+def class_arith(cls, prec):
+    """The arithmetic a kernel class runs in for a precision: fp32, df or fp64."""
+    if prec == 0:
+        return "fp64"
+    if cls.startswith("ref"):
+        return "df" if prec >= 2 else "fp64"
+    if cls == "rk":
+        return "fp64"
+    if prec == 3 and cls.startswith("rhs"):
+        return "df"
+    return "fp32"
+
+
+def class_roofline(cls, n, prec, prof, peaks, peak_kind):
+    """HBM roofline of one kernel class from the library's per-launch CUDA-event
+    timers: algorithmic bytes per launch / mean launch time, against the
+    measured copy bandwidth. The FLOP rate is reported beside it."""
     cnt = prof["counts"].get(cls, 0)
     if not cnt:
         return None
     avg_ms = prof["ms"][cls] / cnt
-    is32 = prec >= 1 and not cls.startswith("ref")
-    isdf = prec == 2 and cls.startswith("ref")
-    flops, nbytes = kernel_work(cls, n, 4 if is32 else 8)
+    ar = class_arith(cls, prec)
+    # the RK update reads FP32 K spectra when the right-hand side is FP32
+    tbytes = 4 if (ar == "fp32" or (cls == "rk" and prec in (1, 2))) else 8
+    flops, nbytes = kernel_work(cls, n, tbytes)
     if flops is None:
         return None
-    if isdf:
-        ach = flops / (avg_ms / 1e3) / 1e12
-        out = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": ach / DF_PEAK_TFLOPS,
-               "peak_source": "derived double-float rate: 152 SMs x 128 FP32 lanes x 2.07 GHz / "
-                              f"{DF_INSTR_PER_FLOP:.1f} FP32 instructions per FP64-equivalent FFT flop"}
-    elif is32:
-        ach = nbytes / (avg_ms / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    else:
-        ach = flops / (avg_ms / 1e3) / 1e12
-        out = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": ach / FP64_PEAK_TFLOPS,
-               "peak_source": "derived FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
-    out.update({"kernel": KERNEL_NAMES.get(cls, cls) + (" FP32" if is32 else (" double-float" if isdf else " FP64")),
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
-                "avg_launch_ms": avg_ms, "launches": cnt})
-    tr = MEASURED_TRAFFIC.get((cls, "fp32" if is32 else ("df" if isdf else "fp64"), n))
-    out["traffic"] = tr["bytes"] if tr else None
-    out["traffic_source"] = tr["source"] if tr else None
-    return out
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ach = nbytes / (avg_ms / 1e3) / 1e9
+    tr = MEASURED_TRAFFIC.get((cls, ar, n))
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": tr["bytes"] if tr else None,
+            "kernel": KERNEL_NAMES.get(cls, cls) + {"fp32": " FP32", "df": " double-float", "fp64": " FP64"}[ar],
+            "algorithmic_bytes": nbytes, "avg_launch_us": avg_ms * 1e3, "launches": cnt,
+            "fp64_equiv_tflops": flops / (avg_ms / 1e3) / 1e12,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs (of {peak_kind})",
+            "traffic_source": tr["source"] if tr else None}
 
 
-def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
-    """W warm-up steps, then K timed RK4 steps of one path; returns its record.
-
-    The host-driven loop (graph = 0) runs the timed steps with the per-launch
-    event timers on; graph mode (graph = 1) cannot time launches inside its
-    conditional nodes and runs without them."""
+def time_path(precision, guess, args, st, n, world, graph=0, learned=None, steps=None, warmup=None,
+              profile=False, tune=None):
+    """W warm-up steps, then K timed RK4 steps of one path; returns (solver,
+    device fields, record). CUDA events on the launching stream bracket the
+    timed call, with a synchronize (and a barrier across ranks) on both sides.
+    profile: the host-driven loop (graph = 0) runs the timed steps with the
+    library's per-launch event timers on."""
     import torch
 
     from paper_2306_09731_gb300.sgn import Solver
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    tune = (not args.no_tune) if tune is None else tune
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
     s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
-    tuning = None if args.no_tune else s.autotune(5)
+    tuning = s.autotune(5) if tune else None
     if learned is not None:
         net, in_scale, out_scale, tau_power = learned
         s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
     stream = torch.cuda.current_stream()
-    if args.warmup > 0:
-        s.rk4_step(*f, DT, args.warmup)
+    if warmup > 0:
+        s.rk4_step(*f, DT, warmup)
     torch.cuda.synchronize()
-    if not graph:
+    if profile and not graph:
         s.set_profiling(True)
     st0 = s.stats()
     l0 = s.profile()["launches"]
@@ -289,7 +311,7 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    s.rk4_step(*f, DT, args.steps)
+    s.rk4_step(*f, DT, steps)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -297,20 +319,125 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None):
     ms = e0.elapsed_time(e1)
     prof = s.profile()
     st1 = s.stats()
-    if not graph:
+    if profile and not graph:
         s.set_profiling(False)
-    value, t_max = throughput(args.steps, ms / 1000.0, world)
+    value, t_max = throughput(steps, ms / 1000.0, world)
     solves = st1["solves"] - st0["solves"]
-    rec = {"value": value, "ms_per_step": t_max * 1e3 / args.steps,
-           "gmres": {"inner_matvecs_per_step": (st1["matvecs"] - st0["matvecs"]) / args.steps,
+    rec = {"value": value, "ms_per_step": t_max * 1e3 / steps, "steps": steps, "warmup": warmup,
+           "precision": precision, "guess": guess, "graph": graph,
+           "gmres": {"inner_matvecs_per_step": (st1["matvecs"] - st0["matvecs"]) / steps,
                      "solves": solves,
                      "iters_per_stage": (st1["matvecs"] - st0["matvecs"]) / max(solves, 1),
-                     "fp64_refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1)},
+                     "refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1),
+                     "max_iters": st1["max_iters"]},
            "launches": prof["launches"] - l0,
-           "prof": None if graph else prof,
+           "prof": prof if (profile and not graph) else None,
            "tuning": tuning}
     return s, f, rec
 
+
+# ---------------------------------------------------------------- the CPU oracle
+
+def _oracle_env():
+    """One BLAS/OpenMP thread per process: the oracle as it stands is serial
+    numpy (pocketfft), and the all-cores timing runs one process per core."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_steps(n, warmup, steps):
+    """Runs in a spawned process: `warmup` untimed, then `steps` timed whole
+    oracle RK4 steps of the Gaussian hump on an n x n grid of the benchmark's
+    box, continuing one trajectory. Returns (seconds per timed step, GMRES
+    iterations of each timed stage)."""
+    from oracle import sgn_oracle as O
+    from paper_2306_09731_gb300 import inputs as I
+    st = I.gaussian_hump(n, L_DEFAULT, ALPHA)
+    G = O.Grid(n, n, L_DEFAULT, L_DEFAULT)
+    s = (st.h, st.vx, st.vy, st.sigma)
+    for _ in range(warmup):
+        s = O.rk4_step(G, *s, DT, 1)
+    times, log = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        s = O.rk4_step(G, *s, DT, 1, log=log)
+        times.append(time.perf_counter() - t0)
+    return times, [i["iters"] for st4 in log for i in st4]
+
+
+def _oracle_matvec_seconds(n, reps=2):
+    """Runs in a spawned process: the best of `reps` timings of one oracle
+    matvec M^-1 L sigma (the unit of GMRES work) on the n x n workload."""
+    import numpy as np
+
+    from oracle import sgn_oracle as O
+    from paper_2306_09731_gb300 import inputs as I
+    st = I.gaussian_hump(n, L_DEFAULT, ALPHA)
+    G = O.Grid(n, n, L_DEFAULT, L_DEFAULT)
+    x = np.cos(G.x)[None, :] * np.sin(G.y)[:, None]
+    best = float("inf")
+    for _ in range(reps + 1):
+        t0 = time.perf_counter()
+        O.precond_solve(G, O.elliptic_apply(G, st.h, x))
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_timing(n_target, n_sample, warmup, steps, all_cores=True):
+    """Times the oracle as it stands on the host: `steps` whole RK4 steps of
+    the workload on an n_sample^2 grid (after `warmup`), in a spawned
+    one-thread process, scaled to n_target^2 by the measured ratio of one
+    oracle matvec at the two sizes; with all_cores, also one step in each of
+    `cores` concurrent one-thread processes (throughput of the whole host)."""
+    import multiprocessing as mp
+    _oracle_env()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        times, iters = pool.apply(_oracle_steps, (n_sample, warmup, steps))
+        if n_target != n_sample:
+            t_big = pool.apply(_oracle_matvec_seconds, (n_target,))
+            t_small = pool.apply(_oracle_matvec_seconds, (n_sample,))
+            scale = t_big / t_small
+        else:
+            scale = 1.0
+    step_s = sum(times) / len(times)
+    out = {"sample_steps": steps, "sample_warmup": warmup, "sample_grid": [n_sample, n_sample],
+           "sample_s_per_step": step_s, "scale_to_target": scale,
+           "scale_nlogn": (n_target ** 2 * math.log2(n_target ** 2)) / (n_sample ** 2 * math.log2(n_sample ** 2)),
+           "target_s_per_step": step_s * scale, "value": 1.0 / (step_s * scale),
+           "iters_per_stage": sum(iters) / max(len(iters), 1), "timed_s": sum(times)}
+    if all_cores:
+        cores = host_cores()
+        with ctx.Pool(cores) as pool:
+            # one untimed step in every worker first (imports, FFT plans)
+            pool.starmap(_oracle_steps, [(n_sample, 0, 1)] * cores)
+            t0 = time.perf_counter()
+            res = pool.starmap(_oracle_steps, [(n_sample, 0, 1)] * cores)
+            wall = time.perf_counter() - t0
+        per = [r[0][0] for r in res]
+        out["all_cores"] = {"cores": cores, "value": cores / (wall * scale), "unit": UNIT,
+                            "wall_s": wall, "mean_s_per_step_per_core": sum(per) / len(per),
+                            "sample": f"one {n_sample}x{n_sample} oracle RK4 step in each of {cores} concurrent "
+                                      f"one-thread processes, scaled x{scale:.2f} to {n_target}x{n_target}"}
+    return out
+
+
+def cpu_sample_text(t, n_target):
+    return (f"{t['sample_steps']} whole oracle RK4 steps (FP64 numpy, GMRES(20) to 1e-10, "
+            f"{t['iters_per_stage']:.2f} iterations per stage) of the same workload on a "
+            f"{t['sample_grid'][0]}x{t['sample_grid'][1]} grid, after {t['sample_warmup']} untimed; "
+            f"scaled x{t['scale_to_target']:.2f} to {n_target}x{n_target} by the measured time of one oracle "
+            f"matvec at both sizes (N log N would give x{t['scale_nlogn']:.2f})")
+
+
+# ---------------------------------------------------------------- extras (--full)
 
 def time_crossing(st, precision, guess, graph, learned, steps, warmup, tune=True):
     """Wall time of `steps` graph-mode RK4 steps (after `warmup`) of one GMRES
@@ -342,7 +469,7 @@ def time_crossing(st, precision, guess, graph, learned, steps, warmup, tune=True
     s.close()
     return {"value": steps / (ms / 1000.0), "ms_per_step": ms / steps,
             "iters_per_stage": (st1["matvecs"] - st0["matvecs"]) / max(solves, 1),
-            "fp64_refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1),
+            "refinements_per_stage": (st1["refinements"] - st0["refinements"]) / max(solves, 1),
             "max_iters": st1["max_iters"]}
 
 
@@ -394,6 +521,107 @@ def transverse_stability(tend=10.0, dt=2e-3, marks=5):
             "runs": out}
 
 
+def run_extras(args, st, n, detail):
+    """The other arms, the learned start, the 64-member ensemble and the
+    4096^2 crossing solitons; results go to the detail record only."""
+    import torch
+
+    from paper_2306_09731_gb300 import inputs as I
+    arms = {}
+    plan = (("mixed_df_graph", 2, 2, 1), ("mixed_df3_poly_graph", 3, 3, 1), ("fp64_poly", 0, 3, 0),
+            ("mixed_df_paper_start", 2, 0, 0))
+    for name, prec, guess, graph in plan:
+        s, f, rec = time_path(prec, guess, args, st, n, 1, graph)
+        s.close()
+        rec.pop("prof", None)
+        arms[name] = rec
+        del f
+    detail["arms"] = arms
+    nets = {}
+    from paper_2306_09731_gb300 import learned as Lm
+    lr = {}
+    for name, prec, guess, graph, tau_power, coarse in (("mixed_df_paper_start_learned", 2, 0, 0, 1, n // 8),
+                                                        ("mixed_df_learned_graph", 2, 2, 1, 2, n // 16)):
+        t0 = time.perf_counter()
+        states = Lm.gaussian_states(n, L_DEFAULT, [0.35, 0.45, 0.55, 0.65], seed=1)
+        samples = Lm.generate(states, coarse, steps=8, dt=DT, precision=prec, guess=guess, tau_power=tau_power)
+        t1 = time.perf_counter()
+        net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2, log_every=100)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        nets[name] = (net, in_scale, out_scale, tau_power)
+        s, f, rec = time_path(prec, guess, args, st, n, 1, graph, nets[name])
+        s.close()
+        rec.pop("prof", None)
+        rec["training"] = {"coarse_n": coarse, "samples": int(samples.shape[0]), "data_s": t1 - t0,
+                           "train_s": t2 - t1, "losses": losses, "params": net.num_params()}
+        lr[name] = rec
+    detail["learned_start"] = lr
+    from paper_2306_09731_gb300.ensemble import GRIDS, Ensemble, perturbed_members
+    members = perturbed_members(64, seed=11)
+    ens = {"members": len(members), "grids": [list(g[:2]) for g in GRIDS], "dt": 2e-3, "steps": args.steps,
+           "unit": "member-steps/s"}
+    for guess in (2, 3):
+        E = Ensemble(members, tune=not args.no_tune, precision=2, guess=guess, graph=1)
+        E.step(2e-3, max(4, args.warmup))
+        torch.cuda.synchronize()
+        b0 = time.perf_counter()
+        E.step(2e-3, args.steps)
+        b1 = time.perf_counter()
+        E.step_one_by_one(2e-3, args.steps)
+        b2 = time.perf_counter()
+        ens[f"guess{guess}"] = {"batch": len(members) * args.steps / (b1 - b0),
+                                "one_by_one": len(members) * args.steps / (b2 - b1)}
+        E.close()
+    detail["ensemble"] = ens
+    torch.cuda.empty_cache()
+    if n == N_DEFAULT:
+        ksteps = max(3, args.steps // 4)
+        cross = {"workload": "crossing_solitons_4096x4096", "a": 0.6, "precision": 2, "graph": True,
+                 "steps": ksteps, "theta": {}}
+        for theta in (15.0, 30.0):
+            cst = I.crossing_solitons(4096, 200.0, 0.6, theta)
+            res = {}
+            for name, guess, lname in (("paper_start", 0, None),
+                                       ("paper_start_learned", 0, "mixed_df_paper_start_learned"),
+                                       ("extrapolated", 2, None), ("extrapolated_learned", 2, "mixed_df_learned_graph"),
+                                       ("polynomial", 3, None)):
+                res[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, 4 if guess == 3 else 2,
+                                          not args.no_tune)
+            cross["theta"][f"{theta:g}"] = res
+            del cst
+        detail["crossing_4096"] = cross
+
+
+def compact_line(head_rec, fp64, roof, share, e2e, clk, args, world, n):
+    """The one JSON object the bench prints last: the headline, the paper's
+    method beside it, the roofline of the dominant kernel, the end-to-end
+    figure and the clocks (a few KB; every table goes to the detail file)."""
+    prec, guess, graph = head_rec["precision"], head_rec["guess"], head_rec["graph"]
+    out = {
+        "metric": METRIC, "value": head_rec["value"], "unit": UNIT, "n_gpus": world, "steps": head_rec["steps"],
+        "warmup": head_rec["warmup"], "ms_per_step": head_rec["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64+f64", "data": "synthetic",
+        "config": dict(config(n, HEADLINE_PATH), parallelism=f"replicas{world}" if world > 1 else "single",
+                       precision_id=prec, guess=guess, graph=graph, tuned=not args.no_tune),
+        "gmres": {k: head_rec["gmres"][k] for k in ("iters_per_stage", "refinements_per_stage", "max_iters")},
+        "gpu_launches": head_rec["launches"],
+        "fp64_plain": fp64,
+        "speedup_vs_fp64": (head_rec["value"] / fp64["value"]) if fp64 else None,
+        "roofline": ({k: roof.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                                "avg_launch_us", "algorithmic_bytes", "time_share",
+                                                "fp64_equiv_tflops", "peak_source")} if roof else None),
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if share:
+        top = sorted(share.items(), key=lambda kv: -kv[1])[:5]
+        out["time_share_top"] = {k: round(v, 4) for k, v in top}
+    return out
+
+
+# ---------------------------------------------------------------- our arm
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -404,334 +632,126 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     n = args.n
     st = I.gaussian_hump(n, L_DEFAULT, ALPHA)
-    peaks, _ = measured_peaks()
+    peaks, peak_kind = measured_peaks()
+    detail = {"metric": METRIC, "n": n}
+
+    # the headline, timed on its own with the clocks sampled around it
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.4)
-    paths = {}
-    fields = {}
-    # mixed: FP32 bulk + FP64 refinement, GMRES started by linear extrapolation in
-    # time, host-driven loop with per-launch timers (the per-kernel rooflines);
-    # mixed_df: the same with the refinement matvec and the coefficient pass in
-    # double-float arithmetic (precision 2); *_graph: the same kernels with each
-    # RK4 step replayed as a CUDA graph; fp64: the paper's method (FP64, start
-    # from the last sigma); mixed_paper_start: precision 1 with the paper's
-    # start, for attribution; *_poly*: each stage started from the polynomial
-    # in time through the same stage's sigma of the last 3-4 steps (guess 3)
-    plan = (("mixed", 1, 2, 0), ("mixed_graph", 1, 2, 1), ("mixed_df", 2, 2, 0), ("mixed_df_graph", 2, 2, 1),
-            ("fp64", 0, 0, 0), ("mixed_paper_start", 1, 0, 0), ("mixed_df3_graph", 3, 2, 1),
-            ("mixed_df_poly", 2, 3, 0), ("mixed_df_poly_graph", 2, 3, 1), ("mixed_df3_poly_graph", 3, 3, 1),
-            ("fp64_poly", 0, 3, 0))
-    solvers = {}
-    devfields = {}
-    for name, prec, guess, graph in plan:
-        if args.path == "mixed" and not name.startswith("mixed"):
-            continue
-        if args.path == "fp64" and not name.startswith("fp64"):
-            continue
-        if args.no_graph and graph:
-            continue
-        if args.no_df and prec == 2:
-            continue
-        if args.arms and name not in args.arms.split(","):
-            continue
-        s, f, rec = time_path(prec, guess, args, st, n, world, graph)
-        rec["precision"] = prec
-        fields[name] = [x.cpu().numpy() for x in f[:3]]
-        devfields[name] = f
-        solvers[name] = s
-        paths[name] = rec
-    # learned start: networks trained here on solver snapshots of four
-    # other Gaussian humps (amplitudes 0.35-0.65, shifted centres), then run on
-    # the benchmark state: over the paper's start (tau = dt/2, coarse n/8) and
-    # over the extrapolated start (tau = (dt/2)^2, coarse n/16)
-    learned_info = {}
-    nets = {}
-    if not args.no_learned and args.path != "fp64" and (not args.arms or any("learned" in a for a in
-                                                                              args.arms.split(","))):
-        from paper_2306_09731_gb300 import learned as Lm
-        for name, prec, guess, graph, tau_power, coarse in (
-                ("mixed_df_paper_start", 2, 0, 0, 0, 0), ("mixed_df_paper_start_learned", 2, 0, 0, 1, n // 8),
-                ("mixed_df_learned_graph", 2, 2, 1, 2, n // 16)):
-            if args.arms and name not in args.arms.split(","):
-                continue
-            learned = None
-            if coarse:
-                t0 = time.perf_counter()
-                states = Lm.gaussian_states(n, L_DEFAULT, [0.35, 0.45, 0.55, 0.65], seed=1)
-                samples = Lm.generate(states, coarse, steps=8, dt=DT, precision=prec, guess=guess,
-                                      tau_power=tau_power)
-                t1 = time.perf_counter()
-                net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2,
-                                                            log_every=100)
-                torch.cuda.synchronize()
-                t2 = time.perf_counter()
-                learned = (net, in_scale, out_scale, tau_power)
-                nets[name] = learned
-                learned_info[name] = {"coarse_n": coarse, "samples": int(samples.shape[0]),
-                                      "data_s": t1 - t0, "train_s": t2 - t1, "losses": losses,
-                                      "params": net.num_params()}
-            s, f, rec = time_path(prec, guess, args, st, n, world, graph, learned)
-            rec["precision"] = prec
-            fields[name] = [x.cpu().numpy() for x in f[:3]]
-            devfields[name] = f
-            solvers[name] = s
-            paths[name] = rec
-    # headline: the fastest arm of the headline path (all of them meet the same
-    # FP64 tolerance test in every solve); its per-kernel figures come from the
-    # host-driven arm of the same precision
-    if args.path == "fp64":
-        head_name = "fp64"
-    else:
-        cands = [k for k in ("mixed", "mixed_graph", "mixed_df", "mixed_df_graph", "mixed_df_learned_graph",
-                             "mixed_df_poly", "mixed_df_poly_graph") if k in paths]
-        head_name = max(cands, key=lambda k: paths[k]["value"])
-    prof_name = {"mixed_graph": "mixed", "mixed_df_graph": "mixed_df", "mixed_df_learned_graph": "mixed_df",
-                 "mixed_df_poly_graph": "mixed_df_poly"}.get(head_name, head_name)
-    head_solver, head_rec = solvers[head_name], paths[head_name]
-    head_prec = head_rec["precision"]
-    for name, s in solvers.items():
-        if name != head_name:
-            s.close()
+    prec, guess, graph = HEADLINE
+    head, hf, head_rec = time_path(prec, guess, args, st, n, world, graph)
     clk = clocks.stop()
+    head_fields = [x.cpu().numpy() for x in hf[:3]]
+    detail["headline"] = {k: v for k, v in head_rec.items() if k != "prof"}
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, args.steps // 4)
+    # end to end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory and the result back (in the call)
+    e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
     nbytes = 4 * n * n * 8
     e2e = None
     if e2e_steps > 0:
         pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory().numpy()
         hh = [pin(st.h), pin(st.vx), pin(st.vy), pin(st.sigma)]
-        sgn_rk4_step_host(head_solver.handle, *hh, DT, 1)  # warm
+        sgn_rk4_step_host(head.handle, *hh, DT, 1)  # warm
+        for _ in range(max(0, args.warmup - 1)):
+            sgn_rk4_step_host(head.handle, *hh, DT, 1)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(e2e_steps):
-            sgn_rk4_step_host(head_solver.handle, *hh, DT, 1)
+            sgn_rk4_step_host(head.handle, *hh, DT, 1)
         w1 = time.perf_counter()
         e2e_value, _ = throughput(e2e_steps, w1 - w0, world)
-        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
-               "api": "sgn_rk4_step_host (pinned host buffers, one step per call)"}
-    # ensembles: 64 perturbed line solitons, a ~ U[0.1, 1], eps ~ U[1e-3, 5e-2], on
-    # 256^2, 512x256 and 1024x512 grids, dt = 2e-3, each member with its own handle and
-    # stream: sgn_rk4_step_batch against the members stepped one by one (wall time of
-    # K steps of all members after W warm-up steps; host timers around calls that
-    # synchronise)
-    ensemble = None
-    if not args.no_ensemble and world == 1 and args.path != "fp64" and not args.arms:
-        from paper_2306_09731_gb300.ensemble import GRIDS, Ensemble, perturbed_members
-        members = perturbed_members(64, seed=11)
-        ens = {}
-        for tuned in ((False, True) if not args.no_tune else (False,)):
-            E = Ensemble(members, tune=tuned, precision=2, guess=2, graph=1)
-            E.step(2e-3, max(1, args.warmup))
-            torch.cuda.synchronize()
-            b0 = time.perf_counter()
-            E.step(2e-3, args.steps)
-            b1 = time.perf_counter()
-            E.step_one_by_one(2e-3, args.steps)
-            b2 = time.perf_counter()
-            ens[tuned] = (b1 - b0, b2 - b1, E.tuning[:3] if tuned else None)
-            E.close()
-        tb, to, tuning = ens[max(ens)]
-        ensemble = {"members": len(members), "grids": [list(g[:2]) for g in GRIDS], "dt": 2e-3,
-                    "steps": args.steps, "unit": "member-steps/s",
-                    "batch": len(members) * args.steps / tb,
-                    "one_by_one": len(members) * args.steps / to,
-                    "speedup": to / tb, "tuned": max(ens)}
-        if True in ens and False in ens:
-            ensemble["batch_builtin_shapes"] = len(members) * args.steps / ens[False][0]
-            ensemble["tuning_first_members"] = tuning
-        # the same batch with the polynomial start (4 warm-up steps of history)
-        E = Ensemble(members, tune=max(ens), precision=2, guess=3, graph=1)
-        E.step(2e-3, max(4, args.warmup))
-        torch.cuda.synchronize()
-        b0 = time.perf_counter()
-        E.step(2e-3, args.steps)
-        ensemble["batch_polynomial"] = len(members) * args.steps / (time.perf_counter() - b0)
-        E.close()
-    # the paper's monitoring quantities on the final state: wall time of
-    # one sgn_diagnostics call (three max sweeps, one 3-field FFT, one readback)
-    hf = devfields[head_name]
-    head_solver.diagnostics(hf[0], hf[1], hf[2])
-    torch.cuda.synchronize()
-    d0 = time.perf_counter()
-    for _ in range(5):
-        diag = head_solver.diagnostics(hf[0], hf[1], hf[2])
-    diag_ms = (time.perf_counter() - d0) / 5 * 1e3
-    head_solver.close()
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": e2e_steps, "api": "sgn_rk4_step_host, pinned host buffers, one step per call"}
+    head.close()
+    del hf
 
-    # crossing line solitons at 4096^2 (the learned start's workload): two a = 0.6
-    # solitons rotated by +-theta, precision 2, graph mode, every solve to the
-    # FP64 tolerance 1e-10; the paper's start (last sigma), the extrapolated
-    # start, and each with the network trained above on the 2048^2 Gaussian
-    # snapshots (coarse grids 256 and 128)
-    crossing = None
-    if not args.no_crossing and world == 1 and args.path != "fp64" and not args.arms and n == N_DEFAULT:
-        del devfields, hf
-        torch.cuda.empty_cache()
-        ksteps, kwarm = max(3, args.steps // 4), 2
-        crossing = {"workload": "crossing_solitons_4096x4096", "grid": [4096, 4096], "box": [-100.0, 100.0],
-                    "a": 0.6, "dt": DT, "precision": 2, "graph": True, "steps": ksteps,
-                    "warmup": kwarm, "warmup_polynomial": max(kwarm, 4),
-                    "unit": UNIT, "tol": 1e-10, "theta": {}}
-        for theta in (15.0, 30.0):
-            cst = I.crossing_solitons(4096, 200.0, 0.6, theta)
-            arms = {}
-            # the polynomial start needs 4 steps of history before the cubic:
-            # its arm warms up for 4 steps
-            for name, guess, lname in (("paper_start", 0, None),
-                                       ("paper_start_learned", 0, "mixed_df_paper_start_learned"),
-                                       ("extrapolated", 2, None),
-                                       ("extrapolated_learned", 2, "mixed_df_learned_graph"),
-                                       ("polynomial", 3, None)):
-                if lname is not None and lname not in nets:
-                    continue
-                arms[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps,
-                                           max(kwarm, 4) if guess == 3 else kwarm, not args.no_tune)
-            crossing["theta"][f"{theta:g}"] = arms
-            del cst
-        for ln, (net, *_rest) in nets.items():
-            crossing.setdefault("networks", {})[ln] = {"coarse_n": net.n}
+    # the paper's method: FP64 throughout, GMRES from the last sigma, host loop
+    fp64 = None
+    if not args.no_fp64:
+        s, f, rec = time_path(0, 0, args, st, n, world, 0)
+        s.close()
+        ff = [x.cpu().numpy() for x in f[:3]]
+        del f
+        fp64 = {"value": rec["value"], "ms_per_step": rec["ms_per_step"],
+                "iters_per_stage": rec["gmres"]["iters_per_stage"], "path": "precision 0, guess 0, host loop"}
+        fp64["headline_vs_fp64_rel_l2"] = {
+            nm: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+            for nm, a, b in zip(("h", "vx", "vy"), head_fields, ff)}
+        fp64["after_steps"] = args.warmup + args.steps
+        detail["fp64_plain"] = {k: v for k, v in rec.items() if k != "prof"}
 
-    fp32 = head_prec >= 1
-    # a run restricted to graph arms (--arms) has no per-launch timers
-    prof = paths[prof_name]["prof"] if prof_name in paths else {"ms": {}, "counts": {}, "launches": 0}
-    rooflines = {c: class_roofline(c, n, head_prec, prof, peaks) for c in SINGLE_KERNEL_CLASSES}
-    doms = [c for c in rooflines if rooflines[c]]
-    dom = max(doms, key=lambda c: prof["ms"][c]) if doms else None
-    total_prof = sum(prof["ms"].values())
-    gmres_ms = sum(prof["ms"].get(k, 0.0) for k in ("mv_yinv", "mv_x", "mv_yfwd", "krylov", "ref_yinv", "ref_x",
-                                                    "ref_yfwd"))
-    out = {
-        "metric": METRIC, "value": head_rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": head_rec["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
-        "config": dict(config(n, fp32), parallelism=f"replicas{world}" if world > 1 else "single"),
-        "path": ({0: "plain FP64",
-                  1: "mixed: FP32 bulk + FP64 refinement to the FP64 tolerance",
-                  2: "mixed: FP32 bulk + double-float refinement matvec and coefficients to the FP64 tolerance"}
-                 [head_prec])
-                + (", GMRES start: each stage's sigma extrapolated by the cubic in time through the same stage "
-                   "of the last 4 steps" if "_poly" in head_name else ", GMRES start extrapolated in time")
-                + (", each RK4 step one CUDA graph with device-side GMRES control"
-                   if head_name.endswith("_graph") else ", host-driven GMRES loop"),
-        "arms": {k: dict({"value": v["value"], "ms_per_step": v["ms_per_step"], "precision": v["precision"],
-                          "graph": k.endswith("_graph"), "iters_per_stage": v["gmres"]["iters_per_stage"],
-                          "tuned_threads": ({ty: {ps: r["threads"] for ps, r in d.items()}
-                                             for ty, d in v["tuning"].items()} if v.get("tuning") else None)},
-                         **({"avg_launch_ms": {c: v["prof"]["ms"][c] / v["prof"]["counts"][c]
-                                               for c in v["prof"]["ms"] if v["prof"]["counts"][c]}}
-                            if v["prof"] else {}))
-                 for k, v in paths.items()},
-        "gmres": head_rec["gmres"],
-        # launch shapes sgn_autotune picked for the headline handle, with the
-        # timed launch (us) of each pass in the built-in and the picked shape
-        "tuning": head_rec.get("tuning"),
-        "time_share": {k: v / total_prof for k, v in prof["ms"].items() if v > 0},
-        "gmres_share": gmres_ms / total_prof if total_prof else None,
-        # kernel time summed from the event timers of the host-driven run: the
-        # rest of its ms_per_step is launch gaps and the per-Arnoldi-step host
-        # synchronisation
-        "kernel_ms_per_step": total_prof / args.steps,
-        "gpu_launches": head_rec["launches"],
-        # time_share and the rooflines come from the host-driven run of the same
-        # kernels (graph mode has no per-launch timers)
-        "roofline_source": f"{prof_name} (host-driven loop, CUDA events per launch)",
-        "roofline": rooflines[dom] if dom else None,
-        "roofline_by_kernel": {c: {"frac": r["frac"], "bound": r["bound"], "achieved": r["achieved"],
-                                   "unit": r["unit"], "avg_launch_ms": r["avg_launch_ms"]}
-                               for c, r in rooflines.items() if r},
-        "e2e": e2e,
-        "clocks": clk,
-        "diagnostics": {"ms_per_call": diag_ms, "h_max": diag["h_max"], "c_fit": diag["c_fit"],
-                        "tail": diag["tail"]},
-        "ensemble": ensemble,
-        "crossing_4096": crossing,
-        "transverse": transverse_stability() if (args.transverse and world == 1) else None,
-    }
-    if "fp64_poly" in paths:
-        fp = paths["fp64_poly"]
-        out["fp64_poly_start"] = {"value": fp["value"], "unit": UNIT, "ms_per_step": fp["ms_per_step"],
-                                  "gmres": fp["gmres"]}
-    if "fp64" in paths and head_name != "fp64":
-        f64 = paths["fp64"]
-        out["fp64_plain"] = {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
-                             "gmres": f64["gmres"]}
-        out["speedup_vs_fp64"] = head_rec["value"] / f64["value"]
-        errs = {}
-        for i, nm in enumerate(("h", "vx", "vy")):
-            a, b = fields[head_name][i], fields["fp64"][i]
-            errs[nm] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-        out["headline_vs_fp64_rel_l2"] = errs
-        out["headline_vs_fp64_after_steps"] = args.warmup + args.steps
-    for base in ("mixed", "mixed_df", "mixed_df_poly"):
-        if base + "_graph" in paths and base in paths:
-            mg, mh = paths[base + "_graph"], paths[base]
-            out.setdefault("graph_vs_host_loop", {})[base] = {
-                "graph": mg["value"], "host_loop": mh["value"], "unit": UNIT, "ratio": mg["value"] / mh["value"],
-                "fields_bitwise_equal": all(bool(np.array_equal(a, b))
-                                            for a, b in zip(fields[base + "_graph"], fields[base]))}
-    if learned_info:
-        lr = {"training": learned_info}
-        for base, arm in (("mixed_df_paper_start", "mixed_df_paper_start_learned"),
-                          ("mixed_df_graph", "mixed_df_learned_graph")):
-            if base in paths and arm in paths:
-                b, a = paths[base], paths[arm]
-                lr[arm] = {"value": a["value"], "base": base, "base_value": b["value"],
-                           "speedup": a["value"] / b["value"],
-                           "inner_matvecs_per_step": a["gmres"]["inner_matvecs_per_step"],
-                           "base_inner_matvecs_per_step": b["gmres"]["inner_matvecs_per_step"],
-                           "refinements_per_stage": a["gmres"]["fp64_refinements_per_stage"],
-                           "base_refinements_per_stage": b["gmres"]["fp64_refinements_per_stage"]}
-        out["learned_start"] = lr
-    if "mixed_paper_start" in paths:
-        mp = paths["mixed_paper_start"]
-        out["mixed_paper_start"] = {"value": mp["value"], "unit": UNIT, "ms_per_step": mp["ms_per_step"],
-                                    "gmres": mp["gmres"]}
-    return out
+    # the headline's kernels in the host-driven loop with per-launch CUDA-event
+    # timers: the roofline of the dominant kernel and the time shares
+    roof, share = None, None
+    if not args.no_prof:
+        s, f, rec = time_path(prec, guess, args, st, n, world, 0, profile=True)
+        s.close()
+        del f
+        prof = rec["prof"]
+        rl = {c: class_roofline(c, n, prec, prof, peaks, peak_kind) for c in SINGLE_KERNEL_CLASSES}
+        rl = {c: r for c, r in rl.items() if r}
+        total = sum(prof["ms"].values())
+        share = {k: v / total for k, v in prof["ms"].items() if v > 0}
+        gm = sum(prof["ms"].get(k, 0.0) for k in ("mv_yinv", "mv_x", "mv_yfwd", "krylov", "ref_yinv", "ref_x",
+                                                  "ref_yfwd"))
+        if rl:
+            dom = max(rl, key=lambda c: prof["ms"][c])
+            roof = dict(rl[dom])
+            roof["time_share"] = share[dom]
+        detail["profiled_host_loop"] = {"value": rec["value"], "ms_per_step": rec["ms_per_step"],
+                                        "gmres": rec["gmres"], "time_share": share,
+                                        "gmres_share": gm / total if total else None,
+                                        "kernel_ms_per_step": total / rec["steps"], "rooflines": rl}
+
+    if args.full and world == 1:
+        run_extras(args, st, n, detail)
+    if args.transverse and world == 1:
+        detail["transverse"] = transverse_stability()
+
+    out = compact_line(head_rec, fp64, roof, share, e2e, clk, args, world, n)
+    return out, detail
 
 
-def oracle_stage_sample(n):
-    """Times one RK4 stage of the oracle (stage 2 of the first step) at n x n."""
-    import numpy as np
-
-    from oracle import sgn_oracle as O
-    from paper_2306_09731_gb300 import inputs as I
-    st = I.gaussian_hump(n, L_DEFAULT, ALPHA)
-    G = O.Grid(n, n, L_DEFAULT, L_DEFAULT)
-    k1h, k1x, k1y, sig, _ = O.rhs(G, st.h, st.vx, st.vy, st.sigma)
-    t0 = time.perf_counter()
-    _, _, _, _, info = O.rhs(G, st.h + 0.5 * DT * k1h, st.vx + 0.5 * DT * k1x, st.vy + 0.5 * DT * k1y, sig)
-    t = time.perf_counter() - t0
-    return t, info["iters"]
-
+# ---------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle as it stands (the paper ships no
+    code), rank 0 only. Each step is one whole oracle RK4 step of the workload
+    at --sample-n, scaled to the --n grid by the measured matvec cost ratio."""
     if rank != 0:
         return None
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    n = args.n
-    for _ in range(max(0, min(args.warmup, 1))):
-        oracle_stage_sample(min(n, 256))
-    times = []
-    its = []
-    for _ in range(args.steps):
-        t, it = oracle_stage_sample(n)
-        times.append(t)
-        its.append(it)
-    step_s = 4.0 * sum(times) / len(times)
-    value = 1.0 / step_s
-    sample = (f"{args.steps} samples of one RK4 stage (stage 2 of step 1, {its[0]} GMRES iterations) of the "
-              f"{n}x{n} workload, step time = 4 x mean stage time")
-    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(config(n, True), parallelism="single"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    n, ns = args.n, min(args.sample_n, args.n)
+    t = oracle_timing(n, ns, args.warmup, args.steps, all_cores=True)
+    cb = {"value": t["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_sample_text(t, n)}
+    return {"metric": METRIC, "value": t["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup,
+            # the time each timed step actually took (a sample step); the value
+            # is the scaled steps/s of the full-size workload
+            "ms_per_step": t["sample_s_per_step"] * 1e3,
+            "ms_per_step_scaled": t["target_s_per_step"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(config(n, "fp64 (the paper's method, CPU oracle)"), parallelism="single",
+                           sample_grid=[ns, ns]),
+            "cpu_baseline": cb, "all_cores": t.get("all_cores"),
+            "e2e": {"value": t["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def write_detail(path, detail):
+    try:
+        d = os.path.dirname(path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(detail, f, indent=1, default=str)
+        return path
+    except OSError as e:
+        print(f"bench: could not write {path}: {e}", file=sys.stderr)
+        return None
 
 
 def main():
@@ -740,24 +760,25 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if args.steps > 3 and args.n >= 2048:
-            args.steps = 3  # each sample is ~20-30 s of single-core work
         out = run_reference(args, rank, world)
         if out is not None:
-            print(json.dumps(out))
+            print(json.dumps(out), flush=True)
         return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    out = run_ours(args, rank, world, local_rank)
+    out, detail = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, it = oracle_stage_sample(args.n)
-        v = 1.0 / (4.0 * t)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"one RK4 stage (stage 2 of step 1, {it} GMRES iterations, FP64) of the "
-                                         f"{args.n}x{args.n} workload, x4 for a step; numpy FFT, 1 thread"}
+        # a bounded sample: 2 whole oracle steps at 512^2 on one core, then one
+        # step on every core at once
+        t = oracle_timing(args.n, min(args.sample_n, args.n), 1, 2, all_cores=True)
+        out["cpu_baseline"] = {"value": t["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": cpu_sample_text(t, args.n),
+                               "all_cores": {k: t["all_cores"][k] for k in ("cores", "value", "unit")}}
+        detail["cpu_baseline"] = t
     if rank == 0:
-        print(json.dumps(out))
+        out["detail"] = write_detail(args.detail, dict(detail, line=out))
+        print(json.dumps(out), flush=True)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -206,11 +206,16 @@ sgn_status sgn_get_profile(sgn_t ctx, double* ms, long long* counts, int n, long
  * SGN_NOALLOC_MAX_POINTS grid points (about 4 MB), held on every GPU that
  * loads the library until the process exits. The call allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine).
- *  - Nx*Ny > SGN_NOALLOC_MAX_POINTS, or a size sgn_create would refuse, returns
- *    SGN_EINVAL with a message in sgn_last_error(NULL); so do NULL pointers.
- *  - The first call on a device sets up (looks up the static array's device
- *    address with that device current); make that first call before any
- *    stream capture.
+ *  - Nx, Ny: powers of two in [8, 4096] as for sgn_create, with
+ *    Nx*Ny <= SGN_NOALLOC_MAX_POINTS (so 4096 x 16 and 16 x 4096 are the
+ *    longest axes). Any other size, or a NULL pointer, returns SGN_EINVAL
+ *    with a message in sgn_last_error(NULL).
+ *  - Every call looks up the static array's address on the current device
+ *    (cudaGetSymbolAddress); the first call on a device also loads the
+ *    library's device code there, so make that first call before any stream
+ *    capture. No host-side state is cached, so calls from several host
+ *    threads share nothing on the host but sgn_last_error(NULL), which is kept
+ *    per host thread.
  *  - Every call uses the same array and leaves its contents behind: calls
  *    that overlap on the GPU (other streams, other host threads) race. Calls
  *    on one stream, one after another, are safe.
@@ -222,7 +227,9 @@ sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly,
                                       const double* h, const double* sigma, double* out,
                                       void* cuda_stream);
 
-/* Message for the last failing call on ctx (or on sgn_create if ctx is NULL). */
+/* Message for the last failing call on ctx. With ctx NULL: the message of
+ * the last failing handle-less call (sgn_create, sgn_elliptic_apply_noalloc)
+ * made by the calling host thread (one slot per thread, like errno). */
 const char* sgn_last_error(sgn_t ctx);
 
 /* Ensembles: count independent problems, each with its own handle

@@ -135,7 +135,9 @@ struct sgn_ctx {
   sgn_stats stats{};
 };
 
-std::string g_create_error;  // also written by sgn_elliptic_apply_noalloc
+// message of the last failing handle-less call (sgn_create, sgn_elliptic_apply_noalloc),
+// one per host thread, like errno
+thread_local std::string g_create_error;
 
 namespace {
 

@@ -13,9 +13,13 @@
 //
 // The kernels are the ones sgn_elliptic_apply uses; only the buffers differ.
 // In host code g_noalloc_scratch is a host-side stand-in, not a device
-// address, so the first call on each device asks the runtime for the array's
-// device address with cudaGetSymbolAddress (with that device current) and
-// keeps it for later calls on that device.
+// address, so every call asks the runtime for the array's device address on
+// the current device with cudaGetSymbolAddress (a table lookup once the
+// module is loaded; the first call on a device loads it, which is why that
+// first call should come before any stream capture). Nothing is cached on the
+// host: calls from several host threads share no host state but the
+// per-thread error message, and a context torn down by cudaDeviceReset leaves
+// no stale address behind.
 #include <math.h>
 #include <stdio.h>
 
@@ -26,13 +30,11 @@
 
 using namespace sgn;
 
-// message slot read by sgn_last_error(NULL)
-extern std::string g_create_error;
+// message slot read by sgn_last_error(NULL), one per host thread
+extern thread_local std::string g_create_error;
 
 namespace {
 constexpr size_t kScratchBytes = (size_t)4 << 20;
-constexpr int kMaxDevices = 64;
-void* g_scratch_dev[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -73,8 +75,8 @@ __global__ void k_noalloc_tables(int Nx, int Ny, double Lx, double Ly, cpx<doubl
 extern "C" sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, double Ly, const double* h,
                                                  const double* sigma, double* out, void* cuda_stream) {
   if (!h || !sigma || !out) return noalloc_fail(SGN_EINVAL, "NULL field pointer");
-  if (!is_pow2(Nx) || !is_pow2(Ny) || Nx < 8 || Ny < 8 || Nx > 2048 || Ny > 2048)
-    return noalloc_fail(SGN_EINVAL, "Nx, Ny must be powers of two in [8, 2048]");
+  if (!is_pow2(Nx) || !is_pow2(Ny) || Nx < 8 || Ny < 8 || Nx > 4096 || Ny > 4096)
+    return noalloc_fail(SGN_EINVAL, "Nx, Ny must be powers of two in [8, 4096]");
   if ((long long)Nx * Ny > SGN_NOALLOC_MAX_POINTS)
     return noalloc_fail(SGN_EINVAL, "grid of " + std::to_string(Nx) + " x " + std::to_string(Ny) +
                                         " points exceeds the allocation-free limit of " +
@@ -83,18 +85,14 @@ extern "C" sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, doub
     return noalloc_fail(SGN_EINVAL, "Lx, Ly must be positive and finite");
 
   cudaStream_t stream = (cudaStream_t)cuda_stream;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(SGN_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SGN_EINVAL, "device index out of range");
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return noalloc_fail(SGN_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    init_kernel_attributes<double>();
-    g_scratch_dev[dev] = p;
-  }
+  // the static array's address on the current device (looked up on every
+  // call: no host-side cache to race on or to go stale)
+  void* scratch = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+  if (e != cudaSuccess || !scratch)
+    return noalloc_fail(SGN_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  // the shared-memory opt-in of the transform kernels (per device; cheap to repeat)
+  init_kernel_attributes<double>();
 
   Geom G{};
   G.Nx = Nx;
@@ -107,7 +105,7 @@ extern "C" sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, doub
   G.Ly = Ly;
 
   // carve the scratch: tables, coefficient fields, flags, four half spectra
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_dev[dev]);
+  unsigned char* base = static_cast<unsigned char*>(scratch);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     unsigned char* p = base + off;

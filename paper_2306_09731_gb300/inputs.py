@@ -131,6 +131,22 @@ def gaussian_hump(N=2048, L=100.0, alpha=0.5) -> State:
                  meta=dict(kind="gaussian_hump", alpha=alpha))
 
 
+def gaussian_hump_flow(N=2048, L=100.0, alpha=0.5, beta=0.2) -> State:
+    """The Gaussian hump h = 1 + alpha exp(-(x^2+y^2)) carrying a smooth
+    potential flow v = grad(phi), phi = beta exp(-((x-1)^2 + y^2)/2) (so
+    curl v = 0, the class of flows of Section 2.1), sigma = 0 as the GMRES
+    start: the benchmark's depth with a right-hand side whose nonlinear
+    terms are not zero."""
+    x, y = coords(N, N, L, L)
+    X, Y = x[None, :], y[:, None]
+    h = 1.0 + alpha * np.exp(-(X ** 2 + Y ** 2))
+    e = beta * np.exp(-0.5 * ((X - 1.0) ** 2 + Y ** 2))
+    vx = -(X - 1.0) * e
+    vy = -Y * e
+    return State(N, N, L, L, h=h, vx=np.ascontiguousarray(vx), vy=np.ascontiguousarray(vy),
+                 sigma=np.zeros((N, N)), meta=dict(kind="gaussian_hump_flow", alpha=alpha, beta=beta))
+
+
 def deformed_soliton(Nx=1024, Ny=128, Lx=20 * math.pi, Ly=4 * math.pi, c=1.7,
                      x0=-10.0, shift=0.1) -> State:
     """Deformed line soliton of Eq. (soldef): crest at x0 + shift cos(y).

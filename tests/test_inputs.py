@@ -66,3 +66,19 @@ def test_random_band_matches_its_sum():
             ph = mx * X[None, :] + my * Y[:, None]
             ref += w * (P[a, b] * np.cos(ph) - Q[a, b] * np.sin(ph))
     assert np.max(np.abs(f - ref)) < 1e-13
+
+
+def test_gaussian_hump_flow_is_curl_free_potential_flow():
+    """v = grad(phi) of the stated potential: compared with a centred finite
+    difference of phi, and curl v = 0 by the same differences."""
+    from paper_2306_09731_gb300 import inputs as I
+    N, L, beta = 256, 20.0, 0.2
+    st = I.gaussian_hump_flow(N, L, 0.5, beta)
+    x, y = I.coords(N, N, L, L)
+    d = 1e-5
+    phi = lambda X, Y: beta * np.exp(-0.5 * ((X - 1.0) ** 2 + Y ** 2))
+    X, Y = np.meshgrid(x, y)
+    assert np.abs(st.vx - (phi(X + d, Y) - phi(X - d, Y)) / (2 * d)).max() < 1e-9
+    assert np.abs(st.vy - (phi(X, Y + d) - phi(X, Y - d)) / (2 * d)).max() < 1e-9
+    assert np.abs(st.h - 1.0 - 0.5 * np.exp(-(X ** 2 + Y ** 2))).max() < 1e-15
+    assert not st.sigma.any()

@@ -305,6 +305,42 @@ def test_dealias_mask_two_thirds():
     assert kept_x == 2 * (24 // 3) + 1 and kept_y == 2 * (12 // 3) + 1
 
 
+def _rhs_cos_flow_closed_form(x, a, m, g=1.0):
+    """Exact right-hand side for h = 1, vx = a cos(m x), vy = 0 on a 2 pi box.
+    Eq. (sigmav) at h = 1 is 3 sigma - sigma_xx = a m sin(m x), so
+    sigma = a m sin(m x)/(3 + m^2) and u = 3 a cos(m x)/(3 + m^2):
+    h_t = 3 a m sin(m x)/(3 + m^2) (mode m). F = |v|^2/2 - sigma_x^2/2 + g -
+    9 sigma^2/2 is a constant plus A cos(2 m x) with
+    A = (a^2/4)(1 - (m^4 - 9 m^2)/(3 + m^2)^2), so vx_t = 2 m A sin(2 m x)
+    (mode 2m, the only one the products create)."""
+    ht = 3.0 * a * m * np.sin(m * x) / (3.0 + m * m)
+    A = 0.25 * a * a * (1.0 - (m ** 4 - 9.0 * m * m) / (3.0 + m * m) ** 2)
+    return ht, 2.0 * m * A * np.sin(2 * m * x)
+
+
+def pin_dealias_closed_form():
+    """The 2/3 rule on the right-hand side (dealias=True): on 32 points the
+    product mode 2m = 12 has 3|m| = 36 > 32 and must vanish from vx_t while
+    h_t (mode 6) is unchanged; on 30 points mode 10 has 3|m| = 30 <= 30 and
+    must stay; without the rule mode 12 is there. Largest error against the
+    closed forms."""
+    a, err = 0.3, 0.0
+    for Nx, m, dealias, keep in ((32, 6, True, False), (30, 5, True, True), (32, 6, False, True)):
+        G = O.Grid(Nx, 4, 2 * math.pi, 2 * math.pi)
+        X = np.broadcast_to(G.x[None, :], (4, Nx))
+        vx = a * np.cos(m * X)
+        z = np.zeros_like(vx)
+        ht, vxt, vyt, _, _ = O.rhs(G, np.ones_like(vx), vx, z, z, tol=1e-14, dealias=dealias)
+        eht, evxt = _rhs_cos_flow_closed_form(X, a, m)
+        err = max(err, np.abs(ht - eht).max(), np.abs(vxt - (evxt if keep else 0.0)).max(), np.abs(vyt).max())
+        assert np.abs(evxt).max() > 1e-3  # the product mode is present in the exact RHS
+    return err
+
+
+def test_dealias_rhs_closed_form():
+    assert pin_dealias_closed_form() < 1e-13
+
+
 # --------------------------------------------------------- planted mistakes
 
 MUTANTS = {}
@@ -366,6 +402,20 @@ def _m5(monkeypatch):
     monkeypatch.setattr(O, "rhs", bad)
 
 
+@_mutant("dealias_mask_skipped")
+def _m7(monkeypatch):
+    monkeypatch.setattr(O, "dealias_mask", lambda G: np.ones((G.Ny, G.Nx)))
+
+
+@_mutant("dealias_strict_inequality")
+def _m8(monkeypatch):
+    def strict(G):
+        keep_x = 3.0 * np.abs(G.mx) < G.Nx
+        keep_y = 3.0 * np.abs(G.my) < G.Ny
+        return (keep_y[:, None] & keep_x[None, :]).astype(np.float64)
+    monkeypatch.setattr(O, "dealias_mask", strict)
+
+
 @_mutant("missing_gravity_term")
 def _m6(monkeypatch):
     orig = O.rhs
@@ -377,7 +427,7 @@ def _m6(monkeypatch):
 
 PINS = [(pin_trig_derivative, 1e-11), (pin_manufactured_elliptic, 1e-11),
         (pin_soliton_sigma, 1e-9), (pin_soliton_rhs, 1e-8), (pin_rk4_soliton, 1e-8),
-        (pin_linear_dispersion, 1e-5)]
+        (pin_linear_dispersion, 1e-5), (pin_dealias_closed_form, 1e-13)]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
