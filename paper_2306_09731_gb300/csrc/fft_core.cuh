@@ -18,8 +18,14 @@
 // (several interleaved columns), see sidx().
 //
 // Twiddles W_N^k = exp(-2 pi i k / N) come from a table in global memory
-// (L1-resident); the inverse transform uses their conjugates. No transform
-// scales its output.
+// (L1-resident) laid out by stage: the stage of sub-transform length
+// Ns = 2^lNs and radix R reads its R - 1 twiddle rows W_{R Ns}^{jm r}
+// (r = 1..R-1, jm = 0..Ns-1) at offset 2^lNs - 8 of the table, row r - 1
+// holding jm = 0..Ns-1 contiguously. The threads of a warp take consecutive jm,
+// so one twiddle load touches one or two cache lines instead of up to one line
+// per thread (the W_N^{jm r} entries of a flat table lie 2^(lN-lNs-3) r
+// entries apart). staged_exponent() gives the k of each entry. The inverse
+// transform uses the conjugates. No transform scales its output.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -109,6 +115,26 @@ __device__ __forceinline__ int sidx<float>(int p, int lcs) {
 // shared-memory elements needed by one transform of length N (either layout)
 __host__ __device__ constexpr int smem_elems(int N) { return N + (N >> 3); }
 
+// Exponent k of entry i of the staged twiddle table of a length-2^lN
+// transform (the entry is W_N^k), or -1 past the last stage's rows. The
+// radix-8 stages have lNs = 3, 6, ..., then one radix-2 or radix-4 stage when
+// 3 does not divide lN (the stage plan of fft_regs); the stage of lNs starts at
+// 2^lNs - 8 and holds (R - 1) rows of 2^lNs entries. Fewer than N entries in all.
+__host__ __device__ inline int staged_exponent(int i, int lN) {
+  const int n8 = lN / 3, rem = lN - 3 * n8;
+  for (int lNs = 3;; lNs += 3) {
+    const bool tail = lNs == 3 * n8;  // the radix-2 or radix-4 stage, if any
+    if (lNs > 3 * n8 || (tail && rem == 0)) return -1;
+    const int lr = tail ? rem : 3;
+    const int Ns = 1 << lNs, off = Ns - 8;
+    if (i < off) return -1;
+    if (i < off + ((1 << lr) - 1) * Ns) {
+      const int q = i - off;
+      return ((q & (Ns - 1)) * (q / Ns + 1)) << (lN - lNs - lr);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- butterflies
 // Forward transforms use W = exp(-2 pi i / n); INV uses exp(+2 pi i / n).
 
@@ -168,7 +194,6 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[8], cpx<T>* sm, const cpx<
   constexpr int NB = 8 / RS;
   const int T_ = 1 << (lN - 3);
   const int Ns = 1 << lNs;
-  const int twshift = lN - lNs - LRS;  // log2(N / (Ns*RS))
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = t + q * T_;
@@ -178,22 +203,24 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[8], cpx<T>* sm, const cpx<
     for (int r = 0; r < RS; ++r) xs[r] = v[q + r * NB];
     if (lNs > 0) {
       cpx<T> w[RS];
+      // this stage's rows of the staged table: entry (r - 1) * Ns + jm is W^{jm r}
+      const cpx<T>* tws = tw + (Ns - 8) + jm;
       if (sizeof(T) == 4 && RS >= 4) {
         // FP32: three table loads and products for the rest (the L1 pipe, not
         // the FMA pipe, limits the FP32 passes); FP64 loads all (FP64 products
         // cost more than loads on this part)
-        w[1] = ldg(tw + (jm << twshift));
-        w[2] = ldg(tw + ((jm * 2) << twshift));
+        w[1] = ldg(tws);
+        w[2] = ldg(tws + Ns);
         w[3] = cmul(w[1], w[2]);
         if (RS == 8) {
-          w[4] = ldg(tw + ((jm * 4) << twshift));
+          w[4] = ldg(tws + 3 * Ns);
           w[5] = cmul(w[1], w[4]);
           w[6] = cmul(w[2], w[4]);
           w[7] = cmul(w[3], w[4]);
         }
       } else {
 #pragma unroll
-        for (int r = 1; r < RS; ++r) w[r] = ldg(tw + ((jm * r) << twshift));
+        for (int r = 1; r < RS; ++r) w[r] = ldg(tws + (r - 1) * Ns);
       }
 #pragma unroll
       for (int r = 1; r < RS; ++r) xs[r] = INV ? cmulc(xs[r], w[r]) : cmul(xs[r], w[r]);

@@ -245,21 +245,23 @@ void free_all(sgn_ctx* ctx) {
   ctx->gst_host = nullptr;
 }
 
+// W_N^k = exp(-2 pi i k/N) in the staged layout of the transforms (entry i
+// holds W_N^staged_exponent(i); unused tail entries are zero)
+std::vector<C64> staged_twiddles(int N, int lN) {
+  std::vector<C64> t(N);
+  for (int i = 0; i < N; ++i) {
+    const int k = staged_exponent(i, lN);
+    double c = 0.0, s = 0.0;
+    if (k >= 0) cos_sin_2pi(k, N, &c, &s);
+    t[i].x = c;
+    t[i].y = -s;
+  }
+  return t;
+}
+
 void build_tables(sgn_ctx* ctx) {
   const Geom& G = ctx->G;
-  std::vector<C64> tx(G.Nx), ty(G.Ny);
-  for (int k = 0; k < G.Nx; ++k) {
-    double c, s;
-    cos_sin_2pi(k, G.Nx, &c, &s);
-    tx[k].x = c;
-    tx[k].y = -s;
-  }
-  for (int k = 0; k < G.Ny; ++k) {
-    double c, s;
-    cos_sin_2pi(k, G.Ny, &c, &s);
-    ty[k].x = c;
-    ty[k].y = -s;
-  }
+  const std::vector<C64> tx = staged_twiddles(G.Nx, G.lNx), ty = staged_twiddles(G.Ny, G.lNy);
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<double> kx(G.Nxh), ky(G.Ny);
   for (int k = 0; k < G.Nxh; ++k) kx[k] = (k == G.Nx / 2) ? 0.0 : two_pi * k / G.Lx;

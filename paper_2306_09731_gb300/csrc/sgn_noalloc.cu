@@ -53,18 +53,22 @@ sgn_status noalloc_fail(sgn_status st, const std::string& msg) {
 // Scratch shared by every call on a device; its contents persist between calls.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Twiddles W_N^k = exp(-2 pi i k/N) and the wavenumbers (Nyquist set to 0).
-__global__ void k_noalloc_tables(int Nx, int Ny, double Lx, double Ly, cpx<double>* twx, cpx<double>* twy,
-                                 double* kx, double* ky) {
+// Twiddles W_N^k = exp(-2 pi i k/N) in the staged layout of the transforms
+// (entry i is W_N^staged_exponent(i)) and the wavenumbers (Nyquist set to 0).
+__global__ void k_noalloc_tables(int Nx, int Ny, int lNx, int lNy, double Lx, double Ly, cpx<double>* twx,
+                                 cpx<double>* twy, double* kx, double* ky) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double two_pi = 6.283185307179586476925286766559;
-  double s, c;
+  double s = 0.0, c = 0.0;
   if (i < Nx) {
-    sincospi(2.0 * (double)i / (double)Nx, &s, &c);
+    const int k = staged_exponent(i, lNx);
+    if (k >= 0) sincospi(2.0 * (double)k / (double)Nx, &s, &c);
     twx[i] = mk(c, -s);
   }
   if (i < Ny) {
-    sincospi(2.0 * (double)i / (double)Ny, &s, &c);
+    const int k = staged_exponent(i, lNy);
+    s = c = 0.0;
+    if (k >= 0) sincospi(2.0 * (double)k / (double)Ny, &s, &c);
     twy[i] = mk(c, -s);
     const int m = i < Ny / 2 ? i : i - Ny;
     ky[i] = (i == Ny / 2) ? 0.0 : two_pi * (double)m / Ly;
@@ -130,7 +134,8 @@ extern "C" sgn_status sgn_elliptic_apply_noalloc(int Nx, int Ny, double Lx, doub
 
   const Exec ex{stream, nullptr};
   const int tn = (Nx > Ny ? Nx : Ny);
-  k_noalloc_tables<<<(tn + 255) / 256, 256, 0, stream>>>(Nx, Ny, Lx, Ly, tb.twx, tb.twy, tb.kx, tb.ky);
+  k_noalloc_tables<<<(tn + 255) / 256, 256, 0, stream>>>(Nx, Ny, G.lNx, G.lNy, Lx, Ly, tb.twx, tb.twy, tb.kx,
+                                                          tb.ky);
   e = cudaGetLastError();
   // the flags keep the previous call's value: clear them first
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), stream);

@@ -86,7 +86,7 @@ def test_gmres_4096_meets_fp64_tolerance(Nx, Ny, Lx, Ly, precision):
 
 
 @pytest.mark.parametrize("Nx,Ny,Lx,Ly", THIN[:2])
-@pytest.mark.parametrize("precision,bar", [(0, 1e-10), (1, 1e-4), (2, 1e-4), (3, 1e-10)])
+@pytest.mark.parametrize("precision,bar", [(0, 1e-10), (1, 1e-5), (2, 1e-5), (3, 1e-10)])
 def test_rhs_4096(Nx, Ny, Lx, Ly, precision, bar):
     st = thin_state(Nx, Ny, Lx, Ly, Nx + 5 * Ny)
     G = O.Grid(Nx, Ny, Lx, Ly)
@@ -94,8 +94,8 @@ def test_rhs_4096(Nx, Ny, Lx, Ly, precision, bar):
     sg = dev(st.sigma)
     ht, vxt, vyt = s.rhs(dev(st.h), dev(st.vx), dev(st.vy), sg)
     rht, rvxt, rvyt, rsg, _ = O.rhs(G, st.h, st.vx, st.vy, st.sigma, tol=1e-13)
-    for a, b in ((ht, rht), (vxt, rvxt), (vyt, rvyt)):
-        assert rel(host(a), b) < bar
+    errs = [rel(host(a), b) for a, b in ((ht, rht), (vxt, rvxt), (vyt, rvyt))]
+    assert max(errs) < bar, errs
     s.close()
 
 

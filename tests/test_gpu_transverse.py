@@ -13,7 +13,9 @@ sigma is 0 and the energy contains sigma) to 1e-9 relative in FP64 (RK4 at dt =
 to 1e-6 with the FP32 bulk (each step's FP32 right-hand side carries ~1e-7
 relative rounding into dt K, ~250 x 2e-3 x 1e-7 at worst), and the
 L-infinity deviation from the line soliton (Section 4.1) equal in both
-precisions to 1e-5 of max |h| (the mixed bar, pointwise).
+precisions to twice the largest pointwise difference of h (a bound that holds
+for the fitted profile of Eq. (sol), derived in the test), that difference
+being held to 1e-5 of max |h| (the mixed bar, pointwise).
 """
 import numpy as np
 import pytest
@@ -89,9 +91,17 @@ def test_transverse_fp64_against_mixed(a):
         _, inv0, inv1, _ = out[prec]
         assert abs(inv1[0] - inv0[0]) <= 1e-12 * abs(inv0[0])
         assert abs(inv1[3] - inv0[3]) <= ebar * abs(inv0[3])
-    # the two deviations differ by at most the pointwise difference of h, which
-    # the mixed bar holds to 1e-5 of h itself (h ~ 2 at a = 1, the deviation
-    # ~ 0.02)
+    # dev_h = max |h - h_c| with h_c the solitary wave of Eq. (sol) fitted to
+    # the crest (height h_max = 1 + a, at x_s). With the same crest point, the
+    # two deviations differ by at most the largest difference of h plus that
+    # of the fitted profiles; h_max moves by at most max |dh|, and
+    # d h_c / d a = S - u S tanh(u) / (1 + a) (S = sech^2 u, u = kappa xi) lies
+    # in [-0.05, 1], so |d dev_h| <= 2 max |dh|. max |dh| is held to the mixed
+    # bar pointwise (1e-5 of max |h|): a diagnostic that is 1% of h inherits
+    # that bar scaled by max |h| / dev_h.
     d0, d1 = out[0][3], out[1][3]
-    assert abs(d1["dev_h"] - d0["dev_h"]) <= 1e-5 * float(np.max(np.abs(hd)))
+    dh = float(np.max(np.abs(hm - hd)))
+    assert dh <= 1e-5 * float(np.max(np.abs(hd))), dh
+    assert d1["x_s"] == d0["x_s"]
+    assert abs(d1["dev_h"] - d0["dev_h"]) <= 2.0 * dh + 1e-15, (d0["dev_h"], d1["dev_h"], dh)
     assert 0.0 < d0["dev_h"] < 0.1
