@@ -323,6 +323,11 @@ constexpr int rhs_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 2 : 1);
 // transform, so that one 8-slot signal is live at a time (plus the a^x half
 // spectra of phase 1 until phase 2 combines them): a = 3 sigma/h^3, then
 // bx = sigma_x/h, then by = sigma_y/h.
+// Shared-memory elements per row pair of the matvec x-pass beyond its
+// transform buffer: phase 1's half spectra a0, a1 (5 slots each per thread)
+// wait there while phase 2 transforms, instead of in 20 live registers.
+__host__ __device__ constexpr int mv_stash_elems(int N) { return 10 * (N >> 3); }
+
 template <typename T, int LN = 0>
 __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k_mv_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restrict__ kx,
                                                const cpx<T>* S, const cpx<T>* Sy, const T* __restrict__ cr,
@@ -333,8 +338,13 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
   const int N = 1 << lN, T_ = N >> 3;
   const size_t o0 = (size_t)L.y0 * G.ldS, o1 = (size_t)L.y1 * G.ldS;
   const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
+  // this row pair's stash, after the P transform buffers of the block; each
+  // thread writes and reads back only its own slots (no barrier needed)
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int P = blockDim.x >> (lN - 3);
+  cpx<T>* stash = reinterpret_cast<cpx<T>*>(smraw) + (size_t)P * smem_elems(N) + (size_t)L.grp * mv_stash_elems(N);
   cpx<T> Z[8];
-  cpx<T> a0[5], a1[5], b0[5], b1[5];
+  cpx<T> b0[5], b1[5];
   // a = 3 sigma / h^3
   load_packed(Z, S + o0, S + o1, false, kx, L.t, lN);
   fft_regs<true>(Z, sm, tw, L.t, lN);
@@ -344,7 +354,12 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
     Z[s] = mk(cc[p0 + x] * Z[s].x, cc[p1 + x] * Z[s].y);
   }
   fft_regs<false>(Z, sm, tw, L.t, lN);
-  split_pair(Z, sm, L.t, lN, a0, a1);
+  split_pair(Z, sm, L.t, lN, b0, b1);
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    stash[(2 * s) * T_ + L.t] = b0[s];
+    stash[(2 * s + 1) * T_ + L.t] = b1[s];
+  }
   __syncthreads();
   // bx = sigma_x / h, combined with a
   load_packed(Z, S + o0, S + o1, true, kx, L.t, lN);
@@ -361,8 +376,8 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
     if (!split_owns(s, L.t) || !L.valid) continue;
     const int k = L.t + s * T_;
     const T kv = ldr(kx + k);
-    Cout[o0 + k] = a0[s] - mul_ik(b0[s], kv);
-    Cout[o1 + k] = a1[s] - mul_ik(b1[s], kv);
+    Cout[o0 + k] = stash[(2 * s) * T_ + L.t] - mul_ik(b0[s], kv);
+    Cout[o1 + k] = stash[(2 * s + 1) * T_ + L.t] - mul_ik(b1[s], kv);
   }
   __syncthreads();
   // by = sigma_y / h
@@ -1069,7 +1084,8 @@ static inline int x_pairs_per_block(const Geom& G) {
   return P;
 }
 template <typename T>
-static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int nf, int tpb = 0) {
+static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int nf, int tpb = 0,
+                            int extra_elems_per_group = 0) {
   int P = x_pairs_per_block<T>(G);
   // tuned shape: whole row pairs, a power of two, within the launch bound
   const int Tn = G.Nx >> 3;
@@ -1079,7 +1095,7 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
   }
   block = dim3((G.Nx >> 3) * P);
   grid = dim3((G.Ny / 2 + P - 1) / P, nf);
-  smem = (size_t)P * smem_elems(G.Nx) * sizeof(cpx<T>);
+  smem = (size_t)P * (smem_elems(G.Nx) + extra_elems_per_group) * sizeof(cpx<T>);
 }
 template <typename T, bool INV, int NIN>
 static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int stage_per_thread = 0,
@@ -1407,7 +1423,7 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
                                                                                            ti, ep);
       ex.end();
     });
-    x_config<T>(G, grid, block, smem, 1, ex.tpb(TT_F32, TP_MV_X));
+    x_config<T>(G, grid, block, smem, 1, ex.tpb(TT_F32, TP_MV_X), mv_stash_elems(G.Nx));
     dispatch_ln<T>(G.lNx, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       ex.begin(PK_MV_X);
@@ -1467,7 +1483,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
                                                                                         ep);
     ex.end();
   });
-  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_MV_X));
+  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_MV_X), mv_stash_elems(G.Nx));
   dispatch_ln<T>(G.lNx, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     ex.begin(PK_MV_X);
