@@ -292,11 +292,18 @@ sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const d
  * kernel compiled for runtime lengths, whose FP32 rounding may differ in the
  * last bit (multiply-adds fused differently), and every solve still meets
  * opt.tol.
+ * Each transform of length 2^l with l not a multiple of 3 has a radix-2 or
+ * radix-4 stage beside its radix-8 stages; the tuner also times the radix plan
+ * of every pass at its picked shape: plan 0 runs that stage last, plan 1 first
+ * (it then needs no twiddles and every radix-8 stage does). Plans change the
+ * rounding of a pass (FP64 and double-float results then differ from the
+ * built-in plan's in the last bits; every solve still meets opt.tol).
  * out (may be NULL): per arithmetic [type] (0 FP32, 1 FP64, 2 double-float)
  * and pass [pass] (0 matvec y-inverse, 1 matvec y-forward, 2 RHS y-inverse,
  * 3 RHS y-forward, 4 matvec x-pass, 5 RHS x-pass): threads per block chosen
- * and built in, and the average launch time of each in microseconds; 0
- * threads for the passes the handle's precision does not run.
+ * and built in, the radix plan chosen, and the average launch time of the
+ * built-in and the chosen configuration in microseconds; 0 threads for the
+ * passes the handle's precision does not run.
  * Overwrites the handle's scratch spectra (not the warm start of sigma);
  * synchronises the handle's stream; call it between steps. reps in [1, 100],
  * else SGN_EINVAL. */
@@ -305,9 +312,18 @@ typedef struct {
   int default_threads[3][6];
   float us_tuned[3][6];
   float us_default[3][6];
+  int plan[3][6];
 } sgn_tuning;
 
 sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out);
+
+/* Applies a tuning (threads and plan of each pass, as sgn_autotune returns
+ * it, e.g. saved from an earlier run on the same grid) without timing
+ * anything: threads 0 keeps a pass's built-in shape, any other value must be
+ * one of the shapes sgn_autotune considers for that pass (SGN_EINVAL
+ * otherwise, and for a plan other than 0 or 1); the other fields are ignored.
+ * Synchronises the handle's stream; captured step graphs are rebuilt. */
+sgn_status sgn_set_tuning(sgn_t ctx, const sgn_tuning* t);
 
 /* ------------------------------------------------------------------------
  * Learned GMRES start. Section 3 starts GMRES from the last computed

@@ -7,8 +7,10 @@
 // ("thread-strided natural order"), so the last stage of an inverse transform
 // hands its outputs straight to the first stage of a forward transform.
 //
-// Stages are radix-8 (Stockham autosort), with one final radix-2 or radix-4
-// stage when log2 N is not a multiple of 3. In a stage of radix Rs < 8 a thread
+// Stages are radix-8 (Stockham autosort), with one radix-2 or radix-4 stage
+// when log2 N is not a multiple of 3: last in plan 0, first in plan 1 (where
+// it needs no twiddles and every radix-8 stage does); sgn_autotune picks the
+// plan per pass. In a stage of radix Rs < 8 a thread
 // runs 8/Rs butterflies; butterfly q of thread t has index j = t + q*T and its
 // inputs j + r*N/Rs are exactly the thread's slots q + r*(8/Rs), so every stage
 // reads the same thread-strided slots. Between stages data goes through shared
@@ -24,8 +26,10 @@
 // holding jm = 0..Ns-1 contiguously. The threads of a warp take consecutive jm,
 // so one twiddle load touches one or two cache lines instead of up to one line
 // per thread (the W_N^{jm r} entries of a flat table lie 2^(lN-lNs-3) r
-// entries apart). staged_exponent() gives the k of each entry. The inverse
-// transform uses the conjugates. No transform scales its output.
+// entries apart). staged_exponent() gives the k of each entry. A table holds
+// plan 0's rows in entries [0, N) and plan 1's in [N, 2N) (in plan 1 the stage
+// of lNs starts at N + 2^lNs - 2^rem, rem = lN mod 3). The inverse transform
+// uses the conjugates. No transform scales its output.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -120,8 +124,21 @@ __host__ __device__ constexpr int smem_elems(int N) { return N + (N >> 3); }
 // radix-8 stages have lNs = 3, 6, ..., then one radix-2 or radix-4 stage when
 // 3 does not divide lN (the stage plan of fft_regs); the stage of lNs starts at
 // 2^lNs - 8 and holds (R - 1) rows of 2^lNs entries. Fewer than N entries in all.
-__host__ __device__ inline int staged_exponent(int i, int lN) {
+__host__ __device__ inline int staged_exponent(int i, int lN, int plan = 0) {
   const int n8 = lN / 3, rem = lN - 3 * n8;
+  if (plan && rem) {
+    // plan 1: the radix-2^rem stage first (no twiddles), then radix-8 stages
+    // at lNs = rem, rem + 3, ..., lN - 3, the stage of lNs at 2^lNs - 2^rem
+    for (int lNs = rem; lNs <= lN - 3; lNs += 3) {
+      const int Ns = 1 << lNs, off = Ns - (1 << rem);
+      if (i < off) return -1;
+      if (i < off + 7 * Ns) {
+        const int q = i - off;
+        return ((q & (Ns - 1)) * (q / Ns + 1)) << (lN - lNs - 3);
+      }
+    }
+    return -1;
+  }
   for (int lNs = 3;; lNs += 3) {
     const bool tail = lNs == 3 * n8;  // the radix-2 or radix-4 stage, if any
     if (lNs > 3 * n8 || (tail && rem == 0)) return -1;
@@ -257,12 +274,39 @@ __device__ __forceinline__ void store_slots(const cpx<T> (&v)[8], cpx<T>* sm, in
 // smem_elems(N) elements at stride 2^lcs. sm must be free on entry and is free
 // again on exit. Contains __syncthreads(): every thread of the block must call
 // it with the same lN (threads of idle groups work on valid dummy data).
+// plan (0 or 1): where the radix-2 or radix-4 stage goes (see the top of
+// the file); tw is the table of both plans.
 template <bool INV, typename T>
 __device__ __forceinline__ void fft_regs(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* __restrict__ tw,
-                                         int t, int lN, int lcs = 0) {
+                                         int t, int lN, int lcs = 0, int plan = 0) {
   const int T_ = 1 << (lN - 3);
   const int n8 = lN / 3;        // radix-8 stages
-  const int rem = lN - 3 * n8;  // 0, 1 or 2 -> final radix 1 (none), 2, 4
+  const int rem = lN - 3 * n8;  // 0, 1 or 2 -> extra stage of radix 1 (none), 2, 4
+  if (plan && rem) {
+    // plan 1's rows start at N; fft_stage reads stage lNs at (2^lNs - 8), so
+    // shift the base by 8 - 2^rem
+    const cpx<T>* tw1 = tw + (1 << lN) + 8 - (1 << rem);
+    if (rem == 1)
+      fft_stage<INV, 2, false>(v, sm, tw1, t, lN, 0, lcs);
+    else
+      fft_stage<INV, 4, false>(v, sm, tw1, t, lN, 0, lcs);
+    __syncthreads();
+    load_slots(v, sm, t, T_, lcs);
+    __syncthreads();
+    int lNs = rem;
+    for (int st = 0; st < n8; ++st) {
+      if (st == n8 - 1) {
+        fft_stage<INV, 8, true>(v, sm, tw1, t, lN, lNs, lcs);
+      } else {
+        fft_stage<INV, 8, false>(v, sm, tw1, t, lN, lNs, lcs);
+        __syncthreads();
+        load_slots(v, sm, t, T_, lcs);
+        __syncthreads();
+      }
+      lNs += 3;
+    }
+    return;
+  }
   int lNs = 0;
   for (int st = 0; st < n8; ++st) {
     const bool last = (st == n8 - 1) && rem == 0;

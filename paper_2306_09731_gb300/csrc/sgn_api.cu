@@ -245,17 +245,19 @@ void free_all(sgn_ctx* ctx) {
   ctx->gst_host = nullptr;
 }
 
-// W_N^k = exp(-2 pi i k/N) in the staged layout of the transforms (entry i
-// holds W_N^staged_exponent(i); unused tail entries are zero)
+// W_N^k = exp(-2 pi i k/N) in the staged layout of the transforms: entry i
+// of [0, N) holds W_N^staged_exponent(i) for radix plan 0, entry N + i that
+// of plan 1 (unused entries are zero)
 std::vector<C64> staged_twiddles(int N, int lN) {
-  std::vector<C64> t(N);
-  for (int i = 0; i < N; ++i) {
-    const int k = staged_exponent(i, lN);
-    double c = 0.0, s = 0.0;
-    if (k >= 0) cos_sin_2pi(k, N, &c, &s);
-    t[i].x = c;
-    t[i].y = -s;
-  }
+  std::vector<C64> t(2 * (size_t)N);
+  for (int plan = 0; plan < 2; ++plan)
+    for (int i = 0; i < N; ++i) {
+      const int k = staged_exponent(i, lN, plan);
+      double c = 0.0, s = 0.0;
+      if (k >= 0) cos_sin_2pi(k, N, &c, &s);
+      t[(size_t)plan * N + i].x = c;
+      t[(size_t)plan * N + i].y = -s;
+    }
   return t;
 }
 
@@ -275,42 +277,42 @@ void build_tables(sgn_ctx* ctx) {
     for (int c = 0; c < G.Nxh; ++c) minv[(size_t)r * G.ldS + c] = 1.0 / (3.0 + kx[c] * kx[c] + ky[r] * ky[r]);
   ctx->tb.minv = dalloc<double>(ctx, minv.size());
   CK(cudaMemcpy(ctx->tb.minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice));
-  ctx->tb.twx = dalloc<C64>(ctx, G.Nx);
-  ctx->tb.twy = dalloc<C64>(ctx, G.Ny);
+  ctx->tb.twx = dalloc<C64>(ctx, 2 * (size_t)G.Nx);
+  ctx->tb.twy = dalloc<C64>(ctx, 2 * (size_t)G.Ny);
   ctx->tb.kx = dalloc<double>(ctx, G.Nxh);
   ctx->tb.ky = dalloc<double>(ctx, G.Ny);
-  CK(cudaMemcpy(ctx->tb.twx, tx.data(), G.Nx * sizeof(C64), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->tb.twy, ty.data(), G.Ny * sizeof(C64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tb.twx, tx.data(), tx.size() * sizeof(C64), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->tb.twy, ty.data(), ty.size() * sizeof(C64), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.kx, kx.data(), G.Nxh * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->tb.ky, ky.data(), G.Ny * sizeof(double), cudaMemcpyHostToDevice));
   if (ctx->opt.precision >= 2) {
     // double-float copies: nearest FP32 pair of each FP64 entry
-    std::vector<CDF> dx(G.Nx), dy(G.Ny);
-    for (int k = 0; k < G.Nx; ++k) dx[k] = CDF{dfl(tx[k].x), dfl(tx[k].y)};
-    for (int k = 0; k < G.Ny; ++k) dy[k] = CDF{dfl(ty[k].x), dfl(ty[k].y)};
+    std::vector<CDF> dx(tx.size()), dy(ty.size());
+    for (size_t k = 0; k < tx.size(); ++k) dx[k] = CDF{dfl(tx[k].x), dfl(tx[k].y)};
+    for (size_t k = 0; k < ty.size(); ++k) dy[k] = CDF{dfl(ty[k].x), dfl(ty[k].y)};
     std::vector<dfl> kxd(kx.begin(), kx.end()), kyd(ky.begin(), ky.end()), md(minv.begin(), minv.end());
-    ctx->tbd.twx = dalloc<CDF>(ctx, G.Nx);
-    ctx->tbd.twy = dalloc<CDF>(ctx, G.Ny);
+    ctx->tbd.twx = dalloc<CDF>(ctx, dx.size());
+    ctx->tbd.twy = dalloc<CDF>(ctx, dy.size());
     ctx->tbd.kx = dalloc<dfl>(ctx, G.Nxh);
     ctx->tbd.ky = dalloc<dfl>(ctx, G.Ny);
     ctx->tbd.minv = dalloc<dfl>(ctx, md.size());
-    CK(cudaMemcpy(ctx->tbd.twx, dx.data(), G.Nx * sizeof(CDF), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->tbd.twy, dy.data(), G.Ny * sizeof(CDF), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.twx, dx.data(), dx.size() * sizeof(CDF), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tbd.twy, dy.data(), dy.size() * sizeof(CDF), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tbd.kx, kxd.data(), G.Nxh * sizeof(dfl), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tbd.ky, kyd.data(), G.Ny * sizeof(dfl), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tbd.minv, md.data(), md.size() * sizeof(dfl), cudaMemcpyHostToDevice));
   }
   if (ctx->opt.precision >= 1) {
-    std::vector<C32> fx(G.Nx), fy(G.Ny);
-    for (int k = 0; k < G.Nx; ++k) fx[k] = C32{(float)tx[k].x, (float)tx[k].y};
-    for (int k = 0; k < G.Ny; ++k) fy[k] = C32{(float)ty[k].x, (float)ty[k].y};
+    std::vector<C32> fx(tx.size()), fy(ty.size());
+    for (size_t k = 0; k < tx.size(); ++k) fx[k] = C32{(float)tx[k].x, (float)tx[k].y};
+    for (size_t k = 0; k < ty.size(); ++k) fy[k] = C32{(float)ty[k].x, (float)ty[k].y};
     std::vector<float> kxf(kx.begin(), kx.end()), kyf(ky.begin(), ky.end());
-    ctx->tb32.twx = dalloc<C32>(ctx, G.Nx);
-    ctx->tb32.twy = dalloc<C32>(ctx, G.Ny);
+    ctx->tb32.twx = dalloc<C32>(ctx, fx.size());
+    ctx->tb32.twy = dalloc<C32>(ctx, fy.size());
     ctx->tb32.kx = dalloc<float>(ctx, G.Nxh);
     ctx->tb32.ky = dalloc<float>(ctx, G.Ny);
-    CK(cudaMemcpy(ctx->tb32.twx, fx.data(), G.Nx * sizeof(C32), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->tb32.twy, fy.data(), G.Ny * sizeof(C32), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tb32.twx, fx.data(), fx.size() * sizeof(C32), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->tb32.twy, fy.data(), fy.size() * sizeof(C32), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tb32.kx, kxf.data(), G.Nxh * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->tb32.ky, kyf.data(), G.Ny * sizeof(float), cudaMemcpyHostToDevice));
   }
@@ -1845,6 +1847,7 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
       int cand[16];
       const int nc = pass_candidates(G, ty, ps, cand, 16);
       ctx->tune.tpb[ty][ps] = def;
+      ctx->tune.plan[ty][ps] = 0;
       remap();
       const double t_def = tune_time(ctx, jb.op, jb.cls[k], reps);
       int best = def;
@@ -1861,8 +1864,22 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
       }
       ctx->tune.tpb[ty][ps] = best;
       remap();
+      // the radix plan of the pass's axis, at the picked shape (one plan when
+      // 3 divides log2 of the length)
+      const int lN = (ps == TP_MV_X || ps == TP_RHS_X) ? G.lNx : G.lNy;
+      int plan = 0;
+      if (lN % 3 != 0) {
+        ctx->tune.plan[ty][ps] = 1;
+        const double t = tune_time(ctx, jb.op, jb.cls[k], reps);
+        if (t < t_best) {
+          t_best = t;
+          plan = 1;
+        }
+        ctx->tune.plan[ty][ps] = plan;
+      }
       res.threads[ty][ps] = best;
       res.default_threads[ty][ps] = def;
+      res.plan[ty][ps] = plan;
       res.us_default[ty][ps] = (float)t_def;
       res.us_tuned[ty][ps] = (float)t_best;
     }
@@ -1872,6 +1889,35 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
   ctx->prof.launches = launches0;
   ctx->prof.on = was_on;
   if (out) *out = res;
+  return SGN_OK;
+  API_END
+}
+
+sgn_status sgn_set_tuning(sgn_t ctx, const sgn_tuning* t) {
+  API_BEGIN
+  if (!t) return fail(ctx, SGN_EINVAL, "sgn_set_tuning: NULL tuning");
+  const Geom& G = ctx->G;
+  Tune nt{};
+  for (int ty = 0; ty < TT_COUNT; ++ty)
+    for (int ps = 0; ps < TP_COUNT; ++ps) {
+      const int th = t->threads[ty][ps], pl = t->plan[ty][ps];
+      if (pl != 0 && pl != 1) return fail(ctx, SGN_EINVAL, "sgn_set_tuning: a plan is not 0 or 1");
+      if (th != 0) {
+        int cand[16];
+        const int nc = pass_candidates(G, ty, ps, cand, 16);
+        bool ok = th == pass_default_threads(G, ty, ps);
+        for (int c = 0; c < nc && !ok; ++c) ok = cand[c] == th;
+        if (!ok) return fail(ctx, SGN_EINVAL, "sgn_set_tuning: a thread count is not a shape of its pass");
+      }
+      nt.tpb[ty][ps] = th;
+      nt.plan[ty][ps] = pl;
+    }
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_graph(ctx);  // a captured step keeps the shapes it was captured with
+  ctx->tune = nt;
+  if (ctx->opt.precision >= 1 && ctx->mvt.ok)
+    make_mv_tma(G, ctx->V32, ctx->opt.restart + 1, ctx->tmp32[0], ctx->tmp32[1], ctx->flags, &ctx->tune,
+                &ctx->mvt);
   return SGN_OK;
   API_END
 }

@@ -39,6 +39,7 @@ enum TunePass : int { TP_MV_YINV = 0, TP_MV_YFWD, TP_RHS_YINV, TP_RHS_YFWD, TP_M
 enum TuneType : int { TT_F32 = 0, TT_F64, TT_DFL, TT_COUNT };
 struct Tune {
   int tpb[TT_COUNT][TP_COUNT];
+  int plan[TT_COUNT][TP_COUNT];  // radix plan of each pass's transforms (0 or 1)
 };
 template <typename T>
 constexpr int tune_type() {
@@ -219,6 +220,7 @@ struct Exec {
   bool refine = false;     // matvec passes count as the FP64 refinement classes
   const Tune* tune = nullptr;
   int tpb(int type, int pass) const { return tune ? tune->tpb[type][pass] : 0; }
+  int plan(int type, int pass) const { return tune ? tune->plan[type][pass] : 0; }
   void begin(int k, int nlaunch = 1) const {
     if (!p) return;
     if (kind_override >= 0) k = kind_override;
@@ -295,6 +297,8 @@ cudaError_t launch_y_inv64(const Geom& G, const Tables<T>& tb, const cpx<double>
 template <typename T>
 cudaError_t launch_y_fwd64(const Geom& G, const Tables<T>& tb, const cpx<T>* in, cpx<double>* out, const Exec& ex);
 void init_kernel_attributes_df();
+// the part of it for precision 3's double-float right-hand side (its own unit)
+void init_kernel_attributes_df_rhs();
 
 // RHS of one stage from state U (3 spectra), sigma_hat, h, cr; K goes through
 // the RK epilogue. tmp: 4 spectra. Writes b_hat of the next stage state.

@@ -25,7 +25,8 @@ EXPORTS = ["sgn_default_options", "sgn_create", "sgn_destroy", "sgn_set_stream",
            "sgn_gmres_solve", "sgn_rhs", "sgn_rk4_step", "sgn_rk4_step_host", "sgn_invariants",
            "sgn_get_stats", "sgn_set_profiling", "sgn_get_profile", "sgn_elliptic_apply_noalloc",
            "sgn_diagnostics", "sgn_set_learned_guess", "sgn_record_learned", "sgn_recorded_count",
-           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_rk4_step_batch", "sgn_autotune", "sgn_last_error"]
+           "sgn_coarse_sample", "sgn_coarse_embed", "sgn_rk4_step_batch", "sgn_autotune", "sgn_set_tuning",
+           "sgn_last_error"]
 
 # index names of sgn_tuning's [type][pass] arrays
 TUNE_TYPES = ["fp32", "fp64", "dfl"]
@@ -55,7 +56,8 @@ class sgn_diag(ctypes.Structure):
 
 class sgn_tuning(ctypes.Structure):
     _fields_ = [("threads", (ctypes.c_int * 6) * 3), ("default_threads", (ctypes.c_int * 6) * 3),
-                ("us_tuned", (ctypes.c_float * 6) * 3), ("us_default", (ctypes.c_float * 6) * 3)]
+                ("us_tuned", (ctypes.c_float * 6) * 3), ("us_default", (ctypes.c_float * 6) * 3),
+                ("plan", (ctypes.c_int * 6) * 3)]
 
 
 class sgn_stats(ctypes.Structure):
@@ -103,6 +105,7 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         "sgn_elliptic_apply_noalloc": (_I, [_I, _I, _D, _D, _P, _P, _P, _P]),
         "sgn_diagnostics": (_I, [_P, _P, _P, _P, ctypes.POINTER(sgn_diag)]),
         "sgn_autotune": (_I, [_P, _I, ctypes.POINTER(sgn_tuning)]),
+        "sgn_set_tuning": (_I, [_P, ctypes.POINTER(sgn_tuning)]),
         "sgn_set_learned_guess": (_I, [_P, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.c_float, _I]),
         "sgn_record_learned": (_I, [_P, _I, _P, _I, _I]),
         "sgn_recorded_count": (_I, [_P, ctypes.POINTER(_I)]),
@@ -232,8 +235,22 @@ def sgn_autotune(handle, reps=5) -> dict:
         for j, ps in enumerate(TUNE_PASSES):
             if t.threads[i][j] > 0:
                 out.setdefault(ty, {})[ps] = dict(threads=t.threads[i][j], default_threads=t.default_threads[i][j],
-                                                  us=t.us_tuned[i][j], us_default=t.us_default[i][j])
+                                                  us=t.us_tuned[i][j], us_default=t.us_default[i][j],
+                                                  plan=t.plan[i][j])
     return out
+
+
+def sgn_set_tuning(handle, tuning: dict):
+    """Applies {type: {pass: {"threads": t, "plan": p}}} (the form sgn_autotune
+    returns; missing passes keep their built-in shape and plan 0)."""
+    t = sgn_tuning()
+    for i, ty in enumerate(TUNE_TYPES):
+        for j, ps in enumerate(TUNE_PASSES):
+            r = tuning.get(ty, {}).get(ps)
+            if r:
+                t.threads[i][j] = int(r.get("threads", 0))
+                t.plan[i][j] = int(r.get("plan", 0))
+    _check(handle, load_library().sgn_set_tuning(handle, ctypes.byref(t)))
 
 
 def _ptr32(x):
@@ -396,6 +413,9 @@ class Solver:
 
     def autotune(self, reps=5):
         return sgn_autotune(self.handle, reps)
+
+    def set_tuning(self, tuning):
+        sgn_set_tuning(self.handle, tuning)
 
     def coarse_sample(self, f, n):
         out = self._torch.empty((n, n), dtype=self._torch.float32, device="cuda")
