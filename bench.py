@@ -573,6 +573,38 @@ def run_extras(args, st, n, detail):
         ens[f"guess{guess}"] = {"batch": len(members) * args.steps / (b1 - b0),
                                 "one_by_one": len(members) * args.steps / (b2 - b1)}
         E.close()
+    # how busy the batched graphs keep the GPU: grid-point-steps/s of each
+    # grid size stepped alone (one member) and batched (its members only),
+    # of the whole batch, and of the 2048^2 headline (whose kernels fill the
+    # GPU); the per-point work of the smaller grids is lower by their shorter
+    # transforms (log2 N of 16-19 against 22)
+    occ = {"unit": "grid-point-steps/s", "grids": {}}
+    for g in GRIDS:
+        sub = [m for m in members if (m.Nx, m.Ny) == tuple(g[:2])]
+        pts = g[0] * g[1]
+        for label, group in (("alone", sub[:1]), ("batched", sub)):
+            E = Ensemble(group, tune=not args.no_tune, precision=2, guess=3, graph=1)
+            E.step(2e-3, 4)
+            torch.cuda.synchronize()
+            b0 = time.perf_counter()
+            E.step(2e-3, args.steps)
+            wall = time.perf_counter() - b0
+            its = [s.stats() for s in E.solvers]
+            E.close()
+            occ["grids"].setdefault(f"{g[0]}x{g[1]}", {})[label] = {
+                "members": len(group), "value": len(group) * pts * args.steps / wall,
+                "iters_per_stage": sum(x["matvecs"] for x in its) / max(sum(x["solves"] for x in its), 1)}
+    E = Ensemble(members, tune=not args.no_tune, precision=2, guess=3, graph=1)
+    E.step(2e-3, 4)
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    E.step(2e-3, args.steps)
+    wall = time.perf_counter() - b0
+    E.close()
+    occ["all_batched"] = sum(m.Nx * m.Ny for m in members) * args.steps / wall
+    if "headline" in detail:
+        occ["headline_2048"] = detail["headline"]["value"] * n * n
+    ens["occupancy"] = occ
     detail["ensemble"] = ens
     torch.cuda.empty_cache()
     if n == N_DEFAULT:
