@@ -545,50 +545,83 @@ __global__ void k_ext_keep(ExtHist* hist, const int* flag) {
 
 // *flag = 1 when every component of the three spectra b is within rel * max|a|
 // of a's (a: the state the handle returned last, b: a call's input state),
-// else 0 (NaN counts as a difference). Block maxima in partials, combined by
-// the last block.
+// else 0 (NaN counts as a difference). The maxima are taken on the bit
+// patterns of |b - a| and |a|: for non-negative doubles the patterns order
+// as the values do (a NaN's sorts above infinity, so it wins the maximum and
+// fails the final test), so only the subtractions use the FP64 pipe. Block
+// maxima in partials, combined by the last block.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) k_same_state(Geom G, const cpx<double>* a0, const cpx<double>* a1,
                                                     const cpx<double>* a2, const cpx<double>* b0,
                                                     const cpx<double>* b1, const cpx<double>* b2, double rel,
                                                     double* partials, unsigned* counter, int* flag) {
-  __shared__ double red[2][32];
+  __shared__ unsigned long long red[2][32];
   const cpx<double>* A[3] = {a0, a1, a2};
   const cpx<double>* B[3] = {b0, b1, b2};
-  double md = 0.0, ma = 0.0;
+  unsigned long long md = 0ull, ma = 0ull;
   for (Walk it(G); it.ok(); it.next()) {
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       const cpx<double> a = A[f][it.e], b = B[f][it.e];
-      const double dx = fabs(b.x - a.x), dy = fabs(b.y - a.y);
-      md = fmax(md, (dx != dx || dy != dy) ? INFINITY : fmax(dx, dy));
-      ma = fmax(ma, fmax(fabs(a.x), fabs(a.y)));
+      const unsigned long long dx = abs_bits(b.x - a.x), dy = abs_bits(b.y - a.y);
+      const unsigned long long ax = abs_bits(a.x), ay = abs_bits(a.y);
+      md = dx > md ? dx : md;
+      md = dy > md ? dy : md;
+      ma = ax > ma ? ax : ma;
+      ma = ay > ma ? ay : ma;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-    ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  md = warp_max_u64(md);
+  ma = warp_max_u64(ma);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   if (lane == 0) {
     red[0][wid] = md;
     red[1][wid] = ma;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      md = fmax(md, red[0][i]);
-      ma = fmax(ma, red[1][i]);
+    for (int i = 1; i < nw; ++i) {
+      md = red[0][i] > md ? red[0][i] : md;
+      ma = red[1][i] > ma ? red[1][i] : ma;
     }
-    partials[blockIdx.x] = md;
-    partials[NBLK + blockIdx.x] = ma;
+    partials[blockIdx.x] = __longlong_as_double((long long)md);
+    partials[NBLK + blockIdx.x] = __longlong_as_double((long long)ma);
   }
-  if (last_block(counter, threadIdx.x == 0) && threadIdx.x == 0) {
-    double D = 0.0, M = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      D = fmax(D, __ldcg(partials + b));
-      M = fmax(M, __ldcg(partials + NBLK + b));
+  if (last_block(counter, threadIdx.x == 0)) {
+    // every thread of the last block takes a share of the block maxima
+    unsigned long long D = 0ull, M = 0ull;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const unsigned long long d = (unsigned long long)__double_as_longlong(__ldcg(partials + b));
+      const unsigned long long m = (unsigned long long)__double_as_longlong(__ldcg(partials + NBLK + b));
+      D = d > D ? d : D;
+      M = m > M ? m : M;
     }
-    *flag = (M > 0.0 && D <= rel * M) ? 1 : 0;
+    D = warp_max_u64(D);
+    M = warp_max_u64(M);
+    __syncthreads();
+    if (lane == 0) {
+      red[0][wid] = D;
+      red[1][wid] = M;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 1; i < nw; ++i) {
+        D = red[0][i] > D ? red[0][i] : D;
+        M = red[1][i] > M ? red[1][i] : M;
+      }
+      const double dd = __longlong_as_double((long long)D), mm = __longlong_as_double((long long)M);
+      *flag = (mm > 0.0 && dd <= rel * mm) ? 1 : 0;
+    }
   }
 }
 

@@ -976,12 +976,14 @@ struct EpiK {
 // part; the linear part comes from the stage state Y and sigma_hat here:
 //   h_t += -i kx vx - i ky vy - (kx^2 + ky^2) sigma,  v_t += -i k g h,
 // with the zeroed-Nyquist wavenumbers and the 2/3 mask of the FP32 pass.
+// c6 = dt/6, cdt = the stage's dt (dt/2 or dt) and thr2 = the squared Krasny
+// threshold times (Nx Ny)^2 come from the host (in every thread they would
+// cost an FP64 division and products on the slow FP64 pipe).
 template <typename T, typename S>
-__global__ void k_rk_update(Geom G, RkK<T, S> a) {
+__global__ void k_rk_update(Geom G, RkK<T, S> a, double c6d, double cdtd, double thr2) {
   const RkArgs rk = a.rk;
-  const double thr2 = rk.krasny_thr * rk.krasny_thr * (double)G.nphys() * (double)G.nphys();
-  const S c6 = (S)(rk.dt / 6.0);
-  const S cdt = (S)(rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt);
+  const S c6 = (S)c6d;
+  const S cdt = (S)cdtd;
   const S g = (S)rk.g;
   for (Walk it(G); it.ok(); it.next()) {
     const size_t e = it.e;
@@ -1738,7 +1740,9 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     a.sig = sig;
     a.rk = rk;
     ex.begin(PK_RK);
-    k_rk_update<T, S><<<NBLK, 256, 0, ex.s>>>(G, a);
+    k_rk_update<T, S><<<NBLK, 256, 0, ex.s>>>(G, a, rk.dt / 6.0, rk.mode == RK_STAGE3 ? rk.dt : 0.5 * rk.dt,
+                                               rk.krasny_thr * rk.krasny_thr * (double)G.nphys() *
+                                                   (double)G.nphys());
     ex.end();
   }
   return cudaGetLastError();
