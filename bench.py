@@ -175,19 +175,25 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# is now, with the summary that holds the command. An entry is removed when its
-# kernel changes, so that the line reports null until the next capture.
+# is now (built-in shape, radix plan 0), and the fractions of cycles it issued
+# instructions and kept the FMA pipe busy (the compute view of a kernel bound
+# by issue rather than by DRAM), with the summary that holds the
+# command. An entry is removed when its kernel changes, and the line reports
+# null when the tuned handle runs the pass in the other radix plan.
 MEASURED_TRAFFIC = {
-    ("ref_x", "df", 2048): {"bytes": 134.603264e6 + 22.911744e6, "source": "profiles/k_mv_x_df_gaussian2048.md"},
-    ("mv_x", "fp32", 2048): {"bytes": 67.196928e6 + 0.668928e6, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
-    ("mv_yinv", "fp32", 2048): {"bytes": 16.893696e6 + 0.13824e6, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
-    ("mv_yfwd", "fp32", 2048): {"bytes": 33.669888e6 + 0.076288e6, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
-    ("rhs_yinv", "fp32", 2048): {"bytes": 102.639616e6 + 31.659264e6,
-                                 "source": "profiles/k_ypass_fp32_gaussian2048.md"},
-    ("rhs_yfwd", "fp32", 2048): {"bytes": 50.482688e6 + 3.486976e6,
-                                 "source": "profiles/k_ypass_fp32_gaussian2048.md"},
-    ("mv_x", "fp64", 2048): {"bytes": 134.8608e6 + 29.78304e6, "source": "profiles/k_mv_x_fp64_gaussian2048.md"},
+    ("ref_x", "df", 2048): {"bytes": 134.6e6 + 22.9e6, "issue": 0.55, "fma": 0.46, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("ref_yinv", "df", 2048): {"bytes": 38.5e6 + 15.7e6, "issue": 0.46, "fma": 0.35, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("ref_yfwd", "df", 2048): {"bytes": 84.6e6 + 9.3e6, "issue": 0.49, "fma": 0.37, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("mv_x", "fp32", 2048): {"bytes": 67.3e6 + 22.7e6, "issue": 0.54, "fma": 0.28, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
+    ("mv_yinv", "fp32", 2048): {"bytes": 16.9e6 + 0.1e6, "issue": 0.35, "fma": 0.21, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
+    ("mv_yfwd", "fp32", 2048): {"bytes": 33.7e6 + 0.1e6, "issue": 0.41, "fma": 0.23, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
+    ("rhs_yinv", "fp32", 2048): {"bytes": 103.1e6 + 29.5e6, "issue": 0.20, "fma": 0.12, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
+    ("rhs_x", "fp32", 2048): {"bytes": 100.9e6 + 7.1e6, "issue": 0.56, "fma": 0.30, "source": "profiles/k_rhs_x_fp32_gaussian2048.md"},
+    ("rhs_yfwd", "fp32", 2048): {"bytes": 50.5e6 + 2.9e6, "issue": 0.26, "fma": 0.16, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
 }
+# the (arithmetic, pass) of the tuning table each kernel class belongs to
+CLASS_TUNE = {"mv_yinv": "mv_yinv", "mv_x": "mv_x", "mv_yfwd": "mv_yfwd", "rhs_yinv": "rhs_yinv", "rhs_x": "rhs_x",
+              "rhs_yfwd": "rhs_yfwd", "ref_yinv": "mv_yinv", "ref_x": "mv_x", "ref_yfwd": "mv_yfwd"}
 
 # kernel classes that are one kernel each (candidates for the roofline line)
 SINGLE_KERNEL_CLASSES = ("mv_x", "mv_yinv", "mv_yfwd", "rhs_x", "rhs_yinv", "rhs_yfwd", "rk", "ref_yinv", "ref_x",
@@ -251,7 +257,7 @@ def class_arith(cls, prec):
     return "fp32"
 
 
-def class_roofline(cls, n, prec, prof, peaks, peak_kind):
+def class_roofline(cls, n, prec, prof, peaks, peak_kind, tuning=None):
     """HBM roofline of one kernel class from the library's per-launch CUDA-event
     timers: algorithmic bytes per launch / mean launch time, against the
     measured copy bandwidth. The FLOP rate is reported beside it."""
@@ -268,8 +274,12 @@ def class_roofline(cls, n, prec, prof, peaks, peak_kind):
     peak = peaks.get("hbm_gbs", 6800.0)
     ach = nbytes / (avg_ms / 1e3) / 1e9
     tr = MEASURED_TRAFFIC.get((cls, ar, n))
+    ty = {"fp32": "fp32", "df": "dfl", "fp64": "fp64"}[ar]
+    if tr and tuning and (tuning.get(ty, {}).get(CLASS_TUNE.get(cls), {}) or {}).get("plan", 0) != 0:
+        tr = None  # the capture is of the plan-0 kernel
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": tr["bytes"] if tr else None,
+            "ncu_issue_active": tr.get("issue") if tr else None, "ncu_fma_pipe": tr.get("fma") if tr else None,
             "kernel": KERNEL_NAMES.get(cls, cls) + {"fp32": " FP32", "df": " double-float", "fp64": " FP64"}[ar],
             "algorithmic_bytes": nbytes, "avg_launch_us": avg_ms * 1e3, "launches": cnt,
             "fp64_equiv_tflops": flops / (avg_ms / 1e3) / 1e12,
@@ -293,7 +303,7 @@ def time_path(precision, guess, args, st, n, world, graph=0, learned=None, steps
     dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda").contiguous()
     f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
     s = Solver(n, n, L_DEFAULT, L_DEFAULT, restart=20, tol=1e-10, precision=precision, guess=guess, graph=graph)
-    tuning = s.autotune(5) if tune else None
+    tuning = s.autotune(10) if tune else None
     if learned is not None:
         net, in_scale, out_scale, tau_power = learned
         s.set_learned_guess(net, net.n, in_scale, out_scale, tau_power)
@@ -642,7 +652,8 @@ def compact_line(head_rec, fp64, roof, share, e2e, clk, args, world, n):
         "speedup_vs_fp64": (head_rec["value"] / fp64["value"]) if fp64 else None,
         "roofline": ({k: roof.get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
                                                 "avg_launch_us", "algorithmic_bytes", "time_share",
-                                                "fp64_equiv_tflops", "peak_source")} if roof else None),
+                                                "fp64_equiv_tflops", "ncu_issue_active", "ncu_fma_pipe",
+                                                "peak_source", "traffic_source")} if roof else None),
         "e2e": e2e,
         "clocks": clk,
     }
@@ -724,7 +735,7 @@ def run_ours(args, rank, world, local_rank):
         s.close()
         del f
         prof = rec["prof"]
-        rl = {c: class_roofline(c, n, prec, prof, peaks, peak_kind) for c in SINGLE_KERNEL_CLASSES}
+        rl = {c: class_roofline(c, n, prec, prof, peaks, peak_kind, rec.get("tuning")) for c in SINGLE_KERNEL_CLASSES}
         rl = {c: r for c, r in rl.items() if r}
         total = sum(prof["ms"].values())
         share = {k: v / total for k, v in prof["ms"].items() if v > 0}

@@ -285,7 +285,9 @@ sgn_status sgn_diagnostics(sgn_t ctx, const double* h, const double* vx, const d
  * a handful of blocks. sgn_autotune times every candidate shape of every pass
  * the handle runs (threads per block: powers of two, whole columns or row
  * pairs, up to each kernel's launch bound), `reps` launches each after one
- * untimed launch, on the handle's own buffers, and keeps the fastest; later
+ * untimed launch, on the handle's own buffers, and keeps the fastest (a shape
+ * or plan other than the built-in one only when it is at least 2% faster, so
+ * that timing noise does not decide); later
  * calls of the handle use those shapes. Shapes change no formula: FP64 and
  * double-float results are bitwise identical to those of the built-in shapes;
  * an FP32 pass whose picked shape differs from the built-in one runs the

@@ -1792,6 +1792,8 @@ void tune_run(sgn_ctx* ctx, int op) {
 
 // Average launch time (us) of profiling class cls over reps runs of op, after
 // one untimed run.
+constexpr double kTuneMargin = 0.02;
+
 double tune_time(sgn_ctx* ctx, int op, int cls, int reps) {
   ctx->prof.on = false;
   tune_run(ctx, op);
@@ -1852,12 +1854,15 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
       const double t_def = tune_time(ctx, jb.op, jb.cls[k], reps);
       int best = def;
       double t_best = t_def;
+      // a candidate replaces the built-in shape or plan only when it is at
+      // least kTuneMargin faster: timings of one pass repeat to ~1%, and a
+      // pick made on noise can lose more than that in the running step
       for (int c = 0; c < nc; ++c) {
         if (cand[c] == def) continue;
         ctx->tune.tpb[ty][ps] = cand[c];
         remap();
         const double t = tune_time(ctx, jb.op, jb.cls[k], reps);
-        if (t < t_best) {
+        if (t < (1.0 - kTuneMargin) * t_best) {
           t_best = t;
           best = cand[c];
         }
@@ -1871,7 +1876,7 @@ sgn_status sgn_autotune(sgn_t ctx, int reps, sgn_tuning* out) {
       if (lN % 3 != 0) {
         ctx->tune.plan[ty][ps] = 1;
         const double t = tune_time(ctx, jb.op, jb.cls[k], reps);
-        if (t < t_best) {
+        if (t < (1.0 - kTuneMargin) * t_best) {
           t_best = t;
           plan = 1;
         }
