@@ -531,6 +531,37 @@ def transverse_stability(tend=10.0, dt=2e-3, marks=5):
             "runs": out}
 
 
+def unet_cost(reps=20):
+    """Device time of one learned-start network use (batch 1): the tensor-core
+    inference against the CUDA-core forward, for the library's default
+    network and the four-level one, on 128^2 and 256^2 coarse grids."""
+    import torch
+
+    from paper_2306_09731_gb300.unet import SPEC_ARCH, UNet
+    out = {"unit": "ms per use", "reps": reps}
+    for label, arch in (("default_60705", None), ("four_level_471873", SPEC_ARCH)):
+        for coarse in (128, 256):
+            net = UNet(coarse, max_batch=1, bf16=True, seed=0, arch=arch)
+            x = torch.randn(1, 4, coarse, coarse, device="cuda")
+            y = torch.empty(1, 1, coarse, coarse, device="cuda")
+            rec = {"params": net.num_params()}
+            for kind, fn in (("tensor_cores", lambda: net.infer(x, y)), ("cuda_cores", lambda: net.forward(x))):
+                for _ in range(3):
+                    fn()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record()
+                for _ in range(reps):
+                    fn()
+                b.record()
+                torch.cuda.synchronize()
+                rec[kind] = a.elapsed_time(b) / reps
+            net.check()
+            net.close()
+            out[f"{label}_n{coarse}"] = rec
+    return out
+
+
 def run_extras(args, st, n, detail):
     """The other arms, the learned start, the 64-member ensemble and the
     4096^2 crossing solitons; results go to the detail record only."""
@@ -549,14 +580,20 @@ def run_extras(args, st, n, detail):
     detail["arms"] = arms
     nets = {}
     from paper_2306_09731_gb300 import learned as Lm
+    from paper_2306_09731_gb300.unet import SPEC_ARCH
+    detail["unet_cost"] = unet_cost()
     lr = {}
-    for name, prec, guess, graph, tau_power, coarse in (("mixed_df_paper_start_learned", 2, 0, 0, 1, n // 8),
-                                                        ("mixed_df_learned_graph", 2, 2, 1, 2, n // 16)):
+    for name, prec, guess, graph, tau_power, coarse, warm in (
+            ("mixed_df_paper_start_learned", 2, 0, 0, 1, n // 16, 1),
+            ("mixed_df_learned_graph", 2, 2, 1, 2, n // 16, 1),
+            ("mixed_df_poly_learned_graph", 2, 3, 1, 2, n // 16, 4)):
         t0 = time.perf_counter()
         states = Lm.gaussian_states(n, L_DEFAULT, [0.35, 0.45, 0.55, 0.65], seed=1)
-        samples = Lm.generate(states, coarse, steps=8, dt=DT, precision=prec, guess=guess, tau_power=tau_power)
+        samples = Lm.generate(states, coarse, steps=8, dt=DT, precision=prec, guess=guess, tau_power=tau_power,
+                              warmup=warm)
         t1 = time.perf_counter()
-        net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2, log_every=100)
+        net, in_scale, out_scale, losses = Lm.train(samples, iters=400, batch=8, lr=2e-3, seed=2, log_every=100,
+                                                    arch=SPEC_ARCH)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         nets[name] = (net, in_scale, out_scale, tau_power)
@@ -627,7 +664,8 @@ def run_extras(args, st, n, detail):
             for name, guess, lname in (("paper_start", 0, None),
                                        ("paper_start_learned", 0, "mixed_df_paper_start_learned"),
                                        ("extrapolated", 2, None), ("extrapolated_learned", 2, "mixed_df_learned_graph"),
-                                       ("polynomial", 3, None)):
+                                       ("polynomial", 3, None),
+                                       ("polynomial_learned", 3, "mixed_df_poly_learned_graph")):
                 res[name] = time_crossing(cst, 2, guess, 1, nets.get(lname), ksteps, 4 if guess == 3 else 2,
                                           not args.no_tune)
             cross["theta"][f"{theta:g}"] = res

@@ -85,8 +85,7 @@ typedef struct {
                          rounding noise of the stage states bounds that gain, and near
                          rest it is gone);
                          it keeps 16 spectra of history (16 * Ny * (Nx/2 + 2) complex
-                         doubles), carried across calls by guess 2's rule; the learned
-                         start (sgn_set_learned_guess) is not available with it */
+                         doubles), carried across calls by guess 2's rule */
   int graph;          /* 1: sgn_rk4_step and sgn_rk4_step_host run each RK4 step as one
                          CUDA graph whose GMRES loops are conditional WHILE nodes driven
                          by device-side tests (no host synchronisation inside the call;
@@ -330,25 +329,26 @@ sgn_status sgn_set_tuning(sgn_t ctx, const sgn_tuning* t);
 /* ------------------------------------------------------------------------
  * Learned GMRES start. Section 3 starts GMRES from the last computed
  * sigma; a network (include/sgn_unet.h) can correct that start. At RK4 stages
- * 2 and 4 (the stages whose state moved by O(dt) since the fallback's), after
- * the start chosen by opt.guess, the library forms on an n x n coarse grid
+ * 2 and 4 (the stages whose state moved by O(dt) since the fallback's; with
+ * guess = 3 at every stage, once the polynomial start is cubic), after the
+ * start chosen by opt.guess, the library forms on an n x n coarse grid
  *   in = (in_scale[0] (h - 1), in_scale[1] vx, in_scale[2] vy,
  *         in_scale[3] sigma_start)
  * as band-limited samples of the stage state (the Fourier modes |m_x|, |m_y|
  * < n/2 evaluated at every (N/n)-th grid point), runs the network on it and
  * adds out_scale * tau * net(in), tau = (dt/2)^tau_power, to the same modes of
  * sigma's spectrum (with guess = 2, not at stage 2 of a call's first step,
- * which has no extrapolation history). Every solve still meets opt.tol. n
- * must be a power of two in [16, min(Nx, Ny)] and equal to the network's side;
- * net = NULL detaches. SGN_EINVAL on a handle with guess = 3, whose start
- * needs no correction of this kind (sgn_record_learned refuses it too).
- * The network runs on the handle's stream (it is re-pointed there). */
+ * which has no extrapolation history; with guess = 3, not before the handle
+ * has solved 4 steps of the trajectory). The network runs as sgn_unet_infer
+ * (BF16 on the tensor cores) on the handle's stream (it is re-pointed there).
+ * Every solve still meets opt.tol. n must be a power of two in
+ * [16, min(Nx, Ny)] and equal to the network's side; net = NULL detaches. */
 sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_scale[4], float out_scale,
                                  int tau_power);
 
 /* Records training samples for the learned start: during sgn_rk4_step and
  * sgn_rk4_step_host with the host-driven loop (graph = 0; SGN_EINVAL
- * otherwise), each stage 2 and 4 appends to buf (device float32, capacity
+ * otherwise), each stage the learned start corrects appends to buf (device float32, capacity
  * samples of [5][n][n]) the four coarse inputs above without in_scale (channels
  * 0-3, sigma_start taken before any learned correction) and the coarse target
  * (sigma_solved - sigma_start) / tau (channel 4). Recording stops silently when

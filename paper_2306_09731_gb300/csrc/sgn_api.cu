@@ -113,6 +113,7 @@ struct sgn_ctx {
   float* rec_buf = nullptr;
   int rec_n = 0, rec_cap = 0, rec_count = 0, rec_tau_pow = 1;
   bool rec_stage = false;  // the current stage is being recorded
+  int ext_lv = 0;          // host copy of ext->levels in the host-driven loop
   float2* rtw = nullptr;
   float2* rY = nullptr;
   C64* sig_fb = nullptr;  // sigma_start of the recorded stage
@@ -673,20 +674,27 @@ bool gmres(sgn_ctx* ctx, int* iters_out, double* relres_out) {
 
 // ------------------------------------------------------- learned start
 // Kernels one network forward pass launches (13) for the launch count.
-constexpr int kUnetLaunches = 13;
+// kernels of one sgn_unet_infer: the weight image, the first layer, two per
+// level above the bottleneck (s_l and its pool), e_l for 0 < l < D-1, b0, b1
+// and D-1 decoder layers
+int unet_launches(sgn_unet_t net) { return 4 * sgn_unet_levels(net) - 1; }
 
 double learned_tau(int pw, double dt) { return pw == 0 ? 1.0 : (pw == 1 ? 0.5 * dt : 0.25 * dt * dt); }
 
-// Stages 2 and 4, after the start of opt.guess: record the coarse inputs (and
-// keep sigma_start) and/or add the network's correction to sigma_hat.
+// Stages 2 and 4 (every stage with guess 3), after the start of opt.guess:
+// record the coarse inputs (and keep sigma_start) and/or add the network's
+// correction to sigma_hat.
 void learned_pre(sgn_ctx* ctx, C64* const* U, int mode, double dt, bool graph = false) {
   ctx->rec_stage = false;
-  if (mode != RK_STAGE2 && mode != RK_FINAL) return;
+  const bool poly = ctx->opt.guess == 3;
+  if (mode == RK_STORE_K || (!poly && mode != RK_STAGE2 && mode != RK_FINAL)) return;
   // with the extrapolated start, stage 2 of a call's first step has no
-  // stage-3 history and starts from sigma_1 instead: a start of another kind,
-  // left alone (graph mode tests the device flag)
-  const bool s2_plain = ctx->opt.guess >= 2 && mode == RK_STAGE2;
+  // stage-3 history and starts from sigma_1 instead, and the polynomial start
+  // is cubic only once the ring holds 4 steps: starts of another kind, left
+  // alone (graph mode tests the device flags)
+  const bool s2_plain = ctx->opt.guess == 2 && mode == RK_STAGE2;
   if (s2_plain && !graph && !ctx->have_s3) return;
+  if (poly && !graph && ctx->ext_lv < 4) return;
   const Geom& G = ctx->G;
   if (ctx->rec_buf && ctx->rec_count < ctx->rec_cap) {
     const int n = ctx->rec_n;
@@ -715,15 +723,15 @@ void learned_pre(sgn_ctx* ctx, C64* const* U, int mode, double dt, bool graph = 
     }
     CK(launch_restrict(G, ci, 4, n, ctx->ltw, ctx->lY, EX(ctx)));
     sgn_unet_set_stream(ctx->net, ctx->stream);
-    const sgn_status st = sgn_unet_forward(ctx->net, ctx->lin, ctx->lout, 1);
+    const sgn_status st = sgn_unet_infer(ctx->net, ctx->lin, ctx->lout, 1);
     if (st != SGN_OK) {
       ctx->err = std::string("learned start: ") + sgn_unet_last_error(ctx->net);
       throw Fail{st};
     }
-    ctx->prof.launches += kUnetLaunches;
+    ctx->prof.launches += unet_launches(ctx->net);
+    const int* gate = !graph ? nullptr : (poly ? &ctx->ext->full : (s2_plain ? &ctx->gst->have_s3 : nullptr));
     CK(launch_prolong_add(G, ctx->lout, n, ctx->ltw, ctx->lY, nullptr,
-                          (double)ctx->out_scale * learned_tau(ctx->tau_pow, dt), ctx->sig, EX(ctx),
-                          s2_plain && graph ? &ctx->gst->have_s3 : nullptr));
+                          (double)ctx->out_scale * learned_tau(ctx->tau_pow, dt), ctx->sig, EX(ctx), gate));
   }
 }
 
@@ -793,7 +801,10 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   }
   if (ext) {
     CK(launch_ext_store(ctx->G, ctx->sig, ctx->ext_ring, mode, ctx->ext, EX(ctx)));
-    if (mode == RK_FINAL) CK(launch_ext_advance(ctx->ext, EX(ctx)));
+    if (mode == RK_FINAL) {
+      CK(launch_ext_advance(ctx->ext, EX(ctx)));
+      ctx->ext_lv = ctx->ext_lv < 4 ? ctx->ext_lv + 1 : 4;
+    }
   }
   RkArgs rk{};
   rk.mode = mode;
@@ -841,10 +852,12 @@ void same_state_flag(sgn_ctx* ctx) {
 // (cont, and the device flag same_state_flag() wrote)
 void ext_history(sgn_ctx* ctx, bool cont) {
   if (ctx->opt.guess != 3) return;
-  if (cont)
+  if (cont) {
     CK(launch_ext_keep(ctx->ext, &ctx->gst->have_s3, EX(ctx)));
-  else
+  } else {
     CK(launch_set_int(&ctx->ext->levels, 0, EX(ctx)));
+    CK(launch_set_int(&ctx->ext->full, 0, EX(ctx)));
+  }
 }
 
 void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, double dt, int nsteps,
@@ -863,6 +876,7 @@ void rk4_device(sgn_ctx* ctx, double* h, double* vx, double* vy, double* sigma, 
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_s3 = keep != 0;
   }
+  if (!(cont && ctx->have_s3)) ctx->ext_lv = 0;
   bool conv = true;
   for (int n = 0; n < nsteps; ++n) {
     conv &= stage(ctx, RK_STAGE1, dt);
@@ -1636,8 +1650,6 @@ sgn_status sgn_set_learned_guess(sgn_t ctx, void* net, int n, const float in_sca
     ctx->net = nullptr;
     return SGN_OK;
   }
-  if (ctx->opt.guess == 3)
-    return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: the learned start corrects the starts of guess 0, 1 and 2");
   sgn_unet_t u = static_cast<sgn_unet_t>(net);
   if (!coarse_side_ok(ctx, n) || sgn_unet_side(u) != n)
     return fail(ctx, SGN_EINVAL, "sgn_set_learned_guess: n must be a power of two in [16, min(Nx, Ny)] and the "
@@ -1666,8 +1678,6 @@ sgn_status sgn_record_learned(sgn_t ctx, int n, float* buf, int capacity, int ta
     return SGN_OK;
   }
   if (ctx->opt.graph) return fail(ctx, SGN_EINVAL, "sgn_record_learned: needs the host-driven loop (graph = 0)");
-  if (ctx->opt.guess == 3)
-    return fail(ctx, SGN_EINVAL, "sgn_record_learned: the learned start corrects the starts of guess 0, 1 and 2");
   if (!coarse_side_ok(ctx, n) || capacity < 1 || tau_power < 0 || tau_power > 2)
     return fail(ctx, SGN_EINVAL, "sgn_record_learned: bad n, capacity or tau_power");
   if (ctx->rec_n != n) {

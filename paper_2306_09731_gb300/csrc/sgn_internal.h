@@ -407,6 +407,7 @@ cudaError_t launch_set_int(int* p, int v, const Exec& ex);
 struct ExtHist {
   int levels;  // steps held, 0..4
   int head;    // slot q of the step being taken
+  int full;    // 1 while levels == 4 (the cubic start): the learned start's gate
 };
 // sigma = the quadratic (levels 3) or cubic (levels 4) extrapolation of stage
 // s from the ring; with fewer levels sigma is left as it is
@@ -415,9 +416,9 @@ cudaError_t launch_ext_start(const Geom& G, const cpx<double>* ring, int s, cons
 // ring slot (head, s) = sigma
 cudaError_t launch_ext_store(const Geom& G, const cpx<double>* sig, cpx<double>* ring, int s, const ExtHist* hist,
                              const Exec& ex);
-// after a step's last stage: head advances, levels += 1 (at most 4)
+// after a step's last stage: head advances, levels += 1 (at most 4), full = (levels == 4)
 cudaError_t launch_ext_advance(ExtHist* hist, const Exec& ex);
-// levels = 0 unless *flag
+// levels = full = 0 unless *flag
 cudaError_t launch_ext_keep(ExtHist* hist, const int* flag, const Exec& ex);
 // *flag = 1 if the three spectra b equal a within rel * max|a| (see sgn_krylov.cu)
 cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const cpx<double>* const* b, double rel,

@@ -534,13 +534,17 @@ __global__ void k_ext_advance(ExtHist* hist) {
   if (threadIdx.x == 0) {
     hist->head = (hist->head + 1) & 3;
     hist->levels = min(hist->levels + 1, 4);
+    hist->full = hist->levels >= 4 ? 1 : 0;
   }
 }
 
 // start of a call: keep the levels only if *flag (the call continues the
 // trajectory the handle returned last)
 __global__ void k_ext_keep(ExtHist* hist, const int* flag) {
-  if (threadIdx.x == 0 && *flag == 0) hist->levels = 0;
+  if (threadIdx.x == 0 && *flag == 0) {
+    hist->levels = 0;
+    hist->full = 0;
+  }
 }
 
 // *flag = 1 when every component of the three spectra b is within rel * max|a|

@@ -1,11 +1,12 @@
-// sgn_unet.cu - forward, backward and Adam kernels of the periodic U-Net
-// (include/sgn_unet.h) that corrects the GMRES starting value of sigma.
+// sgn_unet.cu - the periodic U-Net (include/sgn_unet.h) that corrects the
+// GMRES starting value of sigma: any depth and widths.
 //
-// Direct convolutions on CUDA cores: the network is small (6e4 parameters on a
-// coarse grid of at most 512^2), and every kernel here is far from the cost
-// of one matvec of the solver it serves. Activations are stored as T (BF16 or
-// FP32), everything else is FP32; sums over pixels (weight gradients, the
-// loss) are per-block fixed-order reductions, so results are deterministic.
+// Training (forward, backward, Adam) runs direct convolutions on CUDA cores in
+// NCHW: activations stored as T (BF16 or FP32), everything else FP32; sums over
+// pixels (weight gradients, the loss) are per-block fixed-order reductions, so
+// results are deterministic. Inference (sgn_unet_infer) runs the 3x3 layers
+// after the first as BF16 implicit GEMMs on the tensor cores over NHWC
+// activations (sgn_unet_tc.cuh).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "sgn_unet.h"
+#include "sgn_unet_tc.cuh"
 
 namespace {
 
@@ -289,24 +291,46 @@ __global__ void k_adam(float* p, const float* __restrict__ g, float* m, float* v
 
 inline unsigned blocks_for(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+constexpr int kMaxLevels = 6;
+
 struct Layer {
   int Ci, Co, k;
   long long woff, boff;
+  // tensor-core inference (3x3 layers after the first)
+  int KC = 0, nkb = 0, smem = 0;
+  long long ioff = -1;
 };
+
+// Lower bound of the tensor-core kernel's dynamic shared memory: 200 KB, one
+// CTA per SM, so that every operand address the MMA unit could form from a
+// descriptor of this layout stays inside the CTA's own allocation.
+constexpr int kTcSmemMin = 200 * 1024;
 
 }  // namespace
 
 struct sgn_unet_ctx {
   int n = 0, maxB = 0, bf16 = 1;
+  int D = 0, w[kMaxLevels] = {0};
   cudaStream_t stream = 0;
   std::vector<Layer> L;
   long long P = 0;
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-  // activations (element type by bf16) and FP32 gradient buffers
-  void *A0 = nullptr, *CAT0 = nullptr, *Q0 = nullptr, *A1 = nullptr, *CAT1 = nullptr, *Q1 = nullptr, *A2 = nullptr,
-       *A3 = nullptr, *A4 = nullptr, *A5 = nullptr;
-  float *OUT = nullptr, *gOUT = nullptr, *gN16a = nullptr, *gN16b = nullptr, *gN48 = nullptr, *gH32a = nullptr,
-        *gH32b = nullptr, *gH64 = nullptr, *gH16 = nullptr, *gQ32a = nullptr, *gQ32b = nullptr;
+  // training activations (element type by bf16), NCHW, per level l (grid n / 2^l):
+  //   A[l]   w_l channels: e_l's output (l < D-1), b0's output (l = D-1)
+  //   CAT[l] w_{l+1} + w_l channels: upsampled level below, then s_l's output (l < D-1)
+  //   Q[l]   w_l channels on level l+1's grid: the pooled s_l (l < D-1)
+  //   U[l]   w_l channels: d_l's output (l < D-1), b1's output (l = D-1)
+  void *A[kMaxLevels] = {}, *CAT[kMaxLevels] = {}, *Q[kMaxLevels] = {}, *U[kMaxLevels] = {};
+  float *OUT = nullptr, *gOUT = nullptr;
+  // FP32 gradients: two scratch tensors of wmax channels per level, and the
+  // concatenation's gradient per level
+  float *G[kMaxLevels][2] = {}, *gCAT[kMaxLevels] = {};
+  // inference (NHWC BF16): e_l / b0 outputs, s_l outputs, pooled, d_l / b1 outputs
+  __nv_bfloat16 *tA[kMaxLevels] = {}, *tS[kMaxLevels] = {}, *tQ[kMaxLevels] = {}, *tU[kMaxLevels] = {};
+  __nv_bfloat16* wimg = nullptr;
+  unet_tc::WImgTable wtab{};
+  int* dev_err = nullptr;
+  int tc_smem_max = 0;
   const float* lastIn = nullptr;
   int lastB = 0;
   std::vector<void*> allocs;
@@ -315,7 +339,13 @@ struct sgn_unet_ctx {
 
 namespace {
 
-enum { E0 = 0, S0, E1, S1, B0, B1, D1, D0, OUTL, NLAYERS };
+// parameter order: e_0, s_0, ..., e_{D-2}, s_{D-2}, b0, b1, d_{D-2}, ..., d_0, out
+inline int iE(int l) { return 2 * l; }
+inline int iS(int l) { return 2 * l + 1; }
+inline int iB0(const sgn_unet_ctx* net) { return 2 * (net->D - 1); }
+inline int iB1(const sgn_unet_ctx* net) { return 2 * (net->D - 1) + 1; }
+inline int iD(const sgn_unet_ctx* net, int l) { return 2 * net->D + (net->D - 2 - l); }
+inline int iOut(const sgn_unet_ctx* net) { return 3 * net->D - 1; }
 
 struct Fail {
   sgn_status st;
@@ -354,10 +384,11 @@ void init_params(sgn_unet_ctx* net, unsigned long long seed) {
     z ^= z >> 31;
     return (double)(z >> 11) / 9007199254740992.0;  // [0, 1)
   };
+  const int out_layer = iOut(net);
   for (size_t li = 0; li < net->L.size(); ++li) {
     const Layer& l = net->L[li];
     const double fan_in = (double)l.Ci * l.k * l.k;
-    const double bound = sqrt(6.0 / fan_in) * (li == OUTL ? 0.1 : 1.0);
+    const double bound = sqrt(6.0 / fan_in) * ((int)li == out_layer ? 0.1 : 1.0);
     const long long nw = (long long)l.Co * l.Ci * l.k * l.k;
     for (long long i = 0; i < nw; ++i) h[(size_t)(l.woff + i)] = (float)((2.0 * next() - 1.0) * bound);
   }
@@ -398,121 +429,189 @@ void relu_bwd(sgn_unet_ctx* net, const T* act, size_t abs_, float* g, size_t gbs
   UCK(cudaGetLastError());
 }
 
+inline size_t npix(const sgn_unet_ctx* net, int l) { return (size_t)(net->n >> l) * (size_t)(net->n >> l); }
+
 template <typename T>
 void forward_impl(sgn_unet_ctx* net, const float* in, float* out, int B) {
-  const int n = net->n, h = n / 2, q = n / 4;
-  const size_t N = (size_t)n * n, Hh = (size_t)h * h, Qq = (size_t)q * q;
-  T* A0 = (T*)net->A0;
-  T* CAT0 = (T*)net->CAT0;
-  T* Q0 = (T*)net->Q0;
-  T* A1 = (T*)net->A1;
-  T* CAT1 = (T*)net->CAT1;
-  T* Q1 = (T*)net->Q1;
-  T* A2 = (T*)net->A2;
-  T* A3 = (T*)net->A3;
-  T* A4 = (T*)net->A4;
-  T* A5 = (T*)net->A5;
-  conv3<float, T>(net, in, 4 * N, E0, A0, 16 * N, n, B, true);
-  conv3<T, T>(net, A0, 16 * N, S0, CAT0 + 32 * N, 48 * N, n, B, true);  // s0 -> CAT0[32, 48)
-  k_pool<T><<<blocks_for((size_t)B * 16 * Hh), 256, 0, net->stream>>>(CAT0 + 32 * N, 48 * N, Q0, 16 * Hh, 16, n, n, B);
+  const int D = net->D;
+  const int* w = net->w;
+  // encoder
+  for (int l = 0; l < D - 1; ++l) {
+    const int H = net->n >> l;
+    const size_t N = npix(net, l), Nq = npix(net, l + 1);
+    T* A = (T*)net->A[l];
+    T* S = (T*)net->CAT[l] + (size_t)w[l + 1] * N;  // s_l lives in CAT[l] after the upsampled channels
+    const size_t cs = (size_t)(w[l + 1] + w[l]) * N;
+    if (l == 0)
+      conv3<float, T>(net, in, 4 * N, iE(0), A, (size_t)w[0] * N, H, B, true);
+    else
+      conv3<T, T>(net, (const T*)net->Q[l - 1], (size_t)w[l - 1] * N, iE(l), A, (size_t)w[l] * N, H, B, true);
+    conv3<T, T>(net, A, (size_t)w[l] * N, iS(l), S, cs, H, B, true);
+    k_pool<T><<<blocks_for((size_t)B * w[l] * Nq), 256, 0, net->stream>>>(S, cs, (T*)net->Q[l], (size_t)w[l] * Nq,
+                                                                           w[l], H, H, B);
+    UCK(cudaGetLastError());
+  }
+  // bottleneck
+  {
+    const int l = D - 1, H = net->n >> l;
+    const size_t N = npix(net, l);
+    conv3<T, T>(net, (const T*)net->Q[l - 1], (size_t)w[l - 1] * N, iB0(net), (T*)net->A[l], (size_t)w[l] * N, H, B,
+                true);
+    conv3<T, T>(net, (const T*)net->A[l], (size_t)w[l] * N, iB1(net), (T*)net->U[l], (size_t)w[l] * N, H, B, true);
+  }
+  // decoder
+  for (int l = D - 2; l >= 0; --l) {
+    const int H = net->n >> l;
+    const size_t N = npix(net, l), Nb = npix(net, l + 1);
+    const size_t cs = (size_t)(w[l + 1] + w[l]) * N;
+    k_up<T><<<blocks_for((size_t)B * w[l + 1] * N), 256, 0, net->stream>>>(
+        (const T*)net->U[l + 1], (size_t)w[l + 1] * Nb, (T*)net->CAT[l], cs, w[l + 1], H / 2, H / 2, B);
+    UCK(cudaGetLastError());
+    conv3<T, T>(net, (const T*)net->CAT[l], cs, iD(net, l), (T*)net->U[l], (size_t)w[l] * N, H, B, true);
+  }
+  const Layer& lo = net->L[iOut(net)];
+  const size_t N0 = npix(net, 0);
+  k_conv1_fwd<T><<<blocks_for((size_t)B * N0), 256, 0, net->stream>>>(
+      (const T*)net->U[0], (size_t)w[0] * N0, w[0], net->params + lo.woff, net->params + lo.boff, net->OUT, (int)N0,
+      B);
   UCK(cudaGetLastError());
-  conv3<T, T>(net, Q0, 16 * Hh, E1, A1, 32 * Hh, h, B, true);
-  conv3<T, T>(net, A1, 32 * Hh, S1, CAT1 + 32 * Hh, 64 * Hh, h, B, true);  // s1 -> CAT1[32, 64)
-  k_pool<T><<<blocks_for((size_t)B * 32 * Qq), 256, 0, net->stream>>>(CAT1 + 32 * Hh, 64 * Hh, Q1, 32 * Qq, 32, h, h, B);
-  UCK(cudaGetLastError());
-  conv3<T, T>(net, Q1, 32 * Qq, B0, A2, 32 * Qq, q, B, true);
-  conv3<T, T>(net, A2, 32 * Qq, B1, A3, 32 * Qq, q, B, true);
-  k_up<T><<<blocks_for((size_t)B * 32 * Hh), 256, 0, net->stream>>>(A3, 32 * Qq, CAT1, 64 * Hh, 32, q, q, B);
-  UCK(cudaGetLastError());
-  conv3<T, T>(net, CAT1, 64 * Hh, D1, A4, 32 * Hh, h, B, true);
-  k_up<T><<<blocks_for((size_t)B * 32 * N), 256, 0, net->stream>>>(A4, 32 * Hh, CAT0, 48 * N, 32, h, h, B);
-  UCK(cudaGetLastError());
-  conv3<T, T>(net, CAT0, 48 * N, D0, A5, 16 * N, n, B, true);
-  const Layer& lo = net->L[OUTL];
-  k_conv1_fwd<T><<<blocks_for((size_t)B * N), 256, 0, net->stream>>>(A5, 16 * N, 16, net->params + lo.woff,
-                                                                     net->params + lo.boff, net->OUT, (int)N, B);
-  UCK(cudaGetLastError());
-  if (out) UCK(cudaMemcpyAsync(out, net->OUT, sizeof(float) * B * N, cudaMemcpyDeviceToDevice, net->stream));
+  if (out) UCK(cudaMemcpyAsync(out, net->OUT, sizeof(float) * B * N0, cudaMemcpyDeviceToDevice, net->stream));
 }
 
 template <typename T>
 void backward_impl(sgn_unet_ctx* net, const float* target, double* loss) {
-  const int n = net->n, h = n / 2, q = n / 4, B = net->lastB;
-  const size_t N = (size_t)n * n, Hh = (size_t)h * h, Qq = (size_t)q * q;
-  T* A0 = (T*)net->A0;
-  T* CAT0 = (T*)net->CAT0;
-  T* Q0 = (T*)net->Q0;
-  T* A1 = (T*)net->A1;
-  T* CAT1 = (T*)net->CAT1;
-  T* Q1 = (T*)net->Q1;
-  T* A2 = (T*)net->A2;
-  T* A3 = (T*)net->A3;
-  T* A4 = (T*)net->A4;
-  T* A5 = (T*)net->A5;
-  k_mse<<<1, 1024, 0, net->stream>>>(net->OUT, target, net->gOUT, (int)(B * N), loss);
+  const int D = net->D, B = net->lastB;
+  const int* w = net->w;
+  const size_t N0 = npix(net, 0);
+  k_mse<<<1, 1024, 0, net->stream>>>(net->OUT, target, net->gOUT, (int)(B * N0), loss);
   UCK(cudaGetLastError());
-  // output layer 16 -> 1
-  const Layer& lo = net->L[OUTL];
-  k_conv1_dw<T><<<17, 256, 0, net->stream>>>(A5, 16 * N, 16, net->gOUT, (int)N, B, net->grads + lo.woff,
-                                             net->grads + lo.boff);
+  // output layer w_0 -> 1, then the ReLU of d_0
+  const Layer& lo = net->L[iOut(net)];
+  k_conv1_dw<T><<<w[0] + 1, 256, 0, net->stream>>>((const T*)net->U[0], (size_t)w[0] * N0, w[0], net->gOUT, (int)N0,
+                                                   B, net->grads + lo.woff, net->grads + lo.boff);
   UCK(cudaGetLastError());
-  float* dP7 = net->gN16a;  // d(pre-activation of d0), [16] at n
-  k_conv1_dx_relu<T><<<blocks_for((size_t)B * 16 * N), 256, 0, net->stream>>>(A5, 16 * N, 16, net->params + lo.woff,
-                                                                              net->gOUT, dP7, 16 * N, (int)N, B);
+  k_conv1_dx_relu<T><<<blocks_for((size_t)B * w[0] * N0), 256, 0, net->stream>>>(
+      (const T*)net->U[0], (size_t)w[0] * N0, w[0], net->params + lo.woff, net->gOUT, net->G[0][0],
+      (size_t)w[0] * N0, (int)N0, B);
   UCK(cudaGetLastError());
-  // d0: 48 -> 16 on CAT0
-  conv3_dw<T>(net, CAT0, 48 * N, dP7, 16 * N, D0, n, B);
-  float* dCAT0 = net->gN48;
-  conv3_dx(net, dP7, 16 * N, D0, dCAT0, 48 * N, n, B);
-  // u0: CAT0[0, 32) came from A4 (relu output of d1)
-  float* dP6 = net->gH32a;
-  k_up_bwd<<<blocks_for((size_t)B * 32 * Hh), 256, 0, net->stream>>>(dCAT0, 48 * N, dP6, 32 * Hh, 32, h, h, B);
+  // decoder, from the top level down the U: G[l][0] holds d(pre-activation of d_l)
+  for (int l = 0; l < D - 1; ++l) {
+    const int H = net->n >> l;
+    const size_t N = npix(net, l), Nb = npix(net, l + 1);
+    const size_t cs = (size_t)(w[l + 1] + w[l]) * N;
+    conv3_dw<T>(net, (const T*)net->CAT[l], cs, net->G[l][0], (size_t)w[l] * N, iD(net, l), H, B);
+    conv3_dx(net, net->G[l][0], (size_t)w[l] * N, iD(net, l), net->gCAT[l], cs, H, B);
+    // the upsampled channels came from U[l+1] (the ReLU output of d_{l+1} or b1)
+    float* g = net->G[l + 1][0];
+    k_up_bwd<<<blocks_for((size_t)B * w[l + 1] * Nb), 256, 0, net->stream>>>(net->gCAT[l], cs, g,
+                                                                             (size_t)w[l + 1] * Nb, w[l + 1], H / 2,
+                                                                             H / 2, B);
+    UCK(cudaGetLastError());
+    relu_bwd<T>(net, (const T*)net->U[l + 1], (size_t)w[l + 1] * Nb, g, (size_t)w[l + 1] * Nb, nullptr, 0, w[l + 1],
+                H / 2, B);
+  }
+  // bottleneck: G[D-1][0] = d(pre-activation of b1)
+  {
+    const int l = D - 1, H = net->n >> l;
+    const size_t N = npix(net, l);
+    const size_t bs = (size_t)w[l] * N;
+    conv3_dw<T>(net, (const T*)net->A[l], bs, net->G[l][0], bs, iB1(net), H, B);
+    conv3_dx(net, net->G[l][0], bs, iB1(net), net->G[l][1], bs, H, B);
+    relu_bwd<T>(net, (const T*)net->A[l], bs, net->G[l][1], bs, nullptr, 0, w[l], H, B);
+    conv3_dw<T>(net, (const T*)net->Q[l - 1], (size_t)w[l - 1] * N, net->G[l][1], bs, iB0(net), H, B);
+    // d(pooled s_{D-2}) into G[D-1][0]
+    conv3_dx(net, net->G[l][1], bs, iB0(net), net->G[l][0], (size_t)w[l - 1] * N, H, B);
+  }
+  // encoder, back up to the input: G[l+1][0] holds d(Q[l])
+  for (int l = D - 2; l >= 0; --l) {
+    const int H = net->n >> l;
+    const size_t N = npix(net, l), Nq = npix(net, l + 1);
+    const size_t cs = (size_t)(w[l + 1] + w[l]) * N, bs = (size_t)w[l] * N;
+    float* g0 = net->G[l][0];
+    float* g1 = net->G[l][1];
+    k_pool_bwd<<<blocks_for((size_t)B * w[l] * N), 256, 0, net->stream>>>(net->G[l + 1][0], (size_t)w[l] * Nq, g0, bs,
+                                                                          w[l], H, H, B);
+    UCK(cudaGetLastError());
+    // s_l also feeds the decoder through the concatenation
+    const T* S = (const T*)net->CAT[l] + (size_t)w[l + 1] * N;
+    relu_bwd<T>(net, S, cs, g0, bs, net->gCAT[l] + (size_t)w[l + 1] * N, cs, w[l], H, B);
+    conv3_dw<T>(net, (const T*)net->A[l], bs, g0, bs, iS(l), H, B);
+    conv3_dx(net, g0, bs, iS(l), g1, bs, H, B);
+    relu_bwd<T>(net, (const T*)net->A[l], bs, g1, bs, nullptr, 0, w[l], H, B);
+    if (l == 0) {
+      conv3_dw<float>(net, net->lastIn, 4 * N, g1, bs, iE(0), H, B);
+    } else {
+      conv3_dw<T>(net, (const T*)net->Q[l - 1], (size_t)w[l - 1] * N, g1, bs, iE(l), H, B);
+      conv3_dx(net, g1, bs, iE(l), g0, (size_t)w[l - 1] * N, H, B);
+    }
+  }
+}
+
+// ---------------------------------------------------- tensor-core inference
+void tc_conv(sgn_unet_ctx* net, int li, const __nv_bfloat16* src0, int C0, int up0, const __nv_bfloat16* src1,
+             int C1, int l, int B, __nv_bfloat16* out, const float* head_w = nullptr, const float* head_b = nullptr,
+             float* head_out = nullptr) {
+  const Layer& L = net->L[li];
+  unet_tc::ConvArgs a{};
+  a.src0 = src0;
+  a.src1 = src1;
+  a.C0 = C0;
+  a.C1 = C1;
+  a.up0 = up0;
+  int lg = 0;
+  while ((1 << lg) < (net->n >> l)) ++lg;
+  a.lH = a.lW = lg;
+  a.npix = B * (int)npix(net, l);
+  a.wimg = net->wimg + L.ioff;
+  a.bias = net->params + L.boff;
+  a.Co = L.Co;
+  a.KC = L.KC;
+  a.nkb = L.nkb;
+  uint32_t cols = 32;
+  while ((int)cols < L.Co) cols <<= 1;
+  a.tmem_cols = cols;
+  a.out = out;
+  a.head_w = head_w;
+  a.head_b = head_b;
+  a.head_out = head_out;
+  a.err = net->dev_err;
+  const unsigned grid = (unsigned)((a.npix + unet_tc::kM - 1) / unet_tc::kM);
+  unet_tc::k_conv3_tc<<<grid, unet_tc::kThreads, L.smem, net->stream>>>(a);
   UCK(cudaGetLastError());
-  relu_bwd<T>(net, A4, 32 * Hh, dP6, 32 * Hh, nullptr, 0, 32, h, B);
-  // d1: 64 -> 32 on CAT1
-  conv3_dw<T>(net, CAT1, 64 * Hh, dP6, 32 * Hh, D1, h, B);
-  float* dCAT1 = net->gH64;
-  conv3_dx(net, dP6, 32 * Hh, D1, dCAT1, 64 * Hh, h, B);
-  // u1: CAT1[0, 32) came from A3 (relu output of b1)
-  float* dP5 = net->gQ32a;
-  k_up_bwd<<<blocks_for((size_t)B * 32 * Qq), 256, 0, net->stream>>>(dCAT1, 64 * Hh, dP5, 32 * Qq, 32, q, q, B);
-  UCK(cudaGetLastError());
-  relu_bwd<T>(net, A3, 32 * Qq, dP5, 32 * Qq, nullptr, 0, 32, q, B);
-  // b1: 32 -> 32 on A2
-  conv3_dw<T>(net, A2, 32 * Qq, dP5, 32 * Qq, B1, q, B);
-  float* dP4 = net->gQ32b;
-  conv3_dx(net, dP5, 32 * Qq, B1, dP4, 32 * Qq, q, B);
-  relu_bwd<T>(net, A2, 32 * Qq, dP4, 32 * Qq, nullptr, 0, 32, q, B);
-  // b0: 32 -> 32 on Q1
-  conv3_dw<T>(net, Q1, 32 * Qq, dP4, 32 * Qq, B0, q, B);
-  float* dQ1 = net->gQ32a;
-  conv3_dx(net, dP4, 32 * Qq, B0, dQ1, 32 * Qq, q, B);
-  // p1: s1 = CAT1[32, 64) gets the pool gradient plus the skip gradient dCAT1[32, 64)
-  float* dP3 = net->gH32b;
-  k_pool_bwd<<<blocks_for((size_t)B * 32 * Hh), 256, 0, net->stream>>>(dQ1, 32 * Qq, dP3, 32 * Hh, 32, h, h, B);
-  UCK(cudaGetLastError());
-  relu_bwd<T>(net, CAT1 + 32 * Hh, 64 * Hh, dP3, 32 * Hh, dCAT1 + 32 * Hh, 64 * Hh, 32, h, B);
-  // s1: 32 -> 32 on A1
-  conv3_dw<T>(net, A1, 32 * Hh, dP3, 32 * Hh, S1, h, B);
-  float* dP2 = net->gH32a;
-  conv3_dx(net, dP3, 32 * Hh, S1, dP2, 32 * Hh, h, B);
-  relu_bwd<T>(net, A1, 32 * Hh, dP2, 32 * Hh, nullptr, 0, 32, h, B);
-  // e1: 16 -> 32 on Q0
-  conv3_dw<T>(net, Q0, 16 * Hh, dP2, 32 * Hh, E1, h, B);
-  float* dQ0 = net->gH16;
-  conv3_dx(net, dP2, 32 * Hh, E1, dQ0, 16 * Hh, h, B);
-  // p0: s0 = CAT0[32, 48) gets the pool gradient plus dCAT0[32, 48)
-  float* dP1 = net->gN16a;
-  k_pool_bwd<<<blocks_for((size_t)B * 16 * N), 256, 0, net->stream>>>(dQ0, 16 * Hh, dP1, 16 * N, 16, n, n, B);
-  UCK(cudaGetLastError());
-  relu_bwd<T>(net, CAT0 + 32 * N, 48 * N, dP1, 16 * N, dCAT0 + 32 * N, 48 * N, 16, n, B);
-  // s0: 16 -> 16 on A0
-  conv3_dw<T>(net, A0, 16 * N, dP1, 16 * N, S0, n, B);
-  float* dP0 = net->gN16b;
-  conv3_dx(net, dP1, 16 * N, S0, dP0, 16 * N, n, B);
-  relu_bwd<T>(net, A0, 16 * N, dP0, 16 * N, nullptr, 0, 16, n, B);
-  // e0: 4 -> 16 on the input
-  conv3_dw<float>(net, net->lastIn, 4 * N, dP0, 16 * N, E0, n, B);
+}
+
+void infer_impl(sgn_unet_ctx* net, const float* in, float* out, int B) {
+  const int D = net->D;
+  const int* w = net->w;
+  {
+    const unsigned nb = (unsigned)((net->wtab.total + 255) / 256);
+    unet_tc::k_wimg<<<nb, 256, 0, net->stream>>>(net->wtab, net->params, net->wimg);
+    UCK(cudaGetLastError());
+  }
+  int lg0 = 0;
+  while ((1 << lg0) < net->n) ++lg0;
+  {
+    const Layer& L = net->L[iE(0)];
+    const int np = B * (int)npix(net, 0);
+    unet_tc::k_conv_in_nhwc<<<(np + 127) / 128, 128, sizeof(float) * L.Co * 37, net->stream>>>(
+        in, lg0, lg0, np, net->params + L.woff, net->params + L.boff, L.Co, net->tA[0]);
+    UCK(cudaGetLastError());
+  }
+  for (int l = 0; l < D - 1; ++l) {
+    if (l > 0) tc_conv(net, iE(l), net->tQ[l - 1], w[l - 1], 0, nullptr, 0, l, B, net->tA[l]);
+    tc_conv(net, iS(l), net->tA[l], w[l], 0, nullptr, 0, l, B, net->tS[l]);
+    const int nout = B * (int)npix(net, l + 1);
+    unet_tc::k_pool_nhwc<<<blocks_for((size_t)nout * (w[l] / 8)), 256, 0, net->stream>>>(
+        net->tS[l], lg0 - l, lg0 - l, w[l], nout, net->tQ[l]);
+    UCK(cudaGetLastError());
+  }
+  tc_conv(net, iB0(net), net->tQ[D - 2], w[D - 2], 0, nullptr, 0, D - 1, B, net->tA[D - 1]);
+  tc_conv(net, iB1(net), net->tA[D - 1], w[D - 1], 0, nullptr, 0, D - 1, B, net->tU[D - 1]);
+  for (int l = D - 2; l >= 1; --l)
+    tc_conv(net, iD(net, l), net->tU[l + 1], w[l + 1], 1, net->tS[l], w[l], l, B, net->tU[l]);
+  const Layer& lo = net->L[iOut(net)];
+  tc_conv(net, iD(net, 0), net->tU[1], w[1], 1, net->tS[0], w[0], 0, B, nullptr, net->params + lo.woff,
+          net->params + lo.boff, out);
 }
 
 sgn_status ufail(sgn_unet_ctx* net, sgn_status st, const char* msg) {
@@ -523,6 +622,136 @@ sgn_status ufail(sgn_unet_ctx* net, sgn_status st, const char* msg) {
 void ufree(sgn_unet_ctx* net) {
   for (void* p : net->allocs) cudaFree(p);
   net->allocs.clear();
+}
+
+// channels per K step of a tensor-core layer: the fewest steps per tap whose
+// operands fit one shared-memory stage
+int pick_kc(int Ci, int Co) {
+  for (int nkb = 1; nkb <= Ci / 16; ++nkb) {
+    if (Ci % nkb) continue;
+    const int kc = Ci / nkb;
+    if (kc % 16) continue;
+    if ((int)unet_tc::stage_bytes(Co, kc) <= unet_tc::kStageMax) return kc;
+  }
+  return 16;
+}
+
+sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long seed, int levels, const int* widths,
+                       sgn_unet_t* out) {
+  if (!out) return SGN_EINVAL;
+  *out = nullptr;
+  if (levels < 2 || levels > kMaxLevels || !widths) return SGN_EINVAL;
+  if (n < 16 || n > 512 || (n & (n - 1)) != 0 || max_batch < 1 || max_batch > 64) return SGN_EINVAL;
+  if ((n >> (levels - 1)) < 4) return SGN_EINVAL;
+  for (int l = 0; l < levels; ++l)
+    if (widths[l] < 16 || widths[l] > 256 || widths[l] % 16 != 0) return SGN_EINVAL;
+  // one tensor-core tile of 128 pixels must not need more than 2^31 pixels in all
+  if ((long long)max_batch * n * n > (1ll << 30)) return SGN_EINVAL;
+  sgn_unet_ctx* net = new (std::nothrow) sgn_unet_ctx();
+  if (!net) return SGN_ENOMEM;
+  net->n = n;
+  net->maxB = max_batch;
+  net->bf16 = act_bf16 ? 1 : 0;
+  net->D = levels;
+  for (int l = 0; l < levels; ++l) net->w[l] = widths[l];
+  const int D = levels;
+  const int* w = net->w;
+  std::vector<int> ci, co, kk;
+  auto add = [&](int a, int b, int k) {
+    ci.push_back(a);
+    co.push_back(b);
+    kk.push_back(k);
+  };
+  for (int l = 0; l < D - 1; ++l) {
+    add(l == 0 ? 4 : w[l - 1], w[l], 3);
+    add(w[l], w[l], 3);
+  }
+  add(w[D - 2], w[D - 1], 3);
+  add(w[D - 1], w[D - 1], 3);
+  for (int l = D - 2; l >= 0; --l) add(w[l + 1] + w[l], w[l], 3);
+  add(w[0], 1, 1);
+  long long off = 0, ioff = 0;
+  int smem_max = 0;
+  net->wtab.nl = 0;
+  for (size_t i = 0; i < ci.size(); ++i) {
+    Layer l;
+    l.Ci = ci[i];
+    l.Co = co[i];
+    l.k = kk[i];
+    l.woff = off;
+    off += (long long)l.Co * l.Ci * l.k * l.k;
+    l.boff = off;
+    off += l.Co;
+    if (l.k == 3 && i > 0) {
+      l.KC = pick_kc(l.Ci, l.Co);
+      l.nkb = l.Ci / l.KC;
+      l.ioff = ioff;
+      unet_tc::WImgLayer& t = net->wtab.l[net->wtab.nl++];
+      t.woff = l.woff;
+      t.ioff = ioff;
+      t.Ci = l.Ci;
+      t.Co = l.Co;
+      t.KC = l.KC;
+      t.nkb = l.nkb;
+      ioff += 9ll * l.Ci * l.Co;
+      int sm = 2 * (int)unet_tc::stage_bytes(l.Co, l.KC);
+      // at most 512 / cols CTAs per SM, so that TMEM is never oversubscribed
+      int cols = 32;
+      while (cols < l.Co) cols <<= 1;
+      const int ctas = 512 / cols;
+      const int floor_bytes = 233472 / (ctas + 1) + 1;
+      if (sm < floor_bytes) sm = floor_bytes;
+      if (sm < kTcSmemMin) sm = kTcSmemMin;
+      l.smem = sm;
+      if (sm > smem_max) smem_max = sm;
+    }
+    net->L.push_back(l);
+  }
+  net->wtab.total = ioff;
+  net->P = off;
+  net->tc_smem_max = smem_max;
+  try {
+    const size_t B = (size_t)max_batch;
+    const size_t es = net->bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
+    const size_t bf = sizeof(__nv_bfloat16);
+    int wmax = 4;
+    for (int l = 0; l < D; ++l) wmax = w[l] > wmax ? w[l] : wmax;
+    net->params = (float*)ualloc(net, sizeof(float) * (size_t)off);
+    net->grads = (float*)ualloc(net, sizeof(float) * (size_t)off);
+    net->m = (float*)ualloc(net, sizeof(float) * (size_t)off);
+    net->v = (float*)ualloc(net, sizeof(float) * (size_t)off);
+    for (int l = 0; l < D; ++l) {
+      const size_t N = npix(net, l);
+      net->A[l] = ualloc(net, es * B * w[l] * N);
+      net->U[l] = ualloc(net, es * B * w[l] * N);
+      net->G[l][0] = (float*)ualloc(net, sizeof(float) * B * wmax * N);
+      net->G[l][1] = (float*)ualloc(net, sizeof(float) * B * wmax * N);
+      net->tA[l] = (__nv_bfloat16*)ualloc(net, bf * B * w[l] * N);
+      net->tU[l] = (__nv_bfloat16*)ualloc(net, bf * B * w[l] * N);
+      if (l < D - 1) {
+        net->CAT[l] = ualloc(net, es * B * (w[l + 1] + w[l]) * N);
+        net->Q[l] = ualloc(net, es * B * w[l] * npix(net, l + 1));
+        net->gCAT[l] = (float*)ualloc(net, sizeof(float) * B * (w[l + 1] + w[l]) * N);
+        net->tS[l] = (__nv_bfloat16*)ualloc(net, bf * B * w[l] * N);
+        net->tQ[l] = (__nv_bfloat16*)ualloc(net, bf * B * w[l] * npix(net, l + 1));
+      }
+    }
+    const size_t N0 = npix(net, 0);
+    net->OUT = (float*)ualloc(net, sizeof(float) * B * N0);
+    net->gOUT = (float*)ualloc(net, sizeof(float) * B * N0);
+    net->wimg = (__nv_bfloat16*)ualloc(net, bf * (size_t)(ioff > 0 ? ioff : 1));
+    net->dev_err = (int*)ualloc(net, sizeof(int));
+    UCK(cudaMemset(net->dev_err, 0, sizeof(int)));
+    UCK(cudaFuncSetAttribute(unet_tc::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+    init_params(net, seed);
+    UCK(cudaDeviceSynchronize());
+  } catch (Fail& f) {
+    ufree(net);
+    delete net;
+    return f.st;
+  }
+  *out = net;
+  return SGN_OK;
 }
 
 }  // namespace
@@ -540,66 +769,13 @@ void ufree(sgn_unet_ctx* net) {
 extern "C" {
 
 sgn_status sgn_unet_create(int n, int max_batch, int act_bf16, unsigned long long seed, sgn_unet_t* out) {
-  if (!out) return SGN_EINVAL;
-  *out = nullptr;
-  if (n < 16 || n > 512 || (n & (n - 1)) != 0 || max_batch < 1 || max_batch > 64) return SGN_EINVAL;
-  sgn_unet_ctx* net = new (std::nothrow) sgn_unet_ctx();
-  if (!net) return SGN_ENOMEM;
-  net->n = n;
-  net->maxB = max_batch;
-  net->bf16 = act_bf16 ? 1 : 0;
-  const int spec[NLAYERS][3] = {{4, 16, 3},  {16, 16, 3}, {16, 32, 3}, {32, 32, 3}, {32, 32, 3},
-                                {32, 32, 3}, {64, 32, 3}, {48, 16, 3}, {16, 1, 1}};
-  long long off = 0;
-  for (int i = 0; i < NLAYERS; ++i) {
-    Layer l;
-    l.Ci = spec[i][0];
-    l.Co = spec[i][1];
-    l.k = spec[i][2];
-    l.woff = off;
-    off += (long long)l.Co * l.Ci * l.k * l.k;
-    l.boff = off;
-    off += l.Co;
-    net->L.push_back(l);
-  }
-  net->P = off;
-  try {
-    const size_t B = (size_t)max_batch, N = (size_t)n * n, Hh = N / 4, Qq = N / 16;
-    const size_t es = net->bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
-    net->params = (float*)ualloc(net, sizeof(float) * (size_t)off);
-    net->grads = (float*)ualloc(net, sizeof(float) * (size_t)off);
-    net->m = (float*)ualloc(net, sizeof(float) * (size_t)off);
-    net->v = (float*)ualloc(net, sizeof(float) * (size_t)off);
-    net->A0 = ualloc(net, es * B * 16 * N);
-    net->CAT0 = ualloc(net, es * B * 48 * N);
-    net->Q0 = ualloc(net, es * B * 16 * Hh);
-    net->A1 = ualloc(net, es * B * 32 * Hh);
-    net->CAT1 = ualloc(net, es * B * 64 * Hh);
-    net->Q1 = ualloc(net, es * B * 32 * Qq);
-    net->A2 = ualloc(net, es * B * 32 * Qq);
-    net->A3 = ualloc(net, es * B * 32 * Qq);
-    net->A4 = ualloc(net, es * B * 32 * Hh);
-    net->A5 = ualloc(net, es * B * 16 * N);
-    net->OUT = (float*)ualloc(net, sizeof(float) * B * N);
-    net->gOUT = (float*)ualloc(net, sizeof(float) * B * N);
-    net->gN16a = (float*)ualloc(net, sizeof(float) * B * 16 * N);
-    net->gN16b = (float*)ualloc(net, sizeof(float) * B * 16 * N);
-    net->gN48 = (float*)ualloc(net, sizeof(float) * B * 48 * N);
-    net->gH32a = (float*)ualloc(net, sizeof(float) * B * 32 * Hh);
-    net->gH32b = (float*)ualloc(net, sizeof(float) * B * 32 * Hh);
-    net->gH64 = (float*)ualloc(net, sizeof(float) * B * 64 * Hh);
-    net->gH16 = (float*)ualloc(net, sizeof(float) * B * 16 * Hh);
-    net->gQ32a = (float*)ualloc(net, sizeof(float) * B * 32 * Qq);
-    net->gQ32b = (float*)ualloc(net, sizeof(float) * B * 32 * Qq);
-    init_params(net, seed);
-    UCK(cudaDeviceSynchronize());
-  } catch (Fail& f) {
-    ufree(net);
-    delete net;
-    return f.st;
-  }
-  *out = net;
-  return SGN_OK;
+  const int widths[3] = {16, 32, 32};
+  return create_impl(n, max_batch, act_bf16, seed, 3, widths, out);
+}
+
+sgn_status sgn_unet_create_arch(int n, int max_batch, int act_bf16, unsigned long long seed, int levels,
+                                const int* widths, sgn_unet_t* out) {
+  return create_impl(n, max_batch, act_bf16, seed, levels, widths, out);
 }
 
 sgn_status sgn_unet_destroy(sgn_unet_t net) {
@@ -621,6 +797,13 @@ const char* sgn_unet_last_error(sgn_unet_t net) { return net ? net->err.c_str() 
 long long sgn_unet_num_params(sgn_unet_t net) { return net ? net->P : -1; }
 
 int sgn_unet_side(sgn_unet_t net) { return net ? net->n : -1; }
+
+int sgn_unet_levels(sgn_unet_t net) { return net ? net->D : -1; }
+
+int sgn_unet_width(sgn_unet_t net, int level) {
+  if (!net || level < 0 || level >= net->D) return -1;
+  return net->w[level];
+}
 
 sgn_status sgn_unet_set_params(sgn_unet_t net, const float* p) {
   UAPI_BEGIN
@@ -657,6 +840,97 @@ sgn_status sgn_unet_forward(sgn_unet_t net, const float* in, float* out, int bat
   net->lastB = batch;
   return SGN_OK;
   UAPI_END
+}
+
+sgn_status sgn_unet_infer(sgn_unet_t net, const float* in, float* out, int batch) {
+  UAPI_BEGIN
+  if (!in || !out || batch < 1 || batch > net->maxB)
+    return ufail(net, SGN_EINVAL, "sgn_unet_infer: bad input, output or batch");
+  infer_impl(net, in, out, batch);
+  return SGN_OK;
+  UAPI_END
+}
+
+sgn_status sgn_unet_check(sgn_unet_t net) {
+  UAPI_BEGIN
+  int h = 0;
+  UCK(cudaMemcpyAsync(&h, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+  UCK(cudaStreamSynchronize(net->stream));
+  if (h != 0) {
+    UCK(cudaMemsetAsync(net->dev_err, 0, sizeof(int), net->stream));
+    return ufail(net, SGN_ECUDA, "sgn_unet_infer: a tensor-core wait ran out (the outputs are not valid)");
+  }
+  return SGN_OK;
+  UAPI_END
+}
+
+sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0, int up0, const void* src1, int C1,
+                               const float* weight, const float* bias, int Co, void* out, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
+  const int Ci = C0 + C1;
+  if (batch < 1 || !pow2(H) || !pow2(W) || (long long)batch * H * W > (1ll << 30)) return SGN_EINVAL;
+  if (up0 && (H < 4 || W < 4)) return SGN_EINVAL;
+  if (!src0 || !weight || !bias || !out || !workspace || C0 < 16 || C0 % 16 || C1 < 0 || C1 % 16 ||
+      (C1 > 0 && !src1) || Ci > 1024 || Co < 16 || Co > 256 || Co % 16)
+    return SGN_EINVAL;
+  const size_t img = (size_t)9 * Ci * Co * sizeof(__nv_bfloat16);
+  if (workspace_bytes < sgn_conv3_workspace_bytes(C0 + C1, Co) || ((uintptr_t)workspace & 15u)) return SGN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int lH = 0, lW = 0;
+  while ((1 << lH) < H) ++lH;
+  while ((1 << lW) < W) ++lW;
+  const int KC = pick_kc(Ci, Co);
+  __nv_bfloat16* wimg = (__nv_bfloat16*)workspace;
+  int* err = (int*)((char*)workspace + ((img + 15) & ~(size_t)15));
+  unet_tc::WImgTable t{};
+  t.nl = 1;
+  t.l[0].woff = 0;
+  t.l[0].ioff = 0;
+  t.l[0].Ci = Ci;
+  t.l[0].Co = Co;
+  t.l[0].KC = KC;
+  t.l[0].nkb = Ci / KC;
+  t.total = 9ll * Ci * Co;
+  int cols = 32;
+  while (cols < Co) cols <<= 1;
+  int sm = 2 * (int)unet_tc::stage_bytes(Co, KC);
+  const int floor_bytes = 233472 / (512 / cols + 1) + 1;
+  if (sm < floor_bytes) sm = floor_bytes;
+  if (sm < kTcSmemMin) sm = kTcSmemMin;
+  unet_tc::ConvArgs a{};
+  a.src0 = (const __nv_bfloat16*)src0;
+  a.src1 = (const __nv_bfloat16*)src1;
+  a.C0 = C0;
+  a.C1 = C1;
+  a.up0 = up0 ? 1 : 0;
+  a.lH = lH;
+  a.lW = lW;
+  a.npix = batch * H * W;
+  a.wimg = wimg;
+  a.bias = bias;
+  a.Co = Co;
+  a.KC = KC;
+  a.nkb = Ci / KC;
+  a.tmem_cols = (uint32_t)cols;
+  a.out = (__nv_bfloat16*)out;
+  a.err = err;
+  if (cudaFuncSetAttribute(unet_tc::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+    return SGN_ECUDA;
+  unet_tc::k_wimg<<<(unsigned)((t.total + 255) / 256), 256, 0, st>>>(t, weight, wimg);
+  unet_tc::k_conv3_tc<<<(unsigned)((a.npix + unet_tc::kM - 1) / unet_tc::kM), unet_tc::kThreads, sm, st>>>(a);
+  int h = 0;
+  if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                                              cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || h != 0)
+    return SGN_ECUDA;
+  return SGN_OK;
+}
+
+size_t sgn_conv3_workspace_bytes(int Ci, int Co) {
+  if (Ci < 1 || Co < 1) return 0;
+  return (((size_t)9 * Ci * Co * sizeof(__nv_bfloat16) + 15) & ~(size_t)15) + 16;
 }
 
 sgn_status sgn_unet_backward(sgn_unet_t net, const float* target, double* loss_dev) {

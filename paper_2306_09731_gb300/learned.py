@@ -1,9 +1,10 @@
 """Training of the learned GMRES start on snapshots the solver generates.
 
 Section 3 starts GMRES from the last computed sigma. The learned start adds a
-network's correction to that start at RK4 stages 2 and 4 (include/sgn.h,
-sgn_set_learned_guess). This module orchestrates its training; every
-computation runs in the library's kernels: the solver records coarse samples
+network's correction to that start at RK4 stages 2 and 4, or at every stage
+over the polynomial start of guess 3 (include/sgn.h, sgn_set_learned_guess).
+This module orchestrates its training; every computation runs in the
+library's kernels: the solver records coarse samples
 (sgn_record_learned) and the U-Net kernels (include/sgn_unet.h) run the
 forward pass, the backward pass and Adam.
 
@@ -33,7 +34,9 @@ def gaussian_states(N, L, amplitudes, seed=0):
 
 def generate(states, coarse, steps, dt, precision=2, guess=0, tau_power=1, warmup=1):
     """Runs each state for warmup + steps RK4 steps, recording the steps;
-    returns the samples [S][5][coarse][coarse] (CUDA float32)."""
+    returns the samples [S][5][coarse][coarse] (CUDA float32). With guess 3
+    the solver records only once its polynomial start is cubic (after 4
+    steps of the trajectory): give warmup >= 4."""
     import torch
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     parts = []
@@ -42,7 +45,7 @@ def generate(states, coarse, steps, dt, precision=2, guess=0, tau_power=1, warmu
         f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
         if warmup:
             s.rk4_step(*f, dt, warmup)
-        buf = s.record_learned(coarse, 2 * steps, tau_power)
+        buf = s.record_learned(coarse, 4 * steps, tau_power)
         s.rk4_step(*f, dt, steps)
         count = s.stop_recording()
         parts.append(buf[:count].clone())
@@ -58,9 +61,10 @@ def scales(samples):
     return in_scale, out_scale
 
 
-def train(samples, iters=600, batch=8, lr=2e-3, seed=0, log_every=0):
+def train(samples, iters=600, batch=8, lr=2e-3, seed=0, log_every=0, arch=None):
     """Adam on the mean squared error of the scaled target; returns
-    (net, in_scale, out_scale, losses) with one loss per log_every iterations."""
+    (net, in_scale, out_scale, losses) with one loss per log_every iterations.
+    arch = (levels, widths) of the network (None: the library's default)."""
     import torch
     coarse = samples.shape[-1]
     in_scale, out_scale = scales(samples)
@@ -69,7 +73,7 @@ def train(samples, iters=600, batch=8, lr=2e-3, seed=0, log_every=0):
     T = (samples[:, 4:5] / out_scale).contiguous()
     S = samples.shape[0]
     batch = min(batch, S)
-    net = UNet(coarse, max_batch=batch, bf16=True, seed=seed)
+    net = UNet(coarse, max_batch=batch, bf16=True, seed=seed, arch=arch)
     rng = np.random.default_rng(seed)
     losses = []
     for t in range(1, iters + 1):

@@ -50,6 +50,28 @@ def test_unet_create_rejects_bad_sizes(lib, n, batch):
     assert not h.value
 
 
+@pytest.mark.parametrize("n,levels,widths", [(64, 1, [32]), (64, 7, [16] * 7), (64, 3, [16, 24, 32]),
+                                             (64, 3, [16, 32, 512]), (16, 4, [16, 16, 16, 16]), (64, 2, None)])
+def test_unet_create_arch_rejects_bad_architectures(lib, n, levels, widths):
+    from paper_2306_09731_gb300 import unet as UN
+    UN.load_library()
+    h = ctypes.c_void_p()
+    wa = None if widths is None else (ctypes.c_int * len(widths))(*widths)
+    assert lib.sgn_unet_create_arch(n, 1, 1, 0, levels, wa, ctypes.byref(h)) == 1
+    assert not h.value
+
+
+@pytest.mark.parametrize("H,W,C0,C1,Co", [(12, 16, 16, 0, 16), (16, 16, 8, 0, 16), (16, 16, 16, 8, 16),
+                                          (16, 16, 16, 0, 24), (16, 16, 16, 0, 512), (16, 16, 1024, 16, 16)])
+def test_conv3_tc_rejects_bad_shapes(lib, H, W, C0, C1, Co):
+    from paper_2306_09731_gb300 import unet as UN
+    UN.load_library()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the shape checks come first
+    assert lib.sgn_conv3_relu_bf16(1, H, W, dummy, C0, 0, dummy, C1, dummy, dummy, Co, dummy, dummy, 1 << 30,
+                                   None) == 1
+    assert lib.sgn_conv3_workspace_bytes(32, 32) == ((9 * 32 * 32 * 2 + 15) // 16) * 16 + 16
+
+
 def test_default_options(lib):
     o = S.sgn_default_options()
     assert (o.precision, o.restart, o.maxit, o.tol, o.krasny, o.krasny_thr, o.dealias, o.guess) == \

@@ -140,3 +140,43 @@ def test_trained_network_reduces_iterations_over_the_paper_start():
     for x, y in zip(res[True][0][:3], res[False][0][:3]):
         assert rel(x, y) < 1e-5
     net.close()
+
+
+SPEC = (4, (32, 64, 64, 96))
+
+
+def test_poly_start_learned_graph_mode_bitwise_and_tolerance():
+    """The correction over the polynomial start (guess 3, every stage once the
+    start is cubic): the host-driven loop and the graph (gated on the device)
+    take the same decisions, and a random network keeps every solve at tol."""
+    from paper_2306_09731_gb300.unet import UNet
+    st = I.perturbed_soliton(256, 64, 60.0, 15.0, a=0.5, eps=5e-2, seed=8)
+    net = UNet(32, max_batch=1, bf16=True, seed=7, arch=SPEC)
+    a, sa = run(st, 7, 2e-3, net=net, tau_power=2, precision=2, guess=3, graph=1)
+    b, sb = run(st, 7, 2e-3, net=net, tau_power=2, precision=2, guess=3, graph=0)
+    c, sc = run(st, 7, 2e-3, precision=2, guess=3, graph=0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert sa["matvecs"] == sb["matvecs"]
+    # the random correction changes the starts of steps 5-7 (not the fields beyond the tolerance)
+    assert sb["matvecs"] != sc["matvecs"] or not np.array_equal(b[3], c[3])
+    for x, y in zip(b[:3], c[:3]):
+        assert rel(x, y) < 1e-5
+    assert sb["solves"] == 28 and sb["last_relres"] <= 1e-10
+    net.close()
+
+
+def test_recording_with_the_polynomial_start():
+    """Guess 3 records all four stages of each step once the ring holds 4
+    steps: 6 steps from a fresh handle give steps 5 and 6, 8 samples."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.gaussian_hump(256, 25.0, 0.5)
+    s = Solver(256, 256, 25.0, 25.0, precision=2, guess=3)
+    f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
+    buf = s.record_learned(32, 40, 2)
+    s.rk4_step(*f, 1e-3, 6)
+    n = s.stop_recording()
+    assert n == 8
+    b = host(buf[:n])
+    assert np.all(np.isfinite(b)) and np.max(np.abs(b[:, 4])) > 0
+    s.close()
