@@ -545,7 +545,17 @@ def unet_cost(reps=20):
             x = torch.randn(1, 4, coarse, coarse, device="cuda")
             y = torch.empty(1, 1, coarse, coarse, device="cuda")
             rec = {"params": net.num_params()}
-            for kind, fn in (("tensor_cores", lambda: net.infer(x, y)), ("cuda_cores", lambda: net.forward(x))):
+            # the solver's graph mode replays the inference inside its step graph
+            gs = torch.cuda.Stream()
+            gs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(gs):
+                net.infer(x, y)
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=gs):
+                    net.infer(x, y)
+            torch.cuda.current_stream().wait_stream(gs)
+            for kind, fn in (("tensor_cores", lambda: net.infer(x, y)), ("tensor_cores_graph", graph.replay),
+                             ("cuda_cores", lambda: net.forward(x))):
                 for _ in range(3):
                     fn()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -299,12 +299,13 @@ struct Layer {
   // tensor-core inference (3x3 layers after the first)
   int KC = 0, nkb = 0, smem = 0;
   long long ioff = -1;
+  int level = 0;     // resolution level (grid side n / 2^level)
+  bool row = false;  // rows of >= 128 pixels: the halo-staged row kernel
 };
 
-// Lower bound of the tensor-core kernel's dynamic shared memory: 200 KB, one
-// CTA per SM, so that every operand address the MMA unit could form from a
-// descriptor of this layout stays inside the CTA's own allocation.
-constexpr int kTcSmemMin = 200 * 1024;
+// Lower bound of the tensor-core kernel's dynamic shared memory (beyond the
+// two stages and the TMEM occupancy bound).
+constexpr int kTcSmemMin = 0;
 
 }  // namespace
 
@@ -576,7 +577,10 @@ void tc_conv(sgn_unet_ctx* net, int li, const __nv_bfloat16* src0, int C0, int u
   a.head_out = head_out;
   a.err = net->dev_err;
   const unsigned grid = (unsigned)((a.npix + unet_tc::kM - 1) / unet_tc::kM);
-  unet_tc::k_conv3_tc<<<grid, unet_tc::kThreads, L.smem, net->stream>>>(a);
+  if (L.row)
+    unet_tc::k_conv3_tc_row<<<grid, unet_tc::kThreads, L.smem, net->stream>>>(a);
+  else
+    unet_tc::k_conv3_tc<<<grid, unet_tc::kThreads, L.smem, net->stream>>>(a);
   UCK(cudaGetLastError());
 }
 
@@ -630,8 +634,20 @@ int pick_kc(int Ci, int Co) {
   for (int nkb = 1; nkb <= Ci / 16; ++nkb) {
     if (Ci % nkb) continue;
     const int kc = Ci / nkb;
-    if (kc % 16) continue;
+    if (kc % 16 || kc > unet_tc::kMaxKC) continue;
     if ((int)unet_tc::stage_bytes(Co, kc) <= unet_tc::kStageMax) return kc;
+  }
+  return 16;
+}
+
+// channels per block of the row kernel: the fewest blocks whose halo pair
+// and weight stages fit 110 KB (two CTAs per SM)
+int pick_kc_row(int Ci, int Co) {
+  for (int nkb = 1; nkb <= Ci / 16; ++nkb) {
+    if (Ci % nkb) continue;
+    const int kc = Ci / nkb;
+    if (kc % 16) continue;
+    if ((int)unet_tc::row_smem_bytes(Co, kc) <= 110 * 1024) return kc;
   }
   return 16;
 }
@@ -656,20 +672,21 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
   for (int l = 0; l < levels; ++l) net->w[l] = widths[l];
   const int D = levels;
   const int* w = net->w;
-  std::vector<int> ci, co, kk;
-  auto add = [&](int a, int b, int k) {
+  std::vector<int> ci, co, kk, lv;
+  auto add = [&](int a, int b, int k, int level) {
     ci.push_back(a);
     co.push_back(b);
     kk.push_back(k);
+    lv.push_back(level);
   };
   for (int l = 0; l < D - 1; ++l) {
-    add(l == 0 ? 4 : w[l - 1], w[l], 3);
-    add(w[l], w[l], 3);
+    add(l == 0 ? 4 : w[l - 1], w[l], 3, l);
+    add(w[l], w[l], 3, l);
   }
-  add(w[D - 2], w[D - 1], 3);
-  add(w[D - 1], w[D - 1], 3);
-  for (int l = D - 2; l >= 0; --l) add(w[l + 1] + w[l], w[l], 3);
-  add(w[0], 1, 1);
+  add(w[D - 2], w[D - 1], 3, D - 1);
+  add(w[D - 1], w[D - 1], 3, D - 1);
+  for (int l = D - 2; l >= 0; --l) add(w[l + 1] + w[l], w[l], 3, l);
+  add(w[0], 1, 1, 0);
   long long off = 0, ioff = 0;
   int smem_max = 0;
   net->wtab.nl = 0;
@@ -682,8 +699,10 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
     off += (long long)l.Co * l.Ci * l.k * l.k;
     l.boff = off;
     off += l.Co;
+    l.level = lv[i];
+    l.row = (n >> l.level) >= 128;
     if (l.k == 3 && i > 0) {
-      l.KC = pick_kc(l.Ci, l.Co);
+      l.KC = l.row ? pick_kc_row(l.Ci, l.Co) : pick_kc(l.Ci, l.Co);
       l.nkb = l.Ci / l.KC;
       l.ioff = ioff;
       unet_tc::WImgLayer& t = net->wtab.l[net->wtab.nl++];
@@ -694,7 +713,8 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
       t.KC = l.KC;
       t.nkb = l.nkb;
       ioff += 9ll * l.Ci * l.Co;
-      int sm = 2 * (int)unet_tc::stage_bytes(l.Co, l.KC);
+      int sm = l.row ? (int)unet_tc::row_smem_bytes(l.Co, l.KC)
+                     : unet_tc::kStages * (int)unet_tc::stage_bytes(l.Co, l.KC);
       // at most 512 / cols CTAs per SM, so that TMEM is never oversubscribed
       int cols = 32;
       while (cols < l.Co) cols <<= 1;
@@ -743,6 +763,7 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
     net->dev_err = (int*)ualloc(net, sizeof(int));
     UCK(cudaMemset(net->dev_err, 0, sizeof(int)));
     UCK(cudaFuncSetAttribute(unet_tc::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+    UCK(cudaFuncSetAttribute(unet_tc::k_conv3_tc_row, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
     init_params(net, seed);
     UCK(cudaDeviceSynchronize());
   } catch (Fail& f) {
@@ -880,7 +901,8 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
   int lH = 0, lW = 0;
   while ((1 << lH) < H) ++lH;
   while ((1 << lW) < W) ++lW;
-  const int KC = pick_kc(Ci, Co);
+  const bool row = W >= 128;
+  const int KC = row ? pick_kc_row(Ci, Co) : pick_kc(Ci, Co);
   __nv_bfloat16* wimg = (__nv_bfloat16*)workspace;
   int* err = (int*)((char*)workspace + ((img + 15) & ~(size_t)15));
   unet_tc::WImgTable t{};
@@ -894,7 +916,7 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
   t.total = 9ll * Ci * Co;
   int cols = 32;
   while (cols < Co) cols <<= 1;
-  int sm = 2 * (int)unet_tc::stage_bytes(Co, KC);
+  int sm = row ? (int)unet_tc::row_smem_bytes(Co, KC) : unet_tc::kStages * (int)unet_tc::stage_bytes(Co, KC);
   const int floor_bytes = 233472 / (512 / cols + 1) + 1;
   if (sm < floor_bytes) sm = floor_bytes;
   if (sm < kTcSmemMin) sm = kTcSmemMin;
@@ -915,11 +937,16 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
   a.tmem_cols = (uint32_t)cols;
   a.out = (__nv_bfloat16*)out;
   a.err = err;
-  if (cudaFuncSetAttribute(unet_tc::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+  if (cudaFuncSetAttribute(row ? (const void*)unet_tc::k_conv3_tc_row : (const void*)unet_tc::k_conv3_tc,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
       cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
     return SGN_ECUDA;
   unet_tc::k_wimg<<<(unsigned)((t.total + 255) / 256), 256, 0, st>>>(t, weight, wimg);
-  unet_tc::k_conv3_tc<<<(unsigned)((a.npix + unet_tc::kM - 1) / unet_tc::kM), unet_tc::kThreads, sm, st>>>(a);
+  const unsigned grid = (unsigned)((a.npix + unet_tc::kM - 1) / unet_tc::kM);
+  if (row)
+    unet_tc::k_conv3_tc_row<<<grid, unet_tc::kThreads, sm, st>>>(a);
+  else
+    unet_tc::k_conv3_tc<<<grid, unet_tc::kThreads, sm, st>>>(a);
   int h = 0;
   if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) !=
                                               cudaSuccess ||

@@ -8,15 +8,16 @@
 // t. One CTA of 128 threads computes one tile:
 //   * the accumulator D lives in tensor memory (TMEM lane m = pixel m, one
 //     32-bit column per output channel), allocated by warp 0;
-//   * the K loop runs over (tap, channel block) steps through two shared-memory
-//     stages: the weights of a step arrive by one bulk copy (cp.async.bulk,
-//     the copy engine) from a pre-arranged BF16 image, the 128 gathered input
-//     rows are written by the threads themselves (each thread one pixel;
+//   * the K loop runs over (tap, channel block) steps through three
+//     shared-memory stages: the weights of a step arrive by one bulk copy
+//     (cp.async.bulk, the copy engine) from a pre-arranged BF16 image, issued
+//     one step ahead; the 128 gathered input rows are written by the threads
+//     themselves (each thread one pixel, its loads issued one step ahead;
 //     wrap-around, nearest upsampling and the channel concatenation of the
 //     decoder are folded into this gather);
 //   * one thread issues the step's tcgen05.mma instructions (M = 128,
 //     N = Co, K = 16 each) and commits them to the stage's mbarrier, which
-//     frees the stage for the step after next;
+//     frees the stage for the step three later;
 //   * the epilogue reads D back with tcgen05.ld (each warp its 32 lanes),
 //     adds the bias, applies the ReLU, rounds to BF16 and stores the NHWC row;
 //     for the last layer it also applies the 1x1 output convolution.
@@ -36,6 +37,8 @@ namespace unet_tc {
 constexpr int kM = 128;           // output pixels per CTA = TMEM lanes
 constexpr int kThreads = 128;     // one thread per pixel row
 constexpr int kStageMax = 56 * 1024;
+constexpr int kMaxKC = 128;       // channels per K step at most (the gather's registers)
+constexpr int kStages = 3;        // shared-memory stages of the K loop
 constexpr int SGN_TC_WAIT = 1;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -147,7 +150,7 @@ __host__ __device__ constexpr uint32_t stage_bytes(int Co, int KC) { return a_by
 
 __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_w[2], bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_w[kStages], bar_mma[kStages];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KC = p.KC, Co = p.Co;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
 
   if (warp == 0) tmem_alloc(&tmem_slot, p.tmem_cols);
   if (tid == 32) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStages; ++i) {
       bar_init(&bar_w[i], 1);
       bar_init(&bar_mma[i], 1);
     }
@@ -175,26 +178,12 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   const uint32_t idesc = instr_desc_bf16(kM, Co);
   const int nsteps = 9 * p.nkb;
 
-  bool ok = true;
-  int issued = -1;     // last step whose MMAs were committed (thread 0)
-  int copied = -1;     // last step whose weight copy was issued (thread 0)
-  int copy_done = -1;  // last step whose weight copy was seen complete (thread 0)
-  int s = 0;
-  for (; s < nsteps; ++s) {
-    const int buf = s & 1;
-    if (s >= 2 && !bar_wait(&bar_mma[buf], (unsigned)(((s - 2) >> 1) & 1))) ok = false;
-    if (__syncthreads_or(ok ? 0 : 1)) {
-      ok = false;
-      break;
-    }
-    unsigned char* A = sm + buf * sbytes;
-    unsigned char* Bm = A + abytes;
-    if (tid == 0) {
-      bulk_g2s(Bm, p.wimg + (size_t)s * Co * KC, b_bytes(Co, KC), &bar_w[buf]);
-      copied = s;
-    }
-    // gather: A row m = the KC channels [kb KC, (kb + 1) KC) of the tap's pixel
-    const int tap = s / p.nkb, kb = s - tap * p.nkb;
+  // this thread's gathered row of one K step: KC / 8 16-byte chunks, loaded
+  // one step ahead so that the loads of step s + 1 are in flight while the
+  // MMAs of step s are issued and the next buffer is waited for
+  uint4 row[kMaxKC / 8];
+  auto gather = [&](int step) {
+    const int tap = step / p.nkb, kb = step - tap * p.nkb;
     const int yy = (y + tap / 3 - 1) & (H - 1), xx = (x + tap % 3 - 1) & (W - 1);
     const uint4* r0 = reinterpret_cast<const uint4*>(
         p.up0 ? p.src0 + ((((size_t)b << (p.lH + p.lW - 2)) + ((size_t)(yy >> 1) << (p.lW - 1)) + (xx >> 1)) * p.C0)
@@ -202,17 +191,53 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
     const uint4* r1 = p.src1 ? reinterpret_cast<const uint4*>(
                                    p.src1 + ((((size_t)b << (p.lH + p.lW)) + ((size_t)yy << p.lW) + xx) * p.C1))
                              : r0;
-    unsigned char* arow = A + (tid >> 3) * 128 + (tid & 7) * 16;
-    for (int c = 0; c < KC / 8; ++c) {
+#pragma unroll
+    for (int c = 0; c < kMaxKC / 8; ++c) {
       const int ch = kb * KC + 8 * c;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (valid) v = ch < p.C0 ? __ldg(r0 + (ch >> 3)) : __ldg(r1 + ((ch - p.C0) >> 3));
-      *reinterpret_cast<uint4*>(arow + (size_t)c * (kM / 8) * 128) = v;
+      if (valid && c < KC / 8) v = ch < p.C0 ? __ldg(r0 + (ch >> 3)) : __ldg(r1 + ((ch - p.C0) >> 3));
+      row[c] = v;
     }
+  };
+
+  bool ok = true;
+  int issued = -1;     // last step whose MMAs were committed (thread 0)
+  int copied = -1;     // last step whose weight copy was issued (thread 0)
+  int copy_done = -1;  // last step whose weight copy was seen complete (thread 0)
+  // step s uses stage s % kStages; its k-th use is phase k of the stage's barriers
+  auto stage_of = [](int st) { return st % kStages; };
+  auto parity_of = [](int st) { return (unsigned)((st / kStages) & 1); };
+  if (tid == 0) {
+    bulk_g2s(sm + abytes, p.wimg, b_bytes(Co, KC), &bar_w[0]);
+    copied = 0;
+  }
+  gather(0);
+  for (int s = 0; s < nsteps; ++s) {
+    const int buf = stage_of(s);
+    // the MMAs of step s - 2 (and so of every earlier step) are done: stage
+    // (s + 1) % 3 - last used by step s - 2 - takes step s + 1's weights,
+    // stage s % 3 - last used by step s - 3 - step s's rows
+    if (s >= 2 && !bar_wait(&bar_mma[stage_of(s - 2)], parity_of(s - 2))) ok = false;
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      ok = false;
+      break;
+    }
+    unsigned char* A = sm + buf * sbytes;
+    if (tid == 0 && s + 1 < nsteps) {
+      bulk_g2s(sm + stage_of(s + 1) * sbytes + abytes, p.wimg + (size_t)(s + 1) * Co * KC, b_bytes(Co, KC),
+               &bar_w[stage_of(s + 1)]);
+      copied = s + 1;
+    }
+    // A row m = the KC channels [kb KC, (kb + 1) KC) of the tap's pixel
+    unsigned char* arow = A + (tid >> 3) * 128 + (tid & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < kMaxKC / 8; ++c)
+      if (c < KC / 8) *reinterpret_cast<uint4*>(arow + (size_t)c * (kM / 8) * 128) = row[c];
+    if (s + 1 < nsteps) gather(s + 1);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      if (!bar_wait(&bar_w[buf], (unsigned)((s >> 1) & 1))) {
+      if (!bar_wait(&bar_w[buf], parity_of(s))) {
         ok = false;
       } else {
         copy_done = s;
@@ -232,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   }
   if (ok) {
     const int last = nsteps - 1;
-    if (!bar_wait(&bar_mma[last & 1], (unsigned)((last >> 1) & 1))) ok = false;
+    if (!bar_wait(&bar_mma[stage_of(last)], parity_of(last))) ok = false;
   }
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
   if (ok) {
@@ -259,8 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   } else if (tid == 0) {
     atomicOr(p.err, SGN_TC_WAIT);
     // let what this CTA still has in flight finish before its memory goes
-    if (issued >= 0) bar_wait(&bar_mma[issued & 1], (unsigned)((issued >> 1) & 1));
-    if (copied > copy_done) bar_wait(&bar_w[copied & 1], (unsigned)((copied >> 1) & 1));
+    if (issued >= 0) bar_wait(&bar_mma[stage_of(issued)], parity_of(issued));
+    for (int c = copy_done + 1; c <= copied; ++c) bar_wait(&bar_w[stage_of(c)], parity_of(c));
   }
   tc_fence_before();
   __syncthreads();
@@ -364,6 +389,193 @@ __global__ void k_wimg(WImgTable t, const float* __restrict__ params, __nv_bfloa
   const int tap = step / L.nkb, kb = step % L.nkb;
   const int ci = kb * L.KC + k;
   img[i] = __float2bfloat16_rn(params[L.woff + ((long long)co * L.Ci + ci) * 9 + tap]);
+}
+
+}  // namespace unet_tc
+
+namespace unet_tc {
+
+// Grids whose rows hold at least 128 pixels: a tile is 128 consecutive pixels
+// of one row, and the input it needs - rows y-1..y+1, columns x0-1..x0+128
+// (wrapped) - is staged once per channel block into shared memory as a halo
+// [KC/8 chunks][3 x 130 positions][8 channels]. The A operand of tap (dy, dx)
+// is then that buffer itself: its 128 rows are the 128 consecutive positions
+// from (dy + 1) 130 + dx + 1 on, 16 bytes apart, i.e. a descriptor with
+// SBO = 128 and LBO = the chunk stride, started at that offset. No per-tap
+// gather and no per-tap barrier: one thread issues the nine taps' MMAs, the
+// weights of each tap arriving by bulk copy into three stages; the halo of
+// the next channel block is loaded (cp.async, 16 bytes per thread and piece)
+// while the current one's MMAs run.
+constexpr int kHaloPos = 3 * (kM + 2);
+__host__ __device__ constexpr uint32_t halo_bytes(int KC) { return (uint32_t)kHaloPos * KC * 2u; }
+__host__ __device__ constexpr uint32_t row_smem_bytes(int Co, int KC) {
+  return 2u * halo_bytes(KC) + (uint32_t)kStages * b_bytes(Co, KC);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar_w[kStages], bar_mma[kStages];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int KC = p.KC, Co = p.Co, nkb = p.nkb;
+  const uint32_t hbytes = halo_bytes(KC), bbytes = b_bytes(Co, KC);
+  unsigned char* halo = sm;                     // two buffers of hbytes
+  unsigned char* bst = sm + 2 * hbytes;         // kStages weight stages of bbytes
+  const uint32_t sm0 = smem_addr(sm);
+
+  if (warp == 0) tmem_alloc(&tmem_slot, p.tmem_cols);
+  if (tid == 32) {
+    for (int i = 0; i < kStages; ++i) {
+      bar_init(&bar_w[i], 1);
+      bar_init(&bar_mma[i], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  const int W = 1 << p.lW, H = 1 << p.lH;
+  const int tiles_row = W >> 7;
+  const int tile = blockIdx.x;
+  const int x0 = (tile % tiles_row) << 7;
+  const int y = (tile / tiles_row) & (H - 1);
+  const int b = tile / (tiles_row << p.lH);
+  const int pix = tile * kM + tid;
+  const uint32_t idesc = instr_desc_bf16(kM, Co);
+  const int nsteps = 9 * nkb;
+
+  // channel block kb's halo into buffer hb: piece i = (position, chunk), chunk fastest
+  auto halo_issue = [&](int kb, int hb) {
+    const int chunks = KC >> 3, pieces = kHaloPos * chunks;
+    unsigned char* dst = halo + (size_t)hb * hbytes;
+    for (int i = tid; i < pieces; i += kThreads) {
+      const int pos = i / chunks, c = i - pos * chunks;
+      const int r = pos / (kM + 2), col = pos - r * (kM + 2);
+      const int gy = (y + r - 1) & (H - 1), gx = (x0 + col - 1) & (W - 1);
+      const int ch = kb * KC + 8 * c;
+      const __nv_bfloat16* src;
+      if (ch < p.C0) {
+        src = p.up0 ? p.src0 + ((((size_t)b << (p.lH + p.lW - 2)) + ((size_t)(gy >> 1) << (p.lW - 1)) + (gx >> 1)) *
+                                    p.C0 + ch)
+                    : p.src0 + ((((size_t)b << (p.lH + p.lW)) + ((size_t)gy << p.lW) + gx) * p.C0 + ch);
+      } else {
+        src = p.src1 + ((((size_t)b << (p.lH + p.lW)) + ((size_t)gy << p.lW) + gx) * p.C1 + (ch - p.C0));
+      }
+      cp_async16(dst + ((size_t)c * kHaloPos + pos) * 16, src);
+    }
+  };
+  auto stage_of = [](int st) { return st % kStages; };
+  auto parity_of = [](int st) { return (unsigned)((st / kStages) & 1); };
+  // step s = kb * 9 + tap; its weights are the image block (tap nkb + kb)
+  auto wblock = [&](int st) { return p.wimg + (size_t)((st % 9) * nkb + st / 9) * Co * KC; };
+
+  // A parity wait tells a phase only from the one before it, so every wait
+  // on an mbarrier here is made by thread 0, which sees every commit and every
+  // copy in order; the other threads learn the outcome through the block votes.
+  bool ok = true;
+  int issued = -1, mma_seen = -1, copied = -1, copy_done = -1;
+  auto wait_mma = [&](int st) {  // thread 0: the MMAs of step st (and all before) are done
+    if (st <= mma_seen) return true;
+    if (!bar_wait(&bar_mma[stage_of(st)], parity_of(st))) return false;
+    mma_seen = st;
+    return true;
+  };
+  if (tid == 0) {
+    bulk_g2s(bst, wblock(0), bbytes, &bar_w[0]);
+    copied = 0;
+  }
+  halo_issue(0, 0);
+  cp_async_commit();
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int hb = kb & 1;
+    const bool pre = kb + 1 < nkb;
+    // buffer hb ^ 1 was block kb - 1's: its last MMAs must be done
+    if (tid == 0 && pre && kb >= 1 && !wait_mma(kb * 9 - 1)) ok = false;
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      ok = false;
+      break;
+    }
+    if (pre) halo_issue(kb + 1, hb ^ 1);
+    cp_async_commit();
+    cp_async_wait1();
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t hbase = sm0 + (uint32_t)hb * hbytes;
+      for (int tap = 0; tap < 9 && ok; ++tap) {
+        const int s = kb * 9 + tap;
+        if (s + 1 < nsteps) {
+          // weight stage of step s + 1 was step s - 2's
+          if (s >= 2 && !wait_mma(s - 2)) {
+            ok = false;
+            break;
+          }
+          bulk_g2s(bst + (size_t)stage_of(s + 1) * bbytes, wblock(s + 1), bbytes, &bar_w[stage_of(s + 1)]);
+          copied = s + 1;
+        }
+        if (!bar_wait(&bar_w[stage_of(s)], parity_of(s))) {
+          ok = false;
+          break;
+        }
+        copy_done = s;
+        tc_fence_after();
+        const uint32_t a0 = hbase + (uint32_t)(((tap / 3) * (kM + 2) + tap % 3) * 16);
+        const uint32_t b0 = sm0 + 2 * hbytes + (uint32_t)stage_of(s) * bbytes;
+#pragma unroll 1
+        for (int j = 0; j < KC / 16; ++j) {
+          const uint64_t ad = smem_desc(a0 + (uint32_t)j * 2u * kHaloPos * 16u, kHaloPos * 16u, 128u);
+          const uint64_t bd = smem_desc(b0 + (uint32_t)j * 2u * (uint32_t)(Co / 8) * 128u, (uint32_t)(Co / 8) * 128u,
+                                        128u);
+          mma_bf16(tmem, ad, bd, idesc, (s > 0 || j > 0) ? 1 : 0);
+        }
+        mma_commit(&bar_mma[stage_of(s)]);
+        issued = s;
+      }
+    }
+  }
+  if (ok && tid == 0 && !wait_mma(nsteps - 1)) ok = false;
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (ok) {
+    tc_fence_after();
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    float head = 0.f;
+    for (int q = 0; q < Co / 16; ++q) {
+      float v[16];
+      tmem_ld16(lane_addr + (uint32_t)(q * 16), v);
+      __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float a = fmaxf(v[i] + __ldg(p.bias + q * 16 + i), 0.f);
+        o[i] = __float2bfloat16_rn(a);
+        if (p.head_w) head = fmaf(__ldg(p.head_w + q * 16 + i), __bfloat162float(o[i]), head);
+      }
+      if (p.out) {
+        uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)pix * Co + q * 16);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+      }
+    }
+    if (p.head_w) p.head_out[pix] = head + __ldg(p.head_b);
+  } else if (tid == 0) {
+    atomicOr(p.err, SGN_TC_WAIT);
+    // drain in order what this CTA still has in flight
+    for (int st = mma_seen + 1; st <= issued; ++st)
+      if (!wait_mma(st)) break;
+    for (int c = copy_done + 1; c <= copied; ++c) bar_wait(&bar_w[stage_of(c)], parity_of(c));
+  }
+  cp_async_wait0();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, p.tmem_cols);
 }
 
 }  // namespace unet_tc

@@ -105,9 +105,11 @@ def to_nchw(a):
 
 # (B, H, W, C0, up0, C1, Co): a plain layer; the decoder's upsample + concatenation; a split K loop (336
 # channels in three blocks of 112) on a ragged grid of 192 pixels; a non-square grid with the widest N;
-# 1024 input channels on a 16-pixel grid
+# 1024 input channels on a 16-pixel grid. Rows of >= 128 pixels take the halo-staged row kernel: a plain
+# layer, upsample + concatenation in two channel blocks, and five channel blocks over two images
 LAYER_CASES = [(2, 32, 32, 32, 0, 0, 32), (1, 16, 16, 64, 1, 32, 64), (3, 8, 8, 256, 1, 80, 80),
-               (1, 8, 64, 16, 0, 0, 256), (1, 4, 4, 512, 0, 512, 16)]
+               (1, 8, 64, 16, 0, 0, 256), (1, 4, 4, 512, 0, 512, 16),
+               (1, 4, 128, 64, 0, 0, 64), (1, 4, 256, 32, 1, 32, 48), (2, 8, 128, 96, 1, 64, 64)]
 
 
 @pytest.mark.parametrize("B,H,W,C0,up0,C1,Co", LAYER_CASES)
