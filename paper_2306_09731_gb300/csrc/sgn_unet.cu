@@ -640,14 +640,14 @@ int pick_kc(int Ci, int Co) {
   return 16;
 }
 
-// channels per block of the row kernel: the fewest blocks whose halo pair
-// and weight stages fit 110 KB (two CTAs per SM)
+// channels per block of the row kernel: the fewest blocks whose halo and
+// weight buffers fit 110 KB (two CTAs per SM)
 int pick_kc_row(int Ci, int Co) {
   for (int nkb = 1; nkb <= Ci / 16; ++nkb) {
     if (Ci % nkb) continue;
     const int kc = Ci / nkb;
     if (kc % 16) continue;
-    if ((int)unet_tc::row_smem_bytes(Co, kc) <= 110 * 1024) return kc;
+    if ((int)unet_tc::row_smem_bytes(Co, kc, nkb) <= 110 * 1024) return kc;
   }
   return 16;
 }
@@ -712,8 +712,9 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
       t.Co = l.Co;
       t.KC = l.KC;
       t.nkb = l.nkb;
+      t.kb_major = l.row ? 1 : 0;
       ioff += 9ll * l.Ci * l.Co;
-      int sm = l.row ? (int)unet_tc::row_smem_bytes(l.Co, l.KC)
+      int sm = l.row ? (int)unet_tc::row_smem_bytes(l.Co, l.KC, l.nkb)
                      : unet_tc::kStages * (int)unet_tc::stage_bytes(l.Co, l.KC);
       // at most 512 / cols CTAs per SM, so that TMEM is never oversubscribed
       int cols = 32;
@@ -913,10 +914,12 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
   t.l[0].Co = Co;
   t.l[0].KC = KC;
   t.l[0].nkb = Ci / KC;
+  t.l[0].kb_major = row ? 1 : 0;
   t.total = 9ll * Ci * Co;
   int cols = 32;
   while (cols < Co) cols <<= 1;
-  int sm = row ? (int)unet_tc::row_smem_bytes(Co, KC) : unet_tc::kStages * (int)unet_tc::stage_bytes(Co, KC);
+  int sm = row ? (int)unet_tc::row_smem_bytes(Co, KC, Ci / KC)
+               : unet_tc::kStages * (int)unet_tc::stage_bytes(Co, KC);
   const int floor_bytes = 233472 / (512 / cols + 1) + 1;
   if (sm < floor_bytes) sm = floor_bytes;
   if (sm < kTcSmemMin) sm = kTcSmemMin;

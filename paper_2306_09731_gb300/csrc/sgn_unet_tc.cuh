@@ -361,12 +361,14 @@ __global__ void k_pool_nhwc(const __nv_bfloat16* __restrict__ in, int lH, int lW
 }
 
 // BF16 core-matrix images of the 3x3 layers' FP32 weights [Co][Ci][3][3]:
-// for step s = tap nkb + kb, element (co, k) (input channel kb KC + k) at
-// s Co KC + ((k / 8) (Co / 8) + co / 8) 64 + (co % 8) 8 + k % 8.
+// for step s = tap nkb + kb (kb 9 + tap with kb_major), element (co, k)
+// (input channel kb KC + k) at s Co KC + ((k / 8) (Co / 8) + co / 8) 64 +
+// (co % 8) 8 + k % 8.
 constexpr int kMaxImgLayers = 16;
 struct WImgLayer {
   long long woff, ioff;  // FP32 weight offset in the parameters, element offset in the image
   int Ci, Co, KC, nkb;
+  int kb_major;          // step order kb 9 + tap (the row kernel) instead of tap nkb + kb
 };
 struct WImgTable {
   int nl;
@@ -386,7 +388,7 @@ __global__ void k_wimg(WImgTable t, const float* __restrict__ params, __nv_bfloa
   const int cg = L.Co >> 3;
   const int c = e / (cg * 64), rem = e % (cg * 64);
   const int co = (rem / 64) * 8 + (rem % 64) / 8, k = c * 8 + (rem & 7);
-  const int tap = step / L.nkb, kb = step % L.nkb;
+  const int tap = L.kb_major ? step % 9 : step / L.nkb, kb = L.kb_major ? step / 9 : step % L.nkb;
   const int ci = kb * L.KC + k;
   img[i] = __float2bfloat16_rn(params[L.woff + ((long long)co * L.Ci + ci) * 9 + tap]);
 }
@@ -401,15 +403,18 @@ namespace unet_tc {
 // [KC/8 chunks][3 x 130 positions][8 channels]. The A operand of tap (dy, dx)
 // is then that buffer itself: its 128 rows are the 128 consecutive positions
 // from (dy + 1) 130 + dx + 1 on, 16 bytes apart, i.e. a descriptor with
-// SBO = 128 and LBO = the chunk stride, started at that offset. No per-tap
-// gather and no per-tap barrier: one thread issues the nine taps' MMAs, the
-// weights of each tap arriving by bulk copy into three stages; the halo of
-// the next channel block is loaded (cp.async, 16 bytes per thread and piece)
-// while the current one's MMAs run.
+// SBO = 128 and LBO = the chunk stride, started at that offset. The nine
+// taps' weights of a channel block arrive by one bulk copy (the image is in
+// channel-block-major order for these layers); halo and weights are
+// double-buffered across channel blocks, the next block's loaded while the
+// current block's MMAs run, and one thread issues a block's 9 KC/16 MMAs back
+// to back with one commit.
 constexpr int kHaloPos = 3 * (kM + 2);
 __host__ __device__ constexpr uint32_t halo_bytes(int KC) { return (uint32_t)kHaloPos * KC * 2u; }
-__host__ __device__ constexpr uint32_t row_smem_bytes(int Co, int KC) {
-  return 2u * halo_bytes(KC) + (uint32_t)kStages * b_bytes(Co, KC);
+// one buffer of halo + weights per channel block in flight (two when there
+// are several blocks)
+__host__ __device__ constexpr uint32_t row_smem_bytes(int Co, int KC, int nkb) {
+  return (nkb > 1 ? 2u : 1u) * (halo_bytes(KC) + 9u * b_bytes(Co, KC));
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -421,18 +426,16 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 
 __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_w[kStages], bar_mma[kStages];
+  __shared__ __align__(8) uint64_t bar_w[2], bar_mma[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KC = p.KC, Co = p.Co, nkb = p.nkb;
-  const uint32_t hbytes = halo_bytes(KC), bbytes = b_bytes(Co, KC);
-  unsigned char* halo = sm;                     // two buffers of hbytes
-  unsigned char* bst = sm + 2 * hbytes;         // kStages weight stages of bbytes
+  const uint32_t hbytes = halo_bytes(KC), wbytes = 9u * b_bytes(Co, KC), bufbytes = hbytes + wbytes;
   const uint32_t sm0 = smem_addr(sm);
 
   if (warp == 0) tmem_alloc(&tmem_slot, p.tmem_cols);
   if (tid == 32) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < 2; ++i) {
       bar_init(&bar_w[i], 1);
       bar_init(&bar_mma[i], 1);
     }
@@ -451,12 +454,13 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   const int b = tile / (tiles_row << p.lH);
   const int pix = tile * kM + tid;
   const uint32_t idesc = instr_desc_bf16(kM, Co);
-  const int nsteps = 9 * nkb;
 
-  // channel block kb's halo into buffer hb: piece i = (position, chunk), chunk fastest
-  auto halo_issue = [&](int kb, int hb) {
+  // channel block kb's halo (cp.async, piece i = (position, chunk), chunk
+  // fastest) and its nine taps' weights (one bulk copy, thread 0) into buffer bf
+  auto load_block = [&](int kb, int bf) {
+    unsigned char* dst = sm + (size_t)bf * bufbytes;
+    if (tid == 0) bulk_g2s(dst + hbytes, p.wimg + (size_t)kb * 9 * Co * KC, wbytes, &bar_w[bf]);
     const int chunks = KC >> 3, pieces = kHaloPos * chunks;
-    unsigned char* dst = halo + (size_t)hb * hbytes;
     for (int i = tid; i < pieces; i += kThreads) {
       const int pos = i / chunks, c = i - pos * chunks;
       const int r = pos / (kM + 2), col = pos - r * (kM + 2);
@@ -473,76 +477,69 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
       cp_async16(dst + ((size_t)c * kHaloPos + pos) * 16, src);
     }
   };
-  auto stage_of = [](int st) { return st % kStages; };
-  auto parity_of = [](int st) { return (unsigned)((st / kStages) & 1); };
-  // step s = kb * 9 + tap; its weights are the image block (tap nkb + kb)
-  auto wblock = [&](int st) { return p.wimg + (size_t)((st % 9) * nkb + st / 9) * Co * KC; };
+  // block kb uses buffer kb & 1; its k-th use is phase k of that buffer's barriers
+  auto parity_of = [](int kb) { return (unsigned)((kb >> 1) & 1); };
 
   // A parity wait tells a phase only from the one before it, so every wait
   // on an mbarrier here is made by thread 0, which sees every commit and every
   // copy in order; the other threads learn the outcome through the block votes.
   bool ok = true;
-  int issued = -1, mma_seen = -1, copied = -1, copy_done = -1;
-  auto wait_mma = [&](int st) {  // thread 0: the MMAs of step st (and all before) are done
-    if (st <= mma_seen) return true;
-    if (!bar_wait(&bar_mma[stage_of(st)], parity_of(st))) return false;
-    mma_seen = st;
-    return true;
-  };
-  if (tid == 0) {
-    bulk_g2s(bst, wblock(0), bbytes, &bar_w[0]);
-    copied = 0;
-  }
-  halo_issue(0, 0);
+  int issued = -1, mma_seen = -1, copied = 0, copy_done = -1;
+  load_block(0, 0);
   cp_async_commit();
   for (int kb = 0; kb < nkb; ++kb) {
-    const int hb = kb & 1;
+    const int bf = kb & 1;
     const bool pre = kb + 1 < nkb;
-    // buffer hb ^ 1 was block kb - 1's: its last MMAs must be done
-    if (tid == 0 && pre && kb >= 1 && !wait_mma(kb * 9 - 1)) ok = false;
+    // buffer bf ^ 1 was block kb - 1's: its MMAs must be done
+    if (tid == 0 && pre && kb >= 1) {
+      if (bar_wait(&bar_mma[(kb - 1) & 1], parity_of(kb - 1)))
+        mma_seen = kb - 1;
+      else
+        ok = false;
+    }
     if (__syncthreads_or(ok ? 0 : 1)) {
       ok = false;
       break;
     }
-    if (pre) halo_issue(kb + 1, hb ^ 1);
+    if (pre) {
+      load_block(kb + 1, bf ^ 1);
+      if (tid == 0) copied = kb + 1;
+    }
     cp_async_commit();
     cp_async_wait1();
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      const uint32_t hbase = sm0 + (uint32_t)hb * hbytes;
-      for (int tap = 0; tap < 9 && ok; ++tap) {
-        const int s = kb * 9 + tap;
-        if (s + 1 < nsteps) {
-          // weight stage of step s + 1 was step s - 2's
-          if (s >= 2 && !wait_mma(s - 2)) {
-            ok = false;
-            break;
-          }
-          bulk_g2s(bst + (size_t)stage_of(s + 1) * bbytes, wblock(s + 1), bbytes, &bar_w[stage_of(s + 1)]);
-          copied = s + 1;
-        }
-        if (!bar_wait(&bar_w[stage_of(s)], parity_of(s))) {
-          ok = false;
-          break;
-        }
-        copy_done = s;
+      if (!bar_wait(&bar_w[bf], parity_of(kb))) {
+        ok = false;
+      } else {
+        copy_done = kb;
         tc_fence_after();
-        const uint32_t a0 = hbase + (uint32_t)(((tap / 3) * (kM + 2) + tap % 3) * 16);
-        const uint32_t b0 = sm0 + 2 * hbytes + (uint32_t)stage_of(s) * bbytes;
+        const uint32_t hbase = sm0 + (uint32_t)bf * bufbytes, wbase = hbase + hbytes;
 #pragma unroll 1
-        for (int j = 0; j < KC / 16; ++j) {
-          const uint64_t ad = smem_desc(a0 + (uint32_t)j * 2u * kHaloPos * 16u, kHaloPos * 16u, 128u);
-          const uint64_t bd = smem_desc(b0 + (uint32_t)j * 2u * (uint32_t)(Co / 8) * 128u, (uint32_t)(Co / 8) * 128u,
-                                        128u);
-          mma_bf16(tmem, ad, bd, idesc, (s > 0 || j > 0) ? 1 : 0);
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t a0 = hbase + (uint32_t)(((tap / 3) * (kM + 2) + tap % 3) * 16);
+          const uint32_t b0 = wbase + (uint32_t)tap * b_bytes(Co, KC);
+#pragma unroll 1
+          for (int j = 0; j < KC / 16; ++j) {
+            const uint64_t ad = smem_desc(a0 + (uint32_t)j * 2u * kHaloPos * 16u, kHaloPos * 16u, 128u);
+            const uint64_t bd = smem_desc(b0 + (uint32_t)j * 2u * (uint32_t)(Co / 8) * 128u,
+                                          (uint32_t)(Co / 8) * 128u, 128u);
+            mma_bf16(tmem, ad, bd, idesc, (kb > 0 || tap > 0 || j > 0) ? 1 : 0);
+          }
         }
-        mma_commit(&bar_mma[stage_of(s)]);
-        issued = s;
+        mma_commit(&bar_mma[bf]);
+        issued = kb;
       }
     }
   }
-  if (ok && tid == 0 && !wait_mma(nsteps - 1)) ok = false;
+  // the last block's commit (the one before it was seen before its buffer was refilled)
+  if (ok && tid == 0) {
+    if (bar_wait(&bar_mma[(nkb - 1) & 1], parity_of(nkb - 1)))
+      mma_seen = nkb - 1;
+    else
+      ok = false;
+  }
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
   if (ok) {
     tc_fence_after();
@@ -568,9 +565,9 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   } else if (tid == 0) {
     atomicOr(p.err, SGN_TC_WAIT);
     // drain in order what this CTA still has in flight
-    for (int st = mma_seen + 1; st <= issued; ++st)
-      if (!wait_mma(st)) break;
-    for (int c = copy_done + 1; c <= copied; ++c) bar_wait(&bar_w[stage_of(c)], parity_of(c));
+    for (int k = mma_seen + 1; k <= issued; ++k)
+      if (!bar_wait(&bar_mma[k & 1], parity_of(k))) break;
+    for (int k = copy_done + 1; k <= copied; ++k) bar_wait(&bar_w[k & 1], parity_of(k));
   }
   cp_async_wait0();
   tc_fence_before();

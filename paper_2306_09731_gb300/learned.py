@@ -35,18 +35,23 @@ def gaussian_states(N, L, amplitudes, seed=0):
 def generate(states, coarse, steps, dt, precision=2, guess=0, tau_power=1, warmup=1):
     """Runs each state for warmup + steps RK4 steps, recording the steps;
     returns the samples [S][5][coarse][coarse] (CUDA float32). With guess 3
-    the solver records only once its polynomial start is cubic (after 4
-    steps of the trajectory): give warmup >= 4."""
+    the solver records only once its polynomial start is cubic, 4 steps into
+    a trajectory whose history every other library call restarts: the
+    warm-up and the recorded steps then run as one call (give warmup >= 4)."""
     import torch
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     parts = []
     for st in states:
         s = Solver(st.Nx, st.Ny, st.Lx, st.Ly, precision=precision, guess=guess)
         f = [dev(st.h), dev(st.vx), dev(st.vy), dev(st.sigma)]
-        if warmup:
-            s.rk4_step(*f, dt, warmup)
-        buf = s.record_learned(coarse, 4 * steps, tau_power)
-        s.rk4_step(*f, dt, steps)
+        if guess == 3:
+            buf = s.record_learned(coarse, 4 * (steps + warmup), tau_power)
+            s.rk4_step(*f, dt, warmup + steps)
+        else:
+            if warmup:
+                s.rk4_step(*f, dt, warmup)
+            buf = s.record_learned(coarse, 4 * steps, tau_power)
+            s.rk4_step(*f, dt, steps)
         count = s.stop_recording()
         parts.append(buf[:count].clone())
         s.close()

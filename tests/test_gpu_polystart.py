@@ -151,9 +151,17 @@ def test_poly_start_history_across_calls(graph):
         s.close()
 
 
-def test_poly_start_refuses_learned_start():
-    from paper_2306_09731_gb300.sgn import SGNError, Solver
-    s = Solver(64, 64, 8.0, 8.0, precision=2, guess=3)
-    with pytest.raises(SGNError):
-        s.record_learned(16, 4)
-    s.close()
+def test_poly_start_records_only_once_the_start_is_cubic():
+    """The learned start corrects the polynomial start only once the ring holds
+    4 steps of the trajectory: a call of 4 steps from a fresh history records
+    nothing, one of 6 steps all four stages of its last 2 (every call other
+    than an RK4 step, sgn_record_learned included, restarts the history)."""
+    from paper_2306_09731_gb300.sgn import Solver
+    st = I.gaussian_hump(64, 8.0, 0.5)
+    for steps, expect in ((4, 0), (6, 8)):
+        s = Solver(64, 64, 8.0, 8.0, precision=2, guess=3)
+        f = [dev(a) for a in (st.h, st.vx, st.vy, st.sigma)]
+        s.record_learned(16, 32)
+        s.rk4_step(*f, 1e-3, steps)
+        assert s.stop_recording() == expect
+        s.close()
