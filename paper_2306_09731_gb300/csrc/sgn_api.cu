@@ -779,7 +779,10 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   C64* const* U = (mode == RK_STAGE1 || mode == RK_STORE_K) ? ctx->Un : ctx->Us;
   coef_from_spectral(ctx, U[0]);
   if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
-  if (ctx->opt.guess >= 2) {
+  // guess 3 falls back on guess 2's start (and needs its copies) only while
+  // its ring holds fewer than 3 steps
+  const bool lin2 = ctx->opt.guess == 2 || (ctx->opt.guess == 3 && ctx->ext_lv < 3);
+  if (lin2) {
     // linear extrapolation in time over the stage times t, t+dt/2, t+dt/2, t+dt:
     // stage 2 from sigma(t) and the previous step's sigma(t - dt/2),
     // stage 4 from sigma(t + dt/2) and sigma(t)
@@ -793,9 +796,10 @@ bool stage(sgn_ctx* ctx, int mode, double dt) {
   learned_post(ctx, dt);
   if (ctx->opt.guess >= 2) {
     const size_t bytes = ctx->G.nspec() * sizeof(C64);
-    if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (mode == RK_STAGE1 && lin2)
+      CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (mode == RK_STAGE3) {
-      CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (lin2) CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       ctx->have_s3 = true;
     }
   }
@@ -857,6 +861,7 @@ void ext_history(sgn_ctx* ctx, bool cont) {
   } else {
     CK(launch_set_int(&ctx->ext->levels, 0, EX(ctx)));
     CK(launch_set_int(&ctx->ext->full, 0, EX(ctx)));
+    CK(launch_set_int(&ctx->ext->lin, 1, EX(ctx)));
   }
 }
 
@@ -1055,10 +1060,12 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
   ctx->graph_fixed += count_launches(ctx, [&] {
     coef_from_spectral(ctx, U[0]);
     if (ctx->opt.guess == 1) CK(launch_zero<double>(ctx->G, ctx->sig, EX(ctx)));
+    // guess 3: guess 2's start and copies only while the ring holds < 3 steps
+    const int* lin = ctx->opt.guess == 3 ? &ctx->ext->lin : nullptr;
     if (ctx->opt.guess >= 2) {
       if (mode == RK_STAGE2)
-        CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx), &ctx->gst->have_s3));
-      if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx)));
+        CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s3, 2.0, ctx->sig, EX(ctx), &ctx->gst->have_s3, lin));
+      if (mode == RK_FINAL) CK(launch_axpby<double>(ctx->G, -1.0, ctx->sig_s1, 2.0, ctx->sig, EX(ctx), lin));
     }
     if (ctx->opt.guess == 3) CK(launch_ext_start(ctx->G, ctx->ext_ring, mode, ctx->ext, ctx->sig, EX(ctx)));
     learned_pre(ctx, U, mode, dt, true);  // no recording in graph mode (sgn_record_learned refuses it)
@@ -1066,9 +1073,16 @@ void graph_stage(sgn_ctx* ctx, GraphSeg& top, int mode, double dt) {
   graph_gmres(ctx, top);
   ctx->graph_fixed += count_launches(ctx, [&] {
     if (ctx->opt.guess >= 2) {
-      if (mode == RK_STAGE1) CK(cudaMemcpyAsync(ctx->sig_s1, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      const int* lin = ctx->opt.guess == 3 ? &ctx->ext->lin : nullptr;
+      auto keep = [&](C64* dst) {
+        if (lin)
+          CK(launch_copy_gated<double>(ctx->G, ctx->sig, dst, lin, EX(ctx)));
+        else
+          CK(cudaMemcpyAsync(dst, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      };
+      if (mode == RK_STAGE1) keep(ctx->sig_s1);
       if (mode == RK_STAGE3) {
-        CK(cudaMemcpyAsync(ctx->sig_s3, ctx->sig, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        keep(ctx->sig_s3);
         CK(launch_set_int(&ctx->gst->have_s3, 1, EX(ctx)));
       }
     }
@@ -1142,23 +1156,22 @@ void build_step_graph(sgn_ctx* ctx, double dt) {
   ctx->prof.on = false;
   ctx->graph_fixed = 0;
   GraphSeg top{ctx, ctx->step_graph, {}};
-  bool capturing = false;
   try {
     top.open();
-    capturing = true;
     graph_stage(ctx, top, RK_STAGE1, dt);
     graph_stage(ctx, top, RK_STAGE2, dt);
     graph_stage(ctx, top, RK_STAGE3, dt);
     graph_stage(ctx, top, RK_FINAL, dt);
-    capturing = false;
     top.close();
     check_step_graph(ctx);
     CK(cudaGraphInstantiate(&ctx->step_exec, ctx->step_graph, 0));
   } catch (Fail&) {
-    if (capturing) {
+    // end whichever segment was capturing (the top level or a WHILE body):
+    // the graph it returns belongs to the step graph and goes with it below
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
       cudaGraph_t junk = nullptr;
       cudaStreamEndCapture(ctx->cap, &junk);
-      if (junk && junk != ctx->step_graph) cudaGraphDestroy(junk);
     }
     cudaGetLastError();
     ctx->stream = saved;
@@ -1299,6 +1312,8 @@ sgn_status sgn_create(int Nx, int Ny, double Lx, double Ly, double g, const sgn_
     if (o.guess == 3) {
       ctx->ext_ring = dalloc<C64>(ctx, 16 * ns);
       ctx->ext = dalloc<ExtHist>(ctx, 1);
+      const ExtHist h0{0, 0, 0, 1};
+      CK(cudaMemcpy(ctx->ext, &h0, sizeof(h0), cudaMemcpyHostToDevice));
     }
     ctx->bh = dalloc<C64>(ctx, ns);
     ctx->cvec = dalloc<C64>(ctx, ns);

@@ -385,10 +385,13 @@ cudaError_t launch_axpy_multi(const Geom& G, const cpx<TV>* V, size_t vstride, i
 // x = 0; gate (may be null): only if *gate != 0
 template <typename T>
 cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex, const int* gate = nullptr);
-// y = a x + b y; gate (may be null): only if *gate != 0
+// y = a x + b y; gate, gate2 (may be null): only if *gate != 0 and *gate2 != 0
 template <typename T>
 cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex,
-                         const int* gate = nullptr);
+                         const int* gate = nullptr, const int* gate2 = nullptr);
+// y = x over the spectral entries, only if *gate != 0 (gate not null)
+template <typename T>
+cudaError_t launch_copy_gated(const Geom& G, const cpx<T>* x, cpx<T>* y, const int* gate, const Exec& ex);
 
 // reduce partials[b][0..n) over blocks into out[0..n); if sqrt_out, take sqrt
 cudaError_t launch_reduce(const double* partials, int n, double* out, bool sqrt_out, const int* gate,
@@ -408,6 +411,7 @@ struct ExtHist {
   int levels;  // steps held, 0..4
   int head;    // slot q of the step being taken
   int full;    // 1 while levels == 4 (the cubic start): the learned start's gate
+  int lin;     // 1 while levels < 3: guess 2's linear start (and its copies) still apply
 };
 // sigma = the quadratic (levels 3) or cubic (levels 4) extrapolation of stage
 // s from the ring; with fewer levels sigma is left as it is
@@ -416,9 +420,10 @@ cudaError_t launch_ext_start(const Geom& G, const cpx<double>* ring, int s, cons
 // ring slot (head, s) = sigma
 cudaError_t launch_ext_store(const Geom& G, const cpx<double>* sig, cpx<double>* ring, int s, const ExtHist* hist,
                              const Exec& ex);
-// after a step's last stage: head advances, levels += 1 (at most 4), full = (levels == 4)
+// after a step's last stage: head advances, levels += 1 (at most 4), full =
+// (levels == 4), lin = (levels < 3)
 cudaError_t launch_ext_advance(ExtHist* hist, const Exec& ex);
-// levels = full = 0 unless *flag
+// levels = full = 0 and lin = 1 unless *flag
 cudaError_t launch_ext_keep(ExtHist* hist, const int* flag, const Exec& ex);
 // *flag = 1 if the three spectra b equal a within rel * max|a| (see sgn_krylov.cu)
 cudaError_t launch_same_state(const Geom& G, const cpx<double>* const* a, const cpx<double>* const* b, double rel,

@@ -361,12 +361,19 @@ __global__ void k_axpy_multi(Geom G, const cpx<TV>* V, size_t vstride, int nv, c
 
 // y = a x + b y (FP64 arithmetic); the extrapolated GMRES start
 template <typename T>
-__global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y, const int* gate) {
-  if (gate && *gate == 0) return;
+__global__ void k_axpby(Geom G, double a, const cpx<T>* x, double b, cpx<T>* y, const int* gate,
+                        const int* gate2) {
+  if ((gate && *gate == 0) || (gate2 && *gate2 == 0)) return;
   for (Walk it(G); it.ok(); it.next()) {
     const cpx<T> u = x[it.e], v = y[it.e];
     y[it.e] = mk((T)(a * (double)u.x + b * (double)v.x), (T)(a * (double)u.y + b * (double)v.y));
   }
+}
+
+template <typename T>
+__global__ void k_copy_gated(Geom G, const cpx<T>* x, cpx<T>* y, const int* gate) {
+  if (*gate == 0) return;
+  for (Walk it(G); it.ok(); it.next()) y[it.e] = x[it.e];
 }
 
 template <typename T>
@@ -535,6 +542,7 @@ __global__ void k_ext_advance(ExtHist* hist) {
     hist->head = (hist->head + 1) & 3;
     hist->levels = min(hist->levels + 1, 4);
     hist->full = hist->levels >= 4 ? 1 : 0;
+    hist->lin = hist->levels < 3 ? 1 : 0;
   }
 }
 
@@ -544,6 +552,7 @@ __global__ void k_ext_keep(ExtHist* hist, const int* flag) {
   if (threadIdx.x == 0 && *flag == 0) {
     hist->levels = 0;
     hist->full = 0;
+    hist->lin = 1;
   }
 }
 
@@ -718,9 +727,16 @@ cudaError_t launch_zero(const Geom& G, cpx<T>* x, const Exec& ex, const int* gat
 
 template <typename T>
 cudaError_t launch_axpby(const Geom& G, double a, const cpx<T>* x, double b, cpx<T>* y, const Exec& ex,
-                         const int* gate) {
+                         const int* gate, const int* gate2) {
   ex.begin(PK_KRYLOV);
-  k_axpby<T><<<NBLK, 256, 0, ex.s>>>(G, a, x, b, y, gate);
+  k_axpby<T><<<NBLK, 256, 0, ex.s>>>(G, a, x, b, y, gate, gate2);
+  ex.end();
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_copy_gated(const Geom& G, const cpx<T>* x, cpx<T>* y, const int* gate, const Exec& ex) {
+  ex.begin(PK_KRYLOV);
+  k_copy_gated<T><<<NBLK, 256, 0, ex.s>>>(G, x, y, gate);
   ex.end();
   return cudaGetLastError();
 }
@@ -831,7 +847,8 @@ cudaError_t launch_invariant_sums(const Geom& G, const double* h, const double* 
                                           const Exec&);                                                     \
   template cudaError_t launch_zero<T>(const Geom&, cpx<T>*, const Exec&, const int*);                       \
   template cudaError_t launch_axpby<T>(const Geom&, double, const cpx<T>*, double, cpx<T>*, const Exec&,     \
-                                       const int*);
+                                       const int*, const int*);                                               \
+  template cudaError_t launch_copy_gated<T>(const Geom&, const cpx<T>*, cpx<T>*, const int*, const Exec&);
 
 SGN_KRYLOV_INST(double)
 SGN_KRYLOV_INST(float)
