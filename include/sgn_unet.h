@@ -110,6 +110,16 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
                                size_t workspace_bytes, void* stream);
 size_t sgn_conv3_workspace_bytes(int Ci, int Co);
 
+/* Self-test of the tensor-core kernels' bounded waits (both kernels, a
+ * 16 -> 16 channel layer on 16 x 16 and on 4 x 128 zeros): one launch whose
+ * weight barrier is armed for 16 bytes more than its copy delivers, so that
+ * the phase never completes, must report the run-out wait (the kernel stops,
+ * drains what it has in flight and frees its tensor memory), and the same
+ * layer must then run normally on the same context. SGN_OK if all of that
+ * held, SGN_ECUDA otherwise. Allocates and synchronises on stream; a few
+ * seconds at most (each run-out wait is bounded). */
+sgn_status sgn_conv3_wait_selftest(void* stream);
+
 /* after sgn_unet_forward with the same batch: loss = mean((out - target)^2)
  * over B n^2 values (written to *loss_dev, a device double; may be NULL) and
  * the gradients of that loss with respect to every parameter (overwritten). */

@@ -886,9 +886,14 @@ sgn_status sgn_unet_check(sgn_unet_t net) {
   UAPI_END
 }
 
-sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0, int up0, const void* src1, int C1,
-                               const float* weight, const float* bias, int Co, void* out, void* workspace,
-                               size_t workspace_bytes, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// one tensor-core layer; stall: the self-test's barrier that never completes
+sgn_status conv3_tc_run(int batch, int H, int W, const void* src0, int C0, int up0, const void* src1, int C1,
+                        const float* weight, const float* bias, int Co, void* out, void* workspace,
+                        size_t workspace_bytes, void* stream, int stall) {
   auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
   const int Ci = C0 + C1;
   if (batch < 1 || !pow2(H) || !pow2(W) || (long long)batch * H * W > (1ll << 30)) return SGN_EINVAL;
@@ -940,6 +945,7 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
   a.tmem_cols = (uint32_t)cols;
   a.out = (__nv_bfloat16*)out;
   a.err = err;
+  a.stall = stall;
   if (cudaFuncSetAttribute(row ? (const void*)unet_tc::k_conv3_tc_row : (const void*)unet_tc::k_conv3_tc,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
       cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
@@ -956,6 +962,49 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
       cudaStreamSynchronize(st) != cudaSuccess || h != 0)
     return SGN_ECUDA;
   return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0, int up0, const void* src1, int C1,
+                               const float* weight, const float* bias, int Co, void* out, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  return conv3_tc_run(batch, H, W, src0, C0, up0, src1, C1, weight, bias, Co, out, workspace, workspace_bytes,
+                      stream, 0);
+}
+
+sgn_status sgn_conv3_wait_selftest(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int C = 16, Co = 16;
+  const int shapes[2][2] = {{16, 16}, {4, 128}};  // the gather kernel, the row kernel
+  const size_t ws = sgn_conv3_workspace_bytes(C, Co);
+  void *src = nullptr, *out = nullptr, *wk = nullptr;
+  float *w = nullptr, *bias = nullptr;
+  const size_t npix = 16 * 16 > 4 * 128 ? 16 * 16 : 4 * 128;
+  bool ok = cudaMalloc(&src, npix * C * 2) == cudaSuccess && cudaMalloc(&out, npix * Co * 2) == cudaSuccess &&
+            cudaMalloc(&wk, ws) == cudaSuccess && cudaMalloc((void**)&w, sizeof(float) * Co * C * 9) == cudaSuccess &&
+            cudaMalloc((void**)&bias, sizeof(float) * Co) == cudaSuccess;
+  if (ok)
+    ok = cudaMemsetAsync(src, 0, npix * C * 2, st) == cudaSuccess &&
+         cudaMemsetAsync(w, 0, sizeof(float) * Co * C * 9, st) == cudaSuccess &&
+         cudaMemsetAsync(bias, 0, sizeof(float) * Co, st) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k) {
+    const int H = shapes[k][0], W = shapes[k][1];
+    // the stalled launch must report its run-out wait, and the context must
+    // still run the same layer normally afterwards
+    ok = conv3_tc_run(1, H, W, src, C, 0, nullptr, 0, w, bias, Co, out, wk, ws, stream, 1) == SGN_ECUDA &&
+         cudaGetLastError() == cudaSuccess &&
+         conv3_tc_run(1, H, W, src, C, 0, nullptr, 0, w, bias, Co, out, wk, ws, stream, 0) == SGN_OK;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(src);
+  cudaFree(out);
+  cudaFree(wk);
+  cudaFree(w);
+  cudaFree(bias);
+  return ok ? SGN_OK : SGN_ECUDA;
 }
 
 size_t sgn_conv3_workspace_bytes(int Ci, int Co) {

@@ -75,8 +75,9 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity) {
     if (bar_try(b, parity)) return true;
   return false;
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b,
+                                         unsigned extra_tx = 0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes + extra_tx)
                : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                    smem_addr(dst)),
@@ -141,6 +142,8 @@ struct ConvArgs {
   const float* head_b;
   float* head_out;            // [npix] FP32
   int* err;
+  int stall;                  // self-test only: arm step 0's weight barrier for 16 bytes more
+                              // than its copy delivers, so that its waits run out
 };
 
 // bytes of one K step's operands in shared memory (A rows, then B)
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   auto stage_of = [](int st) { return st % kStages; };
   auto parity_of = [](int st) { return (unsigned)((st / kStages) & 1); };
   if (tid == 0) {
-    bulk_g2s(sm + abytes, p.wimg, b_bytes(Co, KC), &bar_w[0]);
+    bulk_g2s(sm + abytes, p.wimg, b_bytes(Co, KC), &bar_w[0], p.stall ? 16u : 0u);
     copied = 0;
   }
   gather(0);
@@ -459,7 +462,8 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   // fastest) and its nine taps' weights (one bulk copy, thread 0) into buffer bf
   auto load_block = [&](int kb, int bf) {
     unsigned char* dst = sm + (size_t)bf * bufbytes;
-    if (tid == 0) bulk_g2s(dst + hbytes, p.wimg + (size_t)kb * 9 * Co * KC, wbytes, &bar_w[bf]);
+    if (tid == 0)
+      bulk_g2s(dst + hbytes, p.wimg + (size_t)kb * 9 * Co * KC, wbytes, &bar_w[bf], (p.stall && kb == 0) ? 16u : 0u);
     const int chunks = KC >> 3, pieces = kHaloPos * chunks;
     for (int i = tid; i < pieces; i += kThreads) {
       const int pos = i / chunks, c = i - pos * chunks;

@@ -12,7 +12,7 @@ UNET_EXPORTS = ["sgn_unet_create", "sgn_unet_create_arch", "sgn_unet_destroy", "
                 "sgn_unet_last_error", "sgn_unet_num_params", "sgn_unet_side", "sgn_unet_levels", "sgn_unet_width",
                 "sgn_unet_set_params", "sgn_unet_get_params", "sgn_unet_get_grads", "sgn_unet_forward",
                 "sgn_unet_infer", "sgn_unet_check", "sgn_unet_backward", "sgn_unet_adam_step",
-                "sgn_conv3_relu_bf16", "sgn_conv3_workspace_bytes"]
+                "sgn_conv3_relu_bf16", "sgn_conv3_workspace_bytes", "sgn_conv3_wait_selftest"]
 
 # the default network and the four-level one of 471,873 parameters
 DEFAULT_ARCH = (3, (16, 32, 32))
@@ -38,6 +38,7 @@ def load_library():
             "sgn_unet_check": (_I, [_P]),
             "sgn_conv3_relu_bf16": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _P, _I, _P, _P, ctypes.c_size_t, _P]),
             "sgn_conv3_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
+            "sgn_conv3_wait_selftest": (_I, [_P]),
             "sgn_unet_destroy": (_I, [_P]),
             "sgn_unet_set_stream": (_I, [_P, _P]),
             "sgn_unet_last_error": (ctypes.c_char_p, [_P]),

@@ -144,6 +144,20 @@ def test_tensor_core_layer_matches_oracle_convolution(B, H, W, C0, up0, C1, Co):
     assert np.count_nonzero(ref) > 0.3 * ref.size  # the ReLU leaves a real test
 
 
+def test_tensor_core_wait_runs_out_and_the_context_survives():
+    """A barrier that never completes (armed for more bytes than its copy
+    delivers) makes each kernel's bounded wait run out: the launch reports it
+    and the same context then runs the layer normally (sgn_conv3_wait_selftest);
+    a full layer afterwards still matches the oracle."""
+    import time
+    from paper_2306_09731_gb300 import unet as UN
+    lib = UN.load_library()
+    t0 = time.perf_counter()
+    assert lib.sgn_conv3_wait_selftest(torch.cuda.current_stream().cuda_stream) == 0
+    assert time.perf_counter() - t0 < 60
+    test_tensor_core_layer_matches_oracle_convolution(1, 4, 128, 64, 0, 0, 64)
+
+
 def run_infer(n, B, arch, seed):
     rng = np.random.default_rng(seed)
     p = U.init_params(seed, arch).astype(np.float32)
