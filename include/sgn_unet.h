@@ -111,7 +111,7 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
 size_t sgn_conv3_workspace_bytes(int Ci, int Co);
 
 /* Self-test of the tensor-core kernels' bounded waits (both kernels, a
- * 16 -> 16 channel layer on 16 x 16 and on 4 x 128 zeros): one launch whose
+ * 16 -> 16 channel layer on 8 x 8 and on 4 x 128 zeros): one launch whose
  * weight barrier is armed for 16 bytes more than its copy delivers, so that
  * the phase never completes, must report the run-out wait (the kernel stops,
  * drains what it has in flight and frees its tensor memory), and the same

@@ -300,7 +300,7 @@ struct Layer {
   int KC = 0, nkb = 0, smem = 0;
   long long ioff = -1;
   int level = 0;     // resolution level (grid side n / 2^level)
-  bool row = false;  // rows of >= 128 pixels: the halo-staged row kernel
+  bool row = false;  // >= 128 pixels per image: the halo-staged row kernel
 };
 
 // Lower bound of the tensor-core kernel's dynamic shared memory (beyond the
@@ -641,13 +641,16 @@ int pick_kc(int Ci, int Co) {
 }
 
 // channels per block of the row kernel: the fewest blocks whose halo and
-// weight buffers fit 110 KB (two CTAs per SM)
-int pick_kc_row(int Ci, int Co) {
+// weight buffers fit 110 KB (two CTAs per SM), or 200 KB when the layer has
+// fewer tiles than the GPU has SMs (one CTA per SM costs nothing there, and
+// each block is a step of the tile's dependent chain)
+int pick_kc_row(int Ci, int Co, int W, long long tiles) {
+  const int budget = (tiles < 148 ? 200 : 110) * 1024;
   for (int nkb = 1; nkb <= Ci / 16; ++nkb) {
     if (Ci % nkb) continue;
     const int kc = Ci / nkb;
     if (kc % 16) continue;
-    if ((int)unet_tc::row_smem_bytes(Co, kc, nkb) <= 110 * 1024) return kc;
+    if ((int)unet_tc::row_smem_bytes(Co, kc, nkb, W) <= budget) return kc;
   }
   return 16;
 }
@@ -700,9 +703,11 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
     l.boff = off;
     off += l.Co;
     l.level = lv[i];
-    l.row = (n >> l.level) >= 128;
+    const int side = n >> l.level;
+    l.row = side * side >= unet_tc::kM;
     if (l.k == 3 && i > 0) {
-      l.KC = l.row ? pick_kc_row(l.Ci, l.Co) : pick_kc(l.Ci, l.Co);
+      l.KC = l.row ? pick_kc_row(l.Ci, l.Co, side, (long long)max_batch * side * side / unet_tc::kM)
+                   : pick_kc(l.Ci, l.Co);
       l.nkb = l.Ci / l.KC;
       l.ioff = ioff;
       unet_tc::WImgLayer& t = net->wtab.l[net->wtab.nl++];
@@ -714,7 +719,7 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
       t.nkb = l.nkb;
       t.kb_major = l.row ? 1 : 0;
       ioff += 9ll * l.Ci * l.Co;
-      int sm = l.row ? (int)unet_tc::row_smem_bytes(l.Co, l.KC, l.nkb)
+      int sm = l.row ? (int)unet_tc::row_smem_bytes(l.Co, l.KC, l.nkb, side)
                      : unet_tc::kStages * (int)unet_tc::stage_bytes(l.Co, l.KC);
       // at most 512 / cols CTAs per SM, so that TMEM is never oversubscribed
       int cols = 32;
@@ -907,8 +912,8 @@ sgn_status conv3_tc_run(int batch, int H, int W, const void* src0, int C0, int u
   int lH = 0, lW = 0;
   while ((1 << lH) < H) ++lH;
   while ((1 << lW) < W) ++lW;
-  const bool row = W >= 128;
-  const int KC = row ? pick_kc_row(Ci, Co) : pick_kc(Ci, Co);
+  const bool row = H * W >= unet_tc::kM;
+  const int KC = row ? pick_kc_row(Ci, Co, W, (long long)batch * H * W / unet_tc::kM) : pick_kc(Ci, Co);
   __nv_bfloat16* wimg = (__nv_bfloat16*)workspace;
   int* err = (int*)((char*)workspace + ((img + 15) & ~(size_t)15));
   unet_tc::WImgTable t{};
@@ -923,7 +928,7 @@ sgn_status conv3_tc_run(int batch, int H, int W, const void* src0, int C0, int u
   t.total = 9ll * Ci * Co;
   int cols = 32;
   while (cols < Co) cols <<= 1;
-  int sm = row ? (int)unet_tc::row_smem_bytes(Co, KC, Ci / KC)
+  int sm = row ? (int)unet_tc::row_smem_bytes(Co, KC, Ci / KC, W)
                : unet_tc::kStages * (int)unet_tc::stage_bytes(Co, KC);
   const int floor_bytes = 233472 / (512 / cols + 1) + 1;
   if (sm < floor_bytes) sm = floor_bytes;
@@ -978,11 +983,11 @@ sgn_status sgn_conv3_relu_bf16(int batch, int H, int W, const void* src0, int C0
 sgn_status sgn_conv3_wait_selftest(void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int C = 16, Co = 16;
-  const int shapes[2][2] = {{16, 16}, {4, 128}};  // the gather kernel, the row kernel
+  const int shapes[2][2] = {{8, 8}, {4, 128}};  // the gather kernel (64 pixels), the row kernel
   const size_t ws = sgn_conv3_workspace_bytes(C, Co);
   void *src = nullptr, *out = nullptr, *wk = nullptr;
   float *w = nullptr, *bias = nullptr;
-  const size_t npix = 16 * 16 > 4 * 128 ? 16 * 16 : 4 * 128;
+  const size_t npix = 4 * 128;
   bool ok = cudaMalloc(&src, npix * C * 2) == cudaSuccess && cudaMalloc(&out, npix * Co * 2) == cudaSuccess &&
             cudaMalloc(&wk, ws) == cudaSuccess && cudaMalloc((void**)&w, sizeof(float) * Co * C * 9) == cudaSuccess &&
             cudaMalloc((void**)&bias, sizeof(float) * Co) == cudaSuccess;

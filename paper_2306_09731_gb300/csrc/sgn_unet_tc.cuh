@@ -412,12 +412,24 @@ namespace unet_tc {
 // double-buffered across channel blocks, the next block's loaded while the
 // current block's MMAs run, and one thread issues a block's 9 KC/16 MMAs back
 // to back with one commit.
+//
+// Rows of fewer than 128 pixels (W < 128, at least 128 pixels per image): a
+// tile is the 128 / W whole rows y0.. of one image, and the halo holds three
+// copies of rows y0-1 .. y0+128/W, copy kx shifted by kx - 1 columns (wrapped)
+// and stored with row stride exactly W. Output pixel m of the tile then reads
+// tap (ky, kx) at position m + ky W of copy kx: again 128 consecutive 16-byte
+// positions, one descriptor per tap.
 constexpr int kHaloPos = 3 * (kM + 2);
-__host__ __device__ constexpr uint32_t halo_bytes(int KC) { return (uint32_t)kHaloPos * KC * 2u; }
+// positions per chunk of one halo copy, and the copies
+__host__ __device__ constexpr int halo_pos(int W) { return W >= kM ? kHaloPos : kM + 2 * W; }
+__host__ __device__ constexpr int halo_copies(int W) { return W >= kM ? 1 : 3; }
+__host__ __device__ constexpr uint32_t halo_bytes(int KC, int W) {
+  return (uint32_t)halo_copies(W) * halo_pos(W) * KC * 2u;
+}
 // one buffer of halo + weights per channel block in flight (two when there
 // are several blocks)
-__host__ __device__ constexpr uint32_t row_smem_bytes(int Co, int KC, int nkb) {
-  return (nkb > 1 ? 2u : 1u) * (halo_bytes(KC) + 9u * b_bytes(Co, KC));
+__host__ __device__ constexpr uint32_t row_smem_bytes(int Co, int KC, int nkb, int W) {
+  return (nkb > 1 ? 2u : 1u) * (halo_bytes(KC, W) + 9u * b_bytes(Co, KC));
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -433,7 +445,10 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KC = p.KC, Co = p.Co, nkb = p.nkb;
-  const uint32_t hbytes = halo_bytes(KC), wbytes = 9u * b_bytes(Co, KC), bufbytes = hbytes + wbytes;
+  const int W = 1 << p.lW, H = 1 << p.lH;
+  const bool wide = W >= kM;
+  const int P = halo_pos(W);  // positions of one chunk of one halo copy
+  const uint32_t hbytes = halo_bytes(KC, W), wbytes = 9u * b_bytes(Co, KC), bufbytes = hbytes + wbytes;
   const uint32_t sm0 = smem_addr(sm);
 
   if (warp == 0) tmem_alloc(&tmem_slot, p.tmem_cols);
@@ -449,12 +464,19 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  const int W = 1 << p.lW, H = 1 << p.lH;
-  const int tiles_row = W >> 7;
   const int tile = blockIdx.x;
-  const int x0 = (tile % tiles_row) << 7;
-  const int y = (tile / tiles_row) & (H - 1);
-  const int b = tile / (tiles_row << p.lH);
+  int x0, y, b;  // wide: the tile's row y and first column x0; narrow: its first row y
+  if (wide) {
+    const int tiles_row = W >> 7;
+    x0 = (tile % tiles_row) << 7;
+    y = (tile / tiles_row) & (H - 1);
+    b = tile / (tiles_row << p.lH);
+  } else {
+    const int rows = kM >> p.lW, tiles_img = H / rows;
+    x0 = 0;
+    y = (tile % tiles_img) * rows;
+    b = tile / tiles_img;
+  }
   const int pix = tile * kM + tid;
   const uint32_t idesc = instr_desc_bf16(kM, Co);
 
@@ -464,11 +486,20 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
     unsigned char* dst = sm + (size_t)bf * bufbytes;
     if (tid == 0)
       bulk_g2s(dst + hbytes, p.wimg + (size_t)kb * 9 * Co * KC, wbytes, &bar_w[bf], (p.stall && kb == 0) ? 16u : 0u);
-    const int chunks = KC >> 3, pieces = kHaloPos * chunks;
+    const int chunks = KC >> 3, pieces = halo_copies(W) * P * chunks;
     for (int i = tid; i < pieces; i += kThreads) {
-      const int pos = i / chunks, c = i - pos * chunks;
-      const int r = pos / (kM + 2), col = pos - r * (kM + 2);
-      const int gy = (y + r - 1) & (H - 1), gx = (x0 + col - 1) & (W - 1);
+      const int kx = i / (P * chunks), rem = i - kx * P * chunks;
+      const int pos = rem / chunks, c = rem - pos * chunks;
+      int gy, gx;
+      if (wide) {
+        const int r = pos / (kM + 2), col = pos - r * (kM + 2);
+        gy = (y + r - 1) & (H - 1);
+        gx = (x0 + col - 1) & (W - 1);
+      } else {
+        const int r = pos >> p.lW, xx = pos & (W - 1);
+        gy = (y + r - 1) & (H - 1);
+        gx = (xx + kx - 1) & (W - 1);
+      }
       const int ch = kb * KC + 8 * c;
       const __nv_bfloat16* src;
       if (ch < p.C0) {
@@ -478,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
       } else {
         src = p.src1 + ((((size_t)b << (p.lH + p.lW)) + ((size_t)gy << p.lW) + gx) * p.C1 + (ch - p.C0));
       }
-      cp_async16(dst + ((size_t)c * kHaloPos + pos) * 16, src);
+      cp_async16(dst + ((size_t)(kx * chunks + c) * P + pos) * 16, src);
     }
   };
   // block kb uses buffer kb & 1; its k-th use is phase k of that buffer's barriers
@@ -520,13 +551,17 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
         copy_done = kb;
         tc_fence_after();
         const uint32_t hbase = sm0 + (uint32_t)bf * bufbytes, wbase = hbase + hbytes;
+        const uint32_t cstride = (uint32_t)P * 16u;  // bytes between chunks of a copy (LBO)
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
-          const uint32_t a0 = hbase + (uint32_t)(((tap / 3) * (kM + 2) + tap % 3) * 16);
+          const int ky = tap / 3, kx = tap % 3;
+          const uint32_t a0 =
+              hbase + (wide ? (uint32_t)((ky * (kM + 2) + kx) * 16)
+                            : (uint32_t)kx * (uint32_t)(KC >> 3) * cstride + (uint32_t)(ky * W * 16));
           const uint32_t b0 = wbase + (uint32_t)tap * b_bytes(Co, KC);
 #pragma unroll 1
           for (int j = 0; j < KC / 16; ++j) {
-            const uint64_t ad = smem_desc(a0 + (uint32_t)j * 2u * kHaloPos * 16u, kHaloPos * 16u, 128u);
+            const uint64_t ad = smem_desc(a0 + (uint32_t)j * 2u * cstride, cstride, 128u);
             const uint64_t bd = smem_desc(b0 + (uint32_t)j * 2u * (uint32_t)(Co / 8) * 128u,
                                           (uint32_t)(Co / 8) * 128u, 128u);
             mma_bf16(tmem, ad, bd, idesc, (kb > 0 || tap > 0 || j > 0) ? 1 : 0);
