@@ -768,7 +768,15 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
         const bool dup = !(FL & yf_tma(i));
         if (!dup) {
           if (!mbar_wait_bounded(&tbar[m])) {
-            if (tid == 0) atomicOr(tm->flags, FLAG_WAIT);
+            // before the block's shared memory goes: one more bounded wait
+            // for every tensor copy of this block still in flight
+            if (tid == 0) {
+              atomicOr(tm->flags, FLAG_WAIT);
+#pragma unroll 1
+              for (int q = 0; q < NMAP; ++q)
+                for (int it = 0; it < (1 << 20) && !mbar_try_wait(&tbar[q], 0); ++it) {
+                }
+            }
             return;
           }
         }
