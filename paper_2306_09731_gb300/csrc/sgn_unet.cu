@@ -303,9 +303,6 @@ struct Layer {
   bool row = false;  // >= 128 pixels per image: the halo-staged row kernel
 };
 
-// Lower bound of the tensor-core kernel's dynamic shared memory (beyond the
-// two stages and the TMEM occupancy bound).
-constexpr int kTcSmemMin = 0;
 
 }  // namespace
 
@@ -331,7 +328,6 @@ struct sgn_unet_ctx {
   __nv_bfloat16* wimg = nullptr;
   unet_tc::WImgTable wtab{};
   int* dev_err = nullptr;
-  int tc_smem_max = 0;
   const float* lastIn = nullptr;
   int lastB = 0;
   std::vector<void*> allocs;
@@ -727,7 +723,6 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
       const int ctas = 512 / cols;
       const int floor_bytes = 233472 / (ctas + 1) + 1;
       if (sm < floor_bytes) sm = floor_bytes;
-      if (sm < kTcSmemMin) sm = kTcSmemMin;
       l.smem = sm;
       if (sm > smem_max) smem_max = sm;
     }
@@ -735,7 +730,6 @@ sgn_status create_impl(int n, int max_batch, int act_bf16, unsigned long long se
   }
   net->wtab.total = ioff;
   net->P = off;
-  net->tc_smem_max = smem_max;
   try {
     const size_t B = (size_t)max_batch;
     const size_t es = net->bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
@@ -932,7 +926,6 @@ sgn_status conv3_tc_run(int batch, int H, int W, const void* src0, int C0, int u
                : unet_tc::kStages * (int)unet_tc::stage_bytes(Co, KC);
   const int floor_bytes = 233472 / (512 / cols + 1) + 1;
   if (sm < floor_bytes) sm = floor_bytes;
-  if (sm < kTcSmemMin) sm = kTcSmemMin;
   unet_tc::ConvArgs a{};
   a.src0 = (const __nv_bfloat16*)src0;
   a.src1 = (const __nv_bfloat16*)src1;
