@@ -206,10 +206,18 @@ __device__ __forceinline__ dfl ldr(const dfl* p) {
   return dfl(v.x, v.y);
 }
 
-// 16-byte elements: the FP64 padding layout
+// 16-byte elements, eight to a 128-byte shared-memory row: the slot is XOR-ed
+// with (p >> 3) & 7 within its aligned group of 8, which spreads the stride-8
+// writes of the first stage (and the 64a + b writes of the second) over the
+// whole row, as the FP64 layout's padding does, without the padding: the
+// buffers of a length-N transform take N elements (unpadded_smem).
 template <>
 __device__ __forceinline__ int sidx<dfl>(int p, int lcs) {
-  return (p + (p >> 3)) << lcs;
+  return (p ^ ((p >> 3) & 7)) << lcs;
 }
+template <>
+struct unpadded_smem<dfl> {
+  static constexpr bool value = true;
+};
 
 }  // namespace sgn

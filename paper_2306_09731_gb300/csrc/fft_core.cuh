@@ -118,6 +118,16 @@ __device__ __forceinline__ int sidx<float>(int p, int lcs) {
 }
 // shared-memory elements needed by one transform of length N (either layout)
 __host__ __device__ constexpr int smem_elems(int N) { return N + (N >> 3); }
+// element types whose exchange buffers need no padding (their sidx swizzles
+// within aligned groups instead): the double-float passes, see dfloat.cuh
+template <typename T>
+struct unpadded_smem {
+  static constexpr bool value = false;
+};
+template <typename T>
+__host__ __device__ constexpr int smem_elems_of(int N) {
+  return unpadded_smem<T>::value ? N : smem_elems(N);
+}
 
 // Exponent k of entry i of the staged twiddle table of a length-2^lN
 // transform (the entry is W_N^k), or -1 past the last stage's rows. The

@@ -120,7 +120,7 @@ __device__ __forceinline__ XLayout x_layout(const Geom& G) {
 template <typename T>
 __device__ __forceinline__ cpx<T>* x_smem(const Geom& G, int grp) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  return reinterpret_cast<cpx<T>*>(smraw) + grp * smem_elems(G.Nx);
+  return reinterpret_cast<cpx<T>*>(smraw) + grp * smem_elems_of<T>(G.Nx);
 }
 
 // ------------------------------------------------------------ plain x-passes
@@ -318,7 +318,7 @@ __global__ void k_coef_phys(Geom G, const double* __restrict__ hp, T* h, T* cr, 
 template <int LN>
 constexpr int xpass_threads() { return LN == 12 ? 512 : 256; }
 template <typename T, int LN>
-constexpr int mv_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 3 : 2); }
+constexpr int mv_min_blocks() { return LN == 12 ? 1 : ((sizeof(T) == 4 || std::is_same<T, dfl>::value) ? 3 : 2); }
 template <typename T, int LN>
 constexpr int rhs_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 2 : 1); }
 
@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
   // thread writes and reads back only its own slots (no barrier needed)
   extern __shared__ __align__(16) unsigned char smraw[];
   const int P = blockDim.x >> (lN - 3);
-  cpx<T>* stash = reinterpret_cast<cpx<T>*>(smraw) + (size_t)P * smem_elems(N) + (size_t)L.grp * mv_stash_elems(N);
+  cpx<T>* stash =
+      reinterpret_cast<cpx<T>*>(smraw) + (size_t)P * smem_elems_of<T>(N) + (size_t)L.grp * mv_stash_elems(N);
   cpx<T> Z[8];
   cpx<T> b0[5], b1[5];
   // a = 3 sigma / h^3
@@ -608,8 +609,9 @@ __host__ __device__ constexpr int ystage_bytes(int upto) {
 }
 
 // byte offset of the staging area: the transform buffers, rounded up to 16
-__host__ __device__ constexpr size_t ystage_offset(int lN, int lC, int esize) {
-  return ((((size_t)smem_elems(1 << lN) << lC) * (size_t)esize) + 15) & ~(size_t)15;
+template <typename T>
+__host__ __device__ constexpr size_t ystage_offset(int lN, int lC) {
+  return ((((size_t)smem_elems_of<T>(1 << lN) << lC) * sizeof(cpx<T>)) + 15) & ~(size_t)15;
 }
 
 // staging masks of the fused passes (see ypass_body): the matvec y-inverse
@@ -721,7 +723,7 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
   cpx<T> r[NIN][8];
   const size_t soff = in.sel ? (size_t)(*in.sel) * in.sel_stride : 0;
   // staging area: after the C transform buffers of the exchanges
-  unsigned char* stage = smraw + ystage_offset(lN, lC, (int)sizeof(cpx<T>));
+  unsigned char* stage = smraw + ystage_offset<T>(lN, lC);
   const int nthr = blockDim.x, tid = threadIdx.x;
   // tensor-copied tiles: [Ny][C] per map, 128-byte aligned in the shared window
   constexpr int NMAP = ((FL & yf_tma(0)) ? 1 : 0) + ((NIN > 1 && (FL & yf_tma(1))) ? 1 : 0);
@@ -1127,7 +1129,7 @@ static inline void x_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
   }
   block = dim3((G.Nx >> 3) * P);
   grid = dim3((G.Ny / 2 + P - 1) / P, nf);
-  smem = (size_t)P * (smem_elems(G.Nx) + extra_elems_per_group) * sizeof(cpx<T>);
+  smem = (size_t)P * (smem_elems_of<T>(G.Nx) + extra_elems_per_group) * sizeof(cpx<T>);
 }
 template <typename T, bool INV, int NIN>
 static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem, int stage_per_thread = 0,
@@ -1148,7 +1150,7 @@ static inline void y_config(const Geom& G, dim3& grid, dim3& block, size_t& smem
   grid = dim3((G.Nxh + C - 1) / C);
   int lC = 0;
   while ((1 << lC) < C) ++lC;
-  smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + (size_t)block.x * stage_per_thread;
+  smem = ystage_offset<T>(G.lNy, lC) + (size_t)block.x * stage_per_thread;
 }
 
 static constexpr int kMaxDynSmem = 227 * 1024;
@@ -1460,7 +1462,7 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
     ti.z[0] = (int)zj;
     ti.zsel = jsel;
     ti.flags = tma->flags;
-    smem = ystage_offset(G.lNy, lC, (int)sizeof(cpx<T>)) + 128 + tile;
+    smem = ystage_offset<T>(G.lNy, lC) + 128 + tile;
     dispatch_ln<T>(bi ? G.lNy : 0, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       YIn<T, 2> yi{};
@@ -1496,7 +1498,7 @@ static bool matvec_tma(const Geom& G, const Tables<T>& tb, const cpx<T>* sig, co
     tf.map[0] = tma->t0;
     tf.map[1] = tma->t1;
     tf.flags = tma->flags;
-    smem = ystage_offset(G.lNy, lCf, (int)sizeof(cpx<T>)) + 128 + 2 * tilef;
+    smem = ystage_offset<T>(G.lNy, lCf) + 128 + 2 * tilef;
     dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
       constexpr int L = decltype(ln)::value;
       YIn<T, 2> yi{};
