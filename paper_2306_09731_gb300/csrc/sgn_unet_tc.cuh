@@ -151,6 +151,34 @@ __host__ __device__ constexpr uint32_t a_bytes(int KC) { return (uint32_t)kM * K
 __host__ __device__ constexpr uint32_t b_bytes(int Co, int KC) { return (uint32_t)Co * KC * 2u; }
 __host__ __device__ constexpr uint32_t stage_bytes(int Co, int KC) { return a_bytes(KC) + b_bytes(Co, KC); }
 
+// The epilogue of both kernels, after the last MMA completed: this thread's
+// TMEM lane (its pixel) read back 16 columns at a time, bias, ReLU, BF16
+// store of the NHWC row; with a head, the 1x1 output convolution of the BF16
+// values in FP32. Every thread of the CTA calls it (tcgen05.ld is warp-wide);
+// valid: whether the pixel exists (a ragged last tile).
+__device__ __forceinline__ void tc_epilogue(const ConvArgs& p, uint32_t tmem, int warp, int pix, bool valid) {
+  tc_fence_after();
+  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  float head = 0.f;
+  for (int q = 0; q < p.Co / 16; ++q) {
+    float v[16];
+    tmem_ld16(lane_addr + (uint32_t)(q * 16), v);
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float a = fmaxf(v[i] + __ldg(p.bias + q * 16 + i), 0.f);
+      o[i] = __float2bfloat16_rn(a);
+      if (p.head_w) head = fmaf(__ldg(p.head_w + q * 16 + i), __bfloat162float(o[i]), head);
+    }
+    if (valid && p.out) {
+      uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)pix * p.Co + q * 16);
+      dst[0] = reinterpret_cast<const uint4*>(o)[0];
+      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+  }
+  if (valid && p.head_w) p.head_out[pix] = head + __ldg(p.head_b);
+}
+
 __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar_w[kStages], bar_mma[kStages];
@@ -264,26 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs p) {
   }
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
   if (ok) {
-    tc_fence_after();
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    float head = 0.f;
-    for (int q = 0; q < Co / 16; ++q) {
-      float v[16];
-      tmem_ld16(lane_addr + (uint32_t)(q * 16), v);
-      __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float a = fmaxf(v[i] + __ldg(p.bias + q * 16 + i), 0.f);
-        o[i] = __float2bfloat16_rn(a);
-        if (p.head_w) head = fmaf(__ldg(p.head_w + q * 16 + i), __bfloat162float(o[i]), head);
-      }
-      if (valid && p.out) {
-        uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)pix * Co + q * 16);
-        dst[0] = reinterpret_cast<const uint4*>(o)[0];
-        dst[1] = reinterpret_cast<const uint4*>(o)[1];
-      }
-    }
-    if (valid && p.head_w) p.head_out[pix] = head + __ldg(p.head_b);
+    tc_epilogue(p, tmem, warp, pix, valid);
   } else if (tid == 0) {
     atomicOr(p.err, SGN_TC_WAIT);
     // let what this CTA still has in flight finish before its memory goes
@@ -581,26 +590,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc_row(ConvArgs p) {
   }
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
   if (ok) {
-    tc_fence_after();
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    float head = 0.f;
-    for (int q = 0; q < Co / 16; ++q) {
-      float v[16];
-      tmem_ld16(lane_addr + (uint32_t)(q * 16), v);
-      __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float a = fmaxf(v[i] + __ldg(p.bias + q * 16 + i), 0.f);
-        o[i] = __float2bfloat16_rn(a);
-        if (p.head_w) head = fmaf(__ldg(p.head_w + q * 16 + i), __bfloat162float(o[i]), head);
-      }
-      if (p.out) {
-        uint4* dst = reinterpret_cast<uint4*>(p.out + (size_t)pix * Co + q * 16);
-        dst[0] = reinterpret_cast<const uint4*>(o)[0];
-        dst[1] = reinterpret_cast<const uint4*>(o)[1];
-      }
-    }
-    if (p.head_w) p.head_out[pix] = head + __ldg(p.head_b);
+    tc_epilogue(p, tmem, warp, pix, true);
   } else if (tid == 0) {
     atomicOr(p.err, SGN_TC_WAIT);
     // drain in order what this CTA still has in flight
