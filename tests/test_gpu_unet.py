@@ -192,6 +192,32 @@ def test_infer_tensor_cores_match_bf16_oracle(n, B, arch):
     assert rel(out, fwd) < 4 * noise
 
 
+@pytest.mark.parametrize("n,arch", [(64, SPEC), (16, U.DEFAULT_ARCH)])
+def test_infer_partial_batches_match_the_full_batch(n, arch):
+    """Each pixel's sums are the same dot products whatever the batch (an MMA
+    row is one pixel, its K order fixed), so sample i of a call with fewer
+    samples than max_batch equals sample i of the full call bit for bit; the
+    full call meets the BF16-emulating oracle."""
+    from paper_2306_09731_gb300.unet import UNet
+    rng = np.random.default_rng(n + 7)
+    B = 3
+    p = U.init_params(13, arch).astype(np.float32)
+    x = rng.standard_normal((B, 4, n, n)).astype(np.float32)
+    net = UNet(n, max_batch=B, bf16=True, seed=1, arch=None if arch == U.DEFAULT_ARCH else arch)
+    net.set_params(torch.tensor(p, device="cuda"))
+    xd = torch.tensor(x, device="cuda")
+    full = net.infer(xd).clone()
+    one = net.infer(xd[:1].contiguous()).clone()
+    two = net.infer(xd[1:3].contiguous()).clone()
+    net.check()
+    net.close()
+    assert torch.equal(one[0], full[0])
+    assert torch.equal(two, full[1:3])
+    ro, _ = U.forward(p.astype(np.float64), x.astype(np.float64), arch, bf16=True, weights_bf16=True)
+    ro64, _ = U.forward(p.astype(np.float64), x.astype(np.float64), arch)
+    assert rel(full.cpu().numpy(), ro) < max(1e-3, 2 * rel(ro, ro64))
+
+
 def test_infer_is_deterministic_and_graph_capturable():
     from paper_2306_09731_gb300.unet import UNet
     rng = np.random.default_rng(4)
