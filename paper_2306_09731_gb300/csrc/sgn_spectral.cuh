@@ -282,15 +282,24 @@ __global__ void k_coef_x(Geom G, const cpx<T>* __restrict__ tw, const T* __restr
   fft_regs<true>(v, sm, tw, L.t, G.lNx);
   if (!L.valid) return;
   const double invN = 1.0 / (double)G.nphys();
+  if constexpr (std::is_same<T, dfl>::value) {
+    // one slot at a time from the thread's own slots of the transform buffer
+    // (free again after the transform; no other thread touches them): one
+    // copy of the double-float reciprocal code instead of sixteen.
+    // N = Nx Ny is a power of two: the scaling by 1/N is exact.
+    store_slots(v, sm, L.t, T_, 0);
+    const float fN = (float)invN;
+#pragma unroll 1
+    for (int s = 0; s < 8; ++s) {
+      const int x = L.t + s * T_;
+      const cpx<T> z = sm[sidx<T>(x, 0)];
+      coef_point_df(scale_pow2(z.x, fN), fN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
+      coef_point_df(scale_pow2(z.y, fN), fN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
+    }
+  } else {
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int x = L.t + s * T_;
-    if constexpr (std::is_same<T, dfl>::value) {
-      // N = Nx Ny is a power of two: the scaling by 1/N is exact
-      const float fN = (float)invN;
-      coef_point_df(scale_pow2(v[s].x, fN), fN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
-      coef_point_df(scale_pow2(v[s].y, fN), fN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
-    } else {
+    for (int s = 0; s < 8; ++s) {
+      const int x = L.t + s * T_;
       coef_point<T>((double)v[s].x * invN, invN, h, cr, cc, (size_t)L.y0 * N + x, flags, cp);
       coef_point<T>((double)v[s].y * invN, invN, h, cr, cc, (size_t)L.y1 * N + x, flags, cp);
     }
@@ -352,57 +361,57 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), mv_min_blocks<T, LN>()) k
       reinterpret_cast<cpx<T>*>(smraw) + (size_t)P * smem_elems_of<T>(N) + (size_t)L.grp * mv_stash_elems(N);
   cpx<T> Z[8];
   cpx<T> b0[5], b1[5];
-  // a = 3 sigma / h^3
-  load_packed(Z, S + o0, S + o1, false, kx, L.t, lN);
-  fft_regs<true>(Z, sm, tw, L.t, lN, 0, PLAN);
+  // phase 0: a = 3 sigma / h^3 (kept in the stash); phase 1: bx = sigma_x / h,
+  // combined with a into Cout; phase 2: by = sigma_y / h into Byout
+  auto phase = [&](int ph) {
+    const cpx<T>* in = ph == 2 ? Sy : S;
+    const T* __restrict__ cf = ph == 0 ? cc : cr;
+    load_packed(Z, in + o0, in + o1, ph == 1, kx, L.t, lN);
+    fft_regs<true>(Z, sm, tw, L.t, lN, 0, PLAN);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int x = L.t + s * T_;
-    Z[s] = mk(cc[p0 + x] * Z[s].x, cc[p1 + x] * Z[s].y);
-  }
-  fft_regs<false>(Z, sm, tw, L.t, lN, 0, PLAN);
-  split_pair(Z, sm, L.t, lN, b0, b1);
+    for (int s = 0; s < 8; ++s) {
+      const int x = L.t + s * T_;
+      Z[s] = mk(cf[p0 + x] * Z[s].x, cf[p1 + x] * Z[s].y);
+    }
+    fft_regs<false>(Z, sm, tw, L.t, lN, 0, PLAN);
+    split_pair(Z, sm, L.t, lN, b0, b1);
+    if (ph == 0) {
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    stash[(2 * s) * T_ + L.t] = b0[s];
-    stash[(2 * s + 1) * T_ + L.t] = b1[s];
-  }
-  __syncthreads();
-  // bx = sigma_x / h, combined with a
-  load_packed(Z, S + o0, S + o1, true, kx, L.t, lN);
-  fft_regs<true>(Z, sm, tw, L.t, lN, 0, PLAN);
+      for (int s = 0; s < 5; ++s) {
+        stash[(2 * s) * T_ + L.t] = b0[s];
+        stash[(2 * s + 1) * T_ + L.t] = b1[s];
+      }
+    } else {
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int x = L.t + s * T_;
-    Z[s] = mk(cr[p0 + x] * Z[s].x, cr[p1 + x] * Z[s].y);
-  }
-  fft_regs<false>(Z, sm, tw, L.t, lN, 0, PLAN);
-  split_pair(Z, sm, L.t, lN, b0, b1);
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    if (!split_owns(s, L.t) || !L.valid) continue;
-    const int k = L.t + s * T_;
-    const T kv = ldr(kx + k);
-    Cout[o0 + k] = stash[(2 * s) * T_ + L.t] - mul_ik(b0[s], kv);
-    Cout[o1 + k] = stash[(2 * s + 1) * T_ + L.t] - mul_ik(b1[s], kv);
-  }
-  __syncthreads();
-  // by = sigma_y / h
-  load_packed(Z, Sy + o0, Sy + o1, false, kx, L.t, lN);
-  fft_regs<true>(Z, sm, tw, L.t, lN, 0, PLAN);
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int x = L.t + s * T_;
-    Z[s] = mk(cr[p0 + x] * Z[s].x, cr[p1 + x] * Z[s].y);
-  }
-  fft_regs<false>(Z, sm, tw, L.t, lN, 0, PLAN);
-  split_pair(Z, sm, L.t, lN, b0, b1);
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    if (!split_owns(s, L.t) || !L.valid) continue;
-    const int k = L.t + s * T_;
-    Byout[o0 + k] = b0[s];
-    Byout[o1 + k] = b1[s];
+      for (int s = 0; s < 5; ++s) {
+        if (!split_owns(s, L.t) || !L.valid) continue;
+        const int k = L.t + s * T_;
+        if (ph == 1) {
+          const T kv = ldr(kx + k);
+          Cout[o0 + k] = stash[(2 * s) * T_ + L.t] - mul_ik(b0[s], kv);
+          Cout[o1 + k] = stash[(2 * s + 1) * T_ + L.t] - mul_ik(b1[s], kv);
+        } else {
+          Byout[o0 + k] = b0[s];
+          Byout[o1 + k] = b1[s];
+        }
+      }
+    }
+  };
+  if constexpr (std::is_same<T, dfl>::value) {
+    // one copy of the phase for all three: six inlined double-float
+    // transforms do not fit the instruction cache (ncu: "no instruction" was
+    // the largest stall of this pass with them unrolled)
+#pragma unroll 1
+    for (int ph = 0; ph < 3; ++ph) {
+      phase(ph);
+      __syncthreads();
+    }
+  } else {
+    phase(0);
+    __syncthreads();
+    phase(1);
+    __syncthreads();
+    phase(2);
   }
 }
 
@@ -760,6 +769,45 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
       }
     }
     cp_async_commit();
+  }
+  if constexpr (std::is_same<T, dfl>::value && INV && NIN == 2 && (FL & ~yf_pf(1)) == 0) {
+    // double-float y-inverse with two inputs (the refinement matvec): one
+    // copy of the transform for both, as in the x-pass, so that the code fits
+    // the instruction cache; input 1 comes from its staged copy when FL says
+    // so. (The forward pass keeps two copies: rolled, its matvec epilogue
+    // spilled and the pass ran slower.)
+    cpx<T> z[8];
+#pragma unroll 1
+    for (int i = 0; i < NIN; ++i) {
+      const bool der = (i == 0 ? in.deriv[0] : in.deriv[1]) != 0;
+      if ((FL & yf_pf(1)) && i == 1) {
+        cp_async_wait_all();
+        const cpx<S>* st = reinterpret_cast<const cpx<S>*>(stage);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          z[s] = ld_as<T, S>(st + s * nthr + tid);
+          if (der) z[s] = mul_ik(z[s], ldr(ky + t + s * T_));
+        }
+      } else {
+        const cpx<S>* src = (i == 0 ? in.src[0] : in.src[1]) + soff;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int row = t + s * T_;
+          z[s] = ld_as<T, S>(src + (size_t)row * G.ldS + col);
+          if (der) z[s] = mul_ik(z[s], ldr(ky + row));
+        }
+      }
+      fft_regs<INV>(z, smb + c, tw, t, lN, lC, PLAN);
+      // only the first result is carried into the second iteration
+      if (i == 0) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) r[0][s] = z[s];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) r[NIN - 1][s] = z[s];
+    epi(r, col, t, T_, valid, G, ky);
+    return;
   }
   bool waited = false;
 #pragma unroll
