@@ -329,7 +329,12 @@ constexpr int xpass_threads() { return LN == 12 ? 512 : 256; }
 template <typename T, int LN>
 constexpr int mv_min_blocks() { return LN == 12 ? 1 : ((sizeof(T) == 4 || std::is_same<T, dfl>::value) ? 3 : 2); }
 template <typename T, int LN>
-constexpr int rhs_min_blocks() { return LN == 12 ? 1 : (sizeof(T) == 4 ? 2 : 1); }
+constexpr int rhs_min_blocks() { return LN == 12 ? 1 : ((sizeof(T) == 4 || std::is_same<T, dfl>::value) ? 2 : 1); }
+// shared-memory elements per row pair of the fused RHS x-pass beyond its
+// transform buffer: the double-float pass keeps its accumulators QX, QY there
+// (8 slots per thread each)
+template <typename T>
+__host__ __device__ constexpr int rhs_acc_elems(int N) { return std::is_same<T, dfl>::value ? 2 * N : 0; }
 
 // S = y-inverse of sigma_hat, Sy = y-inverse of i ky sigma_hat. Writes
 // Cout = (a - i kx bx)^x and Byout = by^x (x-spectral, y-physical). A block
@@ -443,6 +448,95 @@ __global__ void __launch_bounds__(xpass_threads<LN>(), rhs_min_blocks<T, LN>()) 
   const size_t p0 = (size_t)L.y0 * N, p1 = (size_t)L.y1 * N;
   const T n = (T)(1.0 / (double)G.nphys());
   const T twoN = (T)(2.0 * (double)G.nphys());
+  if constexpr (std::is_same<T, dfl>::value) {
+    // Double-float (precision 3): the same sums with one copy of the inverse
+    // and one of the forward transform code (rolled loops over the five inputs
+    // and the three outputs; eight inlined double-float transforms overflow
+    // the instruction cache) and the accumulators QX, QY in the thread's own
+    // slots of shared memory, so that F and one signal are the registers that
+    // live across a transform (two blocks per SM instead of one that spilled)
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int P = blockDim.x >> (lN - 3);
+    cpx<T>* acc = reinterpret_cast<cpx<T>*>(smraw) + (size_t)P * smem_elems_of<T>(N) +
+                  (size_t)L.grp * rhs_acc_elems<T>(N);
+    cpx<T> F[8], Z[8];
+    // inputs: 0 i kx sigma_hat, 1 Sy = i ky sigma_hat, 2 sigma_hat, 3 vx, 4 vy
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+      const cpx<T>* in = i == 1 ? Sy : (i == 3 ? Vx : (i == 4 ? Vy : S));
+      load_packed(Z, in + o0, in + o1, i == 0, kx, L.t, lN);
+      fft_regs<true>(Z, sm, tw, L.t, lN, 0, PLAN);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int x = L.t + s * T_;
+        cpx<T>* qx = acc + (size_t)s * T_ + L.t;
+        cpx<T>* qy = acc + (size_t)(8 + s) * T_ + L.t;
+        const T z0 = Z[s].x * n, z1 = Z[s].y * n;
+        if (i == 0) {
+          *qx = mk(-z0, -z1);  // -sigma_x
+        } else if (i == 1) {
+          // sigma_y; -|grad sigma|^2 / (2 h^2) with sigma_x from the slot
+          const T r0 = cr[p0 + x] * twoN, r1 = cr[p1 + x] * twoN;
+          const cpx<T> q = *qx;
+          *qy = mk(-z0, -z1);
+          F[s] = mk((T)-0.5 * r0 * r0 * (q.x * q.x + z0 * z0), (T)-0.5 * r1 * r1 * (q.y * q.y + z1 * z1));
+        } else if (i == 2) {
+          // sigma: -9 sigma^2 / (2 h^4)
+          const T r0 = cr[p0 + x] * twoN, r1 = cr[p1 + x] * twoN;
+          const T q0 = z0 * r0 * r0, q1 = z1 * r1 * r1;
+          F[s].x -= (T)4.5 * q0 * q0;
+          F[s].y -= (T)4.5 * q1 * q1;
+        } else {
+          // vx, vy: h v and |v|^2/2; with vy also g (h - 1) (see below)
+          const T a0 = hh[p0 + x], a1 = hh[p1 + x];  // h - 1
+          cpx<T>* q = i == 3 ? qx : qy;
+          cpx<T> w = *q;
+          w.x += z0 + a0 * z0;
+          w.y += z1 + a1 * z1;
+          const T gh0 = i == 4 ? g * a0 : (T)0, gh1 = i == 4 ? g * a1 : (T)0;
+          F[s].x += (T)0.5 * z0 * z0 + gh0;
+          F[s].y += (T)0.5 * z1 * z1 + gh1;
+          // the split returns twice the half spectra: pre-scale by 1/2
+          *q = scl(w, (T)0.5);
+          if (i == 4) F[s] = scl(F[s], (T)0.5);
+        }
+      }
+    }
+    cpx<T> f0[5], f1[5];
+    // F first, so that its registers are free for the loop over QX, QY
+    fft_regs<false>(F, sm, tw, L.t, lN, 0, PLAN);
+    split_pair(F, sm, L.t, lN, f0, f1);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      if (!split_owns(s, L.t) || !L.valid) continue;
+      const int k = L.t + s * T_;
+      Fh[o0 + k] = f0[s];
+      Fh[o1 + k] = f1[s];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) Z[s] = acc[(size_t)(8 * j + s) * T_ + L.t];
+      fft_regs<false>(Z, sm, tw, L.t, lN, 0, PLAN);
+      split_pair(Z, sm, L.t, lN, f0, f1);
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        if (!split_owns(s, L.t) || !L.valid) continue;
+        const int k = L.t + s * T_;
+        if (j == 0) {
+          const T kv = ldr(kx + k);
+          Cq[o0 + k] = mul_ik(f0[s], -kv);
+          Cq[o1 + k] = mul_ik(f1[s], -kv);
+        } else {
+          Qy[o0 + k] = f0[s];
+          Qy[o1 + k] = f1[s];
+        }
+      }
+      __syncthreads();
+    }
+    return;
+  }
   cpx<T> QX[8], QY[8], F[8], Z[8];
   // grad sigma
   load_packed(QX, S + o0, S + o1, true, kx, L.t, lN);
@@ -628,15 +722,17 @@ __host__ __device__ constexpr size_t ystage_offset(int lN, int lC) {
 // first input's raw values in shared memory instead spilled 244 bytes at the
 // 64 registers of the FP32 pass); the y-forward passes stage every input after
 // the first; the RHS y-inverse forms i ky sigma_hat from a staged copy of
-// sigma_hat and, in FP64 and double-float below 4096 points, also stages v_y
-// and sigma_hat (the FP32 one measured 117 against 107 us with them staged:
-// 196 KB of shared memory leave little L1; FP64 at 4096 has no room for them)
+// sigma_hat and, in FP64 below 4096 points, also stages v_y and sigma_hat (the
+// FP32 one measured 117 against 107 us with them staged: 196 KB of shared
+// memory leave little L1; FP64 at 4096 has no room for them; the double-float
+// one transforms one input at a time at three blocks per SM instead)
 constexpr int FL_MV_INV = yf_pf(1);
 constexpr int FL_MV_FWD = yf_pf(1);
 constexpr int FL_RHS_FWD = yf_pf(1) | yf_pf(2);
 template <typename T, int LN>
 constexpr int fl_rhs_inv() {
-  return (sizeof(T) == 4 || LN == 12) ? yf_dup(3) : (yf_pf(1) | yf_pf(2) | yf_dup(3));
+  return (sizeof(T) == 4 || LN == 12 || std::is_same<T, dfl>::value) ? yf_dup(3)
+                                                                      : (yf_pf(1) | yf_pf(2) | yf_dup(3));
 }
 
 template <typename E>
@@ -714,6 +810,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+template <typename T, int NIN>
+struct EpiStore;
+template <class E>
+struct is_epi_store : std::false_type {};
+template <typename T, int NIN>
+struct is_epi_store<EpiStore<T, NIN>> : std::true_type {};
+
 template <typename T, bool INV, int NIN, class Epi, typename S, int LN, int FL, int PLAN>
 __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restrict__ tw, const T* __restrict__ ky,
                                            const YIn<T, NIN, S>& in, const Epi& epi,
@@ -770,26 +873,44 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
     }
     cp_async_commit();
   }
-  if constexpr (std::is_same<T, dfl>::value && INV && NIN == 2 && (FL & ~yf_pf(1)) == 0) {
-    // double-float y-inverse with two inputs (the refinement matvec): one
-    // copy of the transform for both, as in the x-pass, so that the code fits
-    // the instruction cache; input 1 comes from its staged copy when FL says
-    // so. (The forward pass keeps two copies: rolled, its matvec epilogue
-    // spilled and the pass ran slower.)
-    cpx<T> z[8];
+  if constexpr (std::is_same<T, dfl>::value && INV && is_epi_store<Epi>::value && NMAP == 0) {
+    // double-float y-inverse passes whose epilogue only stores (the
+    // refinement matvec's, precision 3's right-hand side): one copy of the
+    // transform code for every input (a rolled loop; inlined double-float
+    // transforms overflow the instruction cache), each output stored right
+    // after its transform, so that one signal is live at a time
+    const cpx<S>* srcs[NIN];
+    int ders[NIN];
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) {
+      srcs[j] = in.src[j] + soff;
+      ders[j] = in.deriv[j];
+    }
 #pragma unroll 1
     for (int i = 0; i < NIN; ++i) {
-      const bool der = (i == 0 ? in.deriv[0] : in.deriv[1]) != 0;
-      if ((FL & yf_pf(1)) && i == 1) {
+      const cpx<S>* src = srcs[0];
+      bool der = ders[0] != 0;
+#pragma unroll
+      for (int j = 1; j < NIN; ++j)
+        if (i == j) {
+          src = srcs[j];
+          der = ders[j] != 0;
+        }
+      const int fpf = (FL >> i) & 1, fdup = (FL >> (8 + i)) & 1, fdup_next = (FL >> (9 + i)) & 1;
+      unsigned char* st_i = stage + (size_t)nthr * ystage_bytes<T, S, FL>(i);
+      cpx<T> z[8];
+      if (i > 0 && fpf) {
         cp_async_wait_all();
-        const cpx<S>* st = reinterpret_cast<const cpx<S>*>(stage);
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-          z[s] = ld_as<T, S>(st + s * nthr + tid);
+          z[s] = ld_as<T, S>(reinterpret_cast<const cpx<S>*>(st_i) + s * nthr + tid);
           if (der) z[s] = mul_ik(z[s], ldr(ky + t + s * T_));
         }
+      } else if (i > 0 && fdup) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          z[s] = mul_ik(reinterpret_cast<const cpx<T>*>(st_i)[s * nthr + tid], ldr(ky + t + s * T_));
       } else {
-        const cpx<S>* src = (i == 0 ? in.src[0] : in.src[1]) + soff;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           const int row = t + s * T_;
@@ -797,16 +918,22 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
           if (der) z[s] = mul_ik(z[s], ldr(ky + row));
         }
       }
-      fft_regs<INV>(z, smb + c, tw, t, lN, lC, PLAN);
-      // only the first result is carried into the second iteration
-      if (i == 0) {
+      if (fdup_next && i + 1 < NIN) {
+        // input i + 1 is i ky times this one: keep the raw values
+        cpx<T>* st = reinterpret_cast<cpx<T>*>(stage + (size_t)nthr * ystage_bytes<T, S, FL>(i + 1));
 #pragma unroll
-        for (int s = 0; s < 8; ++s) r[0][s] = z[s];
+        for (int s = 0; s < 8; ++s) st[s * nthr + tid] = z[s];
+      }
+      fft_regs<INV>(z, smb + c, tw, t, lN, lC, PLAN);
+      if (valid) {
+        cpx<T>* dst = epi.dst[0];
+#pragma unroll
+        for (int j = 1; j < NIN; ++j)
+          if (i == j) dst = epi.dst[j];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) dst[(size_t)(t + s * T_) * G.ldS + col] = z[s];
       }
     }
-#pragma unroll
-    for (int s = 0; s < 8; ++s) r[NIN - 1][s] = z[s];
-    epi(r, col, t, T_, valid, G, ky);
     return;
   }
   bool waited = false;
@@ -907,10 +1034,20 @@ __global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>(), ypass_o2_blo
 constexpr int FL_MV_INV_TMA = yf_tma(0) | yf_dup(1);
 constexpr int FL_MV_FWD_TMA = yf_tma(0) | yf_tma(1);
 
+// Double-float y-inverse passes of two or more inputs that only store (one
+// signal live at a time, see ypass_body): three blocks of 256 per SM (one
+// input keeps k_ypass: 107 registers there, against 80 with 36 bytes spilled)
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
+__global__ void __launch_bounds__(256, 3) k_ypass_df3(Geom G, const cpx<T>* __restrict__ tw,
+                                                      const T* __restrict__ ky, YIn<T, NIN, S> in, Epi epi) {
+  ypass_body<T, INV, NIN, Epi, S, LN, FL, PLAN>(G, tw, ky, in, epi);
+}
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
 constexpr auto ypass_fn() {
   if constexpr (sizeof(T) == 4 && NIN <= 2)
     return &k_ypass_o2<T, INV, NIN, Epi, S, LN, FL, PLAN>;
+  else if constexpr (std::is_same<T, dfl>::value && INV && is_epi_store<Epi>::value && NIN >= 2 && LN != 12)
+    return &k_ypass_df3<T, INV, NIN, Epi, S, LN, FL, PLAN>;
   else
     return &k_ypass<T, INV, NIN, Epi, S, LN, FL, PLAN>;
 }
@@ -1750,7 +1887,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
   });
   // each block reads only its own row pair before writing it, so the outputs
   // may overwrite the inputs
-  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_RHS_X));
+  x_config<T>(G, grid, block, smem, 1, ex.tpb(tune_type<T>(), TP_RHS_X), rhs_acc_elems<T>(G.Nx));
   dispatch_ln<T>(G.lNx, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
     ex.begin(PK_RHS_X);
