@@ -672,7 +672,7 @@ constexpr int ypass_threads() {
   // double-float RHS passes (three or four transforms): the registers of
   // 256 threads, as in FP64
   if (std::is_same<T, dfl>::value && NIN >= 3) return LN == 12 ? 512 : 256;
-  return (sizeof(T) == 4 || LN == 12) ? 512 : ((std::is_same<T, dfl>::value && !INV) ? 512 : 256);
+  return (sizeof(T) == 4 || LN == 12) ? 512 : 256;
 }
 
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
@@ -729,6 +729,17 @@ __host__ __device__ constexpr size_t ystage_offset(int lN, int lC) {
 constexpr int FL_MV_INV = yf_pf(1);
 constexpr int FL_MV_FWD = yf_pf(1);
 constexpr int FL_RHS_FWD = yf_pf(1) | yf_pf(2);
+// the double-float forward passes stage nothing: they transform one input at
+// a time and keep each finished transform in the thread's own shared-memory
+// slots for the epilogue instead (ystash_bytes, see ypass_body)
+template <typename T>
+constexpr int fl_mv_fwd() { return std::is_same<T, dfl>::value ? 0 : FL_MV_FWD; }
+template <typename T>
+constexpr int fl_rhs_fwd() { return std::is_same<T, dfl>::value ? 0 : FL_RHS_FWD; }
+template <typename T, bool INV, int NIN>
+__host__ __device__ constexpr int ystash_bytes() {
+  return (std::is_same<T, dfl>::value && !INV && NIN >= 2) ? (NIN - 1) * 8 * (int)sizeof(cpx<T>) : 0;
+}
 template <typename T, int LN>
 constexpr int fl_rhs_inv() {
   return (sizeof(T) == 4 || LN == 12 || std::is_same<T, dfl>::value) ? yf_dup(3)
@@ -872,6 +883,60 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
       }
     }
     cp_async_commit();
+  }
+  if constexpr (std::is_same<T, dfl>::value && !INV && NIN >= 2 && NMAP == 0 && FL == 0) {
+    // double-float y-forward passes (the refinement matvec's, precision 3's
+    // right-hand side): one copy of the transform code for every input (a
+    // rolled loop), each finished transform but the last kept in the thread's
+    // own slots of shared memory until the epilogue, which needs them all, so
+    // that one signal is live during a transform
+    cpx<T>* stash = reinterpret_cast<cpx<T>*>(stage);
+    const cpx<S>* srcs[NIN];
+    int ders[NIN];
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) {
+      srcs[j] = in.src[j] + soff;
+      ders[j] = in.deriv[j];
+    }
+    cpx<T> z[8];
+#pragma unroll 1
+    for (int i = 0; i < NIN; ++i) {
+      const cpx<S>* src = srcs[0];
+      bool der = ders[0] != 0;
+#pragma unroll
+      for (int j = 1; j < NIN; ++j)
+        if (i == j) {
+          src = srcs[j];
+          der = ders[j] != 0;
+        }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int row = t + s * T_;
+        z[s] = ld_as<T, S>(src + (size_t)row * G.ldS + col);
+        if (der) z[s] = mul_ik(z[s], ldr(ky + row));
+      }
+      fft_regs<INV>(z, smb + c, tw, t, lN, lC, PLAN);
+      if (i + 1 < NIN) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) stash[(size_t)(i * 8 + s) * nthr + tid] = z[s];
+      }
+    }
+    // the epilogue one slot at a time (a rolled loop: the reloads of the
+    // stashed transforms are not hoisted into registers); the last transform
+    // goes to the thread's own slots of its exchange buffer, free after the
+    // transform, so that the loop indexes no register array
+    if (!valid) return;
+    store_slots(z, smb + c, t, T_, lC);
+    const T kxv = ldr(epi.kx + col);
+#pragma unroll 1
+    for (int s = 0; s < 8; ++s) {
+      cpx<T> v[NIN];
+#pragma unroll
+      for (int i = 0; i + 1 < NIN; ++i) v[i] = stash[(size_t)(i * 8 + s) * nthr + tid];
+      v[NIN - 1] = smb[c + sidx<T>(t + s * T_, lC)];
+      epi.at(v, t + s * T_, col, kxv, G, ky);
+    }
+    return;
   }
   if constexpr (std::is_same<T, dfl>::value && INV && is_epi_store<Epi>::value && NMAP == 0) {
     // double-float y-inverse passes whose epilogue only stores (the
@@ -1034,20 +1099,22 @@ __global__ void __launch_bounds__(ypass_threads<T, INV, LN, NIN>(), ypass_o2_blo
 constexpr int FL_MV_INV_TMA = yf_tma(0) | yf_dup(1);
 constexpr int FL_MV_FWD_TMA = yf_tma(0) | yf_tma(1);
 
-// Double-float y-inverse passes of two or more inputs that only store (one
-// signal live at a time, see ypass_body): three blocks of 256 per SM (one
-// input keeps k_ypass: 107 registers there, against 80 with 36 bytes spilled)
-template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
-__global__ void __launch_bounds__(256, 3) k_ypass_df3(Geom G, const cpx<T>* __restrict__ tw,
-                                                      const T* __restrict__ ky, YIn<T, NIN, S> in, Epi epi) {
+// Double-float passes of two or more inputs with one signal live at a time
+// (see ypass_body): the y-inverses that only store and the y-forward passes,
+// 256 threads, MINB blocks per SM: three, two for the three-input y-forward
+// (its stash of two transforms leaves room for two). One input keeps k_ypass:
+// 107 registers there, against 80 with 36 bytes spilled.
+template <int MINB, typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
+__global__ void __launch_bounds__(256, MINB) k_ypass_df(Geom G, const cpx<T>* __restrict__ tw,
+                                                        const T* __restrict__ ky, YIn<T, NIN, S> in, Epi epi) {
   ypass_body<T, INV, NIN, Epi, S, LN, FL, PLAN>(G, tw, ky, in, epi);
 }
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
 constexpr auto ypass_fn() {
   if constexpr (sizeof(T) == 4 && NIN <= 2)
     return &k_ypass_o2<T, INV, NIN, Epi, S, LN, FL, PLAN>;
-  else if constexpr (std::is_same<T, dfl>::value && INV && is_epi_store<Epi>::value && NIN >= 2 && LN != 12)
-    return &k_ypass_df3<T, INV, NIN, Epi, S, LN, FL, PLAN>;
+  else if constexpr (std::is_same<T, dfl>::value && (!INV || is_epi_store<Epi>::value) && NIN >= 2 && LN != 12)
+    return &k_ypass_df<(!INV && NIN >= 3) ? 2 : 3, T, INV, NIN, Epi, S, LN, FL, PLAN>;
   else
     return &k_ypass<T, INV, NIN, Epi, S, LN, FL, PLAN>;
 }
@@ -1105,21 +1172,26 @@ struct EpiMatvec {
   const T* kx;
   int precond;
   const T* minv;
+  // the output at (row, col) from the two transforms' values v there
+  __device__ __forceinline__ void at(const cpx<T> (&v)[2], int row, int col, T kxv, const Geom& G,
+                                     const T* ky) const {
+    const T kyv = ldr(ky + row);
+    const size_t e = (size_t)row * G.ldS + col;
+    cpx<T> z = v[0] - mul_ik(v[1], kyv);
+    if (precond) z = scl(z, minv ? ldr(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
+    if constexpr (std::is_same<T, dfl>::value && std::is_same<SO, double>::value)
+      w[e] = mk(dfl_to_f64(z.x), dfl_to_f64(z.y));
+    else
+      w[e] = mk((SO)z.x, (SO)z.y);
+  }
   __device__ __forceinline__ void operator()(cpx<T> (&r)[2][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
     const T kxv = ldr(kx + col);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const int row = t + s * T_;
-      const T kyv = ldr(ky + row);
-      const size_t e = (size_t)row * G.ldS + col;
-      cpx<T> z = r[0][s] - mul_ik(r[1][s], kyv);
-      if (precond) z = scl(z, minv ? ldr(minv + e) : (T)1 / ((T)3 + kxv * kxv + kyv * kyv));
-      if constexpr (std::is_same<T, dfl>::value && std::is_same<SO, double>::value)
-        w[e] = mk(dfl_to_f64(z.x), dfl_to_f64(z.y));
-      else
-        w[e] = mk((SO)z.x, (SO)z.y);
+      const cpx<T> v[2] = {r[0][s], r[1][s]};
+      at(v, t + s * T_, col, kxv, G, ky);
     }
   }
 };
@@ -1134,30 +1206,34 @@ struct EpiK {
   cpx<T>* K[3];
   const T* kx;
   int dealias;
+  // the outputs at (row, col) from the three transforms' values v there
+  __device__ __forceinline__ void at(const cpx<T> (&v)[3], int row, int col, T kxv, const Geom& G,
+                                     const T* ky) const {
+    const T kyv = ldr(ky + row);
+    const size_t e = (size_t)row * G.ldS + col;
+    cpx<T> k0 = v[0] - mul_ik(v[1], kyv);
+    cpx<T> k1 = mul_ik(v[2], -kxv);
+    cpx<T> k2 = mul_ik(v[2], -kyv);
+    if (dealias) {
+      const int my = row <= (G.Ny >> 1) ? row : G.Ny - row;
+      if (3 * col > G.Nx || 3 * my > G.Ny) {
+        k0 = mk((T)0, (T)0);
+        k1 = k0;
+        k2 = k0;
+      }
+    }
+    K[0][e] = k0;
+    K[1][e] = k1;
+    K[2][e] = k2;
+  }
   __device__ __forceinline__ void operator()(cpx<T> (&r)[3][8], int col, int t, int T_, bool valid,
                                              const Geom& G, const T* ky) const {
     if (!valid) return;
     const T kxv = ldr(kx + col);
-    const bool keepx = !dealias || 3 * col <= G.Nx;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const int row = t + s * T_;
-      const T kyv = ldr(ky + row);
-      const size_t e = (size_t)row * G.ldS + col;
-      cpx<T> k0 = r[0][s] - mul_ik(r[1][s], kyv);
-      cpx<T> k1 = mul_ik(r[2][s], -kxv);
-      cpx<T> k2 = mul_ik(r[2][s], -kyv);
-      if (dealias) {
-        const int my = row <= (G.Ny >> 1) ? row : G.Ny - row;
-        if (!keepx || 3 * my > G.Ny) {
-          k0 = mk((T)0, (T)0);
-          k1 = k0;
-          k2 = k0;
-        }
-      }
-      K[0][e] = k0;
-      K[1][e] = k1;
-      K[2][e] = k2;
+      const cpx<T> v[3] = {r[0][s], r[1][s], r[2][s]};
+      at(v, t + s * T_, col, kxv, G, ky);
     }
   }
 };
@@ -1361,13 +1437,13 @@ static void set_attrs_ln_plan() {
   set_smem<T>((const void*)k_mv_x<T, L, P>);
   set_smem<T>((const void*)k_rhs_x<T, L, P>);
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, T, L, FL_MV_INV, P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L, FL_MV_FWD, P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, L, fl_mv_fwd<T>(), P>());
   if constexpr (sizeof(T) == 4) {
     set_smem<T>((const void*)k_ypass_tma<T, true, 2, EpiStore<T, 2>, L, FL_MV_INV_TMA, P>);
     set_smem<T>((const void*)k_ypass_tma<T, false, 2, EpiMatvec<T, T>, L, FL_MV_FWD_TMA, P>);
   }
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, L, fl_rhs_inv<T, L>(), P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L, FL_RHS_FWD, P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, L, fl_rhs_fwd<T>(), P>());
 }
 
 template <typename T, int L>
@@ -1392,8 +1468,8 @@ static void set_attrs_plan() {
     set_smem<T>((const void*)k_ypass_tma<T, false, 2, EpiMatvec<T, T>, 0, FL_MV_FWD_TMA, P>);
   }
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, T, 0, fl_rhs_inv<T, 0>(), P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, 0, FL_MV_FWD, P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, FL_RHS_FWD, P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T>, T, 0, fl_mv_fwd<T>(), P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, fl_rhs_fwd<T>(), P>());
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 0, fl_rhs_inv<T, 0>(), P>());
 }
 
@@ -1742,7 +1818,8 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     ex.end();
   });
   bool bf = true;
-  y_config<T, false, 2>(G, grid, block, smem, ystage_bytes<T, T, FL_MV_FWD>(2), ex.tpb(tune_type<T>(), TP_MV_YFWD),
+  y_config<T, false, 2>(G, grid, block, smem, ystage_bytes<T, T, fl_mv_fwd<T>()>(2) + ystash_bytes<T, false, 2>(),
+                        ex.tpb(tune_type<T>(), TP_MV_YFWD),
                         &bf);
   dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
@@ -1752,7 +1829,7 @@ cudaError_t launch_matvec_io(const Geom& G, const Tables<T>& tb, const cpx<S>* s
     EpiMatvec<T, S> ep{w, tb.kx, precond ? 1 : 0, tb.minv};
     ex.begin(PK_MV_YFWD);
     dispatch_plan<L>(ex.plan(tune_type<T>(), TP_MV_YFWD), [&](auto pl) {
-      ypass_fn<T, false, 2, EpiMatvec<T, S>, T, L, FL_MV_FWD, decltype(pl)::value>()<<<grid, block, smem, ex.s>>>(
+      ypass_fn<T, false, 2, EpiMatvec<T, S>, T, L, fl_mv_fwd<T>(), decltype(pl)::value>()<<<grid, block, smem, ex.s>>>(
           G, tb.twy, tb.ky, yi, ep);
     });
     ex.end();
@@ -1811,11 +1888,11 @@ static void set_attrs_df_plan() {
   typedef dfl T;
   set_smem<T>((const void*)k_mv_x<T, 0, P>);
   set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 0, FL_MV_INV, P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 0, FL_MV_FWD, P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 0, fl_mv_fwd<T>(), P>());
   if constexpr (P == 0) {  // 4096 points: one plan
     set_smem<T>((const void*)k_mv_x<T, 12, P>);
     set_smem<T>((const void*)ypass_fn<T, true, 2, EpiStore<T, 2>, double, 12, FL_MV_INV, P>());
-    set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12, FL_MV_FWD, P>());
+    set_smem<T>((const void*)ypass_fn<T, false, 2, EpiMatvec<T, double>, T, 12, fl_mv_fwd<T>(), P>());
   }
 }
 
@@ -1825,11 +1902,11 @@ static void set_attrs_df_rhs_plan() {
   typedef dfl T;
   set_smem<T>((const void*)k_rhs_x<T, 0, P>);
   set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 0, fl_rhs_inv<T, 0>(), P>());
-  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, FL_RHS_FWD, P>());
+  set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 0, fl_rhs_fwd<T>(), P>());
   if constexpr (P == 0) {  // 4096 points: one plan
     set_smem<T>((const void*)k_rhs_x<T, 12, P>);
     set_smem<T>((const void*)ypass_fn<T, true, 4, EpiStore<T, 4>, double, 12, fl_rhs_inv<T, 12>(), P>());
-    set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 12, FL_RHS_FWD, P>());
+    set_smem<T>((const void*)ypass_fn<T, false, 3, EpiK<T>, T, 12, fl_rhs_fwd<T>(), P>());
   }
 }
 
@@ -1899,7 +1976,8 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     ex.end();
   });
   bool bf = true;
-  y_config<T, false, 3>(G, grid, block, smem, ystage_bytes<T, T, FL_RHS_FWD>(3), ex.tpb(tune_type<T>(), TP_RHS_YFWD),
+  y_config<T, false, 3>(G, grid, block, smem, ystage_bytes<T, T, fl_rhs_fwd<T>()>(3) + ystash_bytes<T, false, 3>(),
+                        ex.tpb(tune_type<T>(), TP_RHS_YFWD),
                         &bf);
   dispatch_ln<T>(bf ? G.lNy : 0, [&](auto ln) {
     constexpr int L = decltype(ln)::value;
@@ -1915,7 +1993,7 @@ cudaError_t launch_rhs(const Geom& G, const Tables<T>& tb, const Tables<S>& tbs,
     ep.dealias = rk.dealias;
     ex.begin(PK_RHS_YFWD);
     dispatch_plan<L>(ex.plan(tune_type<T>(), TP_RHS_YFWD), [&](auto pl) {
-      ypass_fn<T, false, 3, EpiK<T>, T, L, FL_RHS_FWD, decltype(pl)::value>()<<<grid, block, smem, ex.s>>>(
+      ypass_fn<T, false, 3, EpiK<T>, T, L, fl_rhs_fwd<T>(), decltype(pl)::value>()<<<grid, block, smem, ex.s>>>(
           G, tb.twy, tb.ky, yi, ep);
     });
     ex.end();
