@@ -181,9 +181,9 @@ def measured_peaks():
 # command. An entry is removed when its kernel changes, and the line reports
 # null when the tuned handle runs the pass in the other radix plan.
 MEASURED_TRAFFIC = {
-    ("ref_x", "df", 2048): {"bytes": 134.6e6 + 23.7e6, "issue": 0.70, "fma": 0.57, "source": "profiles/k_mv_x_df_gaussian2048.md"},
-    ("ref_yinv", "df", 2048): {"bytes": 38.0e6 + 15.1e6, "issue": 0.49, "fma": 0.35, "source": "profiles/k_mv_x_df_gaussian2048.md"},
-    ("ref_yfwd", "df", 2048): {"bytes": 84.7e6 + 11.9e6, "issue": 0.41, "fma": 0.37, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("ref_x", "df", 2048): {"bytes": 134.5e6 + 23.5e6, "issue": 0.70, "fma": 0.57, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("ref_yinv", "df", 2048): {"bytes": 38.5e6 + 15.7e6, "issue": 0.57, "fma": 0.42, "source": "profiles/k_mv_x_df_gaussian2048.md"},
+    ("ref_yfwd", "df", 2048): {"bytes": 84.6e6 + 8.6e6, "issue": 0.53, "fma": 0.39, "source": "profiles/k_mv_x_df_gaussian2048.md"},
     ("mv_x", "fp32", 2048): {"bytes": 67.3e6 + 22.7e6, "issue": 0.54, "fma": 0.28, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
     ("mv_yinv", "fp32", 2048): {"bytes": 16.9e6 + 0.1e6, "issue": 0.35, "fma": 0.21, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
     ("mv_yfwd", "fp32", 2048): {"bytes": 33.7e6 + 0.1e6, "issue": 0.41, "fma": 0.23, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
