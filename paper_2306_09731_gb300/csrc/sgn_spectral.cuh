@@ -731,14 +731,20 @@ constexpr int FL_MV_FWD = yf_pf(1);
 constexpr int FL_RHS_FWD = yf_pf(1) | yf_pf(2);
 // the double-float forward passes stage nothing: they transform one input at
 // a time and keep each finished transform in the thread's own shared-memory
-// slots for the epilogue instead (ystash_bytes, see ypass_body)
+// slots for the epilogue instead (ystash_bytes, see ypass_body). (The FP32 RHS
+// y-forward the same way, at two blocks of 512 per SM without its prefetch,
+// ran 68 us against 53.5: that pass is latency bound.)
+template <typename T, bool INV, int NIN>
+__host__ __device__ constexpr bool y_stashed() {
+  return !INV && std::is_same<T, dfl>::value && NIN >= 2;
+}
 template <typename T>
-constexpr int fl_mv_fwd() { return std::is_same<T, dfl>::value ? 0 : FL_MV_FWD; }
+constexpr int fl_mv_fwd() { return y_stashed<T, false, 2>() ? 0 : FL_MV_FWD; }
 template <typename T>
-constexpr int fl_rhs_fwd() { return std::is_same<T, dfl>::value ? 0 : FL_RHS_FWD; }
+constexpr int fl_rhs_fwd() { return y_stashed<T, false, 3>() ? 0 : FL_RHS_FWD; }
 template <typename T, bool INV, int NIN>
 __host__ __device__ constexpr int ystash_bytes() {
-  return (std::is_same<T, dfl>::value && !INV && NIN >= 2) ? (NIN - 1) * 8 * (int)sizeof(cpx<T>) : 0;
+  return y_stashed<T, INV, NIN>() ? (NIN - 1) * 8 * (int)sizeof(cpx<T>) : 0;
 }
 template <typename T, int LN>
 constexpr int fl_rhs_inv() {
@@ -884,7 +890,7 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
     }
     cp_async_commit();
   }
-  if constexpr (std::is_same<T, dfl>::value && !INV && NIN >= 2 && NMAP == 0 && FL == 0) {
+  if constexpr (y_stashed<T, INV, NIN>() && NMAP == 0 && FL == 0) {
     // double-float y-forward passes (the refinement matvec's, precision 3's
     // right-hand side): one copy of the transform code for every input (a
     // rolled loop), each finished transform but the last kept in the thread's
@@ -938,12 +944,15 @@ __device__ __forceinline__ void ypass_body(const Geom& G, const cpx<T>* __restri
     }
     return;
   }
-  if constexpr (std::is_same<T, dfl>::value && INV && is_epi_store<Epi>::value && NMAP == 0) {
+  if constexpr ((std::is_same<T, dfl>::value || (sizeof(T) == 4 && NIN >= 3)) && INV && is_epi_store<Epi>::value &&
+                NMAP == 0) {
     // double-float y-inverse passes whose epilogue only stores (the
-    // refinement matvec's, precision 3's right-hand side): one copy of the
-    // transform code for every input (a rolled loop; inlined double-float
-    // transforms overflow the instruction cache), each output stored right
-    // after its transform, so that one signal is live at a time
+    // refinement matvec's, precision 3's right-hand side) and the FP32 RHS
+    // y-inverse: one copy of the transform code for every input (a rolled
+    // loop; inlined double-float transforms overflow the instruction cache),
+    // each output stored right after its transform, so that one signal is
+    // live at a time (FP32: 64 registers, two blocks of 512 per SM instead of
+    // one at 128, 92.5 -> 73.8 us at 2048^2)
     const cpx<S>* srcs[NIN];
     int ders[NIN];
 #pragma unroll
@@ -1109,10 +1118,19 @@ __global__ void __launch_bounds__(256, MINB) k_ypass_df(Geom G, const cpx<T>* __
                                                         const T* __restrict__ ky, YIn<T, NIN, S> in, Epi epi) {
   ypass_body<T, INV, NIN, Epi, S, LN, FL, PLAN>(G, tw, ky, in, epi);
 }
+// FP32 y-inverses of three or more inputs that only store (the RHS's), one
+// signal live at a time (see ypass_body): two blocks of 512 per SM
+template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
+__global__ void __launch_bounds__(512, 2) k_ypass_f2(Geom G, const cpx<T>* __restrict__ tw,
+                                                     const T* __restrict__ ky, YIn<T, NIN, S> in, Epi epi) {
+  ypass_body<T, INV, NIN, Epi, S, LN, FL, PLAN>(G, tw, ky, in, epi);
+}
 template <typename T, bool INV, int NIN, class Epi, typename S = T, int LN = 0, int FL = 0, int PLAN = 0>
 constexpr auto ypass_fn() {
   if constexpr (sizeof(T) == 4 && NIN <= 2)
     return &k_ypass_o2<T, INV, NIN, Epi, S, LN, FL, PLAN>;
+  else if constexpr (sizeof(T) == 4 && INV && is_epi_store<Epi>::value && LN != 12)
+    return &k_ypass_f2<T, INV, NIN, Epi, S, LN, FL, PLAN>;
   else if constexpr (std::is_same<T, dfl>::value && (!INV || is_epi_store<Epi>::value) && NIN >= 2 && LN != 12)
     return &k_ypass_df<(!INV && NIN >= 3) ? 2 : 3, T, INV, NIN, Epi, S, LN, FL, PLAN>;
   else
