@@ -187,7 +187,7 @@ MEASURED_TRAFFIC = {
     ("mv_x", "fp32", 2048): {"bytes": 67.3e6 + 22.7e6, "issue": 0.54, "fma": 0.28, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
     ("mv_yinv", "fp32", 2048): {"bytes": 16.9e6 + 0.1e6, "issue": 0.35, "fma": 0.21, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
     ("mv_yfwd", "fp32", 2048): {"bytes": 33.7e6 + 0.1e6, "issue": 0.41, "fma": 0.23, "source": "profiles/k_mv_x_fp32_gaussian2048.md"},
-    ("rhs_yinv", "fp32", 2048): {"bytes": 103.1e6 + 29.5e6, "issue": 0.20, "fma": 0.12, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
+    ("rhs_yinv", "fp32", 2048): {"bytes": 102.2e6 + 28.0e6, "issue": 0.34, "fma": 0.18, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
     ("rhs_x", "fp32", 2048): {"bytes": 100.9e6 + 7.1e6, "issue": 0.56, "fma": 0.30, "source": "profiles/k_rhs_x_fp32_gaussian2048.md"},
     ("rhs_yfwd", "fp32", 2048): {"bytes": 50.5e6 + 2.9e6, "issue": 0.26, "fma": 0.16, "source": "profiles/k_ypass_fp32_gaussian2048.md"},
 }
