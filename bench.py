@@ -18,7 +18,7 @@ CUDA events for the roofline of its dominant kernel.
 
 The LAST stdout line is one compact JSON object (a few KB). Everything else
 (per-kernel tables, extra arms, ensembles, 4096^2 runs) goes to the detail
-file (--detail, default gpurun_out/bench_detail.json). Under torchrun every
+file (--detail, default bench_detail.json). Under torchrun every
 rank steps its own replica (weak scaling, no collective on the data path);
 value = total steps of all ranks / max time over ranks.
 
@@ -76,7 +76,7 @@ def parse(argv=None):
                          "crossing solitons (detail file only)")
     ap.add_argument("--transverse", action="store_true",
                     help="also run the transverse-stability workload to t = 10 (detail file only)")
-    ap.add_argument("--detail", default=os.path.join("gpurun_out", "bench_detail.json"),
+    ap.add_argument("--detail", default="bench_detail.json",
                     help="where the detailed record goes")
     return ap.parse_args(argv)
 
