@@ -657,10 +657,10 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 // all NIN results of the thread's 8 rows.
 // Threads of a y-pass block. FP32: 512 (two columns per block at Ny = 2048,
 // twice the bytes per row segment). FP64: 256, the registers of one column per
-// block. Double-float: 256 for the inverse passes, 512 for the forward pass
-// with the matvec epilogue (measured at 2048^2: FP64 inverse 321 against 371 us
-// and forward 327 against 386 us; double-float inverse 158 against 182 us,
-// forward 140 against 172 us).
+// block (measured at 2048^2: inverse 321 against 371 us and forward 327
+// against 386 us with 512). Double-float: 256, one column per block, three
+// blocks per SM for the passes that hold one signal at a time (see
+// ypass_body).
 // At 4096 points (LN = 12) one column takes 512 threads in every type.
 // FP32 passes with at most two inputs (NIN <= 2): 1024 threads, four columns
 // per block at Ny = 2048, so that a warp's access covers 8 rows x 32 bytes (8
