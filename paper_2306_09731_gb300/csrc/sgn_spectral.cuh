@@ -669,9 +669,6 @@ __device__ __forceinline__ cpx<T> ld_as(const cpx<S>* p) {
 template <typename T, bool INV, int LN = 0, int NIN = 0>
 constexpr int ypass_threads() {
   if (sizeof(T) == 4 && NIN >= 1 && NIN <= 2) return 1024;
-  // double-float RHS passes (three or four transforms): the registers of
-  // 256 threads, as in FP64
-  if (std::is_same<T, dfl>::value && NIN >= 3) return LN == 12 ? 512 : 256;
   return (sizeof(T) == 4 || LN == 12) ? 512 : 256;
 }
 
