@@ -101,3 +101,20 @@ def test_kernel_byte_model():
     assert bench.class_arith("ref_x", 2) == "df" and bench.class_arith("mv_x", 2) == "fp32"
     assert bench.class_arith("rhs_x", 3) == "df" and bench.class_arith("rk", 2) == "fp64"
     assert bench.class_arith("mv_x", 0) == "fp64"
+
+
+def test_measured_traffic_matches_its_profile_summary():
+    """Every DRAM figure the roofline reports as `traffic` names a summary
+    under profiles/, and that summary's table carries the same read and write
+    megabytes for the kernel (so a kernel change that leaves an old figure in
+    the bench, or a summary that no longer backs it, fails here)."""
+    import re
+
+    import bench
+    for (cls, arith, n), tr in bench.MEASURED_TRAFFIC.items():
+        path = os.path.join(ROOT, tr["source"])
+        assert os.path.isfile(path), tr["source"]
+        text = open(path).read()
+        pairs = {(float(a), float(b)) for a, b in re.findall(r"\|\s*([\d.]+)\s*/\s*([\d.]+)\s*\|", text)}
+        assert any(abs((a + b) * 1e6 - tr["bytes"]) < 0.06e6 for a, b in pairs), (cls, arith, n, tr["bytes"])
+        assert 0.0 < tr["issue"] <= 1.0 and 0.0 < tr["fma"] <= 1.0
